@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Benchmark of the trace-analysis path on B300 (one JSON line on rank 0).
+
+A step is one pass of the whole path over one synthetic trace already
+resident in device memory: packet index + validation, warp/CTA-per-packet
+decode with timestamp scan, in-packet and cross-packet entry/exit pairing,
+per-(host, pid, tid, function) tally, and the sorted interval timeline
+(thapi_trace_load_device), then both results copied out to device buffers
+(thapi_tally_device, thapi_timeline_device) and the trace released.
+
+Workload (default): 8 hosts x 8 pids x 8 threads, portable (60 fns) over
+vendor (120 fns) plus a message-passing layer (30 fns), 100M calls = 200M
+events (~8.4 GB), depth <= 6, log-normal durations (median 5 us), 1 % error
+results, 16 KB packets.  Inputs are 8.4 GB, far larger than the 126 MB L2, so
+no flush is needed between steps.
+
+``--impl reference`` times the CPU oracle (the plain sequential definition)
+on a bounded sample of the same trace instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "large": dict(preset="large", desc="8 hosts x 8 pids x 8 threads; portable(60)/vendor(120)/mpi(30) layers; "
+                                       "100M calls = 200M events; depth<=6; 1% errors; 16 KB packets"),
+    "tiny": dict(preset="tiny", desc="1 host x 1 pid x 4 threads; one API of 40 functions; 100k calls; "
+                                     "depth<=3; 4 KB packets"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--calls", type=int, default=0, help="override total calls (smaller runs)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-streams", type=int, default=0, help="streams in the CPU-baseline sample (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-once", action="store_true", help="one load only (for a profiler), no JSON")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def trace_config(args, rank):
+    import tracegen as tg
+    over = {}
+    if args.calls:
+        over["total_calls"] = args.calls
+    cfg = tg.preset(WORKLOADS[args.workload]["preset"], **over)
+    cfg.seed = cfg.seed + 1000 * rank
+    return cfg
+
+
+def generate_pinned(cfg):
+    """Writes the trace straight into pinned host memory (a torch tensor)."""
+    import torch
+    import tracegen as tg
+    plan = tg.Plan(cfg)
+    host = torch.empty(plan.nbytes, dtype=torch.uint8, pin_memory=True)
+    plan.write(host.data_ptr())
+    meta = dict(nbytes=plan.nbytes, n_packets=plan.n_packets, n_streams=plan.n_streams)
+    plan.close()
+    return host, meta
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def profile_traffic(kernel_file):
+    """DRAM traffic per launch recorded by the committed ncu summary, if it still matches the kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_analyze_large.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    src = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()[:16]
+    rec = {}
+    for line in text.splitlines():
+        if line.startswith("traffic_bytes_per_launch:"):
+            rec["traffic"] = float(line.split(":", 1)[1])
+        if line.startswith("kernel_source_sha256_16:"):
+            rec["sha"] = line.split(":", 1)[1].strip()
+    if rec.get("sha") != src or "traffic" not in rec:
+        return None
+    return rec["traffic"]
+
+
+def cpu_sample(host_np, n_streams, max_streams):
+    """The oracle, as it stands, on the first k streams of the same trace (1 core)."""
+    import oracle
+    k = max(1, min(n_streams, max_streams))
+    t = time.perf_counter()
+    r = oracle.run(host_np, streams=list(range(k)))
+    dt = time.perf_counter() - t
+    return dict(value=r.diag["events"] / dt, unit="events/s", cores=1, kind="oracle",
+                sample="streams 0..%d of %d of the same trace (%d events), decode+pair+tally+timeline, "
+                       "one thread" % (k - 1, n_streams, r.diag["events"]), seconds=round(dt, 3))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    cfg = trace_config(args, 0)
+    import tracegen as tg
+    host, _c, _e = tg.generate(cfg)
+    plan = tg.Plan(cfg)
+    n_streams = plan.n_streams
+    plan.close()
+    max_streams = args.cpu_streams or (64 if args.workload == "large" else n_streams)
+    samples = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_sample(host, n_streams, max_streams)
+        if i >= args.warmup:
+            samples.append(s)
+    value = statistics.median(x["value"] for x in samples)
+    ms = statistics.median(x["seconds"] for x in samples) * 1e3
+    line = {
+        "impl": "reference", "metric": "events/s decode+pair+tally+timeline", "value": value, "unit": "events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                   "calls": int(cfg.total_calls), "seed": int(cfg.seed)},
+        "cpu_baseline": {"value": value, "unit": "events/s", "cores": 1, "kind": "oracle",
+                         "sample": samples[0]["sample"]},
+        "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    from paper_2504_03683_b300 import thapi
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg = trace_config(args, rank)
+    host, meta = generate_pinned(cfg)
+    dev = host.to("cuda", non_blocking=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ctx = thapi.Context(local)
+    thapi.thapi_ctx_set_timing(ctx.handle, True)
+
+    if args.profile_once:
+        tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), stream)
+        torch.cuda.synchronize()
+        ctx.free(tid)
+        ctx.close()
+        return
+
+    # first load sizes the output buffers
+    tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), stream)
+    info = ctx.info(tid)
+    ctx.free(tid)
+    rows_d = torch.empty(max(1, info["tally_rows"]) * 56, dtype=torch.uint8, device="cuda")
+    ivs_d = torch.empty(max(1, info["intervals"]) * 24, dtype=torch.uint8, device="cuda")
+    events = info["events"]
+    timings = []
+
+    def step(record=False):
+        t = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), stream)
+        thapi.thapi_tally_device(ctx.handle, t, rows_d.data_ptr(), info["tally_rows"], stream)
+        thapi.thapi_timeline_device(ctx.handle, t, 0, 2**64 - 1, ivs_d.data_ptr(), info["intervals"], stream)
+        if record:
+            timings.append(thapi.thapi_trace_timing(ctx.handle, t))
+        thapi.thapi_trace_free(ctx.handle, t)
+
+    for _ in range(args.warmup):
+        step()
+    barrier = (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None)
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = thapi.thapi_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(record=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = thapi.thapi_kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = ms
+    total_events = events
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+        ev = torch.tensor([float(events)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(ev)
+        total_events = float(ev.item())
+        lt = torch.tensor([float(launches)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(lt)
+        launches = int(lt.item())
+    value = total_events / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (decode + pair + tally), CUDA events inside the library
+    peaks, peak_src = measured_peaks()
+    an_ms = statistics.mean(t["analyze_ms"] for t in timings)
+    an_bytes = timings[0]["analyze_read_bytes"] + timings[0]["analyze_write_bytes"]
+    achieved = an_bytes / (an_ms / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    phase = {k: round(statistics.mean(t[k] for t in timings), 4)
+             for k in ("index_ms", "analyze_ms", "frontier_ms", "tally_ms", "compact_ms", "sort_ms", "gather_ms",
+                       "total_ms")}
+    traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze.cu"))
+
+    # end to end through the public API: host bytes in, host results out
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        rows_h = np.zeros(max(1, info["tally_rows"]), dtype=thapi.ROW_DTYPE)
+        ivs_pinned = torch.empty(max(1, info["intervals"]) * 24, dtype=torch.uint8, pin_memory=True)
+        ivs_h = ivs_pinned.numpy().view(thapi.INTERVAL_DTYPE)
+        n_iv = info["intervals"]
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tid = thapi.thapi_trace_load(ctx.handle, (host.data_ptr(), host.numel()), stream)
+            rows, _d = thapi.thapi_tally(ctx.handle, tid)
+            thapi.thapi_timeline(ctx.handle, tid, out=ivs_h)
+            thapi.thapi_trace_free(ctx.handle, tid)
+            dt = time.perf_counter() - t0
+            if i > 0:
+                times.append(dt)
+        e2e_s = statistics.median(times)
+        h2d = meta["n_packets"] * int(cfg.packet_bytes)
+        d2h = info["tally_rows"] * 56 + n_iv * 24
+        e2e = {"value": events / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        host_np = host.numpy()
+        cpu = cpu_sample(host_np, meta["n_streams"], args.cpu_streams or (200 if args.workload == "large" else 10**9))
+
+    if rank == 0:
+        line = {
+            "metric": "events/s decode+pair+tally+timeline", "value": value, "unit": "events/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                       "calls": int(cfg.total_calls), "events_per_rank": events, "trace_bytes": meta["nbytes"],
+                       "packets": meta["n_packets"], "seed": int(cfg.seed), "parallelism": "replicas" if world > 1
+                       else "single", "l2": "inputs larger than L2 (8.4 GB trace vs 126 MB L2); no flush"},
+            "trace_gbs": meta["nbytes"] / (ms_max / 1e3) / 1e9 * (world if world > 1 else 1),
+            "phases_ms": phase,
+            "roofline": {"kernel": "k_analyze (decode+pair+tally, interval slots)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": peak_src + " hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                         else "fallback",
+                         "bytes_per_launch": an_bytes, "launch_ms": an_ms, "traffic": traffic},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

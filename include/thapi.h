@@ -1,0 +1,216 @@
+/* thapi.h — C ABI of the B300 trace-analysis library (libthapi.so).
+ *
+ * The library turns a binary trace of intercepted API entry/exit events into
+ * (i) the per-(hostname, pid, tid, function) tally — call count, total / min /
+ * max inclusive duration, error-result count — and (ii) the time-ordered
+ * interval timeline.  These are the summary ("Tally") and timeline views that
+ * THAPI derives from its traces with Babeltrace2 plugins (arxiv 2504.03683,
+ * Sec. 3.2: entry and exit points traced with arguments and results;
+ * Sec. 3.4: plugins fed messages serialised by time, tally per
+ * hostname / process / thread; Sec. 3.6: timeline of host API calls;
+ * Sec. 4.3: the worked tally, whose HIP rows include the time of the
+ * Level-Zero calls they make).  All arithmetic is on integer nanoseconds; the
+ * results are exact.
+ *
+ * Trace layout ("THPT", little-endian; the paper fixes no layout beyond naming
+ * CTF, Sec. 3.1):
+ *   header (128 B): u32 magic "THPT", u16 version 1, u16 header_bytes 128,
+ *     u32 packet_bytes, u32 n_streams, u32 n_classes, u32 n_funcs,
+ *     u32 n_hosts, u32 0, u64 n_packets, u64 stream_table_off,
+ *     u64 class_table_off, u64 func_table_off, u64 host_table_off,
+ *     u64 strings_off, u64 strings_bytes, u64 packets_off, 32 B reserved;
+ *   stream rows {u32 host_id, pid, tid, flags}; class rows {u16 func_id,
+ *     u8 kind (0 ENTRY, 1 EXIT, 2 DEV_BEGIN, 3 DEV_END, 4 SAMPLE), u8 0,
+ *     u16 fixed_bytes, i16 result_off, i16 cmd_off, 6 B 0}; function rows
+ *     {u32 name_off, u16 layer, u16 0}; host rows {u32 name_off, u32 0};
+ *     NUL-terminated strings;
+ *   n_packets packets of packet_bytes (power of two, 256..65536) from
+ *     packets_off (multiple of 256): 32-byte header {u32 magic "PKT1",
+ *     u32 stream_id, u64 ts_begin, u32 content_bytes, u32 n_events, u32 seq,
+ *     u32 discarded} then 4-byte-aligned events {u32 tsw (bits 26:0 delta ns
+ *     from the previous event or ts_begin, bit 27 EXT = a u64 absolute ts
+ *     follows and the delta bits are 0, bits 31:28 zero), u16 class_id,
+ *     u16 var_len, [u64 ts], fixed part, payload, pad to 4}.
+ * Validation order (first failure wins): file header and tables; every packet
+ * header in file order; every packet's events in file order.  See
+ * thapi_last_error_location.
+ *
+ * Semantics: one stream = one thread.  Per stream, events are paired with a
+ * call stack: an EXIT pops the latest open ENTRY; equal functions make an
+ * interval [entry ts, exit ts] (level = depth of the entry, 0 outermost,
+ * saturated at 255; error flag = the exit's i32 result is nonzero).  An EXIT
+ * on an empty stack is an unmatched exit, a pop of another function a
+ * mismatched pair, entries still open at the end unmatched entries; all three
+ * are counted in thapi_diag and excluded from tally and timeline (events can
+ * be dropped by the tracer, Sec. 3.1).  DEV_BEGIN / DEV_END / SAMPLE events are
+ * decoded and counted as other events.
+ *
+ * Threading: a context may be used from one host thread at a time.
+ * Errors: every call returns a THAPI_* status; nothing falls back to the CPU.
+ */
+#ifndef THAPI_H
+#define THAPI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define THAPI_OK 0
+#define THAPI_E_INVALID 1     /* bad argument (null pointer, unknown id, misaligned device pointer) */
+#define THAPI_E_FORMAT 2      /* the trace breaks a layout rule */
+#define THAPI_E_TRUNCATED 3   /* the trace ends inside a table, packet or event */
+#define THAPI_E_NOMEM 4       /* device allocation failed, or admission over the context's HBM cap */
+#define THAPI_E_TIMEOUT 5     /* a bounded device-side wait gave up */
+#define THAPI_E_CUDA 6        /* a CUDA runtime call failed */
+#define THAPI_E_RANGE 7       /* output capacity too small; the needed count is returned */
+#define THAPI_E_UNSUPPORTED 8 /* valid trace outside this build's limits (see thapi_trace_load) */
+
+typedef struct thapi_ctx thapi_ctx;
+typedef uint64_t thapi_trace_id;
+
+/* One tally row (56 B).  Rows are ordered by (host_id, pid, tid, func_id).
+ * total_ns / min_ns / max_ns are inclusive call durations (exit ts - entry ts,
+ * u64); err_count counts calls whose exit result was nonzero. */
+typedef struct thapi_tally_row {
+  uint32_t host_id, pid, tid, func_id;
+  uint64_t count, total_ns, min_ns, max_ns, err_count;
+} thapi_tally_row;
+
+/* One timeline interval (24 B).  Timeline order is (start_ns, stream_id,
+ * position of the entry in its stream).  flags bit 0 = error result. */
+typedef struct thapi_interval {
+  uint64_t start_ns, end_ns;
+  uint32_t stream_id;
+  uint16_t func_id;
+  uint8_t level;
+  uint8_t flags;
+} thapi_interval;
+
+/* Diagnostics of one trace (64 B).
+ * events = 2*(pairs + mismatched_pairs) + unmatched_entries + unmatched_exits + other_events. */
+typedef struct thapi_diag {
+  uint64_t events;            /* events decoded */
+  uint64_t pairs;             /* matched calls = intervals = sum of tally counts */
+  uint64_t unmatched_entries; /* entries still open at the end of their stream */
+  uint64_t unmatched_exits;   /* exits met with an empty stack */
+  uint64_t mismatched_pairs;  /* pops whose entry had another function */
+  uint64_t other_events;      /* DEV_BEGIN, DEV_END and SAMPLE events */
+  uint64_t discarded;         /* sum of the packets' discarded counters */
+  uint64_t packets;
+} thapi_diag;
+
+/* Facts about a loaded trace. */
+typedef struct thapi_trace_info {
+  uint64_t nbytes, n_packets, events, intervals, tally_rows, device_bytes;
+  uint32_t n_streams, n_classes, n_funcs, n_hosts, packet_bytes, reserved;
+  uint64_t t_min, t_max;      /* smallest / largest event timestamp */
+} thapi_trace_info;
+
+/* Optional device allocator.  alloc returns device memory of at least `bytes`
+ * (aligned to 256 B) usable in stream order on `stream`, or NULL; free
+ * releases it in stream order.  Without hooks the library uses
+ * cudaMallocAsync / cudaFreeAsync on the call's stream. */
+typedef void *(*thapi_alloc_fn)(uint64_t bytes, void *stream, void *user);
+typedef void (*thapi_free_fn)(void *ptr, uint64_t bytes, void *stream, void *user);
+
+/* Creates a context on CUDA device `device`.  hbm_cap_bytes caps the device
+ * memory held by resident traces (results plus load temporaries); 0 = no cap.
+ * *out receives the context.  Errors: E_INVALID (null out), E_CUDA. */
+int thapi_ctx_create(thapi_ctx **out, int device, uint64_t hbm_cap_bytes);
+
+/* Installs allocator hooks (both or neither; NULLs restore the default).
+ * Must be called before the first load. */
+int thapi_ctx_set_allocator(thapi_ctx *ctx, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user);
+
+/* Frees every trace of the context and the context. */
+int thapi_ctx_destroy(thapi_ctx *ctx);
+
+/* Loads a trace from HOST memory: copies `bytes` (caller-owned, may be freed on
+ * return) to the device on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream), validates it, decodes every packet, pairs entry/exit events,
+ * builds the tally and the sorted timeline, and keeps those results resident
+ * on the device.  The raw bytes are released before returning.  Blocks until
+ * done.  *out receives the trace id.
+ * Errors: E_INVALID, E_FORMAT / E_TRUNCATED (see thapi_last_error_location),
+ * E_NOMEM (allocation failed or the HBM cap would be exceeded), E_UNSUPPORTED
+ * (streams x functions above 2^28 tally cells), E_TIMEOUT, E_CUDA. */
+int thapi_trace_load(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, void *cuda_stream, thapi_trace_id *out);
+
+/* As thapi_trace_load, for a trace already in DEVICE memory (16-byte aligned,
+ * caller-owned, read during the call only; not copied). */
+int thapi_trace_load_device(thapi_ctx *ctx, const void *dev_bytes, uint64_t nbytes, void *cuda_stream,
+                            thapi_trace_id *out);
+
+/* Releases a loaded trace's device results.  Errors: E_INVALID (unknown id). */
+int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id);
+
+/* Copies the tally rows to HOST memory `rows` (capacity `cap` rows) and the
+ * diagnostics to `diag` (may be NULL).  *n_rows = number of rows.  cap = 0 is
+ * a size query (returns OK); 0 < cap < rows returns E_RANGE with *n_rows set. */
+int thapi_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                thapi_diag *diag);
+
+/* Copies the timeline intervals with start_ns < t1 and end_ns >= t0 (t0 = 0,
+ * t1 = UINT64_MAX: all), in timeline order, to HOST memory `out` (capacity
+ * `cap`).  *n_out = number selected; cap semantics as thapi_tally. */
+int thapi_timeline(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
+                   uint64_t cap, uint64_t *n_out);
+
+/* Device-output forms: `rows` / `out` are DEVICE pointers written in order on
+ * `cuda_stream`; the call returns once the copy is enqueued and *n is known. */
+int thapi_tally_device(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                       thapi_diag *diag, void *cuda_stream);
+int thapi_timeline_device(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
+                          uint64_t cap, uint64_t *n_out, void *cuda_stream);
+
+/* Facts about a loaded trace. */
+int thapi_trace_info_get(thapi_ctx *ctx, thapi_trace_id id, thapi_trace_info *info);
+
+/* Copies a NUL-terminated name of a loaded trace into buf (capacity cap):
+ * kind 0 = host name of host_id `index`, kind 1 = function name of func_id
+ * `index`.  *len = name length without the NUL.  E_RANGE if it does not fit. */
+int thapi_trace_strings(thapi_ctx *ctx, thapi_trace_id id, int kind, uint32_t index, char *buf, uint64_t cap,
+                        uint64_t *len);
+
+/* Where the last failed load of this context failed: level 0 = file header or
+ * tables, 1 = packet header (packet = file index), 2 = packet content
+ * (packet = file index, event = index of the event within the packet, or the
+ * event count for a count mismatch). */
+int thapi_last_error_location(thapi_ctx *ctx, int *level, uint64_t *packet, uint64_t *event);
+
+/* Per-phase device time of a load, measured with CUDA events on the load
+ * stream when timing is enabled on the context (thapi_ctx_set_timing). */
+typedef struct thapi_load_timing {
+  float index_ms;     /* packet headers, group by stream, seq check, event offsets */
+  float analyze_ms;   /* decode + in-packet pairing + tally kernel(s) */
+  float frontier_ms;  /* depth carry and pairing across packets */
+  float tally_ms;     /* tally rows and interval offsets */
+  float compact_ms;   /* timeline slot compaction */
+  float sort_ms;      /* timeline radix sort */
+  float gather_ms;    /* timeline gather */
+  float total_ms;     /* first to last event of the load (includes host waits) */
+  uint64_t analyze_read_bytes;   /* sum over packets of 32 + content_bytes (what the analysis must read) */
+  uint64_t analyze_write_bytes;  /* interval slots written by the analysis (24 B each) */
+  uint64_t analyze_launches;     /* analysis kernel launches of the load */
+  uint64_t launches;             /* all kernel launches of the load */
+} thapi_load_timing;
+
+/* Enables (1) or disables (0) per-phase timing of subsequent loads. */
+int thapi_ctx_set_timing(thapi_ctx *ctx, int enable);
+
+/* Timing of a loaded trace (zeros if timing was off when it was loaded). */
+int thapi_trace_timing(thapi_ctx *ctx, thapi_trace_id id, thapi_load_timing *out);
+
+/* Kernels this library has launched in this process (all contexts). */
+uint64_t thapi_kernel_launches(void);
+
+/* Static description of a status code. */
+const char *thapi_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* THAPI_H */

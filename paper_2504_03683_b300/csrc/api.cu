@@ -1,0 +1,917 @@
+// api.cu — the C ABI: contexts, trace loading (validate, index, decode, pair,
+// tally, timeline) and queries over the resident results.
+//
+// Host code here checks the small file header and tables (the packet area is
+// validated on the device), numbers the (host, pid, tid) groups in order,
+// stages the packets in device memory and drives the kernels of index.cu,
+// analyze.cu, frontier.cu, tally.cu and timeline.cu on the caller's stream.
+// No step of the analysis runs on the CPU.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "internal.cuh"
+
+struct TraceRec {
+  cudaStream_t stream = nullptr;
+  thapi_trace_info info{};
+  thapi_diag diag{};
+  thapi_tally_row *rows = nullptr;
+  uint64_t rows_bytes = 0;
+  thapi_interval *tl = nullptr;
+  uint64_t tl_bytes = 0;
+  std::vector<char> strings;
+  std::vector<uint32_t> host_name, func_name;
+  thapi_load_timing timing{};
+};
+
+struct thapi_ctx {
+  int device = 0;
+  uint64_t cap = 0;
+  uint64_t used = 0;
+  thapi_alloc_fn alloc_fn = nullptr;
+  thapi_free_fn free_fn = nullptr;
+  void *user = nullptr;
+  int num_sms = 0;
+  int smem_per_sm = 0;
+  std::map<uint64_t, TraceRec *> traces;
+  uint64_t next_id = 1;
+  int err_level = 0;
+  uint64_t err_packet = 0, err_event = 0;
+  int timing = 0;
+};
+
+namespace thapi {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+// CUDA events bracketing the phases of one load (only when timing is on).
+struct PhaseClock {
+  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kTa1, kCo0, kCo1, kSo1, kGa1, kN };
+  cudaEvent_t ev[kN] = {};
+  bool on = false, dense = false;
+  void init(bool enable) {
+    on = enable;
+    if (!on) return;
+    for (auto &e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        on = false;
+        cudaGetLastError();
+        return;
+      }
+  }
+  void rec(int i, cudaStream_t s) {
+    if (on) cudaEventRecord(ev[i], s);
+  }
+  float ms(int a, int b) {
+    float t = 0.f;
+    if (on && cudaEventElapsedTime(&t, ev[a], ev[b]) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.f;
+    }
+    return t;
+  }
+  ~PhaseClock() {
+    for (auto &e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+
+static void *dev_alloc(thapi_ctx *c, uint64_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255u) & ~255ull;
+  if (c->alloc_fn) return c->alloc_fn(bytes, (void *)s, c->user);
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void dev_free(thapi_ctx *c, void *p, uint64_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255u) & ~255ull;
+  if (c->free_fn)
+    c->free_fn(p, bytes, (void *)s, c->user);
+  else
+    cudaFreeAsync(p, s);
+}
+
+void *Scratch::get(uint64_t bytes) {
+  void *p = dev_alloc(ctx, bytes, stream);
+  if (!p) {
+    failed = 1;
+    return nullptr;
+  }
+  bufs.push_back({p, bytes});
+  return p;
+}
+
+void Scratch::adopt(void *p, uint64_t bytes) {
+  if (p) bufs.push_back({p, bytes});
+}
+
+void Scratch::release_all() {
+  for (auto &b : bufs) dev_free(ctx, b.first, b.second, stream);
+  bufs.clear();
+}
+
+// ------------------------------------------------------------ host parse
+struct Reader {
+  const uint8_t *host;
+  const uint8_t *dev;
+  uint64_t n;
+  cudaStream_t s;
+  bool get(uint64_t off, uint64_t len, std::vector<uint8_t> &out) const {
+    out.resize(len);
+    if (!len) return true;
+    if (host) {
+      std::memcpy(out.data(), host + off, len);
+      return true;
+    }
+    if (cudaMemcpyAsync(out.data(), dev + off, len, cudaMemcpyDeviceToHost, s) != cudaSuccess) return false;
+    return cudaStreamSynchronize(s) == cudaSuccess;
+  }
+};
+
+template <class T>
+static T rd(const uint8_t *p) {
+  T v;
+  std::memcpy(&v, p, sizeof(T));
+  return v;
+}
+
+static bool in_file(uint64_t off, uint64_t count, uint64_t size, uint64_t n) {
+  if (off > n) return false;
+  if (size && count > (n - off) / size) return false;
+  return true;
+}
+
+static bool name_ok(const std::vector<uint8_t> &strs, uint32_t off) {
+  if (off >= strs.size()) return false;
+  return std::memchr(strs.data() + off, 0, strs.size() - off) != nullptr;
+}
+
+struct HostLayout {
+  uint32_t P = 0, n_streams = 0, n_classes = 0, n_funcs = 0, n_hosts = 0;
+  uint64_t n_packets = 0, packets_off = 0;
+  std::vector<uint64_t> cls;
+  std::vector<uint32_t> srow;  // 4 words per stream
+  std::vector<uint32_t> host_name, func_name;
+  std::vector<uint8_t> strings;
+};
+
+// File header and tables, in the documented check order.
+static int parse_layout(const Reader &r, HostLayout &L) {
+  if (r.n < kHeaderBytes) return THAPI_E_TRUNCATED;
+  std::vector<uint8_t> h;
+  if (!r.get(0, kHeaderBytes, h)) return THAPI_E_CUDA;
+  const uint8_t *b = h.data();
+  if (rd<uint32_t>(b) != kTraceMagic || rd<uint16_t>(b + 4) != 1 || rd<uint16_t>(b + 6) != kHeaderBytes)
+    return THAPI_E_FORMAT;
+  L.P = rd<uint32_t>(b + 8);
+  L.n_streams = rd<uint32_t>(b + 12);
+  L.n_classes = rd<uint32_t>(b + 16);
+  L.n_funcs = rd<uint32_t>(b + 20);
+  L.n_hosts = rd<uint32_t>(b + 24);
+  L.n_packets = rd<uint64_t>(b + 32);
+  const uint64_t st = rd<uint64_t>(b + 40), cl = rd<uint64_t>(b + 48), fn = rd<uint64_t>(b + 56),
+                 ho = rd<uint64_t>(b + 64), so = rd<uint64_t>(b + 72), sb = rd<uint64_t>(b + 80);
+  L.packets_off = rd<uint64_t>(b + 88);
+  if (L.P < 256 || L.P > kMaxPacket || (L.P & (L.P - 1))) return THAPI_E_FORMAT;
+  if (L.n_classes > 65536 || L.n_funcs > 65536) return THAPI_E_FORMAT;
+  if (!in_file(st, L.n_streams, 16, r.n) || !in_file(cl, L.n_classes, 16, r.n) || !in_file(fn, L.n_funcs, 8, r.n) ||
+      !in_file(ho, L.n_hosts, 8, r.n) || !in_file(so, sb, 1, r.n))
+    return THAPI_E_TRUNCATED;
+  if (L.packets_off % 256 != 0) return THAPI_E_FORMAT;
+  if (!in_file(L.packets_off, L.n_packets, L.P, r.n)) return THAPI_E_TRUNCATED;
+  std::vector<uint8_t> hs, fs, cs, ss;
+  if (!r.get(so, sb, L.strings) || !r.get(ho, 8ull * L.n_hosts, hs) || !r.get(fn, 8ull * L.n_funcs, fs) ||
+      !r.get(cl, 16ull * L.n_classes, cs) || !r.get(st, 16ull * L.n_streams, ss))
+    return THAPI_E_CUDA;
+  L.host_name.resize(L.n_hosts);
+  for (uint32_t i = 0; i < L.n_hosts; ++i) {
+    L.host_name[i] = rd<uint32_t>(hs.data() + 8ull * i);
+    if (!name_ok(L.strings, L.host_name[i])) return THAPI_E_FORMAT;
+  }
+  L.func_name.resize(L.n_funcs);
+  for (uint32_t i = 0; i < L.n_funcs; ++i) {
+    L.func_name[i] = rd<uint32_t>(fs.data() + 8ull * i);
+    if (!name_ok(L.strings, L.func_name[i])) return THAPI_E_FORMAT;
+  }
+  L.cls.resize(L.n_classes);
+  for (uint32_t k = 0; k < L.n_classes; ++k) {
+    const uint8_t *row = cs.data() + 16ull * k;
+    uint32_t func = rd<uint16_t>(row);
+    uint32_t kind = row[2];
+    uint32_t fixed = rd<uint16_t>(row + 4);
+    int32_t roff = rd<int16_t>(row + 6), coff = rd<int16_t>(row + 8);
+    if (func >= L.n_funcs || kind > kSample || (fixed & 3u)) return THAPI_E_FORMAT;
+    if (roff != -1 && (roff < 0 || (roff & 3) || (uint32_t)roff + 4 > fixed)) return THAPI_E_FORMAT;
+    if (coff != -1 && (coff < 0 || (coff & 3) || (uint32_t)coff + 8 > fixed)) return THAPI_E_FORMAT;
+    L.cls[k] = (uint64_t)(fixed >> 2) | ((uint64_t)kind << 14) | ((uint64_t)func << 17) |
+               ((uint64_t)(roff >= 0 ? (roff >> 2) + 1 : 0) << 33) |
+               ((uint64_t)(coff >= 0 ? (coff >> 2) + 1 : 0) << 48);
+  }
+  L.srow.resize(4ull * L.n_streams);
+  for (uint32_t s = 0; s < L.n_streams; ++s) {
+    for (int j = 0; j < 4; ++j) L.srow[4ull * s + j] = rd<uint32_t>(ss.data() + 16ull * s + 4 * j);
+    if (L.srow[4ull * s] >= L.n_hosts) return THAPI_E_FORMAT;
+  }
+  return THAPI_OK;
+}
+
+// Misc device words of one load.
+enum Misc {
+  mHdrErr = 0,
+  mContentErr,
+  mDiag0,
+  mTmin = mDiag0 + dCount,
+  mTmax,
+  mFrontTop,
+  mDense,
+  mEvents,
+  mStatus,
+  mRows,
+  mIv,
+  mReadBytes,
+  mSlots,
+  mCount
+};
+
+#define CK(x)                                   \
+  do {                                          \
+    if ((x) != cudaSuccess) {                   \
+      cudaGetLastError();                       \
+      return THAPI_E_CUDA;                      \
+    }                                           \
+  } while (0)
+
+class Loader {
+ public:
+  Loader(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, uint64_t nbytes, cudaStream_t s)
+      : c_(c), host_(host), dev_(dev), nbytes_(nbytes), s_(s) {
+    sc_.ctx = c;
+    sc_.stream = s;
+  }
+  ~Loader() {
+    sc_.release_all();
+    if (tr_) {
+      dev_free(c_, tr_->rows, tr_->rows_bytes, s_);
+      dev_free(c_, tr_->tl, tr_->tl_bytes, s_);
+      delete tr_;
+    }
+    cudaStreamSynchronize(s_);
+  }
+  int run();
+  TraceRec *take() {
+    TraceRec *t = tr_;
+    tr_ = nullptr;
+    return t;
+  }
+
+ private:
+  template <class T>
+  T *alloc(uint64_t count) {
+    return static_cast<T *>(sc_.get((count ? count : 1) * sizeof(T)));
+  }
+  int sync_misc() {
+    CK(cudaMemcpyAsync(misc_h_, misc_, sizeof(misc_h_), cudaMemcpyDeviceToHost, s_));
+    CK(cudaStreamSynchronize(s_));
+    return THAPI_OK;
+  }
+
+  thapi_ctx *c_;
+  const uint8_t *host_, *dev_;
+  uint64_t nbytes_;
+  cudaStream_t s_;
+  Scratch sc_;
+  TraceRec *tr_ = nullptr;
+  uint64_t *misc_ = nullptr;
+  unsigned long long misc_h_[mCount];
+  PhaseClock clk_;
+};
+
+static int blocks_per_sm(thapi_ctx *c, uint32_t smem) {
+  int b = std::min(16, c->smem_per_sm / (int)(smem + 1024));
+  return b < 1 ? 1 : b;
+}
+
+int Loader::run() {
+  HostLayout L;
+  const Reader r{host_, dev_, nbytes_, s_};
+  int rc = parse_layout(r, L);
+  if (rc != THAPI_OK) return rc;
+  const uint64_t n = L.n_packets;
+  const uint32_t P = L.P, S = L.n_streams, F = L.n_funcs;
+
+  // (host, pid, tid) groups numbered in order
+  std::vector<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>> keyed(S);
+  for (uint32_t i = 0; i < S; ++i)
+    keyed[i] = std::make_tuple(L.srow[4ull * i], L.srow[4ull * i + 1], L.srow[4ull * i + 2], i);
+  std::sort(keyed.begin(), keyed.end());
+  std::vector<uint32_t> stream_group(S ? S : 1, 0), group_keys;
+  uint32_t G = 0;
+  for (uint32_t i = 0; i < S; ++i) {
+    if (i == 0 || std::get<0>(keyed[i]) != std::get<0>(keyed[i - 1]) ||
+        std::get<1>(keyed[i]) != std::get<1>(keyed[i - 1]) || std::get<2>(keyed[i]) != std::get<2>(keyed[i - 1])) {
+      group_keys.push_back(std::get<0>(keyed[i]));
+      group_keys.push_back(std::get<1>(keyed[i]));
+      group_keys.push_back(std::get<2>(keyed[i]));
+      ++G;
+    }
+    stream_group[std::get<3>(keyed[i])] = G - 1;
+  }
+  const uint64_t cells = (uint64_t)G * F;
+  if (cells > (1ull << 28) || n >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+
+  // admission: coarse peak of this load (packets, index, table, slots, sort)
+  const uint64_t est_events = n * (uint64_t)((P - kPacketHeader) / 8);
+  const uint64_t est = (host_ ? n * (uint64_t)P : 0) + n * 128 + cells * 80 + est_events * 24;
+  if (c_->cap && c_->used + est > c_->cap) return THAPI_E_NOMEM;
+
+  tr_ = new (std::nothrow) TraceRec();
+  if (!tr_) return THAPI_E_NOMEM;
+  tr_->stream = s_;
+  clk_.init(c_->timing != 0);
+  const uint64_t launches0 = launches_total();
+  uint64_t analyze_launches = 0;
+
+  // ---- the packet area on the device
+  const uint8_t *packets = nullptr;
+  if (host_) {
+    uint8_t *pk = alloc<uint8_t>(n * (uint64_t)P);
+    if (!pk) return THAPI_E_NOMEM;
+    if (n) CK(cudaMemcpyAsync(pk, host_ + L.packets_off, n * (uint64_t)P, cudaMemcpyHostToDevice, s_));
+    packets = pk;
+  } else {
+    packets = dev_ + L.packets_off;
+    if (reinterpret_cast<uintptr_t>(packets) % 16 != 0) return THAPI_E_INVALID;
+  }
+
+  // ---- small tables and counters
+  misc_ = alloc<uint64_t>(mCount);
+  uint64_t *d_cls = alloc<uint64_t>(L.n_classes);
+  uint32_t *d_group = alloc<uint32_t>(S);
+  uint32_t *d_gkeys = alloc<uint32_t>(group_keys.size());
+  if (!misc_ || !d_cls || !d_group || !d_gkeys) return THAPI_E_NOMEM;
+  for (int i = 0; i < mCount; ++i) misc_h_[i] = 0;
+  misc_h_[mHdrErr] = misc_h_[mContentErr] = misc_h_[mTmin] = ~0ull;
+  CK(cudaMemcpyAsync(misc_, misc_h_, sizeof(misc_h_), cudaMemcpyHostToDevice, s_));
+  if (L.n_classes) CK(cudaMemcpyAsync(d_cls, L.cls.data(), 8ull * L.n_classes, cudaMemcpyHostToDevice, s_));
+  if (S) CK(cudaMemcpyAsync(d_group, stream_group.data(), 4ull * S, cudaMemcpyHostToDevice, s_));
+  if (G) CK(cudaMemcpyAsync(d_gkeys, group_keys.data(), 4ull * group_keys.size(), cudaMemcpyHostToDevice, s_));
+
+  // ---- index: headers, group by stream (stable), seq check, event offsets
+  uint32_t *pk_stream = alloc<uint32_t>(n), *pk_nev = alloc<uint32_t>(n), *pk_content = alloc<uint32_t>(n);
+  uint32_t *pk_seq = alloc<uint32_t>(n), *pk_disc = alloc<uint32_t>(n);
+  uint64_t *pk_tsb = alloc<uint64_t>(n), *keys = alloc<uint64_t>(n), *keys_alt = alloc<uint64_t>(n);
+  uint32_t *vals = alloc<uint32_t>(n), *vals_alt = alloc<uint32_t>(n);
+  uint64_t *evbase = alloc<uint64_t>(n);
+  uint32_t *stream_first = alloc<uint32_t>(S), *stream_count = alloc<uint32_t>(S);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  CK(cudaMemsetAsync(stream_first, 0, 4ull * (S ? S : 1), s_));
+  CK(cudaMemsetAsync(stream_count, 0, 4ull * (S ? S : 1), s_));
+  unsigned long long *hdr_err = reinterpret_cast<unsigned long long *>(misc_ + mHdrErr);
+  clk_.rec(PhaseClock::kIdx0, s_);
+  launch_packet_headers(IndexParams{packets, reinterpret_cast<unsigned long long *>(misc_ + mReadBytes), P, n, S,
+                                    pk_stream, pk_nev, pk_content, pk_seq, pk_disc, pk_tsb, hdr_err},
+                        s_);
+  launch_stream_keys(pk_stream, n, keys, vals, s_);
+  bool in_alt = false;
+  int sbits = 1;
+  while ((1ull << sbits) <= (uint64_t)S) ++sbits;  // the invalid-stream sentinel S must fit
+  radix_sort_pairs(keys, vals, keys_alt, vals_alt, n, sbits, &in_alt, sc_, s_);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  const uint64_t *skey = in_alt ? keys_alt : keys;
+  const uint32_t *order = in_alt ? vals_alt : vals;
+  launch_stream_bounds(skey, order, pk_seq, pk_nev, n, S, stream_first, stream_count, evbase, hdr_err, s_);
+  scan_exclusive_u64(evbase, n, misc_ + mEvents, sc_, s_);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  clk_.rec(PhaseClock::kIdx1, s_);
+  CK(cudaGetLastError());
+  if ((rc = sync_misc()) != THAPI_OK) return rc;
+  if (misc_h_[mHdrErr] != ~0ull) {
+    c_->err_level = 1;
+    c_->err_packet = misc_h_[mHdrErr];
+    return THAPI_E_FORMAT;
+  }
+  const uint64_t total_events = n ? misc_h_[mEvents] : 0;
+
+  // ---- decode + pair + tally per packet
+  Cell *tally = alloc<Cell>(cells);
+  uint32_t *sum_pend = alloc<uint32_t>(n), *sum_open = alloc<uint32_t>(n), *sum_nslot = alloc<uint32_t>(n);
+  uint32_t *sum_nvalid = alloc<uint32_t>(n), *dense_list = alloc<uint32_t>(n);
+  uint32_t *A = alloc<uint32_t>(n), *base = alloc<uint32_t>(n);
+  uint64_t *sum_fbase = alloc<uint64_t>(n);
+  thapi_interval *slots = alloc<thapi_interval>(total_events);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  uint64_t fcap = total_events / 4 + 4096;
+  Frontier *frontier = nullptr;
+  unsigned *status = reinterpret_cast<unsigned *>(misc_ + mStatus);
+  for (int attempt = 0;; ++attempt) {
+    frontier = static_cast<Frontier *>(dev_alloc(c_, fcap * sizeof(Frontier), s_));
+    if (!frontier) return THAPI_E_NOMEM;
+    sc_.adopt(frontier, fcap * sizeof(Frontier));
+    launch_tally_init(tally, cells, s_);
+    misc_h_[mContentErr] = ~0ull;
+    for (int d = 0; d < dCount; ++d) misc_h_[mDiag0 + d] = 0;
+    misc_h_[mTmin] = ~0ull;
+    misc_h_[mTmax] = misc_h_[mFrontTop] = misc_h_[mDense] = misc_h_[mStatus] = 0;
+    CK(cudaMemcpyAsync(misc_ + mContentErr, misc_h_ + mContentErr, sizeof(uint64_t) * (mStatus - mContentErr + 1),
+                       cudaMemcpyHostToDevice, s_));
+    misc_h_[mSlots] = 0;
+    CK(cudaMemcpyAsync(misc_ + mSlots, misc_h_ + mSlots, sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
+    AnalyzeParams ap{};
+    ap.packets = packets;
+    ap.P = P;
+    ap.emax = ((P - kPacketHeader) / 4) / 4;
+    ap.n_order = n;
+    ap.order = order;
+    ap.poslist = nullptr;
+    ap.pk_stream = pk_stream;
+    ap.pk_nev = pk_nev;
+    ap.pk_content = pk_content;
+    ap.pk_disc = pk_disc;
+    ap.pk_tsb = pk_tsb;
+    ap.evbase = evbase;
+    ap.classes = d_cls;
+    ap.n_classes = L.n_classes;
+    ap.n_funcs = F;
+    ap.stream_group = d_group;
+    ap.tally = tally;
+    ap.sum_pend = sum_pend;
+    ap.sum_open = sum_open;
+    ap.sum_nslot = sum_nslot;
+    ap.sum_nvalid = sum_nvalid;
+    ap.sum_fbase = sum_fbase;
+    ap.frontier = frontier;
+    ap.frontier_top = reinterpret_cast<unsigned long long *>(misc_ + mFrontTop);
+    ap.frontier_cap = fcap;
+    ap.slots = slots;
+    ap.content_err = reinterpret_cast<unsigned long long *>(misc_ + mContentErr);
+    ap.diag = reinterpret_cast<unsigned long long *>(misc_ + mDiag0);
+    ap.tminmax = reinterpret_cast<unsigned long long *>(misc_ + mTmin);
+    ap.dense_list = dense_list;
+    ap.dense_count = reinterpret_cast<unsigned long long *>(misc_ + mDense);
+    ap.slots_written = reinterpret_cast<unsigned long long *>(misc_ + mSlots);
+    const int stages = 2;
+    if (n) {
+      uint32_t smem = analyze_smem_bytes(P, ap.emax, stages, L.n_classes, F);
+      uint64_t grid = (uint64_t)c_->num_sms * blocks_per_sm(c_, smem);
+      uint64_t per = (n + grid - 1) / grid;
+      ap.per_cta = (uint32_t)per;
+      grid = (n + per - 1) / per;
+      clk_.rec(PhaseClock::kAn0, s_);
+      CK(launch_analyze(ap, stages, (uint32_t)grid, s_, status));
+      clk_.rec(PhaseClock::kAn1, s_);
+      analyze_launches = 1;
+      if ((rc = sync_misc()) != THAPI_OK) return rc;
+      if (misc_h_[mDense]) {
+        AnalyzeParams dp = ap;
+        dp.emax = ((P - kPacketHeader) / 4) / 2 + 1;
+        dp.n_order = misc_h_[mDense];
+        dp.poslist = dense_list;
+        dp.dense_list = nullptr;
+        dp.dense_count = nullptr;
+        uint32_t dsmem = analyze_smem_bytes(P, dp.emax, stages, L.n_classes, F);
+        uint64_t dgrid = std::min<uint64_t>(dp.n_order, (uint64_t)c_->num_sms * blocks_per_sm(c_, dsmem));
+        uint64_t dper = (dp.n_order + dgrid - 1) / dgrid;
+        dp.per_cta = (uint32_t)dper;
+        dgrid = (dp.n_order + dper - 1) / dper;
+        clk_.rec(PhaseClock::kDn0, s_);
+        CK(launch_analyze(dp, stages, (uint32_t)dgrid, s_, status));
+        clk_.rec(PhaseClock::kDn1, s_);
+        clk_.dense = true;
+        analyze_launches = 2;
+        if ((rc = sync_misc()) != THAPI_OK) return rc;
+      }
+    }
+    if (misc_h_[mStatus] == THAPI_E_TIMEOUT) return THAPI_E_TIMEOUT;
+    if (misc_h_[mContentErr] != ~0ull) {
+      const unsigned long long k = misc_h_[mContentErr];
+      c_->err_level = 2;
+      c_->err_packet = k >> 20;
+      c_->err_event = (k >> 3) & 0x1FFFFu;
+      return (int)(k & 7u);
+    }
+    if (misc_h_[mFrontTop] <= fcap || attempt >= 1) break;
+    fcap = misc_h_[mFrontTop];  // retry once with the exact frontier size
+  }
+  if (misc_h_[mFrontTop] > fcap) return THAPI_E_NOMEM;
+
+  // ---- pairing across packets
+  {
+    FrontierParams fp{};
+    fp.n_order = n;
+    fp.n_streams = S;
+    fp.order = order;
+    fp.pk_stream = pk_stream;
+    fp.stream_first = stream_first;
+    fp.stream_count = stream_count;
+    fp.sum_pend = sum_pend;
+    fp.sum_open = sum_open;
+    fp.sum_fbase = sum_fbase;
+    fp.A = A;
+    fp.base = base;
+    fp.evbase = evbase;
+    fp.frontier = frontier;
+    fp.stream_group = d_group;
+    fp.n_funcs = F;
+    fp.tally = tally;
+    fp.slots = slots;
+    fp.sum_nvalid = sum_nvalid;
+    fp.diag = reinterpret_cast<unsigned long long *>(misc_ + mDiag0);
+    clk_.rec(PhaseClock::kFr0, s_);
+    launch_frontier(fp, s_);
+    clk_.rec(PhaseClock::kFr1, s_);
+  }
+
+  // ---- tally rows and interval offsets
+  uint64_t *flags = alloc<uint64_t>(cells);
+  thapi_tally_row *rows_tmp = alloc<thapi_tally_row>(cells);
+  uint64_t *obase = alloc<uint64_t>(n);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  launch_tally_compact(tally, cells, d_gkeys, F, flags, rows_tmp, misc_ + mRows, sc_, s_);
+  launch_widen_u32(sum_nvalid, obase, n, s_);
+  scan_exclusive_u64(obase, n, misc_ + mIv, sc_, s_);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  clk_.rec(PhaseClock::kTa1, s_);
+  CK(cudaGetLastError());
+  if ((rc = sync_misc()) != THAPI_OK) return rc;
+  const uint64_t n_rows = cells ? misc_h_[mRows] : 0;
+  const uint64_t n_iv = n ? misc_h_[mIv] : 0;
+  if (n_iv >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+  tr_->rows_bytes = std::max<uint64_t>(n_rows, 1) * sizeof(thapi_tally_row);
+  tr_->rows = static_cast<thapi_tally_row *>(dev_alloc(c_, tr_->rows_bytes, s_));
+  if (!tr_->rows) return THAPI_E_NOMEM;
+  if (n_rows)
+    CK(cudaMemcpyAsync(tr_->rows, rows_tmp, n_rows * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice, s_));
+
+  // ---- timeline: compact valid slots, sort by start, gather
+  thapi_interval *rec = alloc<thapi_interval>(n_iv);
+  uint64_t *k1 = alloc<uint64_t>(n_iv), *k2 = alloc<uint64_t>(n_iv);
+  uint32_t *v1 = alloc<uint32_t>(n_iv), *v2 = alloc<uint32_t>(n_iv);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  const uint64_t tmin = misc_h_[mTmin], tmax = misc_h_[mTmax];
+  clk_.rec(PhaseClock::kCo0, s_);
+  launch_timeline_compact(slots, evbase, sum_nslot, obase, A, order, pk_stream, n, n_iv ? tmin : 0, rec, k1, v1,
+                          c_->num_sms, s_);
+  clk_.rec(PhaseClock::kCo1, s_);
+  int bits = 0;
+  if (n_iv && tmax > tmin) {
+    const uint64_t span = tmax - tmin;
+    while (bits < 64 && (span >> bits)) ++bits;
+  }
+  bool alt = false;
+  radix_sort_pairs(k1, v1, k2, v2, n_iv, bits, &alt, sc_, s_);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  clk_.rec(PhaseClock::kSo1, s_);
+  tr_->tl_bytes = std::max<uint64_t>(n_iv, 1) * sizeof(thapi_interval);
+  tr_->tl = static_cast<thapi_interval *>(dev_alloc(c_, tr_->tl_bytes, s_));
+  if (!tr_->tl) return THAPI_E_NOMEM;
+  launch_timeline_gather(rec, alt ? v2 : v1, n_iv, tr_->tl, s_);
+  clk_.rec(PhaseClock::kGa1, s_);
+  CK(cudaGetLastError());
+  if ((rc = sync_misc()) != THAPI_OK) return rc;
+  {
+    thapi_load_timing &t = tr_->timing;
+    t.launches = launches_total() - launches0;
+    t.analyze_launches = analyze_launches;
+    t.analyze_read_bytes = misc_h_[mReadBytes];
+    t.analyze_write_bytes = misc_h_[mSlots] * sizeof(thapi_interval);
+    if (clk_.on && n) {
+      t.index_ms = clk_.ms(PhaseClock::kIdx0, PhaseClock::kIdx1);
+      t.analyze_ms = clk_.ms(PhaseClock::kAn0, PhaseClock::kAn1) +
+                     (clk_.dense ? clk_.ms(PhaseClock::kDn0, PhaseClock::kDn1) : 0.f);
+      t.frontier_ms = clk_.ms(PhaseClock::kFr0, PhaseClock::kFr1);
+      t.tally_ms = clk_.ms(PhaseClock::kFr1, PhaseClock::kTa1);
+      t.compact_ms = clk_.ms(PhaseClock::kCo0, PhaseClock::kCo1);
+      t.sort_ms = clk_.ms(PhaseClock::kCo1, PhaseClock::kSo1);
+      t.gather_ms = clk_.ms(PhaseClock::kSo1, PhaseClock::kGa1);
+      t.total_ms = clk_.ms(PhaseClock::kIdx0, PhaseClock::kGa1);
+    }
+  }
+
+  // ---- record
+  thapi_diag &d = tr_->diag;
+  d.events = misc_h_[mDiag0 + dEvents];
+  d.pairs = misc_h_[mDiag0 + dPairs];
+  d.unmatched_entries = misc_h_[mDiag0 + dUnEntry];
+  d.unmatched_exits = misc_h_[mDiag0 + dUnExit];
+  d.mismatched_pairs = misc_h_[mDiag0 + dMismatch];
+  d.other_events = misc_h_[mDiag0 + dOther];
+  d.discarded = misc_h_[mDiag0 + dDiscarded];
+  d.packets = misc_h_[mDiag0 + dPackets];
+  thapi_trace_info &inf = tr_->info;
+  inf.nbytes = nbytes_;
+  inf.n_packets = n;
+  inf.events = d.events;
+  inf.intervals = n_iv;
+  inf.tally_rows = n_rows;
+  inf.n_streams = S;
+  inf.n_classes = L.n_classes;
+  inf.n_funcs = F;
+  inf.n_hosts = L.n_hosts;
+  inf.packet_bytes = P;
+  inf.t_min = tmin == ~0ull ? 0 : tmin;
+  inf.t_max = tmax;
+  inf.device_bytes = tr_->rows_bytes + tr_->tl_bytes;
+  tr_->strings.assign(L.strings.begin(), L.strings.end());
+  tr_->host_name = L.host_name;
+  tr_->func_name = L.func_name;
+  return THAPI_OK;
+}
+
+static int load_common(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, uint64_t nbytes, void *stream,
+                       thapi_trace_id *out) {
+  if (!c || !out || (!host && !dev)) return THAPI_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
+  c->err_level = 0;
+  c->err_packet = c->err_event = 0;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc;
+  TraceRec *tr = nullptr;
+  {
+    Loader ld(c, host, dev, nbytes, s);
+    rc = ld.run();
+    if (rc == THAPI_OK) tr = ld.take();
+  }
+  if (rc != THAPI_OK) return rc;
+  const uint64_t id = c->next_id++;
+  c->traces[id] = tr;
+  c->used += tr->info.device_bytes;
+  *out = id;
+  return THAPI_OK;
+}
+
+static TraceRec *find(thapi_ctx *c, thapi_trace_id id) {
+  if (!c) return nullptr;
+  auto it = c->traces.find(id);
+  return it == c->traces.end() ? nullptr : it->second;
+}
+
+// Selects the window [t0, t1) of a resident timeline into dst (device memory),
+// or only counts it when dst is null.  Returns the count through *n.
+static int select_window(thapi_ctx *c, TraceRec *tr, uint64_t t0, uint64_t t1, thapi_interval *dst, uint64_t cap,
+                         uint64_t *n, cudaStream_t s, bool *is_full) {
+  const uint64_t total = tr->info.intervals;
+  *is_full = t0 == 0 && t1 == ~0ull;
+  if (*is_full || total == 0) {
+    *n = *is_full ? total : 0;
+    return THAPI_OK;
+  }
+  Scratch sc;
+  sc.ctx = c;
+  sc.stream = s;
+  uint64_t *words = static_cast<uint64_t *>(sc.get(2 * sizeof(uint64_t)));
+  if (!words) return THAPI_E_NOMEM;
+  launch_lower_bound_start(tr->tl, total, t1, words, s);
+  uint64_t hi = 0;
+  if (cudaMemcpyAsync(&hi, words, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    sc.release_all();
+    return THAPI_E_CUDA;
+  }
+  uint64_t *flags = static_cast<uint64_t *>(sc.get((hi ? hi : 1) * sizeof(uint64_t)));
+  if (!flags) {
+    sc.release_all();
+    return THAPI_E_NOMEM;
+  }
+  launch_window_count(tr->tl, total, t0, t1, words, flags, words + 1, sc, s, hi);
+  uint64_t cnt = 0;
+  if (cudaMemcpyAsync(&cnt, words + 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    sc.release_all();
+    return THAPI_E_CUDA;
+  }
+  *n = cnt;
+  if (dst && cnt <= cap) launch_window_write(tr->tl, hi, t0, t1, flags, dst, s);
+  int rc = cudaGetLastError() == cudaSuccess ? THAPI_OK : THAPI_E_CUDA;
+  sc.release_all();
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+static int timeline_impl(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
+                         uint64_t cap, uint64_t *n_out, bool device_out, cudaStream_t s) {
+  TraceRec *tr = find(c, id);
+  if (!tr || !n_out || (cap && !out)) return THAPI_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
+  bool full = false;
+  uint64_t cnt = 0;
+  int rc = select_window(c, tr, t0, t1, nullptr, 0, &cnt, s, &full);
+  if (rc != THAPI_OK) return rc;
+  *n_out = cnt;
+  if (cap == 0) return THAPI_OK;
+  if (cap < cnt) return THAPI_E_RANGE;
+  if (cnt == 0) return THAPI_OK;
+  if (full) {
+    cudaError_t e = cudaMemcpyAsync(out, tr->tl, cnt * sizeof(thapi_interval),
+                                    device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return THAPI_E_CUDA;
+    if (!device_out && cudaStreamSynchronize(s) != cudaSuccess) return THAPI_E_CUDA;
+    return THAPI_OK;
+  }
+  if (device_out) return select_window(c, tr, t0, t1, out, cap, &cnt, s, &full);
+  Scratch sc;
+  sc.ctx = c;
+  sc.stream = s;
+  thapi_interval *tmp = static_cast<thapi_interval *>(sc.get(cnt * sizeof(thapi_interval)));
+  if (!tmp) return THAPI_E_NOMEM;
+  rc = select_window(c, tr, t0, t1, tmp, cnt, &cnt, s, &full);
+  if (rc == THAPI_OK) {
+    if (cudaMemcpyAsync(out, tmp, cnt * sizeof(thapi_interval), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = THAPI_E_CUDA;
+  }
+  sc.release_all();
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+static int tally_impl(thapi_ctx *c, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                      thapi_diag *diag, bool device_out, cudaStream_t s) {
+  TraceRec *tr = find(c, id);
+  if (!tr || !n_rows || (cap && !rows)) return THAPI_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
+  const uint64_t n = tr->info.tally_rows;
+  *n_rows = n;
+  if (diag) *diag = tr->diag;
+  if (cap == 0) return THAPI_OK;
+  if (cap < n) return THAPI_E_RANGE;
+  if (!n) return THAPI_OK;
+  if (cudaMemcpyAsync(rows, tr->rows, n * sizeof(thapi_tally_row),
+                      device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return THAPI_E_CUDA;
+  if (!device_out && cudaStreamSynchronize(s) != cudaSuccess) return THAPI_E_CUDA;
+  return THAPI_OK;
+}
+
+}  // namespace thapi
+
+using namespace thapi;
+
+extern "C" {
+
+int thapi_ctx_create(thapi_ctx **out, int device, uint64_t hbm_cap_bytes) {
+  if (!out) return THAPI_E_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return device < 0 || (ndev > 0 && device >= ndev) ? THAPI_E_INVALID : THAPI_E_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return THAPI_E_CUDA;
+  thapi_ctx *c = new (std::nothrow) thapi_ctx();
+  if (!c) return THAPI_E_NOMEM;
+  c->device = device;
+  c->cap = hbm_cap_bytes;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) {
+    delete c;
+    return THAPI_E_CUDA;
+  }
+  *out = c;
+  return THAPI_OK;
+}
+
+int thapi_ctx_set_allocator(thapi_ctx *ctx, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user) {
+  if (!ctx || (!alloc) != (!free_fn)) return THAPI_E_INVALID;
+  if (!ctx->traces.empty()) return THAPI_E_INVALID;
+  ctx->alloc_fn = alloc;
+  ctx->free_fn = free_fn;
+  ctx->user = user;
+  return THAPI_OK;
+}
+
+int thapi_ctx_destroy(thapi_ctx *ctx) {
+  if (!ctx) return THAPI_E_INVALID;
+  cudaSetDevice(ctx->device);
+  for (auto &kv : ctx->traces) {
+    TraceRec *t = kv.second;
+    dev_free(ctx, t->rows, t->rows_bytes, t->stream);
+    dev_free(ctx, t->tl, t->tl_bytes, t->stream);
+    cudaStreamSynchronize(t->stream);
+    delete t;
+  }
+  ctx->traces.clear();
+  delete ctx;
+  return THAPI_OK;
+}
+
+int thapi_trace_load(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, void *cuda_stream, thapi_trace_id *out) {
+  if (!bytes) return THAPI_E_INVALID;
+  return load_common(ctx, static_cast<const uint8_t *>(bytes), nullptr, nbytes, cuda_stream, out);
+}
+
+int thapi_trace_load_device(thapi_ctx *ctx, const void *dev_bytes, uint64_t nbytes, void *cuda_stream,
+                            thapi_trace_id *out) {
+  if (!dev_bytes) return THAPI_E_INVALID;
+  if (reinterpret_cast<uintptr_t>(dev_bytes) % 16 != 0) return THAPI_E_INVALID;
+  return load_common(ctx, nullptr, static_cast<const uint8_t *>(dev_bytes), nbytes, cuda_stream, out);
+}
+
+int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id) {
+  TraceRec *t = find(ctx, id);
+  if (!t) return THAPI_E_INVALID;
+  cudaSetDevice(ctx->device);
+  dev_free(ctx, t->rows, t->rows_bytes, t->stream);
+  dev_free(ctx, t->tl, t->tl_bytes, t->stream);
+  cudaStreamSynchronize(t->stream);
+  ctx->used -= std::min(ctx->used, t->info.device_bytes);
+  ctx->traces.erase(id);
+  delete t;
+  return THAPI_OK;
+}
+
+int thapi_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                thapi_diag *diag) {
+  TraceRec *t = find(ctx, id);
+  return tally_impl(ctx, id, rows, cap, n_rows, diag, false, t ? t->stream : nullptr);
+}
+
+int thapi_tally_device(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                       thapi_diag *diag, void *cuda_stream) {
+  return tally_impl(ctx, id, rows, cap, n_rows, diag, true, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int thapi_timeline(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out, uint64_t cap,
+                   uint64_t *n_out) {
+  TraceRec *t = find(ctx, id);
+  return timeline_impl(ctx, id, t0, t1, out, cap, n_out, false, t ? t->stream : nullptr);
+}
+
+int thapi_timeline_device(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
+                          uint64_t cap, uint64_t *n_out, void *cuda_stream) {
+  return timeline_impl(ctx, id, t0, t1, out, cap, n_out, true, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int thapi_trace_info_get(thapi_ctx *ctx, thapi_trace_id id, thapi_trace_info *info) {
+  TraceRec *t = find(ctx, id);
+  if (!t || !info) return THAPI_E_INVALID;
+  *info = t->info;
+  return THAPI_OK;
+}
+
+int thapi_trace_strings(thapi_ctx *ctx, thapi_trace_id id, int kind, uint32_t index, char *buf, uint64_t cap,
+                        uint64_t *len) {
+  TraceRec *t = find(ctx, id);
+  if (!t || !len) return THAPI_E_INVALID;
+  const std::vector<uint32_t> &tab = kind == 0 ? t->host_name : t->func_name;
+  if ((kind != 0 && kind != 1) || index >= tab.size()) return THAPI_E_INVALID;
+  const char *s = t->strings.data() + tab[index];
+  uint64_t l = std::strlen(s);
+  *len = l;
+  if (!buf || cap < l + 1) return THAPI_E_RANGE;
+  std::memcpy(buf, s, l + 1);
+  return THAPI_OK;
+}
+
+int thapi_ctx_set_timing(thapi_ctx *ctx, int enable) {
+  if (!ctx) return THAPI_E_INVALID;
+  ctx->timing = enable ? 1 : 0;
+  return THAPI_OK;
+}
+
+int thapi_trace_timing(thapi_ctx *ctx, thapi_trace_id id, thapi_load_timing *out) {
+  TraceRec *t = find(ctx, id);
+  if (!t || !out) return THAPI_E_INVALID;
+  *out = t->timing;
+  return THAPI_OK;
+}
+
+uint64_t thapi_kernel_launches(void) { return launches_total(); }
+
+int thapi_last_error_location(thapi_ctx *ctx, int *level, uint64_t *packet, uint64_t *event) {
+  if (!ctx || !level || !packet || !event) return THAPI_E_INVALID;
+  *level = ctx->err_level;
+  *packet = ctx->err_packet;
+  *event = ctx->err_event;
+  return THAPI_OK;
+}
+
+const char *thapi_strerror(int code) {
+  switch (code) {
+    case THAPI_OK: return "ok";
+    case THAPI_E_INVALID: return "invalid argument";
+    case THAPI_E_FORMAT: return "trace breaks a layout rule";
+    case THAPI_E_TRUNCATED: return "trace is truncated";
+    case THAPI_E_NOMEM: return "out of device memory or over the context's HBM cap";
+    case THAPI_E_TIMEOUT: return "a bounded device wait gave up";
+    case THAPI_E_CUDA: return "CUDA runtime error";
+    case THAPI_E_RANGE: return "output capacity too small";
+    case THAPI_E_UNSUPPORTED: return "trace outside this build's limits";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

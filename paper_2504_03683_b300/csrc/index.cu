@@ -1,0 +1,121 @@
+// index.cu — packet index and header validation.
+//
+// One thread per packet reads the 32-byte header (two 16-byte loads), checks
+// it and records stream, event count, content size, seq, ts_begin and the
+// discarded counter.  Packets are then grouped by stream with the stable
+// radix sort (file order is kept inside a stream), seq monotonicity is checked
+// between neighbours of one stream, and an exclusive scan of the event counts
+// in stream order gives every packet its first event slot.
+#include "internal.cuh"
+
+namespace thapi {
+
+__global__ void k_packet_headers(IndexParams p) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long rb = 0;
+  if (i < p.n_packets) {
+  const uint4 *h = reinterpret_cast<const uint4 *>(p.packets + i * (uint64_t)p.P);
+  uint4 a = __ldg(h);
+  uint4 b = __ldg(h + 1);
+  uint32_t magic = a.x, stream = a.y, content = b.x, nev = b.y, seq = b.z, disc = b.w;
+  uint64_t tsb = (uint64_t)a.z | ((uint64_t)a.w << 32);
+  bool bad = magic != kPacketMagic || stream >= p.n_streams || (content & 3u) != 0 ||
+             content > p.P - kPacketHeader || nev > content / 8u;
+  if (bad) {
+    atomicMin(p.hdr_err, (unsigned long long)i);
+    stream = p.n_streams;  // sentinel group, sorted last
+    content = 0;
+    nev = 0;
+  }
+  p.pk_stream[i] = stream;
+  p.pk_nev[i] = nev;
+  p.pk_content[i] = content;
+  p.pk_seq[i] = seq;
+  p.pk_disc[i] = disc;
+  p.pk_tsb[i] = tsb;
+  if (!bad) rb = kPacketHeader + content;
+  }
+  for (int o = 16; o > 0; o >>= 1) rb += __shfl_down_sync(0xffffffffu, rb, o);
+  if ((threadIdx.x & 31) == 0 && rb) atomicAdd(p.read_bytes, rb);
+}
+
+// Sort keys/values for grouping by stream.
+__global__ void k_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = pk_stream[i];
+  vals[i] = (uint32_t)i;
+}
+
+// Stream bounds and seq check over the stream-ordered list; also gathers the
+// per-packet event counts in stream order for the scan.
+__global__ void k_stream_bounds(const uint64_t *skey, const uint32_t *order, const uint32_t *pk_seq,
+                                const uint32_t *pk_nev, uint64_t n, uint32_t n_streams, uint32_t *stream_first,
+                                uint64_t *ev, unsigned long long *hdr_err) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t s = (uint32_t)skey[i];
+  uint32_t pk = order[i];
+  ev[i] = pk_nev[pk];
+  if (s >= n_streams) return;
+  bool first = i == 0 || (uint32_t)skey[i - 1] != s;
+  if (first) stream_first[s] = (uint32_t)i;
+  if (!first && pk_seq[pk] <= pk_seq[order[i - 1]]) atomicMin(hdr_err, (unsigned long long)pk);
+}
+
+// count = last + 1 - first (second pass, after stream_first is known)
+__global__ void k_stream_counts(const uint64_t *skey, uint64_t n, uint32_t n_streams, const uint32_t *stream_first,
+                                uint32_t *stream_count) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  uint32_t s = (uint32_t)skey[i];
+  if (s >= n_streams) return;
+  bool last = i + 1 == n || (uint32_t)skey[i + 1] != s;
+  if (last) stream_count[s] = (uint32_t)(i + 1 - stream_first[s]);
+}
+
+}  // namespace thapi
+
+namespace thapi {
+
+static unsigned grid_for(uint64_t n, unsigned t) { return (unsigned)((n + t - 1) / t); }
+
+void launch_packet_headers(const IndexParams &p, cudaStream_t s) {
+  if (p.n_packets) {
+    k_packet_headers<<<grid_for(p.n_packets, 256), 256, 0, s>>>(p);
+    count_launches(1);
+  }
+}
+void launch_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals, cudaStream_t s) {
+  if (n) {
+    k_stream_keys<<<grid_for(n, 256), 256, 0, s>>>(pk_stream, n, keys, vals);
+    count_launches(1);
+  }
+}
+void launch_stream_bounds(const uint64_t *skey, const uint32_t *order, const uint32_t *pk_seq, const uint32_t *pk_nev,
+                          uint64_t n, uint32_t n_streams, uint32_t *stream_first, uint32_t *stream_count,
+                          uint64_t *ev, unsigned long long *hdr_err, cudaStream_t s) {
+  if (!n) return;
+  k_stream_bounds<<<grid_for(n, 256), 256, 0, s>>>(skey, order, pk_seq, pk_nev, n, n_streams, stream_first, ev,
+                                                    hdr_err);
+  k_stream_counts<<<grid_for(n, 256), 256, 0, s>>>(skey, n, n_streams, stream_first, stream_count);
+  count_launches(2);
+}
+
+}  // namespace thapi
+
+namespace thapi {
+
+__global__ void k_widen_u32(const uint32_t *in, uint64_t *out, uint64_t n) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = in[i];
+}
+
+void launch_widen_u32(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s) {
+  if (n) {
+    k_widen_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
+    count_launches(1);
+  }
+}
+
+}  // namespace thapi

@@ -1,0 +1,182 @@
+// internal.cuh — shared declarations of the CUDA trace-analysis library.
+//
+// The library reads the THPT layout described in include/thapi.h.  Its own
+// restatement of that layout lives here; nothing is shared with the CPU
+// oracle used by the tests.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+#include <vector>
+
+#include "../../include/thapi.h"
+
+namespace thapi {
+
+// ------------------------------------------------------------- layout
+constexpr uint32_t kTraceMagic = 0x54504854u;   // "THPT"
+constexpr uint32_t kPacketMagic = 0x31544B50u;  // "PKT1"
+constexpr uint32_t kExtBit = 1u << 27;
+constexpr uint32_t kDeltaMask = (1u << 27) - 1u;
+constexpr uint32_t kHeaderBytes = 128;
+constexpr uint32_t kPacketHeader = 32;
+constexpr uint32_t kMaxPacket = 65536;
+
+enum Kind : uint32_t { kEntry = 0, kExit = 1, kDevBegin = 2, kDevEnd = 3, kSample = 4 };
+
+// Packed class row: fixed words (14 bits) | kind << 14 (3) | func << 17 (16)
+//   | (result word + 1) << 33 (15, 0 = none) | (cmd word + 1) << 48 (15, 0 = none)
+__host__ __device__ inline uint32_t cls_fixedw(uint64_t c) { return (uint32_t)(c & 0x3FFFu); }
+__host__ __device__ inline uint32_t cls_kind(uint64_t c) { return (uint32_t)((c >> 14) & 7u); }
+__host__ __device__ inline uint32_t cls_func(uint64_t c) { return (uint32_t)((c >> 17) & 0xFFFFu); }
+__host__ __device__ inline int32_t cls_resw(uint64_t c) { return (int32_t)((c >> 33) & 0x7FFFu) - 1; }
+__host__ __device__ inline int32_t cls_cmdw(uint64_t c) { return (int32_t)((c >> 48) & 0x7FFFu) - 1; }
+
+// Interval slot flags (the output keeps bit 0 only).
+constexpr uint8_t kIvErr = 1u;
+constexpr uint8_t kIvOpen = 1u << 6;
+constexpr uint8_t kIvValid = 1u << 7;
+
+// Frontier item: an entry still open at the end of its packet, or an exit
+// that pops below the packet's starting depth.
+struct __align__(16) Frontier {
+  uint64_t ts;
+  uint32_t aux;   // open: interval slot rank in its packet (or ~0u); pending exit: error flag
+  uint16_t func;
+  uint16_t flags;
+};
+
+// Tally cell of the global (group, function) table.
+struct __align__(8) Cell {
+  unsigned long long count, total, mn, mx, err;
+};
+
+// Device error word: packet file index << 20 | event << 3 | code; ~0 = none.
+__host__ __device__ inline unsigned long long err_key(uint64_t packet, uint32_t event, uint32_t code) {
+  return ((unsigned long long)packet << 20) | ((unsigned long long)(event & 0x1FFFFu) << 3) | (code & 7u);
+}
+
+// Diagnostic counters (device), same order as thapi_diag.
+enum Diag { dEvents = 0, dPairs, dUnEntry, dUnExit, dMismatch, dOther, dDiscarded, dPackets, dCount };
+
+// ------------------------------------------------------ kernel params
+struct IndexParams {
+  const uint8_t *packets;  // first packet
+  unsigned long long *read_bytes;  // sum of 32 + content_bytes over valid packets
+  uint32_t P;
+  uint64_t n_packets;
+  uint32_t n_streams;
+  uint32_t *pk_stream, *pk_nev, *pk_content, *pk_seq, *pk_disc;
+  uint64_t *pk_tsb;
+  unsigned long long *hdr_err;  // min packet index with a header error
+};
+
+struct AnalyzeParams {
+  const uint8_t *packets;
+  uint32_t P;
+  uint32_t emax;                 // SoA capacity (events per packet) of this launch
+  uint64_t n_order;              // work items of this launch
+  const uint32_t *order;         // stream-ordered packet file indices (full list)
+  const uint32_t *poslist;       // work item -> order position (null: identity)
+  const uint32_t *pk_stream, *pk_nev, *pk_content, *pk_disc;
+  const uint64_t *pk_tsb;
+  const uint64_t *evbase;        // per order position: first event slot of the packet
+  const uint64_t *classes;       // packed class rows
+  uint32_t n_classes, n_funcs;
+  const uint32_t *stream_group;  // stream -> (host, pid, tid) group
+  Cell *tally;                   // [groups * n_funcs]
+  uint32_t *sum_pend, *sum_open, *sum_nslot, *sum_nvalid;  // per order position
+  uint64_t *sum_fbase;
+  Frontier *frontier;
+  unsigned long long *frontier_top;
+  uint64_t frontier_cap;
+  thapi_interval *slots;         // null: no timeline
+  unsigned long long *content_err;
+  unsigned long long *diag;      // dCount counters
+  unsigned long long *tminmax;   // [0] min ts, [1] max ts
+  unsigned long long *slots_written;  // interval slots written (24 B each)
+  uint32_t *dense_list;          // packets with more events than emax (order positions)
+  unsigned long long *dense_count;
+  uint32_t per_cta;              // order positions per CTA
+};
+
+struct FrontierParams {
+  uint64_t n_order;
+  uint32_t n_streams;
+  const uint32_t *order;
+  const uint32_t *pk_stream;
+  const uint32_t *stream_first, *stream_count;  // per stream: first order position, packet count
+  const uint32_t *sum_pend, *sum_open;
+  const uint64_t *sum_fbase;
+  uint32_t *A, *base;            // per order position
+  const uint64_t *evbase;
+  const Frontier *frontier;
+  const uint32_t *stream_group;
+  uint32_t n_funcs;
+  Cell *tally;
+  thapi_interval *slots;
+  uint32_t *sum_nvalid;
+  unsigned long long *diag;
+};
+
+// ---------------------------------------------------------- launchers
+// Kernels launched by this library since the process started (every launch
+// site adds to it; loads report their own delta).
+void count_launches(uint64_t k);
+uint64_t launches_total();
+
+// Device-wide scans and sorts (scan.cu, radix.cu).  Scratch is allocated by
+// the caller through the context allocator.
+struct Scratch;
+void scan_exclusive_u64(uint64_t *data, uint64_t n, uint64_t *total_dev, Scratch &sc, cudaStream_t s);
+void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
+                      int bits, bool *result_in_alt, Scratch &sc, cudaStream_t s);
+
+// Scratch allocator used inside one library call: every buffer it hands out
+// is released (in stream order) by release_all.
+struct Scratch {
+  thapi_ctx *ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<std::pair<void *, uint64_t>> bufs;
+  int failed = 0;
+  void *get(uint64_t bytes);
+  void adopt(void *p, uint64_t bytes);
+  void release_all();
+};
+
+}  // namespace thapi
+
+namespace thapi {
+
+// index.cu
+void launch_widen_u32(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
+void launch_packet_headers(const IndexParams &p, cudaStream_t s);
+void launch_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals, cudaStream_t s);
+void launch_stream_bounds(const uint64_t *skey, const uint32_t *order, const uint32_t *pk_seq, const uint32_t *pk_nev,
+                          uint64_t n, uint32_t n_streams, uint32_t *stream_first, uint32_t *stream_count,
+                          uint64_t *ev, unsigned long long *hdr_err, cudaStream_t s);
+// analyze.cu
+uint32_t analyze_smem_bytes(uint32_t P, uint32_t emax, int stages, uint32_t n_classes, uint32_t n_funcs);
+cudaError_t launch_analyze(const AnalyzeParams &p, int stages, uint32_t grid, cudaStream_t s, unsigned *status);
+// frontier.cu
+void launch_frontier(const FrontierParams &p, cudaStream_t s);
+// tally.cu
+void launch_tally_init(Cell *cells, uint64_t n, cudaStream_t s);
+void launch_tally_compact(const Cell *cells, uint64_t n, const uint32_t *group_keys, uint32_t n_funcs,
+                          uint64_t *flags, thapi_tally_row *rows, uint64_t *n_rows_dev, Scratch &sc, cudaStream_t s);
+// timeline.cu
+void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
+                             const uint64_t *out_base, const uint32_t *A, const uint32_t *order,
+                             const uint32_t *pk_stream, uint64_t n_order, uint64_t t_min, thapi_interval *rec,
+                             uint64_t *keys, uint32_t *vals, int num_sms, cudaStream_t s);
+void launch_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uint64_t n, thapi_interval *out,
+                            cudaStream_t s);
+void launch_window_count(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *hi_dev,
+                         uint64_t *flags, uint64_t *n_dev, Scratch &sc, cudaStream_t s, uint64_t hi_host);
+void launch_window_write(const thapi_interval *tl, uint64_t hi, uint64_t t0, uint64_t t1, const uint64_t *pos,
+                         thapi_interval *out, cudaStream_t s);
+void launch_lower_bound_start(const thapi_interval *tl, uint64_t n, uint64_t t1, uint64_t *out, cudaStream_t s);
+
+}  // namespace thapi

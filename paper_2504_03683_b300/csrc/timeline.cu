@@ -1,0 +1,142 @@
+// timeline.cu — global interval timeline.
+//
+// Interval slots are written per packet in entry order and packets are laid
+// out in stream order, so the slot array is already ordered by
+// (stream, entry position).  A warp per packet compacts the valid slots
+// (finishing their absolute level with the depth carried into the packet),
+// then a stable LSD radix sort on start time (relative to the trace's first
+// timestamp, only as many bits as the span needs) gives the timeline order
+// (start, stream, entry position).  Window queries [t0, t1) select intervals
+// with start < t1 and end >= t0 from the sorted array.
+#include "internal.cuh"
+
+namespace thapi {
+
+__global__ void k_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
+                                   const uint64_t *out_base, const uint32_t *A, const uint32_t *order,
+                                   const uint32_t *pk_stream, uint64_t n_order, uint64_t t_min,
+                                   thapi_interval *rec, uint64_t *keys, uint32_t *vals) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t wg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t i = wg; i < n_order; i += nw) {
+    const uint64_t sb = evbase[i];
+    const uint32_t n = nslot[i];
+    const uint32_t a = A[i];
+    const uint32_t stream = pk_stream[order[i]];
+    uint64_t ob = out_base[i];
+    for (uint32_t c = 0; c < n; c += 32) {
+      bool in = c + lane < n;
+      thapi_interval iv;
+      bool valid = false;
+      if (in) {
+        iv = slots[sb + c + lane];
+        valid = (iv.flags & kIvValid) != 0;
+      }
+      uint32_t bal = __ballot_sync(0xffffffffu, valid);
+      if (valid) {
+        uint64_t at = ob + __popc(bal & ((1u << lane) - 1u));
+        uint32_t npend = iv.stream_id;
+        uint32_t above = a > npend ? a - npend : 0u;
+        uint32_t lvl = above + iv.level;
+        iv.level = (uint8_t)(lvl > 255u ? 255u : lvl);
+        iv.stream_id = stream;
+        iv.flags &= kIvErr;
+        rec[at] = iv;
+        keys[at] = iv.start_ns - t_min;
+        vals[at] = (uint32_t)at;
+      }
+      ob += __popc(bal);
+    }
+  }
+}
+
+__global__ void k_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uint64_t n, thapi_interval *out) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = rec[vals[i]];
+}
+
+// Window selection: flags[i] = (start < t1 && end >= t0) over the sorted timeline.
+__global__ void k_window_flags(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *flags) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const thapi_interval &v = tl[i];
+  flags[i] = (v.start_ns < t1 && v.end_ns >= t0) ? 1u : 0u;
+}
+
+__global__ void k_window_write(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, const uint64_t *pos,
+                               thapi_interval *out) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const thapi_interval v = tl[i];
+  if (v.start_ns < t1 && v.end_ns >= t0) out[pos[i]] = v;
+}
+
+// First index with start >= t1 (sorted by start), single thread.
+__global__ void k_lower_bound_start(const thapi_interval *tl, uint64_t n, uint64_t t1, uint64_t *out) {
+  uint64_t lo = 0, hi = n;
+  while (lo < hi) {
+    uint64_t mid = lo + (hi - lo) / 2;
+    if (tl[mid].start_ns < t1)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  *out = lo;
+}
+
+}  // namespace thapi
+
+namespace thapi {
+
+void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
+                             const uint64_t *out_base, const uint32_t *A, const uint32_t *order,
+                             const uint32_t *pk_stream, uint64_t n_order, uint64_t t_min, thapi_interval *rec,
+                             uint64_t *keys, uint32_t *vals, int num_sms, cudaStream_t s) {
+  if (!n_order) return;
+  uint64_t warps = n_order;
+  uint64_t cap = (uint64_t)num_sms * 64;  // 64 warps per SM worth of CTAs
+  if (warps > cap) warps = cap;
+  unsigned grid = (unsigned)((warps * 32 + 255) / 256);
+  k_timeline_compact<<<grid, 256, 0, s>>>(slots, evbase, nslot, out_base, A, order, pk_stream, n_order, t_min, rec,
+                                          keys, vals);
+  count_launches(1);
+}
+
+void launch_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uint64_t n, thapi_interval *out,
+                            cudaStream_t s) {
+  if (n) {
+    k_timeline_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec, vals, n, out);
+    count_launches(1);
+  }
+}
+
+// Selects the window of the sorted timeline into `out` (capacity checked by
+// the caller through *n_dev, computed first when out == nullptr).
+void launch_window_count(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *hi_dev,
+                         uint64_t *flags, uint64_t *n_dev, Scratch &sc, cudaStream_t s, uint64_t hi_host) {
+  (void)hi_dev;
+  if (!hi_host) {
+    cudaMemsetAsync(n_dev, 0, sizeof(uint64_t), s);
+    return;
+  }
+  k_window_flags<<<(unsigned)((hi_host + 255) / 256), 256, 0, s>>>(tl, hi_host, t0, t1, flags);
+  count_launches(1);
+  scan_exclusive_u64(flags, hi_host, n_dev, sc, s);
+}
+
+void launch_window_write(const thapi_interval *tl, uint64_t hi, uint64_t t0, uint64_t t1, const uint64_t *pos,
+                         thapi_interval *out, cudaStream_t s) {
+  if (hi) {
+    k_window_write<<<(unsigned)((hi + 255) / 256), 256, 0, s>>>(tl, hi, t0, t1, pos, out);
+    count_launches(1);
+  }
+}
+
+void launch_lower_bound_start(const thapi_interval *tl, uint64_t n, uint64_t t1, uint64_t *out, cudaStream_t s) {
+  k_lower_bound_start<<<1, 1, 0, s>>>(tl, n, t1, out);
+  count_launches(1);
+}
+
+}  // namespace thapi

@@ -1,0 +1,333 @@
+"""CUDA path vs the CPU oracle, element by element (tolerance 0: integer ns).
+
+Every case loads a trace through the C ABI (libthapi.so via the ctypes
+binding), reads back the tally rows, diagnostics and timeline, and compares
+them with the oracle on the same bytes.
+"""
+from __future__ import annotations
+
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import tracegen as tg
+from paper_2504_03683_b300 import thapi
+from tests import _malformed
+from tests._util import intervals_equal, rows_equal
+from tracegen.handbuilt import DEV_BEGIN, ENTRY, EXIT, SAMPLE, Ev, TraceBuilder
+
+pytestmark = pytest.mark.gpu
+U64MAX = 2**64 - 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    assert torch.cuda.is_available()
+    c = thapi.Context(0)
+    yield c
+    c.close()
+
+
+def gpu_run(ctx, trace, windows=()):
+    tid = ctx.load(trace)
+    try:
+        rows, diag = ctx.tally(tid)
+        ivs = ctx.timeline(tid)
+        win = [ctx.timeline(tid, t0, t1) for (t0, t1) in windows]
+        info = ctx.info(tid)
+    finally:
+        ctx.free(tid)
+    return rows, diag, ivs, win, info
+
+
+def assert_parity(ctx, trace, windows=()):
+    o = oracle.run(trace)
+    assert o.code == oracle.OK
+    rows, diag, ivs, win, info = gpu_run(ctx, trace, windows)
+    for k in oracle.DIAG_FIELDS:
+        assert diag[k] == o.diag[k], (k, diag[k], o.diag[k])
+    assert rows_equal(rows, o.rows)
+    assert intervals_equal(ivs, o.intervals)
+    for (t0, t1), w in zip(windows, win):
+        ow = oracle.run(trace, t0=t0, t1=t1)
+        assert intervals_equal(w, ow.intervals), (t0, t1)
+    assert info["intervals"] == len(o.intervals) and info["tally_rows"] == len(o.rows)
+    return o
+
+
+def _windows(o, k=4, seed=0):
+    if not len(o.intervals):
+        return [(0, U64MAX), (5, 6)]
+    rng = random.Random(seed)
+    s = o.intervals["start_ns"]
+    e = o.intervals["end_ns"]
+    lo, hi = int(s.min()), int(e.max())
+    out = [(0, U64MAX), (lo, lo + 1), (hi, hi + 1), (int(s[len(s) // 2]), int(e[len(e) // 2]))]
+    for _ in range(k):
+        a = rng.randrange(lo, hi + 1)
+        out.append((a, a + rng.randrange(1, max(2, (hi - lo) // 50))))
+    return out
+
+
+# ------------------------------------------------------------- workloads
+def test_tiny_workload(ctx):
+    b, _c, _e = tg.generate(tg.preset("tiny"))
+    o = oracle.run(b)
+    assert_parity(ctx, b, _windows(o))
+
+
+@pytest.mark.parametrize("over", [
+    dict(total_calls=200_000, n_hosts=2, pids_per_host=2, tids_per_pid=4),
+    dict(total_calls=100_000, n_hosts=1, pids_per_host=2, tids_per_pid=3, p_drop=0.002, p_sample=0.05,
+         p_long_gap=0.01, p_ext=0.02, packet_bytes=1024, seed=5),
+    dict(total_calls=30_000, n_hosts=1, pids_per_host=1, tids_per_pid=3, packet_bytes=256, seed=6, p_drop=0.01),
+    dict(total_calls=60_000, n_hosts=1, pids_per_host=2, tids_per_pid=2, packet_bytes=32768, seed=7, p_drop=0.001),
+    dict(total_calls=80_000, n_hosts=1, pids_per_host=1, tids_per_pid=2, packet_bytes=65536, seed=8, p_err=0.2),
+])
+def test_layered_workloads(ctx, over):
+    b, _c, _e = tg.generate(tg.preset("large", **over))
+    o = oracle.run(b)
+    assert_parity(ctx, b, _windows(o, seed=over.get("seed", 1)))
+
+
+def test_device_workload_counts_other_events(ctx):
+    b, _c, _e = tg.generate(tg.preset("device", total_calls=20_000, n_hosts=1, pids_per_host=2, tids_per_pid=2,
+                                      n_device_streams=3))
+    o = assert_parity(ctx, b)
+    assert o.diag["other_events"] > 0
+
+
+def test_ground_truth_through_gpu(ctx):
+    from tests._util import expected_from_truth
+    b, calls, _e = tg.generate(tg.preset("large", total_calls=50_000, n_hosts=1, pids_per_host=2, tids_per_pid=2,
+                                         seed=9), truth=True)
+    rows, diag, ivs, _w, _i = gpu_run(ctx, b)
+    er, ei = expected_from_truth(b, calls)
+    assert rows_equal(rows, er) and intervals_equal(ivs, ei)
+
+
+# ------------------------------------------------------------ edge cases
+def _builder(P=256, n_funcs=3):
+    tb = TraceBuilder(packet_bytes=P)
+    h = tb.add_host("node")
+    ids = [tb.add_call_func("fn%d" % i) for i in range(n_funcs)]
+    return tb, h, ids
+
+
+def test_empty_trace(ctx):
+    tb, h, ids = _builder()
+    tb.add_stream(h, 1, 1)
+    assert_parity(ctx, tb.build())
+
+
+def test_no_streams_no_packets(ctx):
+    tb = TraceBuilder(packet_bytes=256)
+    tb.add_host("h")
+    tb.add_call_func("f")
+    assert_parity(ctx, tb.build())
+
+
+def test_packets_without_events(ctx):
+    tb, h, ids = _builder()
+    s = tb.add_stream(h, 1, 1)
+    tb.raw_packet(s, 100, [], discarded=4)
+    tb.raw_packet(s, 100, [tb.encode_event(ids[0][1], 5), tb.encode_event(ids[0][2], 5)])
+    tb.raw_packet(s, 100, [], discarded=1)
+    assert_parity(ctx, tb.build())
+
+
+def test_dense_packets_take_second_pass(ctx):
+    # minimum-size events (8-byte entries, 12-byte exits) fill 16 KB packets past the fast-path capacity
+    tb, h, ids = _builder(P=16384)
+    s0 = tb.add_stream(h, 7, 7)
+    s1 = tb.add_stream(h, 7, 8)
+    for s in (s0, s1):
+        evs = []
+        t = 1000
+        for k in range(5000):
+            evs.append(Ev(ids[k % 3][1], t))
+            evs.append(Ev(ids[k % 3][2], t + 3 + k % 5, result=k % 7 == 0))
+            t += 10
+        tb.place(tb.stream_events(s, evs, ts_begin=1000))
+    b = tb.build()
+    o = assert_parity(ctx, b)
+    assert o.diag["packets"] >= 2
+
+
+def test_deep_nesting_across_packets_saturates_level(ctx):
+    tb, h, ids = _builder(P=256)
+    s = tb.add_stream(h, 3, 3)
+    depth = 300
+    evs = [Ev(ids[d % 3][1], 100 + d) for d in range(depth)]
+    evs += [Ev(ids[d % 3][2], 100000 - d, result=d % 11 == 0) for d in reversed(range(depth))]
+    evs += [Ev(ids[0][2], 200000)]  # one unmatched exit at the end
+    evs += [Ev(ids[1][1], 200001)]  # one unmatched entry
+    tb.place(tb.stream_events(s, evs, ts_begin=100))
+    o = assert_parity(ctx, tb.build())
+    assert o.intervals["level"].max() == 255
+
+
+def test_other_kinds_and_ext(ctx):
+    tb, h, ids = _builder(P=256)
+    fs = tb.add_func("sample")
+    cs = tb.add_class(fs, SAMPLE, 8)
+    cb = tb.add_class(fs, DEV_BEGIN, 8, cmd_off=0)
+    s = tb.add_stream(h, 1, 1)
+    evs = [Ev(ids[0][1], 10), Ev(cs, 12), Ev(cb, 13, cmd=99), Ev(ids[0][2], 20, result=3),
+           Ev(ids[1][1], 20 + (1 << 27)), Ev(ids[1][2], 21 + (1 << 27), force_ext=True),
+           Ev(ids[2][1], 5), Ev(ids[2][2], 7)]  # timestamps going backwards use EXT
+    tb.place(tb.stream_events(s, evs, ts_begin=5))
+    assert_parity(ctx, tb.build())
+
+
+def test_equal_start_ties_across_streams(ctx):
+    tb, h, ids = _builder(P=256)
+    streams = [tb.add_stream(h, 9, 9 + k) for k in range(5)]
+    for k, s in reversed(list(enumerate(streams))):  # file order differs from stream order
+        evs = [Ev(ids[0][1], 500), Ev(ids[1][1], 500), Ev(ids[1][2], 500), Ev(ids[0][2], 501 + k)]
+        tb.place(tb.stream_events(s, evs, ts_begin=500))
+    assert_parity(ctx, tb.build())
+
+
+def test_brute_force_sequences_in_one_trace(ctx):
+    rng = random.Random(77)
+    tb, h, ids = _builder(P=256, n_funcs=2)
+    packed = []
+    for k in range(300):
+        s = tb.add_stream(h, 100 + k // 7, 1000 + k)
+        n = rng.choice([1, 2, 5, 10, 17, 40, 90])
+        evs, t = [], 1000 + k
+        for j in range(n):
+            t += rng.choice([0, 1, 5, 30])
+            kind = rng.choice([ENTRY, ENTRY, EXIT, EXIT, EXIT])
+            f = rng.randrange(2)
+            evs.append(Ev(ids[f][1] if kind == ENTRY else ids[f][2], t, payload=b"\x07" * rng.choice([0, 4, 40]),
+                          result=rng.choice([0, 0, 1]) if kind == EXIT else None))
+        packed.append(tb.stream_events(s, evs, ts_begin=1000))
+    # interleave packets of all streams, each stream's in order
+    queues = [list(p) for p in packed]
+    while any(queues):
+        q = rng.choice([q for q in queues if q])
+        tb.place([q.pop(0)])
+    assert_parity(ctx, tb.build())
+
+
+def test_payloads_that_look_like_headers(ctx):
+    # payload words that parse as valid events make speculative walks go astray
+    tb, h, ids = _builder(P=1024)
+    import struct
+    s = tb.add_stream(h, 1, 1)
+    evs, t = [], 100
+    for k in range(400):
+        fake = struct.pack("<IHH", k % 9, ids[k % 3][1], 4 * (k % 5)) * (1 + k % 6)
+        evs.append(Ev(ids[k % 3][1], t, payload=fake[: 4 * (k % 12)]))
+        evs.append(Ev(ids[k % 3][2], t + 5, payload=fake[: 4 * (k % 7)]))
+        t += 9
+    tb.place(tb.stream_events(s, evs, ts_begin=100))
+    assert_parity(ctx, tb.build())
+
+
+# ---------------------------------------------------------------- errors
+@pytest.mark.parametrize("name,trace", _malformed.cases(), ids=[c[0] for c in _malformed.cases()])
+def test_errors_match_oracle(ctx, name, trace):
+    o = oracle.run(trace)
+    if o.code == oracle.OK:
+        assert_parity(ctx, trace)
+        return
+    with pytest.raises(thapi.ThapiError) as ei:
+        ctx.load(trace)
+    assert ei.value.code == o.code, name
+    if o.loc[0] > 0:
+        assert ei.value.location == o.loc, name
+
+
+# ------------------------------------------------------------ the paper
+def test_paper_table_trace(ctx):
+    from tests import _paper_trace as pt
+    trace, golden, names = pt.build()
+    o = oracle.run(trace, want_intervals=True)
+    rows, diag, ivs, _w, _i = gpu_run(ctx, trace)
+    assert rows_equal(rows, o.rows)
+    assert intervals_equal(ivs, o.intervals)
+    got = pt.render(rows, names)
+    for g in golden:
+        assert got[g["name"]] == (g["time"], g["pct"], str(g["calls"]), g["avg"], g["min"], g["max"])
+
+
+# ---------------------------------------------------------- API surface
+def test_device_load_and_device_outputs(ctx):
+    import torch
+    b, _c, _e = tg.generate(tg.preset("large", total_calls=40_000, n_hosts=1, pids_per_host=2, tids_per_pid=2,
+                                      seed=12))
+    o = oracle.run(b)
+    stream = torch.cuda.Stream()
+    dev = torch.from_numpy(b).to("cuda")
+    tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), stream)
+    try:
+        info = ctx.info(tid)
+        rows_d = torch.empty(info["tally_rows"] * 56, dtype=torch.uint8, device="cuda")
+        ivs_d = torch.empty(info["intervals"] * 24, dtype=torch.uint8, device="cuda")
+        n, diag = thapi.thapi_tally_device(ctx.handle, tid, rows_d.data_ptr(), info["tally_rows"], stream)
+        m = thapi.thapi_timeline_device(ctx.handle, tid, 0, U64MAX, ivs_d.data_ptr(), info["intervals"], stream)
+        stream.synchronize()
+        rows = rows_d.cpu().numpy().view(thapi.ROW_DTYPE)
+        ivs = ivs_d.cpu().numpy().view(thapi.INTERVAL_DTYPE)
+        assert n == len(o.rows) and m == len(o.intervals)
+        assert rows_equal(rows, o.rows) and intervals_equal(ivs, o.intervals)
+        # a window into device memory
+        t0 = int(o.intervals["start_ns"][len(o.intervals) // 3])
+        t1 = t0 + 500_000
+        ow = oracle.run(b, t0=t0, t1=t1).intervals
+        wd = torch.empty(max(1, len(ow)) * 24, dtype=torch.uint8, device="cuda")
+        k = thapi.thapi_timeline_device(ctx.handle, tid, t0, t1, wd.data_ptr(), len(ow), stream)
+        stream.synchronize()
+        assert k == len(ow)
+        assert intervals_equal(wd.cpu().numpy().view(thapi.INTERVAL_DTYPE)[:k], ow)
+    finally:
+        ctx.free(tid)
+
+
+def test_capacity_and_names(ctx):
+    b, _c, _e = tg.generate(tg.preset("tiny", total_calls=3000))
+    tid = ctx.load(b)
+    try:
+        info = ctx.info(tid)
+        with pytest.raises(thapi.ThapiError) as ei:
+            buf = np.zeros(1, dtype=thapi.INTERVAL_DTYPE)
+            thapi.thapi_timeline(ctx.handle, tid, out=buf)
+        assert ei.value.code == thapi.E_RANGE
+        assert thapi.thapi_trace_strings(ctx.handle, tid, 1, 0) == "apiFunc0"
+        assert thapi.thapi_trace_strings(ctx.handle, tid, 0, 0).startswith("x4204")
+        assert info["events"] == 6000
+    finally:
+        ctx.free(tid)
+    with pytest.raises(thapi.ThapiError) as ei:
+        ctx.tally(tid)
+    assert ei.value.code == thapi.E_INVALID
+
+
+def test_default_allocator_and_timing():
+    b, _c, _e = tg.generate(tg.preset("tiny", total_calls=20_000))
+    o = oracle.run(b)
+    with thapi.Context(0, use_torch_allocator=False) as c:
+        thapi.thapi_ctx_set_timing(c.handle, True)
+        before = thapi.thapi_kernel_launches()
+        tid = c.load(b)
+        rows, diag = c.tally(tid)
+        t = thapi.thapi_trace_timing(c.handle, tid)
+        assert rows_equal(rows, o.rows)
+        assert t["analyze_ms"] > 0 and t["launches"] > 5 and t["analyze_launches"] == 1
+        assert thapi.thapi_kernel_launches() - before == t["launches"]
+        assert t["analyze_read_bytes"] > 0
+
+
+def test_hbm_cap_admission():
+    b, _c, _e = tg.generate(tg.preset("tiny", total_calls=20_000))
+    with thapi.Context(0, hbm_cap_bytes=1 << 16) as c:
+        with pytest.raises(thapi.ThapiError) as ei:
+            c.load(b)
+        assert ei.value.code == thapi.E_NOMEM
