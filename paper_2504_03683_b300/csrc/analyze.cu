@@ -3,29 +3,35 @@
 // Each persistent CTA (128 threads) walks a contiguous run of the
 // stream-ordered packet list.  Packets are staged into shared memory with
 // cp.async.bulk (TMA bulk copy, mbarrier completion), double-buffered so the
-// next packet is in flight while the current one is analysed:
+// next packet is in flight while the current one is analysed; the packet
+// descriptors are loaded one packet further ahead.
 //
 //  1. boundaries: event sizes depend on the class and var_len, so finding
 //     where events start is a serial chain.  Every thread walks its own
-//     32-word segment speculatively from the segment start, marking the
-//     offsets it visits in a bitmap; then segments are stitched: a thread
-//     whose true entry offset (the previous segment's exit) lies on its chain
-//     keeps the chain from there, otherwise it re-walks until the chains
-//     merge.  Iterated until no exit changes, the bitmap holds exactly the
-//     true event starts (the chain from offset 0).
-//  2. validation of every true event in the documented check order.
+//     32-word segment speculatively from the segment start (crossing runs of
+//     unknown class ids in one jump), marking the offsets it visits.  Chains
+//     started anywhere merge within a few events, so a thread's speculative
+//     exit is usually already the true one.  Stitching: each lane assumes its
+//     entry is its predecessor's speculative exit; the first lane whose exit
+//     breaks that assumption passes the right entry on (a warp ballot per
+//     fix), and a warp whose guessed entry was wrong is redone.  The result is
+//     exactly the chain from offset 0.
+//  2. validation of every true event in the documented check order, and
+//     per-thread summaries.
 //  3. decode: timestamps by a CTA-wide scan of (has-absolute, sum) over the
 //     deltas seeded with ts_begin (EXT events reset it), depth by a scan of
 //     the (sum, min-prefix) monoid over +1 entry / -1 exit; events go to a
 //     shared-memory table {ts, post-depth|kind|err, func}.
 //  4. in-packet matching: an entry at depth r pairs with the first later event
-//     whose post-depth is <= r (necessarily its exit); entries with none are
-//     "open", exits that reach a new minimum are "pending" — both go to a
-//     per-packet frontier that frontier.cu resolves across packets.  Matched
-//     pairs are tallied per function in shared memory (the CTA's packets
-//     belong to one stream at a time) and flushed to the global
-//     (group, function) table when the stream changes.
-//  5. optional interval slots (timeline), dense per packet in entry order.
+//     whose post-depth is <= r (necessarily its exit); per-thread and
+//     per-warp minima of the depth let a search skip whole thread ranges.
+//     Entries with no exit in the packet are "open", exits that reach a new
+//     minimum are "pending" — both go to a per-packet frontier that
+//     frontier.cu resolves across packets.  Matched pairs are tallied per
+//     function in shared memory (a CTA's packets belong to one stream at a
+//     time) and flushed to the global (group, function) table when the stream
+//     changes.  Every entry gets an interval slot (dense per packet in entry
+//     order) for the timeline.
 #include "internal.cuh"
 
 namespace thapi {
@@ -37,6 +43,7 @@ constexpr int kWarps = kT / 32;
 constexpr int kClsSmemMax = 1024;
 constexpr int kTallySmemMax = 512;
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kFrontierChunk = 2048;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -86,10 +93,10 @@ struct ScanSmem {
   uint32_t c[kWarps];
   TsM t[kWarps];
   DM d[kWarps];
-  uint32_t c2[kWarps];
 };
 
-// CTA-wide exclusive scans of the three per-thread summaries; totals returned.
+// CTA-wide exclusive scans of three per-thread summaries (c: events in the
+// low 16 bits + entries in the high 16 bits; timestamps; depth); totals too.
 __device__ __forceinline__ void cta_scan3(uint32_t c, TsM t, DM d, uint32_t &c_ex, TsM &t_ex, DM &d_ex, uint32_t &c_tot,
                                           TsM &t_tot, DM &d_tot, ScanSmem &ss) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -114,7 +121,6 @@ __device__ __forceinline__ void cta_scan3(uint32_t c, TsM t, DM d, uint32_t &c_e
     ss.t[warp] = ti;
     ss.d[warp] = di;
   }
-  // exclusive within the warp
   uint32_t ce = __shfl_up_sync(0xffffffffu, ci, 1);
   uint32_t he = __shfl_up_sync(0xffffffffu, ti.has, 1);
   uint64_t ve = __shfl_up_sync(0xffffffffu, ti.v, 1);
@@ -131,55 +137,38 @@ __device__ __forceinline__ void cta_scan3(uint32_t c, TsM t, DM d, uint32_t &c_e
   uint32_t cw = 0;
   TsM tw{0, 0};
   DM dw{0, 0};
-  for (int w = 0; w < warp; ++w) {
-    cw += ss.c[w];
-    tw = ts_op(tw, ss.t[w]);
-    dw = d_op(dw, ss.d[w]);
-  }
-  c_ex = cw + ce;
-  t_ex = ts_op(tw, TsM{he, ve});
-  d_ex = d_op(dw, DM{se, me});
   c_tot = 0;
   t_tot = TsM{0, 0};
   d_tot = DM{0, 0};
+#pragma unroll
   for (int w = 0; w < kWarps; ++w) {
+    if (w < warp) {
+      cw += ss.c[w];
+      tw = ts_op(tw, ss.t[w]);
+      dw = d_op(dw, ss.d[w]);
+    }
     c_tot += ss.c[w];
     t_tot = ts_op(t_tot, ss.t[w]);
     d_tot = d_op(d_tot, ss.d[w]);
   }
-  __syncthreads();
-}
-
-__device__ __forceinline__ uint32_t cta_scan_u32(uint32_t v, uint32_t &tot, ScanSmem &ss) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  if (lane == 31) ss.c2[warp] = inc;
-  __syncthreads();
-  uint32_t base = 0;
-  tot = 0;
-  for (int w = 0; w < kWarps; ++w) {
-    if (w < warp) base += ss.c2[w];
-    tot += ss.c2[w];
-  }
-  __syncthreads();
-  return base + inc - v;
+  c_ex = cw + ce;
+  t_ex = ts_op(tw, TsM{he, ve});
+  d_ex = d_op(dw, DM{se, me});
 }
 
 // ---------------------------------------------------------- smem layout
+enum Misc { kErrKey = 0, kFbLo, kFbHi, kValid, kNextStream, kMiscWords = 16 };
+
 struct Layout {
-  uint32_t buf_bytes, off_buf, off_ts, off_dk, off_fn, off_mt, off_cls, off_tally, off_thr, total;
+  uint32_t buf_bytes, off_meta, off_buf, off_ts, off_dk, off_fn, off_cls, off_tally, off_thr, total;
 };
 
 __host__ __device__ inline Layout make_layout(uint32_t P, uint32_t emax, uint32_t stages, uint32_t n_classes,
                                               uint32_t n_funcs, bool cls_smem, bool tally_smem) {
   Layout L;
   L.buf_bytes = P + 32;  // packet + zeroed tail words
-  L.off_buf = 64;
+  L.off_meta = 16;
+  L.off_buf = 128;
   uint32_t o = L.off_buf + stages * L.buf_bytes;
   o = (o + 15u) & ~15u;
   L.off_ts = o;
@@ -188,17 +177,16 @@ __host__ __device__ inline Layout make_layout(uint32_t P, uint32_t emax, uint32_
   o += emax * 4;
   L.off_fn = o;
   o += emax * 2;
-  L.off_mt = o;
-  o += emax * 2;
   o = (o + 15u) & ~15u;
   L.off_cls = o;
   if (cls_smem) o += n_classes * 8;
   o = (o + 15u) & ~15u;
   L.off_tally = o;
-  if (tally_smem) o += n_funcs * 32 + 16;
+  if (tally_smem) o += n_funcs * 24 + 16;
   o = (o + 15u) & ~15u;
   L.off_thr = o;
-  o += kT * 4 /*ex*/ + (kT + 4) * 4 /*tk0*/ + kT * 4 /*segmin*/ + 64 /*misc*/ + sizeof(ScanSmem) + 64;
+  o += kT * 4 /*sx*/ + 2 * kWarps * 4 /*wx*/ + (kT + 4) * 4 /*tk0*/ + kT * 4 /*segmin*/ + kT * 4 /*sufmin*/ +
+       kWarps * 4 /*wmin*/ + kMiscWords * 4 + sizeof(ScanSmem) + 64;
   L.total = (o + 127u) & ~127u;
   return L;
 }
@@ -235,6 +223,22 @@ struct Bits {
         w[k] &= ~((1u << (i - lo)) - 1u);
     }
   }
+  // smallest set index greater than i, or 32 * BW
+  __device__ __forceinline__ uint32_t next_after(uint32_t i) const {
+#pragma unroll
+    for (int k = 0; k < BW; ++k) {
+      const uint32_t lo = (uint32_t)k * 32;
+      if (i + 1 >= lo + 32) continue;
+      uint32_t m = w[k];
+      if (i + 1 > lo) m &= ~((1u << (i + 1 - lo)) - 1u);
+      if (m) return lo + (uint32_t)(__ffs(m) - 1);
+    }
+    return 32u * BW;
+  }
+  __device__ __forceinline__ void merge(const Bits &o) {
+#pragma unroll
+    for (int k = 0; k < BW; ++k) w[k] |= o.w[k];
+  }
   __device__ __forceinline__ uint32_t count() const {
     uint32_t c = 0;
 #pragma unroll
@@ -249,15 +253,45 @@ __device__ __forceinline__ uint64_t class_row(const uint64_t *cls_s, const uint6
   return __ldg(cls_g + c);
 }
 
-// Next offset of the event chain (same function for speculative and true walks).
-template <bool CLS_SMEM>
-__device__ __forceinline__ uint32_t chain_next(const uint32_t *C, uint32_t o, const uint64_t *cls_s,
-                                               const uint64_t *cls_g, uint32_t n_classes) {
-  uint32_t w0 = C[o], w1 = C[o + 1];
-  uint32_t c = w1 & 0xFFFFu;
-  if (c >= n_classes) return o + 1;
-  uint32_t fw = cls_fixedw(class_row<CLS_SMEM>(cls_s, cls_g, c));
-  return o + 2 + ((w0 >> 26) & 2u) + fw + (((w1 >> 16) + 3u) >> 2);
+// Walks the event chain from o inside the segment [a, b): marks o and every
+// offset reached by a full event step; runs of unknown class ids are crossed
+// one word at a time (jumping to the next candidate).  Stops when the chain
+// leaves the segment or, if `stop` is given, lands on one of its offsets.
+template <int BW, bool CLS_SMEM>
+__device__ __forceinline__ uint32_t seg_walk(const uint32_t *C, uint32_t o, uint32_t a, uint32_t b,
+                                             const Bits<BW> &cand, const Bits<BW> *stop, Bits<BW> &marks,
+                                             const uint64_t *cls_s, const uint64_t *cls_g) {
+  while (o < b) {
+    const uint32_t i = o - a;
+    if (stop && stop->test(i)) return o;
+    marks.set(i);
+    if (!cand.test(i)) {
+      const uint32_t nxt = cand.next_after(i);
+      if (a + nxt >= b) return b;
+      o = a + nxt;
+    }
+    const uint32_t w0 = C[o], w1 = C[o + 1];
+    const uint32_t fw = cls_fixedw(class_row<CLS_SMEM>(cls_s, cls_g, w1 & 0xFFFFu));
+    o = o + 2 + ((w0 >> 26) & 2u) + fw + (((w1 >> 16) + 3u) >> 2);
+  }
+  return o;
+}
+
+__device__ __forceinline__ PkDesc load_desc(const PkDesc *d) {
+  PkDesc r;
+  const uint4 *s = reinterpret_cast<const uint4 *>(d);
+  const uint4 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2);
+  r.pk = a.x;
+  r.content = a.y;
+  r.nev = a.z;
+  r.stream = a.w;
+  r.group = b.x;
+  r.disc = b.y;
+  r.pad0 = b.z;
+  r.pad1 = b.w;
+  r.tsb = (uint64_t)c.x | ((uint64_t)c.y << 32);
+  r.evbase = (uint64_t)c.z | ((uint64_t)c.w << 32);
+  return r;
 }
 
 template <int BW, int STAGES, bool CLS_SMEM, bool TALLY_SMEM>
@@ -265,28 +299,33 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
   extern __shared__ __align__(128) uint8_t sm[];
   constexpr uint32_t SEGW = 32u * BW;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const uint32_t F = p.n_funcs;
   const Layout L = make_layout(p.P, p.emax, STAGES, p.n_classes, F, CLS_SMEM, TALLY_SMEM);
   uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+  PkDesc *meta = reinterpret_cast<PkDesc *>(sm + L.off_meta);
   uint64_t *s_ts = reinterpret_cast<uint64_t *>(sm + L.off_ts);
   uint32_t *s_dk = reinterpret_cast<uint32_t *>(sm + L.off_dk);
   uint16_t *s_fn = reinterpret_cast<uint16_t *>(sm + L.off_fn);
-  int16_t *s_mt = reinterpret_cast<int16_t *>(sm + L.off_mt);
   uint64_t *s_cls = reinterpret_cast<uint64_t *>(sm + L.off_cls);
   uint32_t *t_cnt = reinterpret_cast<uint32_t *>(sm + L.off_tally);
   uint32_t *t_err = t_cnt + F;
-  unsigned long long *t_tot = reinterpret_cast<unsigned long long *>(sm + L.off_tally + ((F * 8u + 15u) & ~15u));
-  unsigned long long *t_mn = t_tot + F;
-  unsigned long long *t_mx = t_mn + F;
-  uint32_t *s_ex = reinterpret_cast<uint32_t *>(sm + L.off_thr);
-  uint32_t *s_tk0 = s_ex + kT;
-  int *s_segmin = reinterpret_cast<int *>(s_tk0 + kT + 4);
-  uint32_t *s_misc = reinterpret_cast<uint32_t *>(s_segmin + kT);  // [0] ok, [1] err key lo, [2] fbase lo, [3] fbase hi
-  ScanSmem &ss = *reinterpret_cast<ScanSmem *>(s_misc + 16);
+  uint32_t *t_mn = t_err + F;
+  uint32_t *t_mx = t_mn + F;
+  unsigned long long *t_tot = reinterpret_cast<unsigned long long *>(sm + L.off_tally + ((F * 16u + 15u) & ~15u));
+  uint32_t *s_sx = reinterpret_cast<uint32_t *>(sm + L.off_thr);  // speculative exits
+  uint32_t *s_wx = s_sx + kT;                                       // warp exits, double-buffered
+  uint32_t *s_tk0 = s_wx + 2 * kWarps;                              // first event of each thread
+  int *s_segmin = reinterpret_cast<int *>(s_tk0 + kT + 4);           // min post-depth per thread
+  int *s_sufmin = s_segmin + kT;                                    // suffix min within the warp
+  int *s_wmin = s_sufmin + kT;                                      // min per warp
+  uint32_t *s_misc = reinterpret_cast<uint32_t *>(s_wmin + kWarps);
+  ScanSmem &ss = *reinterpret_cast<ScanSmem *>(s_misc + kMiscWords);
 
   const uint64_t w_begin = (uint64_t)blockIdx.x * p.per_cta;
   const uint64_t w_end = (w_begin + p.per_cta < p.n_order) ? w_begin + p.per_cta : p.n_order;
   if (w_begin >= w_end) return;
+  auto pos_of = [&](uint64_t w) -> uint64_t { return p.poslist ? p.poslist[w] : w; };
 
   // ---- one-time setup
   if (CLS_SMEM)
@@ -295,62 +334,52 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
     for (uint32_t f = tid; f < F; f += kT) {
       t_cnt[f] = 0;
       t_err[f] = 0;
-      t_tot[f] = 0;
-      t_mn[f] = ~0ull;
+      t_mn[f] = 0xFFFFFFFFu;
       t_mx[f] = 0;
+      t_tot[f] = 0;
     }
-  if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // dense packets (more events than the SoA holds) go to a second launch
-  if (p.dense_list)
-    for (uint64_t w = w_begin + tid; w < w_end; w += kT) {
-      uint32_t pk = p.order[w];
-      if (p.pk_nev[pk] > p.emax) {
-        unsigned long long k = atomicAdd(p.dense_count, 1ull);
-        p.dense_list[k] = (uint32_t)w;
-      }
-    }
-  __syncthreads();
-
-  auto pos_of = [&](uint64_t w) -> uint64_t { return p.poslist ? p.poslist[w] : w; };
-  auto skip = [&](uint64_t w) -> bool { return p.dense_list && p.pk_nev[p.order[w]] > p.emax; };
-  auto next_work = [&](uint64_t w) -> uint64_t {
-    while (w < w_end && skip(w)) ++w;
-    return w;
-  };
-  auto issue = [&](uint64_t w, int s) {
-    uint64_t pos = pos_of(w);
-    uint32_t pk = p.order[pos];
-    uint32_t bytes = align16(kPacketHeader + p.pk_content[pk]);
+  auto issue = [&](const PkDesc &d, int s) {
+    const uint32_t bytes = align16(kPacketHeader + d.content);
     uint8_t *dst = sm + L.off_buf + s * L.buf_bytes;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&bar[s], bytes);
-    bulk_copy_g2s(dst, p.packets + (uint64_t)pk * p.P, bytes, &bar[s]);
+    bulk_copy_g2s(dst, p.packets + (uint64_t)d.pk * p.P, bytes, &bar[s]);
   };
+  PkDesc dnext;  // thread 0: descriptor of the packet after the one in flight
+  uint64_t fr_base = 0;
+  uint32_t fr_left = 0;  // thread 0: current frontier chunk
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const PkDesc d0 = load_desc(p.desc + pos_of(w_begin));
+    meta[0] = d0;
+    issue(d0, 0);
+    if (w_begin + 1 < w_end) dnext = load_desc(p.desc + pos_of(w_begin + 1));
+  }
+  __syncthreads();
 
-  // thread-local diagnostics
   unsigned long long n_mismatch = 0, n_other = 0, n_pairs = 0;
   unsigned long long n_events = 0, n_disc = 0, n_pk = 0, n_slots = 0;
   uint64_t tmin = ~0ull, tmax = 0;
   uint32_t phase = 0;  // bit s = parity expected next on bar[s]
+  uint32_t pending_mask = 1u;
   bool timed_out = false;
-  int stage = 0;
-  uint32_t pending_mask = 0;  // stages with a copy in flight (tracked by every thread identically)
 
-  uint64_t w = next_work(w_begin);
-  if (w < w_end) {
-    if (tid == 0) issue(w, 0);
-    pending_mask |= 1u;
-  }
-  while (w < w_end) {
-    const uint64_t wn = next_work(w + 1);
-    if (STAGES == 2 && wn < w_end) {
-      if (tid == 0) issue(wn, stage ^ 1);
-      pending_mask |= 1u << (stage ^ 1);
+  for (uint64_t w = w_begin, it = 0; w < w_end; ++w, ++it) {
+    const int stage = STAGES == 2 ? (int)(it & 1) : 0;
+    const bool has_next = w + 1 < w_end;
+    if (tid == 0) {
+      s_misc[kErrKey] = 0xFFFFFFFFu;
+      s_misc[kValid] = 0;
+      s_misc[kNextStream] = has_next ? dnext.stream : 0xFFFFFFFFu;
+      if (STAGES == 2 && has_next) {
+        meta[stage ^ 1] = dnext;
+        issue(dnext, stage ^ 1);
+        if (w + 2 < w_end) dnext = load_desc(p.desc + pos_of(w + 2));
+      }
     }
-    bool ok_wait = mbar_wait_bounded(&bar[stage], (phase >> stage) & 1u);
+    if (STAGES == 2 && has_next) pending_mask |= 1u << (stage ^ 1);
+    const bool ok_wait = mbar_wait_bounded(&bar[stage], (phase >> stage) & 1u);
     if (__syncthreads_or(!ok_wait)) {
       timed_out = true;
       break;
@@ -358,222 +387,319 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
     phase ^= 1u << stage;
     pending_mask &= ~(1u << stage);
 
+    const PkDesc d = meta[stage];
     const uint64_t pos = pos_of(w);
-    const uint32_t pk = p.order[pos];
-    const uint32_t content = p.pk_content[pk];
-    const uint32_t nev = p.pk_nev[pk];
-    const uint32_t W = content >> 2;
-    const uint32_t stream = p.pk_stream[pk];
-    const uint32_t group = p.stream_group[stream];
-    uint32_t *C = reinterpret_cast<uint32_t *>(sm + L.off_buf + stage * L.buf_bytes + kPacketHeader);
-    if (tid < 4) C[W + tid] = 0;
-    __syncthreads();
-
-    // ---- 1. speculative segment walks
-    const uint32_t a = (uint32_t)tid * SEGW;
-    const uint32_t b = min(a + SEGW, W);
-    Bits<BW> bits;
-    bits.clear();
-    uint32_t o = a;
-    while (o < b) {
-      bits.set(o - a);
-      o = chain_next<CLS_SMEM>(C, o, s_cls, p.classes, p.n_classes);
-    }
-    uint32_t x = max(o, a);
-    uint32_t entry = a;
-    s_ex[tid] = x;
-    // ---- stitch segments until no exit changes (converges in at most kT rounds:
-    // after round r the first r segments are final)
-    bool stitch_ok = true;
-    for (int round = 0;; ++round) {
-      if (round > 2 * kT + 2) {  // unreachable unless the walk is broken; never spin
-        stitch_ok = false;
-        break;
-      }
+    const bool dense = p.dense_list && d.nev > p.emax;
+    if (dense) {
+      if (tid == 0) p.dense_list[atomicAdd(p.dense_count, 1ull)] = (uint32_t)pos;
+    } else {
+      const uint32_t W = d.content >> 2;
+      uint32_t *C = reinterpret_cast<uint32_t *>(sm + L.off_buf + stage * L.buf_bytes + kPacketHeader);
+      if (tid < 4) C[W + tid] = 0;
       __syncthreads();
-      uint32_t y = tid == 0 ? 0u : s_ex[tid - 1];
-      bool changed = false;
-      if (y != entry) {
-        entry = y;
-        uint32_t nx = x;
+
+      // ---- 1. event boundaries
+      const uint32_t a = (uint32_t)tid * SEGW;
+      const uint32_t b = min(a + SEGW, W);
+      // candidate words: a chain standing on a word whose class id is unknown
+      // steps one word at a time, so it can jump straight to the next candidate
+      Bits<BW> cand;
+      cand.clear();
+#pragma unroll 4
+      for (uint32_t k = 0; k < SEGW; ++k) {
+        const uint32_t i = (k + (uint32_t)lane) & (SEGW - 1);  // rotated: the lanes of a warp hit distinct banks
+        const uint32_t o = a + i;
+        if (o < b && (C[o + 1] & 0xFFFFu) < p.n_classes) cand.set(i);
+      }
+      Bits<BW> spec;
+      spec.clear();
+      const uint32_t spec_x =
+          a < b ? seg_walk<BW, CLS_SMEM>(C, a, a, b, cand, nullptr, spec, s_cls, p.classes) : a;
+      s_sx[tid] = spec_x;
+      __syncthreads();
+      Bits<BW> bits;
+      // chain entering my segment at y: walk until it meets my speculative
+      // chain (from there both are the same chain) or leaves the segment
+      auto resolve = [&](uint32_t y) -> uint32_t {
+        if (y == a && a < b) {
+          bits = spec;
+          return spec_x;
+        }
         if (y >= b) {
           bits.clear();
-          nx = y;
-        } else if (bits.test(y - a)) {
-          bits.keep_from(y - a);
-        } else {
-          uint32_t m = y;
-          while (m < b && !bits.test(m - a)) m = chain_next<CLS_SMEM>(C, m, s_cls, p.classes, p.n_classes);
-          if (m < b) {
-            bits.keep_from(m - a);
-          } else {
-            bits.clear();
-            nx = m;
-          }
-          uint32_t q = y;
-          while (q < m && q < b) {
-            bits.set(q - a);
-            q = chain_next<CLS_SMEM>(C, q, s_cls, p.classes, p.n_classes);
+          return y;
+        }
+        Bits<BW> walked;
+        walked.clear();
+        const uint32_t m = seg_walk<BW, CLS_SMEM>(C, y, a, b, cand, &spec, walked, s_cls, p.classes);
+        if (m < b) {
+          bits = spec;
+          bits.keep_from(m - a);
+          bits.merge(walked);
+          return spec_x;
+        }
+        bits = walked;
+        return m;
+      };
+      // warp stitch: one ballot round per lane whose exit breaks its
+      // successor's assumed entry
+      const bool succ_live = a + SEGW < W;
+      uint32_t ent, x;
+      auto warp_resolve = [&](uint32_t E) {
+        ent = lane == 0 ? E : s_sx[tid - 1];
+        x = resolve(ent);
+        for (int r = 0; r < 32; ++r) {
+          const uint32_t next_ent = __shfl_down_sync(0xffffffffu, ent, 1);
+          const uint32_t bal = __ballot_sync(0xffffffffu, lane < 31 && succ_live && x != next_ent);
+          if (!bal) break;
+          const int k = __ffs(bal) - 1;
+          const uint32_t xk = __shfl_sync(0xffffffffu, x, k);
+          if (lane == k + 1) {
+            ent = xk;
+            x = resolve(ent);
           }
         }
-        if (nx != x) {
-          x = nx;
-          changed = true;
+      };
+      uint32_t E = warp == 0 ? 0u : s_sx[warp * 32 - 1];
+      warp_resolve(E);
+      // across warps: redo a warp whose guessed entry was wrong (at most kWarps rounds)
+      bool stitch_ok = true;
+      for (int r = 0;; ++r) {
+        if (r > kWarps + 1) {  // unreachable unless the walk is broken; never spin
+          stitch_ok = false;
+          break;
         }
+        const uint32_t xl = __shfl_sync(0xffffffffu, x, 31);
+        if (lane == 0) s_wx[(r & 1) * kWarps + warp] = xl;
+        __syncthreads();
+        const uint32_t want = warp == 0 ? 0u : s_wx[(r & 1) * kWarps + warp - 1];
+        const bool redo = warp > 0 && want != E && (uint32_t)warp * 32u * SEGW < W;
+        if (redo) {
+          E = want;
+          warp_resolve(E);
+        }
+        if (!__syncthreads_or(redo)) break;
       }
-      __syncthreads();
-      s_ex[tid] = x;
-      if (!__syncthreads_or(changed)) break;
-    }
 
-    // ---- 2. validation + per-thread summaries
-    uint32_t cnt = bits.count();
-    TsM tsum{0, 0};
-    DM dsum{0, 0};
-    int err_local = -1;
-    uint32_t err_code = 0;
-    {
-      uint32_t local = 0;
-#pragma unroll
-      for (int k = 0; k < BW; ++k) {
-        uint32_t m = bits.w[k];
-        while (m) {
-          uint32_t oo = a + k * 32 + (__ffs(m) - 1);
-          m &= m - 1;
-          uint32_t code = 0;
-          uint32_t w0 = C[oo], w1 = C[oo + 1];
-          uint32_t c = w1 & 0xFFFFu;
-          uint64_t cr = 0;
-          bool ext = (w0 & kExtBit) != 0;
-          if (oo + 2 > W) {
-            code = THAPI_E_TRUNCATED;
-          } else if ((w0 >> 28) != 0 || c >= p.n_classes || (ext && (w0 & kDeltaMask) != 0)) {
-            code = THAPI_E_FORMAT;
-          } else {
-            cr = class_row<CLS_SMEM>(s_cls, p.classes, c);
-            uint32_t sz = 2 + (ext ? 2 : 0) + cls_fixedw(cr) + (((w1 >> 16) + 3u) >> 2);
-            if (oo + sz > W) code = THAPI_E_TRUNCATED;
-          }
-          if (code) {
-            if (err_local < 0) {
-              err_local = (int)local;
-              err_code = code;
-            }
-          } else {
-            uint32_t kd = cls_kind(cr);
-            int e = kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
-            dsum.s += e;
-            dsum.m = min(dsum.m, dsum.s);
-            if (ext) {
-              tsum.has = 1;
-              tsum.v = (uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32);
-            } else {
-              tsum.v += w0 & kDeltaMask;
-            }
-          }
-          ++local;
-        }
-      }
-    }
-    uint32_t c_ex, c_tot;
-    TsM t_ex, t_tot_m;
-    DM d_ex, d_tot;
-    if (tid == 0) s_misc[1] = 0xFFFFFFFFu;
-    cta_scan3(cnt, tsum, dsum, c_ex, t_ex, d_ex, c_tot, t_tot_m, d_tot, ss);
-    if (err_local >= 0) atomicMin(&s_misc[1], ((c_ex + (uint32_t)err_local) << 3) | err_code);
-    __syncthreads();
-    const uint32_t ekey = s_misc[1];
-    const bool pk_ok = stitch_ok && ekey == 0xFFFFFFFFu && c_tot == nev && c_tot <= p.emax;
-    if (!stitch_ok) {
-      if (tid == 0) atomicExch(status, (unsigned)THAPI_E_TIMEOUT);
-    } else if (!pk_ok) {
-      if (tid == 0) {
-        if (ekey != 0xFFFFFFFFu)
-          atomicMin(p.content_err, err_key(pk, ekey >> 3, ekey & 7u));
-        else
-          atomicMin(p.content_err, err_key(pk, c_tot, THAPI_E_FORMAT));
-      }
-    } else {
-      // ---- 3. decode into the shared table
-      const uint64_t tsb = p.pk_tsb[pk];
-      uint64_t t = t_ex.has ? t_ex.v : tsb + t_ex.v;
-      int depth = d_ex.s;
-      int segmin = 0x7FFFFFFF;
-      uint32_t k = c_ex;
-#pragma unroll
-      for (int kk = 0; kk < BW; ++kk) {
-        uint32_t m = bits.w[kk];
-        while (m) {
-          uint32_t oo = a + kk * 32 + (__ffs(m) - 1);
-          m &= m - 1;
-          uint32_t w0 = C[oo], w1 = C[oo + 1];
-          bool ext = (w0 & kExtBit) != 0;
-          uint64_t cr = class_row<CLS_SMEM>(s_cls, p.classes, w1 & 0xFFFFu);
-          uint32_t kd = cls_kind(cr);
-          uint32_t base = oo + 2 + (ext ? 2 : 0);
-          t = ext ? ((uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32)) : t + (w0 & kDeltaMask);
-          int e = kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
-          depth += e;
-          uint32_t err = 0;
-          int32_t rw = cls_resw(cr);
-          if (kd == kExit && rw >= 0) err = C[base + rw] != 0 ? 1u : 0u;
-          s_ts[k] = t;
-          s_dk[k] = ((uint32_t)depth & 0xFFFFu) | (kd << 16) | (err << 19);
-          s_fn[k] = (uint16_t)cls_func(cr);
-          segmin = min(segmin, depth);
-          tmin = min(tmin, t);
-          tmax = max(tmax, t);
-          ++k;
-        }
-      }
-      s_tk0[tid] = c_ex;
-      if (tid == 0) s_tk0[kT] = c_tot;
-      s_segmin[tid] = cnt ? segmin : 0x7FFFFFFF;
-      __syncthreads();
-
-      // ---- 4a. in-packet matching and tally
-      uint32_t nslot = 0;
+      // ---- 2. validation + per-thread summaries
+      const uint32_t cnt = bits.count();
+      uint32_t n_entry = 0;
+      TsM tsum{0, 0};
+      DM dsum{0, 0};
+      int err_local = -1;
+      uint32_t err_code = 0;
       {
+        uint32_t local = 0;
+#pragma unroll
+        for (int k = 0; k < BW; ++k) {
+          uint32_t m = bits.w[k];
+          while (m) {
+            const uint32_t oo = a + k * 32 + (__ffs(m) - 1);
+            m &= m - 1;
+            uint32_t code = 0;
+            const uint32_t w0 = C[oo], w1 = C[oo + 1];
+            const uint32_t c = w1 & 0xFFFFu;
+            uint64_t cr = 0;
+            const bool ext = (w0 & kExtBit) != 0;
+            if (oo + 2 > W) {
+              code = THAPI_E_TRUNCATED;
+            } else if ((w0 >> 28) != 0 || c >= p.n_classes || (ext && (w0 & kDeltaMask) != 0)) {
+              code = THAPI_E_FORMAT;
+            } else {
+              cr = class_row<CLS_SMEM>(s_cls, p.classes, c);
+              const uint32_t sz = 2 + (ext ? 2 : 0) + cls_fixedw(cr) + (((w1 >> 16) + 3u) >> 2);
+              if (oo + sz > W) code = THAPI_E_TRUNCATED;
+            }
+            if (code) {
+              if (err_local < 0) {
+                err_local = (int)local;
+                err_code = code;
+              }
+            } else {
+              const uint32_t kd = cls_kind(cr);
+              const int e = kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
+              n_entry += kd == kEntry ? 1u : 0u;
+              dsum.s += e;
+              dsum.m = min(dsum.m, dsum.s);
+              if (ext) {
+                tsum.has = 1;
+                tsum.v = (uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32);
+              } else {
+                tsum.v += w0 & kDeltaMask;
+              }
+            }
+            ++local;
+          }
+        }
+      }
+      uint32_t c_ex2, c_tot2;
+      TsM t_ex, t_tot_m;
+      DM d_ex, d_tot;
+      cta_scan3(cnt | (n_entry << 16), tsum, dsum, c_ex2, t_ex, d_ex, c_tot2, t_tot_m, d_tot, ss);
+      const uint32_t c_ex = c_ex2 & 0xFFFFu, e_ex = c_ex2 >> 16;
+      const uint32_t c_tot = c_tot2 & 0xFFFFu, e_tot = c_tot2 >> 16;
+      if (err_local >= 0) atomicMin(&s_misc[kErrKey], ((c_ex + (uint32_t)err_local) << 3) | err_code);
+      const bool fits = stitch_ok && c_tot == d.nev && c_tot <= p.emax;
+      const uint32_t P_p = (uint32_t)(-d_tot.m);
+      const uint32_t O_p = (uint32_t)(d_tot.s - d_tot.m);
+      if (fits) {
+        if (tid == 0) {
+          // frontier room from this CTA's chunk (a global atomic only per chunk)
+          const uint32_t need = P_p + O_p;
+          uint64_t fb = 0;
+          if (need) {
+            if (need > fr_left) {
+              const uint32_t grab = need > kFrontierChunk ? need : kFrontierChunk;
+              fr_base = atomicAdd(p.frontier_top, (unsigned long long)grab);
+              fr_left = grab;
+              if (fr_base + grab > p.frontier_cap) fr_left = 0;  // overflow: the host retries with more room
+            }
+            if (need <= fr_left) {
+              fb = fr_base;
+              fr_base += need;
+              fr_left -= need;
+            } else {
+              fb = ~0ull;
+            }
+          }
+          s_misc[kFbLo] = (uint32_t)fb;
+          s_misc[kFbHi] = (uint32_t)(fb >> 32);
+        }
+        // ---- 3. decode into the shared table
+        uint64_t t = t_ex.has ? t_ex.v : d.tsb + t_ex.v;
+        int depth = d_ex.s;
+        int segmin = 0x7FFFFFFF;
+        uint32_t k = c_ex;
+#pragma unroll
+        for (int kk = 0; kk < BW; ++kk) {
+          uint32_t m = bits.w[kk];
+          while (m) {
+            const uint32_t oo = a + kk * 32 + (__ffs(m) - 1);
+            m &= m - 1;
+            const uint32_t w0 = C[oo], w1 = C[oo + 1];
+            const bool ext = (w0 & kExtBit) != 0;
+            const uint32_t c = w1 & 0xFFFFu;
+            const uint64_t cr = c < p.n_classes ? class_row<CLS_SMEM>(s_cls, p.classes, c) : 0ull;
+            const uint32_t kd = cls_kind(cr);
+            const uint32_t base = oo + 2 + (ext ? 2 : 0);
+            t = ext ? ((uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32)) : t + (w0 & kDeltaMask);
+            depth += kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
+            uint32_t err = 0;
+            const int32_t rw = cls_resw(cr);
+            if (kd == kExit && rw >= 0 && base + (uint32_t)rw < W) err = C[base + rw] != 0 ? 1u : 0u;
+            s_ts[k] = t;
+            s_dk[k] = ((uint32_t)depth & 0xFFFFu) | (kd << 16) | (err << 19);
+            s_fn[k] = (uint16_t)cls_func(cr);
+            segmin = min(segmin, depth);
+            tmin = min(tmin, t);
+            tmax = max(tmax, t);
+            ++k;
+          }
+        }
+        s_tk0[tid] = c_ex;
+        if (tid == 0) s_tk0[kT] = c_tot;
+        segmin = cnt ? segmin : 0x7FFFFFFF;
+        s_segmin[tid] = segmin;
+        int suf = segmin;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_down_sync(0xffffffffu, suf, o);
+          if (lane + o < 32) suf = min(suf, u);
+        }
+        s_sufmin[tid] = suf;
+        if (lane == 0) s_wmin[warp] = suf;
+      }
+      __syncthreads();
+      const uint32_t ekey = s_misc[kErrKey];
+      const bool pk_ok = fits && ekey == 0xFFFFFFFFu;
+      if (!pk_ok) {
+        if (tid == 0) {
+          if (!stitch_ok)
+            atomicExch(status, (unsigned)THAPI_E_TIMEOUT);
+          else if (ekey != 0xFFFFFFFFu)
+            atomicMin(p.content_err, err_key(d.pk, ekey >> 3, ekey & 7u));
+          else
+            atomicMin(p.content_err, err_key(d.pk, c_tot, THAPI_E_FORMAT));
+        }
+      } else {
+        // ---- 4. match, tally, frontier, interval slots
+        const uint64_t fbase = (uint64_t)s_misc[kFbLo] | ((uint64_t)s_misc[kFbHi] << 32);
         const uint32_t k0 = c_ex, k1 = c_ex + cnt;
+        const uint32_t wlast = (uint32_t)warp * 32 + 31;
+        int mrun = d_ex.m;  // running minimum of the post-depth before event i (<= 0)
+        uint32_t rank = e_ex;
+        uint32_t valid = 0;
         for (uint32_t i = k0; i < k1; ++i) {
-          uint32_t dk = s_dk[i];
-          uint32_t kd = (dk >> 16) & 7u;
+          const uint32_t dk = s_dk[i];
+          const uint32_t kd = (dk >> 16) & 7u;
+          const int post = post_of(dk);
           if (kd == kEntry) {
-            int r = post_of(dk) - 1;
+            const int r = post - 1;
+            // the exit: first later event with post-depth <= r
             int j = -1;
             for (uint32_t q = i + 1; q < k1; ++q)
               if (post_of(s_dk[q]) <= r) {
                 j = (int)q;
                 break;
               }
-            if (j < 0)
-              for (int t2 = tid + 1; t2 < kT && j < 0; ++t2)
+            if (j < 0 && (uint32_t)tid < wlast && s_sufmin[tid + 1] <= r) {
+              for (uint32_t t2 = tid + 1; t2 <= wlast; ++t2)
                 if (s_segmin[t2] <= r) {
-                  uint32_t e2 = s_tk0[t2 + 1];
+                  const uint32_t e2 = s_tk0[t2 + 1];
                   for (uint32_t q = s_tk0[t2]; q < e2; ++q)
                     if (post_of(s_dk[q]) <= r) {
                       j = (int)q;
                       break;
                     }
+                  break;
                 }
+            }
+            if (j < 0)
+              for (int w2 = warp + 1; w2 < kWarps; ++w2)
+                if (s_wmin[w2] <= r) {
+                  for (uint32_t t2 = (uint32_t)w2 * 32; t2 < (uint32_t)w2 * 32 + 32; ++t2)
+                    if (s_segmin[t2] <= r) {
+                      const uint32_t e2 = s_tk0[t2 + 1];
+                      for (uint32_t q = s_tk0[t2]; q < e2; ++q)
+                        if (post_of(s_dk[q]) <= r) {
+                          j = (int)q;
+                          break;
+                        }
+                      break;
+                    }
+                  break;
+                }
+            thapi_interval iv;
+            iv.start_ns = s_ts[i];
+            iv.stream_id = (uint32_t)(-mrun);  // pending exits before this entry (the level is finished later)
+            iv.func_id = s_fn[i];
+            iv.level = (uint8_t)min(r - mrun, 255);
             if (j < 0) {
-              s_mt[i] = -1;
-              ++nslot;
+              iv.end_ns = 0;
+              iv.flags = kIvOpen;
+              if (fbase != ~0ull) {
+                Frontier fr;
+                fr.ts = s_ts[i];
+                fr.aux = p.slots ? rank : 0xFFFFFFFFu;
+                fr.func = s_fn[i];
+                fr.flags = 0;
+                p.frontier[fbase + P_p + (uint32_t)(r - d_tot.m)] = fr;
+              }
             } else if (s_fn[j] == s_fn[i]) {
-              s_mt[i] = (int16_t)j;
-              ++nslot;
-              ++n_pairs;
-              uint64_t dur = s_ts[j] - s_ts[i];
-              uint32_t err = (s_dk[j] >> 19) & 1u;
-              uint32_t f = s_fn[i];
-              if (TALLY_SMEM) {
+              ++valid;
+              const uint64_t dur = s_ts[j] - s_ts[i];
+              const uint32_t err = (s_dk[j] >> 19) & 1u;
+              const uint32_t f = s_fn[i];
+              iv.end_ns = s_ts[j];
+              iv.flags = (uint8_t)(kIvValid | err);
+              if (TALLY_SMEM && dur < (1ull << 32)) {
                 atomicAdd(&t_cnt[f], 1u);
                 atomicAdd(&t_tot[f], (unsigned long long)dur);
-                atomicMin(&t_mn[f], (unsigned long long)dur);
-                atomicMax(&t_mx[f], (unsigned long long)dur);
+                atomicMin(&t_mn[f], (uint32_t)dur);
+                atomicMax(&t_mx[f], (uint32_t)dur);
                 if (err) atomicAdd(&t_err[f], 1u);
               } else {
-                Cell &cell = p.tally[(uint64_t)group * F + f];
+                Cell &cell = p.tally[(uint64_t)d.group * F + f];
                 atomicAdd(&cell.count, 1ull);
                 atomicAdd(&cell.total, (unsigned long long)dur);
                 atomicMin(&cell.mn, (unsigned long long)dur);
@@ -581,116 +707,73 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
                 if (err) atomicAdd(&cell.err, 1ull);
               }
             } else {
-              s_mt[i] = -2;
+              iv.end_ns = s_ts[j];
+              iv.flags = 0;  // mismatched pair: no interval
               ++n_mismatch;
             }
-          } else if (kd != kExit) {
-            ++n_other;
-          }
-        }
-      }
-      uint32_t slot_tot;
-      uint32_t slot_ex = cta_scan_u32(nslot, slot_tot, ss);
-      const uint32_t P_p = (uint32_t)(-d_tot.m);
-      const uint32_t O_p = (uint32_t)(d_tot.s - d_tot.m);
-      if (tid == 0) {
-        uint64_t fb = 0;
-        if (P_p + O_p) {
-          fb = atomicAdd(p.frontier_top, (unsigned long long)(P_p + O_p));
-          if (fb + P_p + O_p > p.frontier_cap) fb = ~0ull;  // overflow: host retries with more room
-        }
-        s_misc[2] = (uint32_t)fb;
-        s_misc[3] = (uint32_t)(fb >> 32);
-        p.sum_pend[pos] = P_p;
-        p.sum_open[pos] = O_p;
-        p.sum_fbase[pos] = fb;
-        p.sum_nslot[pos] = slot_tot;
-        p.sum_nvalid[pos] = slot_tot - O_p;
-        n_events += c_tot;
-        if (p.slots) n_slots += slot_tot;
-        n_disc += p.pk_disc[pk];
-        n_pk += 1;
-      }
-      __syncthreads();
-      const uint64_t fbase = (uint64_t)s_misc[2] | ((uint64_t)s_misc[3] << 32);
-
-      // ---- 4b. frontier items and interval slots
-      {
-        const uint32_t k0 = c_ex, k1 = c_ex + cnt;
-        int mrun = d_ex.m;  // running minimum of post-depth before event i (<= 0)
-        uint32_t rank = slot_ex;
-        const uint64_t sbase = p.evbase[pos];
-        for (uint32_t i = k0; i < k1; ++i) {
-          uint32_t dk = s_dk[i];
-          uint32_t kd = (dk >> 16) & 7u;
-          int post = post_of(dk);
-          if (kd == kEntry) {
-            int mt = s_mt[i];
-            if (mt >= -1) {
-              int pre = post - 1;
-              if (p.slots) {
-                thapi_interval iv;
-                iv.start_ns = s_ts[i];
-                iv.end_ns = mt >= 0 ? s_ts[mt] : 0;
-                iv.stream_id = (uint32_t)(-mrun);
-                iv.func_id = s_fn[i];
-                iv.level = (uint8_t)min(pre - mrun, 255);
-                iv.flags = mt >= 0 ? (uint8_t)(kIvValid | ((s_dk[mt] >> 19) & 1u)) : kIvOpen;
-                p.slots[sbase + rank] = iv;
-              }
-              if (mt == -1 && fbase != ~0ull) {
-                Frontier fr;
-                fr.ts = s_ts[i];
-                fr.aux = p.slots ? rank : 0xFFFFFFFFu;
-                fr.func = s_fn[i];
-                fr.flags = 0;
-                p.frontier[fbase + P_p + (uint32_t)(pre - d_tot.m)] = fr;
-              }
-              ++rank;
+            if (p.slots) p.slots[d.evbase + rank] = iv;
+            ++rank;
+          } else if (kd == kExit) {
+            if (post < mrun && fbase != ~0ull) {
+              Frontier fr;
+              fr.ts = s_ts[i];
+              fr.aux = (dk >> 19) & 1u;
+              fr.func = s_fn[i];
+              fr.flags = 0;
+              p.frontier[fbase + (uint32_t)(-post - 1)] = fr;
             }
-          } else if (kd == kExit && post < mrun && fbase != ~0ull) {
-            Frontier fr;
-            fr.ts = s_ts[i];
-            fr.aux = (dk >> 19) & 1u;
-            fr.func = s_fn[i];
-            fr.flags = 0;
-            p.frontier[fbase + (uint32_t)(-post - 1)] = fr;
+          } else {
+            ++n_other;
           }
           mrun = min(mrun, post);
         }
+        n_pairs += valid;
+        if (valid) atomicAdd(&s_misc[kValid], valid);
+      }
+      __syncthreads();
+      if (pk_ok && tid == 0) {
+        p.sum_pend[pos] = P_p;
+        p.sum_open[pos] = O_p;
+        p.sum_fbase[pos] = (uint64_t)s_misc[kFbLo] | ((uint64_t)s_misc[kFbHi] << 32);
+        p.sum_nslot[pos] = e_tot;
+        p.sum_nvalid[pos] = s_misc[kValid];
+        n_events += c_tot;
+        if (p.slots) n_slots += e_tot;
+        n_disc += d.disc;
+        n_pk += 1;
       }
     }
-    __syncthreads();
 
     // ---- 5. flush the shared tally when the stream changes
     if (TALLY_SMEM) {
-      bool flush = wn >= w_end || p.pk_stream[p.order[pos_of(wn)]] != stream;
-      if (flush) {
+      if (s_misc[kNextStream] != d.stream) {
         for (uint32_t f = tid; f < F; f += kT) {
-          uint32_t c = t_cnt[f];
+          const uint32_t c = t_cnt[f];
           if (c) {
-            Cell &cell = p.tally[(uint64_t)group * F + f];
+            Cell &cell = p.tally[(uint64_t)d.group * F + f];
             atomicAdd(&cell.count, (unsigned long long)c);
             atomicAdd(&cell.total, t_tot[f]);
-            atomicMin(&cell.mn, t_mn[f]);
-            atomicMax(&cell.mx, t_mx[f]);
+            atomicMin(&cell.mn, (unsigned long long)t_mn[f]);
+            atomicMax(&cell.mx, (unsigned long long)t_mx[f]);
             if (t_err[f]) atomicAdd(&cell.err, (unsigned long long)t_err[f]);
             t_cnt[f] = 0;
             t_err[f] = 0;
-            t_tot[f] = 0;
-            t_mn[f] = ~0ull;
+            t_mn[f] = 0xFFFFFFFFu;
             t_mx[f] = 0;
+            t_tot[f] = 0;
           }
         }
-        __syncthreads();
       }
     }
-    if (STAGES == 1 && wn < w_end) {
-      if (tid == 0) issue(wn, 0);
+    __syncthreads();  // buffers, table and misc words free for the next packet
+    if (STAGES == 1 && has_next) {
+      if (tid == 0) {
+        meta[0] = dnext;
+        issue(dnext, 0);
+        if (w + 2 < w_end) dnext = load_desc(p.desc + pos_of(w + 2));
+      }
       pending_mask |= 1u;
     }
-    if (STAGES == 2) stage ^= 1;
-    w = wn;
   }
 
   if (timed_out) {
@@ -708,7 +791,7 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
     tmin = min(tmin, __shfl_down_sync(0xffffffffu, tmin, off));
     tmax = max(tmax, __shfl_down_sync(0xffffffffu, tmax, off));
   }
-  if ((tid & 31) == 0) {
+  if (lane == 0) {
     if (n_mismatch) atomicAdd(&p.diag[dMismatch], n_mismatch);
     if (n_other) atomicAdd(&p.diag[dOther], n_other);
     if (n_pairs) atomicAdd(&p.diag[dPairs], n_pairs);
@@ -750,6 +833,9 @@ uint32_t analyze_smem_bytes(uint32_t P, uint32_t emax, int stages, uint32_t n_cl
                          n_funcs <= kTallySmemMax);
   return L.total;
 }
+
+// Frontier items a launch may leave unused at the end of its CTAs' chunks.
+uint64_t analyze_frontier_slack(uint32_t grid) { return (uint64_t)grid * kFrontierChunk; }
 
 // Launches the analysis over p.n_order work items with `grid` CTAs.
 cudaError_t launch_analyze(const AnalyzeParams &p, int stages, uint32_t grid, cudaStream_t s, unsigned *status) {

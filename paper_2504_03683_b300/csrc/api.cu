@@ -38,6 +38,7 @@ struct thapi_ctx {
   void *user = nullptr;
   int num_sms = 0;
   int smem_per_sm = 0;
+  int smem_per_block = 0;
   std::map<uint64_t, TraceRec *> traces;
   uint64_t next_id = 1;
   int err_level = 0;
@@ -300,6 +301,13 @@ class Loader {
   PhaseClock clk_;
 };
 
+// Double-buffered packets when they fit the per-CTA shared memory, else single.
+static int pick_stages(thapi_ctx *c, uint32_t P, uint32_t emax, uint32_t n_classes, uint32_t n_funcs) {
+  for (int st = 2; st >= 1; --st)
+    if ((int)analyze_smem_bytes(P, emax, st, n_classes, n_funcs) <= c->smem_per_block) return st;
+  return 0;
+}
+
 static int blocks_per_sm(thapi_ctx *c, uint32_t smem) {
   int b = std::min(16, c->smem_per_sm / (int)(smem + 1024));
   return b < 1 ? 1 : b;
@@ -414,7 +422,21 @@ int Loader::run() {
   uint64_t *sum_fbase = alloc<uint64_t>(n);
   thapi_interval *slots = alloc<thapi_interval>(total_events);
   if (sc_.failed) return THAPI_E_NOMEM;
-  uint64_t fcap = total_events / 4 + 4096;
+  PkDesc *desc = alloc<PkDesc>(n);
+  if (!desc) return THAPI_E_NOMEM;
+  launch_build_desc(order, pk_stream, pk_nev, pk_content, pk_disc, pk_tsb, d_group, evbase, n, desc, s_);
+  const uint32_t emax_main = ((P - kPacketHeader) / 4) / 4;
+  const int stages = n ? pick_stages(c_, P, emax_main, L.n_classes, F) : 1;
+  if (!stages) return THAPI_E_UNSUPPORTED;
+  uint64_t grid = 1, per = 1;
+  if (n) {
+    const uint32_t smem = analyze_smem_bytes(P, emax_main, stages, L.n_classes, F);
+    grid = (uint64_t)c_->num_sms * blocks_per_sm(c_, smem);
+    per = (n + grid - 1) / grid;
+    grid = (n + per - 1) / per;
+  }
+  uint64_t fcap = total_events / 16 + 4096 + analyze_frontier_slack((uint32_t)grid) +
+                  analyze_frontier_slack((uint32_t)c_->num_sms * 16);
   Frontier *frontier = nullptr;
   unsigned *status = reinterpret_cast<unsigned *>(misc_ + mStatus);
   for (int attempt = 0;; ++attempt) {
@@ -433,20 +455,13 @@ int Loader::run() {
     AnalyzeParams ap{};
     ap.packets = packets;
     ap.P = P;
-    ap.emax = ((P - kPacketHeader) / 4) / 4;
+    ap.emax = emax_main;
     ap.n_order = n;
-    ap.order = order;
     ap.poslist = nullptr;
-    ap.pk_stream = pk_stream;
-    ap.pk_nev = pk_nev;
-    ap.pk_content = pk_content;
-    ap.pk_disc = pk_disc;
-    ap.pk_tsb = pk_tsb;
-    ap.evbase = evbase;
+    ap.desc = desc;
     ap.classes = d_cls;
     ap.n_classes = L.n_classes;
     ap.n_funcs = F;
-    ap.stream_group = d_group;
     ap.tally = tally;
     ap.sum_pend = sum_pend;
     ap.sum_open = sum_open;
@@ -463,13 +478,8 @@ int Loader::run() {
     ap.dense_list = dense_list;
     ap.dense_count = reinterpret_cast<unsigned long long *>(misc_ + mDense);
     ap.slots_written = reinterpret_cast<unsigned long long *>(misc_ + mSlots);
-    const int stages = 2;
     if (n) {
-      uint32_t smem = analyze_smem_bytes(P, ap.emax, stages, L.n_classes, F);
-      uint64_t grid = (uint64_t)c_->num_sms * blocks_per_sm(c_, smem);
-      uint64_t per = (n + grid - 1) / grid;
       ap.per_cta = (uint32_t)per;
-      grid = (n + per - 1) / per;
       clk_.rec(PhaseClock::kAn0, s_);
       CK(launch_analyze(ap, stages, (uint32_t)grid, s_, status));
       clk_.rec(PhaseClock::kAn1, s_);
@@ -482,13 +492,15 @@ int Loader::run() {
         dp.poslist = dense_list;
         dp.dense_list = nullptr;
         dp.dense_count = nullptr;
-        uint32_t dsmem = analyze_smem_bytes(P, dp.emax, stages, L.n_classes, F);
+        const int dstages = pick_stages(c_, P, dp.emax, L.n_classes, F);
+        if (!dstages) return THAPI_E_UNSUPPORTED;
+        uint32_t dsmem = analyze_smem_bytes(P, dp.emax, dstages, L.n_classes, F);
         uint64_t dgrid = std::min<uint64_t>(dp.n_order, (uint64_t)c_->num_sms * blocks_per_sm(c_, dsmem));
         uint64_t dper = (dp.n_order + dgrid - 1) / dgrid;
         dp.per_cta = (uint32_t)dper;
         dgrid = (dp.n_order + dper - 1) / dper;
         clk_.rec(PhaseClock::kDn0, s_);
-        CK(launch_analyze(dp, stages, (uint32_t)dgrid, s_, status));
+        CK(launch_analyze(dp, dstages, (uint32_t)dgrid, s_, status));
         clk_.rec(PhaseClock::kDn1, s_);
         clk_.dense = true;
         analyze_launches = 2;
@@ -776,7 +788,8 @@ int thapi_ctx_create(thapi_ctx **out, int device, uint64_t hbm_cap_bytes) {
   c->device = device;
   c->cap = hbm_cap_bytes;
   if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess) {
+      cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
     delete c;
     return THAPI_E_CUDA;
   }

@@ -119,3 +119,37 @@ void launch_widen_u32(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_
 }
 
 }  // namespace thapi
+
+namespace thapi {
+
+// One descriptor per order position, so the analysis reads a packet's facts
+// with three 16-byte loads instead of a chain of dependent ones.
+__global__ void k_build_desc(const uint32_t *order, const uint32_t *pk_stream, const uint32_t *pk_nev,
+                             const uint32_t *pk_content, const uint32_t *pk_disc, const uint64_t *pk_tsb,
+                             const uint32_t *stream_group, const uint64_t *evbase, uint64_t n, PkDesc *desc) {
+  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t pk = order[i];
+  PkDesc d;
+  d.pk = pk;
+  d.content = pk_content[pk];
+  d.nev = pk_nev[pk];
+  d.stream = pk_stream[pk];
+  d.group = stream_group[d.stream];
+  d.disc = pk_disc[pk];
+  d.pad0 = d.pad1 = 0;
+  d.tsb = pk_tsb[pk];
+  d.evbase = evbase[i];
+  desc[i] = d;
+}
+
+void launch_build_desc(const uint32_t *order, const uint32_t *pk_stream, const uint32_t *pk_nev,
+                       const uint32_t *pk_content, const uint32_t *pk_disc, const uint64_t *pk_tsb,
+                       const uint32_t *stream_group, const uint64_t *evbase, uint64_t n, PkDesc *desc, cudaStream_t s) {
+  if (!n) return;
+  k_build_desc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(order, pk_stream, pk_nev, pk_content, pk_disc, pk_tsb,
+                                                           stream_group, evbase, n, desc);
+  count_launches(1);
+}
+
+}  // namespace thapi

@@ -11,7 +11,7 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/thapi.h"
+#include "thapi.h"
 
 namespace thapi {
 
@@ -73,19 +73,22 @@ struct IndexParams {
   unsigned long long *hdr_err;  // min packet index with a header error
 };
 
+// What the analysis needs of one packet, gathered per order position.
+struct __align__(16) PkDesc {
+  uint32_t pk, content, nev, stream;  // file index, content bytes, events, stream id
+  uint32_t group, disc, pad0, pad1;   // (host, pid, tid) group, discarded counter
+  uint64_t tsb, evbase;               // ts_begin, first event slot
+};
+
 struct AnalyzeParams {
   const uint8_t *packets;
   uint32_t P;
-  uint32_t emax;                 // SoA capacity (events per packet) of this launch
+  uint32_t emax;                 // shared-memory event table capacity of this launch
   uint64_t n_order;              // work items of this launch
-  const uint32_t *order;         // stream-ordered packet file indices (full list)
   const uint32_t *poslist;       // work item -> order position (null: identity)
-  const uint32_t *pk_stream, *pk_nev, *pk_content, *pk_disc;
-  const uint64_t *pk_tsb;
-  const uint64_t *evbase;        // per order position: first event slot of the packet
+  const PkDesc *desc;            // per order position
   const uint64_t *classes;       // packed class rows
   uint32_t n_classes, n_funcs;
-  const uint32_t *stream_group;  // stream -> (host, pid, tid) group
   Cell *tally;                   // [groups * n_funcs]
   uint32_t *sum_pend, *sum_open, *sum_nslot, *sum_nvalid;  // per order position
   uint64_t *sum_fbase;
@@ -99,7 +102,7 @@ struct AnalyzeParams {
   unsigned long long *slots_written;  // interval slots written (24 B each)
   uint32_t *dense_list;          // packets with more events than emax (order positions)
   unsigned long long *dense_count;
-  uint32_t per_cta;              // order positions per CTA
+  uint32_t per_cta;              // work items per CTA
 };
 
 struct FrontierParams {
@@ -152,6 +155,9 @@ namespace thapi {
 
 // index.cu
 void launch_widen_u32(const uint32_t *in, uint64_t *out, uint64_t n, cudaStream_t s);
+void launch_build_desc(const uint32_t *order, const uint32_t *pk_stream, const uint32_t *pk_nev,
+                       const uint32_t *pk_content, const uint32_t *pk_disc, const uint64_t *pk_tsb,
+                       const uint32_t *stream_group, const uint64_t *evbase, uint64_t n, PkDesc *desc, cudaStream_t s);
 void launch_packet_headers(const IndexParams &p, cudaStream_t s);
 void launch_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals, cudaStream_t s);
 void launch_stream_bounds(const uint64_t *skey, const uint32_t *order, const uint32_t *pk_seq, const uint32_t *pk_nev,
@@ -159,6 +165,7 @@ void launch_stream_bounds(const uint64_t *skey, const uint32_t *order, const uin
                           uint64_t *ev, unsigned long long *hdr_err, cudaStream_t s);
 // analyze.cu
 uint32_t analyze_smem_bytes(uint32_t P, uint32_t emax, int stages, uint32_t n_classes, uint32_t n_funcs);
+uint64_t analyze_frontier_slack(uint32_t grid);
 cudaError_t launch_analyze(const AnalyzeParams &p, int stages, uint32_t grid, cudaStream_t s, unsigned *status);
 // frontier.cu
 void launch_frontier(const FrontierParams &p, cudaStream_t s);
