@@ -206,6 +206,30 @@ int thapi_trace_timing(thapi_ctx *ctx, thapi_trace_id id, thapi_load_timing *out
 /* Kernels this library has launched in this process (all contexts). */
 uint64_t thapi_kernel_launches(void);
 
+/* Tally of a small trace with no device allocation at all (the paper has no
+ * counterpart; this is a deployment aid).  For callers that cannot allocate
+ * device memory: a tracing agent that tallies on the node while the traced
+ * application runs in the same CUDA context, where the application or its
+ * framework's caching allocator holds nearly all device memory and an
+ * allocation by the agent could fail or disturb the application it observes.
+ * `dev_bytes` is the whole trace in DEVICE memory (16-byte aligned, caller-
+ * owned); rows are written to DEVICE memory `rows` (capacity `cap`; cap = 0 is
+ * a size query, 0 < cap < rows gives E_RANGE) on `cuda_stream`; *n_rows and
+ * *diag (may be NULL) are host outputs.  Results equal thapi_trace_load_device
+ * followed by thapi_tally.  Working memory is one 32 MiB array in device
+ * global memory that belongs to the library (every GPU that loads the library
+ * holds it until the process exits).  Limits: at most 4096 packets, 2^20
+ * events, 2^16 (host, pid, tid) groups x functions, and a cross-packet pairing
+ * frontier that fits what the array has left; beyond them the call returns
+ * E_UNSUPPORTED.  The first call on a device looks up the array's device
+ * address, so make that first call before any stream capture.  Calls share
+ * the array: host calls are serialised, each returns after its GPU work is
+ * done, and work of two calls overlapping on the GPU would race.  Errors:
+ * E_INVALID, E_FORMAT / E_TRUNCATED (no location is recorded), E_UNSUPPORTED,
+ * E_TIMEOUT, E_RANGE, E_CUDA. */
+int thapi_tally_static(const void *dev_bytes, uint64_t nbytes, thapi_tally_row *rows, uint64_t cap,
+                       uint64_t *n_rows, thapi_diag *diag, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *thapi_strerror(int code);
 

@@ -230,6 +230,41 @@ static int parse_layout(const Reader &r, HostLayout &L) {
   return THAPI_OK;
 }
 
+// Header, tables and (host, pid, tid) group numbering of a trace in device
+// memory, for callers outside the loader (the static-scratch tally).
+int describe_device_trace(const uint8_t *dev, uint64_t nbytes, cudaStream_t s, TraceDescription &td) {
+  HostLayout L;
+  const Reader r{nullptr, dev, nbytes, s};
+  const int rc = parse_layout(r, L);
+  if (rc != THAPI_OK) return rc;
+  td.P = L.P;
+  td.n_streams = L.n_streams;
+  td.n_classes = L.n_classes;
+  td.n_funcs = L.n_funcs;
+  td.n_hosts = L.n_hosts;
+  td.n_packets = L.n_packets;
+  td.packets_off = L.packets_off;
+  td.cls = L.cls;
+  std::vector<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>> keyed(L.n_streams);
+  for (uint32_t i = 0; i < L.n_streams; ++i)
+    keyed[i] = std::make_tuple(L.srow[4ull * i], L.srow[4ull * i + 1], L.srow[4ull * i + 2], i);
+  std::sort(keyed.begin(), keyed.end());
+  td.stream_group.assign(L.n_streams ? L.n_streams : 1, 0);
+  td.group_keys.clear();
+  td.groups = 0;
+  for (uint32_t i = 0; i < L.n_streams; ++i) {
+    if (i == 0 || std::get<0>(keyed[i]) != std::get<0>(keyed[i - 1]) ||
+        std::get<1>(keyed[i]) != std::get<1>(keyed[i - 1]) || std::get<2>(keyed[i]) != std::get<2>(keyed[i - 1])) {
+      td.group_keys.push_back(std::get<0>(keyed[i]));
+      td.group_keys.push_back(std::get<1>(keyed[i]));
+      td.group_keys.push_back(std::get<2>(keyed[i]));
+      ++td.groups;
+    }
+    td.stream_group[std::get<3>(keyed[i])] = td.groups - 1;
+  }
+  return THAPI_OK;
+}
+
 // Misc device words of one load.
 enum Misc {
   mHdrErr = 0,

@@ -137,6 +137,16 @@ void scan_exclusive_u64(uint64_t *data, uint64_t n, uint64_t *total_dev, Scratch
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
                       int bits, bool *result_in_alt, Scratch &sc, cudaStream_t s);
 
+// File header and tables of a trace, checked, with streams numbered into
+// (host, pid, tid) groups in order (api.cu).
+struct TraceDescription {
+  uint32_t P = 0, n_streams = 0, n_classes = 0, n_funcs = 0, n_hosts = 0, groups = 0;
+  uint64_t n_packets = 0, packets_off = 0;
+  std::vector<uint64_t> cls;
+  std::vector<uint32_t> stream_group, group_keys;
+};
+int describe_device_trace(const uint8_t *dev, uint64_t nbytes, cudaStream_t s, TraceDescription &td);
+
 // Scratch allocator used inside one library call: every buffer it hands out
 // is released (in stream order) by release_all.
 struct Scratch {

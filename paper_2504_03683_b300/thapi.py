@@ -31,6 +31,7 @@ EXPORTED = (
     "thapi_trace_load_device", "thapi_trace_free", "thapi_tally", "thapi_timeline", "thapi_tally_device",
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
+    "thapi_tally_static",
 )
 
 
@@ -105,6 +106,7 @@ def library():
         "thapi_ctx_set_timing": ([vp, i32], i32),
         "thapi_trace_timing": ([vp, u64, P(LoadTiming)], i32),
         "thapi_kernel_launches": ([], u64),
+        "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -264,6 +266,18 @@ def thapi_trace_timing(ctx: int, trace_id: int) -> dict:
 
 def thapi_kernel_launches() -> int:
     return int(library().thapi_kernel_launches())
+
+
+def thapi_tally_static(dev_ptr: int, nbytes: int, rows_dev_ptr: int, cap: int, stream=None):
+    """Tally of a device-resident trace using only the library's static device
+    scratch (for callers that must not allocate device memory); rows go to
+    device memory.  Returns (n_rows, diag dict)."""
+    n = ctypes.c_uint64()
+    d = Diag()
+    _check(library().thapi_tally_static(ctypes.c_void_p(dev_ptr), nbytes, ctypes.c_void_p(rows_dev_ptr), cap,
+                                        ctypes.byref(n), ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream))),
+           "thapi_tally_static")
+    return n.value, d.as_dict()
 
 
 # ------------------------------------------------- torch device memory
