@@ -463,10 +463,18 @@ int Loader::run() {
   const uint32_t emax_main = ((P - kPacketHeader) / 4) / 4;
   const int stages = n ? pick_stages(c_, P, emax_main, L.n_classes, F) : 1;
   if (!stages) return THAPI_E_UNSUPPORTED;
+  // warp-per-packet kernel for packets up to 32 KB, the CTA kernel otherwise
+  const bool warp_path = analyze_warp_bw(P) != 0;
   uint64_t grid = 1, per = 1;
   if (n) {
-    const uint32_t smem = analyze_smem_bytes(P, emax_main, stages, L.n_classes, F);
-    grid = (uint64_t)c_->num_sms * blocks_per_sm(c_, smem);
+    if (warp_path) {
+      const uint32_t smem = analyze_warp_smem_bytes(P, F);
+      const int blocks = std::max(1, std::min(32, c_->smem_per_sm / (int)(smem + 1024)));
+      grid = (uint64_t)c_->num_sms * blocks;
+    } else {
+      const uint32_t smem = analyze_smem_bytes(P, emax_main, stages, L.n_classes, F);
+      grid = (uint64_t)c_->num_sms * blocks_per_sm(c_, smem);
+    }
     per = (n + grid - 1) / grid;
     grid = (n + per - 1) / per;
   }
@@ -516,7 +524,10 @@ int Loader::run() {
     if (n) {
       ap.per_cta = (uint32_t)per;
       clk_.rec(PhaseClock::kAn0, s_);
-      CK(launch_analyze(ap, stages, (uint32_t)grid, s_, status));
+      if (warp_path)
+        CK(launch_analyze_warp(ap, (uint32_t)grid, s_, status));
+      else
+        CK(launch_analyze(ap, stages, (uint32_t)grid, s_, status));
       clk_.rec(PhaseClock::kAn1, s_);
       analyze_launches = 1;
       if ((rc = sync_misc()) != THAPI_OK) return rc;
@@ -609,23 +620,21 @@ int Loader::run() {
   uint32_t *v1 = alloc<uint32_t>(n_iv), *v2 = alloc<uint32_t>(n_iv);
   if (sc_.failed) return THAPI_E_NOMEM;
   const uint64_t tmin = misc_h_[mTmin], tmax = misc_h_[mTmax];
-  clk_.rec(PhaseClock::kCo0, s_);
-  launch_timeline_compact(slots, evbase, sum_nslot, obase, A, order, pk_stream, n, n_iv ? tmin : 0, rec, k1, v1,
-                          c_->num_sms, s_);
-  clk_.rec(PhaseClock::kCo1, s_);
   int bits = 0;
   if (n_iv && tmax > tmin) {
     const uint64_t span = tmax - tmin;
     while (bits < 64 && (span >> bits)) ++bits;
   }
-  bool alt = false;
-  radix_sort_pairs(k1, v1, k2, v2, n_iv, bits, &alt, sc_, s_);
-  if (sc_.failed) return THAPI_E_NOMEM;
-  clk_.rec(PhaseClock::kSo1, s_);
+  clk_.rec(PhaseClock::kCo0, s_);
+  launch_timeline_compact(slots, evbase, sum_nslot, obase, A, order, pk_stream, n, n_iv ? tmin : 0, rec, k1,
+                          bits <= 32, v1, c_->num_sms, s_);
+  clk_.rec(PhaseClock::kCo1, s_);
   tr_->tl_bytes = std::max<uint64_t>(n_iv, 1) * sizeof(thapi_interval);
   tr_->tl = static_cast<thapi_interval *>(dev_alloc(c_, tr_->tl_bytes, s_));
   if (!tr_->tl) return THAPI_E_NOMEM;
-  launch_timeline_gather(rec, alt ? v2 : v1, n_iv, tr_->tl, s_);
+  radix_sort_gather(k1, v1, k2, v2, n_iv, bits, rec, tr_->tl, sc_, s_);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  clk_.rec(PhaseClock::kSo1, s_);
   clk_.rec(PhaseClock::kGa1, s_);
   CK(cudaGetLastError());
   if ((rc = sync_misc()) != THAPI_OK) return rc;

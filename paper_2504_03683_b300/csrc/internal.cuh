@@ -136,6 +136,11 @@ struct Scratch;
 void scan_exclusive_u64(uint64_t *data, uint64_t n, uint64_t *total_dev, Scratch &sc, cudaStream_t s);
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n,
                       int bits, bool *result_in_alt, Scratch &sc, cudaStream_t s);
+void radix_sort_pairs32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
+                        bool *result_in_alt, Scratch &sc, cudaStream_t s);
+// keys hold u32 values when bits <= 32 (u64 otherwise); rec_out[i] = rec[value of the i-th smallest key]
+void radix_sort_gather(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
+                       const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc, cudaStream_t s);
 
 // File header and tables of a trace, checked, with streams numbered into
 // (host, pid, tid) groups in order (api.cu).
@@ -176,6 +181,10 @@ void launch_stream_bounds(const uint64_t *skey, const uint32_t *order, const uin
 // analyze.cu
 uint32_t analyze_smem_bytes(uint32_t P, uint32_t emax, int stages, uint32_t n_classes, uint32_t n_funcs);
 uint64_t analyze_frontier_slack(uint32_t grid);
+// analyze_warp.cu: one warp per packet (packets up to 32 KB)
+int analyze_warp_bw(uint32_t P);
+uint32_t analyze_warp_smem_bytes(uint32_t P, uint32_t n_funcs);
+cudaError_t launch_analyze_warp(const AnalyzeParams &p, uint32_t grid, cudaStream_t s, unsigned *status);
 cudaError_t launch_analyze(const AnalyzeParams &p, int stages, uint32_t grid, cudaStream_t s, unsigned *status);
 // frontier.cu
 void launch_frontier(const FrontierParams &p, cudaStream_t s);
@@ -187,7 +196,7 @@ void launch_tally_compact(const Cell *cells, uint64_t n, const uint32_t *group_k
 void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
                              const uint64_t *out_base, const uint32_t *A, const uint32_t *order,
                              const uint32_t *pk_stream, uint64_t n_order, uint64_t t_min, thapi_interval *rec,
-                             uint64_t *keys, uint32_t *vals, int num_sms, cudaStream_t s);
+                             void *keys, bool key32, uint32_t *vals, int num_sms, cudaStream_t s);
 void launch_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uint64_t n, thapi_interval *out,
                             cudaStream_t s);
 void launch_window_count(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *hi_dev,

@@ -1,7 +1,10 @@
-// radix.cu — stable LSD radix sort of (u64 key, u32 value) pairs, 8-bit
-// digits.  Per pass: tile digit histograms, one exclusive scan over the
-// (digit-major, tile-minor) histogram, then a stable scatter in which each
-// warp ranks its items with match-any and the CTA combines the warps' counts.
+// radix.cu — stable LSD radix sort of (key, u32 value) pairs, 8-bit digits,
+// keys u32 or u64.  Per pass: tile digit histograms (warp-aggregated),
+// one exclusive scan over the (digit-major, tile-minor) histogram, then a
+// stable scatter: each tile is loaded into registers, ranked per warp with
+// match-any, laid out digit by digit in shared memory, and written out in
+// runs of equal digits so that stores coalesce.  The last pass can gather the
+// final records (out[pos] = rec[value]) instead of writing (key, value).
 // Used to group packets by stream (stable in file order) and to order
 // timeline intervals by start time (stable over stream order).
 #include "internal.cuh"
@@ -17,87 +20,147 @@ constexpr int kWarps = kT / 32;
 constexpr int kRounds = 16;                   // 32-item rounds per warp
 constexpr int kTile = kWarps * 32 * kRounds;  // 4096 items
 
-__global__ void __launch_bounds__(kT) k_hist(const uint64_t *keys, uint64_t n, int shift, uint64_t *hist,
-                                              uint64_t ntiles) {
+template <class K>
+__global__ void __launch_bounds__(kT) k_hist(const K *keys, uint64_t n, int shift, uint64_t *hist, uint64_t ntiles) {
   __shared__ uint32_t h[kBins];
   for (int b = threadIdx.x; b < kBins; b += kT) h[b] = 0;
   __syncthreads();
-  uint64_t base = (uint64_t)blockIdx.x * kTile;
+  const int lane = threadIdx.x & 31;
+  const uint64_t base = (uint64_t)blockIdx.x * kTile;
   for (int k = threadIdx.x; k < kTile; k += kT) {
-    uint64_t i = base + k;
-    if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & (kBins - 1)], 1u);
+    const uint64_t i = base + k;
+    const bool in = i < n;
+    const uint32_t d = in ? (uint32_t)(keys[i] >> shift) & (kBins - 1) : kBins + lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    if (in && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
   for (int b = threadIdx.x; b < kBins; b += kT) hist[(uint64_t)b * ntiles + blockIdx.x] = h[b];
 }
 
-__global__ void __launch_bounds__(kT) k_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout,
-                                                 uint32_t *vout, uint64_t n, int shift, const uint64_t *offs,
-                                                 uint64_t ntiles) {
+template <class K>
+__global__ void __launch_bounds__(kT) k_scatter(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, uint64_t n,
+                                                 int shift, const uint64_t *offs, uint64_t ntiles,
+                                                 const thapi_interval *rec, thapi_interval *rec_out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  K *s_key = reinterpret_cast<K *>(smem);
+  uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + sizeof(K) * kTile);
   __shared__ uint32_t wcount[kWarps][kBins];
+  __shared__ uint32_t dstart[kBins];  // first tile-local index of each digit
+  __shared__ uint64_t dglob[kBins];   // first global index of each digit for this tile
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int b = lane; b < kBins; b += 32) wcount[warp][b] = 0;
   __syncwarp();
   const uint64_t wbase = (uint64_t)blockIdx.x * kTile + (uint64_t)warp * 32 * kRounds;
   const uint32_t lt = (1u << lane) - 1u;
-  uint32_t local[kRounds];
-  uint32_t dig[kRounds];
+  K key[kRounds];
+  uint32_t val[kRounds];
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
-    uint64_t i = wbase + (uint64_t)r * 32 + lane;
-    bool valid = i < n;
-    uint32_t d = valid ? ((uint32_t)(kin[i] >> shift) & (kBins - 1)) : kBins + lane;
-    uint32_t peers = __match_any_sync(0xffffffffu, d);
-    uint32_t rank = __popc(peers & lt);
-    uint32_t before = valid ? wcount[warp][d] : 0;
+    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+    key[r] = i < n ? kin[i] : (K)0;
+    val[r] = i < n ? vin[i] : 0u;
+  }
+  uint32_t local[kRounds];
+#pragma unroll
+  for (int r = 0; r < kRounds; ++r) {
+    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
+    const bool valid = i < n;
+    const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & (kBins - 1)) : kBins + lane;
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t rank = __popc(peers & lt);
+    const uint32_t before = valid ? wcount[warp][d] : 0u;
     __syncwarp();
     if (valid && rank == 0) wcount[warp][d] = before + __popc(peers);
     __syncwarp();
     local[r] = before + rank;
-    dig[r] = d;
   }
   __syncthreads();
-  // exclusive prefix over warps for each digit
+  // per digit: exclusive prefix over warps, the tile's count, and its global start
   for (int b = threadIdx.x; b < kBins; b += kT) {
     uint32_t run = 0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-      uint32_t t = wcount[w][b];
+      const uint32_t t = wcount[w][b];
       wcount[w][b] = run;
       run += t;
     }
+    dstart[b] = run;  // temporarily the tile count of digit b
+    dglob[b] = offs[(uint64_t)b * ntiles + blockIdx.x];
   }
   __syncthreads();
+  if (warp == 0) {  // exclusive scan of the tile's digit counts
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < kBins; b0 += 32) {
+      const uint32_t c = dstart[b0 + lane];
+      uint32_t inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+      }
+      dstart[b0 + lane] = carry + inc - c;
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+  }
+  __syncthreads();
+  // lay the tile out digit by digit in shared memory
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
-    uint64_t i = wbase + (uint64_t)r * 32 + lane;
+    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
     if (i < n) {
-      uint32_t d = dig[r];
-      uint64_t pos = offs[(uint64_t)d * ntiles + blockIdx.x] + wcount[warp][d] + local[r];
-      kout[pos] = kin[i];
-      vout[pos] = vin[i];
+      const uint32_t d = (uint32_t)(key[r] >> shift) & (kBins - 1);
+      const uint32_t at = dstart[d] + wcount[warp][d] + local[r];
+      s_key[at] = key[r];
+      s_val[at] = val[r];
+    }
+  }
+  __syncthreads();
+  // write runs of equal digits to consecutive global positions
+  const uint64_t rest = n - (uint64_t)blockIdx.x * kTile;
+  const uint64_t tile_n = rest < (uint64_t)kTile ? rest : (uint64_t)kTile;
+  for (uint32_t j = threadIdx.x; j < tile_n; j += kT) {
+    const K k = s_key[j];
+    const uint32_t d = (uint32_t)(k >> shift) & (kBins - 1);
+    const uint64_t pos = dglob[d] + (j - dstart[d]);
+    if (rec_out) {
+      rec_out[pos] = rec[s_val[j]];
+    } else {
+      kout[pos] = k;
+      vout[pos] = s_val[j];
     }
   }
 }
 
-}  // namespace
-
-void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
-                      bool *result_in_alt, Scratch &sc, cudaStream_t s) {
+template <class K>
+void sort_impl(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_t n, int bits, bool *result_in_alt,
+               const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc, cudaStream_t s) {
   *result_in_alt = false;
-  if (n <= 1 || bits <= 0) return;
-  uint64_t ntiles = (n + kTile - 1) / kTile;
+  const bool gather = rec_out != nullptr;
+  if (n == 0) return;
+  if (bits <= 0) {
+    if (gather) {
+      launch_timeline_gather(rec, vals, n, rec_out, s);
+    }
+    return;
+  }
+  const uint64_t ntiles = (n + kTile - 1) / kTile;
   uint64_t *hist = static_cast<uint64_t *>(sc.get(ntiles * kBins * sizeof(uint64_t)));
   if (!hist) return;
-  uint64_t *ki = keys, *ko = keys_alt;
+  const size_t smem = (sizeof(K) + sizeof(uint32_t)) * kTile;
+  cudaFuncSetAttribute(k_scatter<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  K *ki = keys, *ko = keys_alt;
   uint32_t *vi = vals, *vo = vals_alt;
   bool alt = false;
   for (int shift = 0; shift < bits; shift += kBits) {
-    k_hist<<<(unsigned)ntiles, kT, 0, s>>>(ki, n, shift, hist, ntiles);
+    const bool last = shift + kBits >= bits;
+    k_hist<K><<<(unsigned)ntiles, kT, 0, s>>>(ki, n, shift, hist, ntiles);
     scan_exclusive_u64(hist, ntiles * kBins, nullptr, sc, s);
-    k_scatter<<<(unsigned)ntiles, kT, 0, s>>>(ki, vi, ko, vo, n, shift, hist, ntiles);
+    k_scatter<K><<<(unsigned)ntiles, kT, smem, s>>>(ki, vi, ko, vo, n, shift, hist, ntiles, rec,
+                                                     last && gather ? rec_out : nullptr);
     count_launches(2);
-    uint64_t *tk = ki;
+    if (last && gather) break;
+    K *tk = ki;
     ki = ko;
     ko = tk;
     uint32_t *tv = vi;
@@ -106,6 +169,30 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
     alt = !alt;
   }
   *result_in_alt = alt;
+}
+
+}  // namespace
+
+void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
+                      bool *result_in_alt, Scratch &sc, cudaStream_t s) {
+  sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, nullptr, nullptr, sc, s);
+}
+
+void radix_sort_pairs32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
+                        bool *result_in_alt, Scratch &sc, cudaStream_t s) {
+  sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, nullptr, nullptr, sc, s);
+}
+
+// Sorts (key, value) pairs and writes rec_out[i] = rec[value of the i-th smallest key] (stable).
+void radix_sort_gather(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
+                       const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc, cudaStream_t s) {
+  bool alt = false;
+  if (bits <= 32) {
+    sort_impl<uint32_t>(reinterpret_cast<uint32_t *>(keys), vals, reinterpret_cast<uint32_t *>(keys_alt), vals_alt, n,
+                        bits, &alt, rec, rec_out, sc, s);
+  } else {
+    sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, &alt, rec, rec_out, sc, s);
+  }
 }
 
 }  // namespace thapi

@@ -15,7 +15,7 @@ namespace thapi {
 __global__ void k_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
                                    const uint64_t *out_base, const uint32_t *A, const uint32_t *order,
                                    const uint32_t *pk_stream, uint64_t n_order, uint64_t t_min,
-                                   thapi_interval *rec, uint64_t *keys, uint32_t *vals) {
+                                   thapi_interval *rec, void *keys, bool key32, uint32_t *vals) {
   const int lane = threadIdx.x & 31;
   const uint64_t wg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -43,7 +43,11 @@ __global__ void k_timeline_compact(const thapi_interval *slots, const uint64_t *
         iv.stream_id = stream;
         iv.flags &= kIvErr;
         rec[at] = iv;
-        keys[at] = iv.start_ns - t_min;
+        const uint64_t key = iv.start_ns - t_min;
+        if (key32)
+          static_cast<uint32_t *>(keys)[at] = (uint32_t)key;
+        else
+          static_cast<uint64_t *>(keys)[at] = key;
         vals[at] = (uint32_t)at;
       }
       ob += __popc(bal);
@@ -93,14 +97,14 @@ namespace thapi {
 void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
                              const uint64_t *out_base, const uint32_t *A, const uint32_t *order,
                              const uint32_t *pk_stream, uint64_t n_order, uint64_t t_min, thapi_interval *rec,
-                             uint64_t *keys, uint32_t *vals, int num_sms, cudaStream_t s) {
+                             void *keys, bool key32, uint32_t *vals, int num_sms, cudaStream_t s) {
   if (!n_order) return;
   uint64_t warps = n_order;
   uint64_t cap = (uint64_t)num_sms * 64;  // 64 warps per SM worth of CTAs
   if (warps > cap) warps = cap;
   unsigned grid = (unsigned)((warps * 32 + 255) / 256);
   k_timeline_compact<<<grid, 256, 0, s>>>(slots, evbase, nslot, out_base, A, order, pk_stream, n_order, t_min, rec,
-                                          keys, vals);
+                                          keys, key32, vals);
   count_launches(1);
 }
 
