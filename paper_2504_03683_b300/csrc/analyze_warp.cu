@@ -1,31 +1,33 @@
 // analyze_warp.cu — decode + in-packet pairing + tally, one warp per packet.
 //
-// Each persistent CTA is one warp and walks a contiguous run of the
-// stream-ordered packet list; the next packet is staged with a TMA bulk copy
-// (mbarrier completion) as soon as the current packet's bytes are decoded.
-// Every lane owns a 32*BW-word segment of the packet:
+// A CTA holds NW independent warps that share the class table and two tally
+// tables.  The CTA takes a contiguous run of the stream-ordered packet list
+// and its warps take the run's packets in turn.  Each warp stages its packet
+// with a TMA bulk copy (mbarrier completion) and then works on it alone:
 //
-//  1. boundaries: each lane walks its segment speculatively from the segment
-//     start (marking the offsets it visits), then the warp stitches the
-//     segments: a lane assumes its entry offset is its predecessor's
+//  1. boundaries: every lane walks a 32*BW-word segment speculatively from
+//     the segment start, marking the offsets it visits; the warp stitches
+//     the segments (a lane assumes its entry offset is its predecessor's
 //     speculative exit; the first lane whose exit breaks that assumption
-//     hands its successor the right entry (one ballot round per such lane).
+//     hands its successor the right entry, one ballot round per such lane).
 //     The marks are then exactly the event starts of the chain from offset 0.
-//  2. validation and per-lane summaries (events, entries, timestamp monoid,
-//     depth monoid, deepest local stack), then warp shuffle scans: each lane
-//     learns its first event index, timestamp and depth.
-//  3. decode with a per-lane call stack: entries are pushed, exits pop the
+//  2. the event offsets are compacted in order and dealt out in equal runs,
+//     one run per lane, so that every lane decodes the same number of events;
+//  3. validation and per-lane summaries (entries, timestamp monoid, depth
+//     monoid, stack slots used), then warp shuffle scans of the summaries;
+//  4. decode with a per-lane call stack: entries are pushed, exits pop the
 //     lane's own entries (pairs are tallied and their interval slots written
-//     at once); exits on an empty lane stack are lane-pending, entries left
-//     are lane-open.
-//  4. warp merge of the lane frontiers with the bracket monoid
+//     at once), exits on an empty lane stack are kept as lane-pending;
+//  5. merge of the lane frontiers with the bracket monoid
 //     (p1,o1).(p2,o2) = (p1 + max(p2-o1,0), o2 + max(o1-p2,0)): the k-th
-//     pending exit of lane j pops height A_j-1-k, held by the latest earlier
-//     lane whose base is <= that height; what no lane of the packet pops
-//     becomes the packet's frontier (pending exits, open entries) for
-//     frontier.cu.
-// Packets whose lane stacks would exceed kStack entries go to the CTA kernel
-// of analyze.cu (pushed on the fallback list).
+//     pending exit of lane i pops height A_i-1-k, held by the latest earlier
+//     lane whose base is <= that height (found from per-height ballots);
+//     what no lane of the packet pops is the packet's frontier (pending exits,
+//     open entries), resolved across packets by frontier.cu.
+// Packets with more than kEvMax events, or whose lanes need more than kStack
+// stack slots, are appended to the fallback list for the CTA kernel.
+#include <algorithm>
+
 #include "device_util.cuh"
 #include "internal.cuh"
 
@@ -34,61 +36,70 @@ namespace thapi {
 namespace {
 using namespace dev;
 
-constexpr int kStack = 8;                 // per-lane stack / pending capacity
-constexpr uint32_t kChunk = 2048;         // frontier items grabbed per global atomic
-constexpr int kTallySmemMax = 512;
+constexpr int kStack = 8;              // lane stack slots (pending exits below open entries)
+constexpr uint32_t kEvMax = 1024;      // events of one packet the warp path takes
+constexpr uint32_t kClsMax = 4096;     // class rows held in shared memory
+constexpr uint32_t kTallyMax = 512;    // functions tallied in shared memory
+constexpr uint32_t kHMax = 64;         // heights with a precomputed owner mask
+constexpr uint32_t kChunk = 2048;      // frontier items grabbed per global atomic
+constexpr uint32_t kMaxWarps = 16;     // warps per CTA
+
+__host__ __device__ inline uint32_t rup(uint32_t v, uint32_t a) { return (v + a - 1u) / a * a; }
 
 struct WLayout {
-  uint32_t off_buf, off_ots, off_pts, off_ofn, off_orank, off_onp, off_pfn, off_olvl, off_perr, off_base, off_tally,
-      total;
+  uint32_t off_stk, off_off, off_bpc, off_hm, off_bar, warp_bytes;  // within one warp's block
+  uint32_t off_ctab, off_cfn, off_tally, total;                     // CTA-wide
 };
 
-__host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t n_funcs, bool tally_smem) {
+__host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t NW, uint32_t NC, uint32_t F, bool tally_smem) {
   WLayout L;
-  uint32_t o = 16;  // mbarrier
-  L.off_buf = 128;
-  o = L.off_buf + P + 48;  // packet + zeroed tail
-  o = (o + 15u) & ~15u;
-  L.off_ots = o;
-  o += 32 * kStack * 8;
-  L.off_pts = o;
-  o += 32 * kStack * 8;
-  L.off_ofn = o;
-  o += 32 * kStack * 2;
-  L.off_orank = o;
-  o += 32 * kStack * 2;
-  L.off_onp = o;
-  o += 32 * kStack * 2;
-  L.off_pfn = o;
-  o += 32 * kStack * 2;
-  L.off_olvl = o;
-  o += 32 * kStack;
-  L.off_perr = o;
-  o += 32 * kStack;
-  L.off_base = o;
-  o += 32 * 4;
-  o = (o + 15u) & ~15u;
+  uint32_t o = rup(P + 48u, 128u);  // packet (header + content) and a zeroed tail
+  L.off_stk = o;
+  o += kStack * 32u * 16u;  // slot timestamps, slot metadata
+  L.off_off = o;
+  o += kEvMax * 2u;
+  L.off_bpc = o;
+  o += 32u * 4u;
+  L.off_hm = o;
+  o += kHMax * 4u;
+  L.off_bar = o;
+  o += 16u;
+  L.warp_bytes = rup(o, 128u);
+  o = L.warp_bytes * NW;
+  L.off_ctab = o;
+  o += rup((NC + 1u) * 4u, 16u);
+  L.off_cfn = o;
+  o += rup(NC * 2u, 16u);
   L.off_tally = o;
-  if (tally_smem) o += n_funcs * 24 + 16;
-  L.total = (o + 127u) & ~127u;
+  if (tally_smem) o += 2u * F * 24u;
+  L.total = rup(o, 128u);
   return L;
 }
 
-// Event chain step from offset o (unknown class ids step one word).
-__device__ __forceinline__ uint32_t step_from(const uint32_t *C, uint32_t o, const uint64_t *cls, uint32_t ncls) {
+// Shared-memory class row: fixed words (14 bits) | kind << 14 (3) | (result word + 1) << 17 (15).
+__device__ __forceinline__ uint32_t row_fixedw(uint32_t r) { return r & 0x3FFFu; }
+__device__ __forceinline__ uint32_t row_kind(uint32_t r) { return (r >> 14) & 7u; }
+__device__ __forceinline__ int32_t row_resw(uint32_t r) { return (int32_t)(r >> 17) - 1; }
+
+// Event chain step from word offset o; class ids out of range step one word.
+__device__ __forceinline__ uint32_t step(const uint32_t *C, uint32_t o, const uint32_t *ctab, uint32_t NC) {
   const uint32_t w0 = C[o], w1 = C[o + 1];
   const uint32_t c = w1 & 0xFFFFu;
-  if (c >= ncls) return o + 1;
-  return o + 2 + ((w0 >> 26) & 2u) + cls_fixedw(__ldg(cls + c)) + (((w1 >> 16) + 3u) >> 2);
+  const bool ok = c < NC;
+  const uint32_t r = ctab[ok ? c : NC];
+  const uint32_t len = 2u + ((w0 >> 26) & 2u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+  return o + (ok ? len : 1u);
 }
 
-template <int BW>
-__device__ __forceinline__ uint32_t walk(const uint32_t *C, uint32_t o, uint32_t a, uint32_t b, const Bits<BW> *stop,
-                                         Bits<BW> &marks, const uint64_t *cls, uint32_t ncls) {
+// Walks from o while o < b, marking the offsets visited; with STOP, returns at
+// the first offset already marked in `stop`.
+template <bool STOP, int BW>
+__device__ __forceinline__ uint32_t walk(const uint32_t *C, uint32_t o, uint32_t a, uint32_t b, const Bits<BW> &stop,
+                                         Bits<BW> &marks, const uint32_t *ctab, uint32_t NC) {
   while (o < b) {
-    if (stop && stop->test(o - a)) return o;
+    if (STOP && stop.test(o - a)) return o;
     marks.set(o - a);
-    o = step_from(C, o, cls, ncls);
+    o = step(C, o, ctab, NC);
   }
   return o;
 }
@@ -101,75 +112,108 @@ __device__ __forceinline__ void bm(uint32_t &p1, uint32_t &o1, uint32_t p2, uint
   o1 = no;
 }
 
+// Interval slot, written as three 8-byte words.
+__device__ __forceinline__ void put_interval(thapi_interval *dst, uint64_t start, uint64_t end, uint32_t np,
+                                             uint32_t fn, uint32_t lvl, uint32_t flags) {
+  unsigned long long *q = reinterpret_cast<unsigned long long *>(dst);
+  q[0] = start;
+  q[1] = end;
+  q[2] = (unsigned long long)np | ((unsigned long long)fn << 32) | ((unsigned long long)lvl << 48) |
+         ((unsigned long long)flags << 56);
+}
+
+// Open-entry slot metadata: func | rank << 16 | level << 32 | pending-before << 40.
+// Pending-exit slot metadata: func | error << 16.
+__device__ __forceinline__ uint64_t open_meta(uint32_t fn, uint32_t rank, uint32_t lvl, uint32_t np) {
+  return (uint64_t)fn | ((uint64_t)rank << 16) | ((uint64_t)lvl << 32) | ((uint64_t)np << 40);
+}
+
 template <int BW, bool TALLY_SMEM>
-__global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned int *status) {
+__global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p, uint32_t NW, unsigned int *status) {
   extern __shared__ __align__(128) uint8_t sm[];
   constexpr uint32_t SEGW = 32u * BW;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = threadIdx.x >> 5;
   const uint32_t F = p.n_funcs;
   const uint32_t NC = p.n_classes;
-  const WLayout L = wlayout(p.P, F, TALLY_SMEM);
-  uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
-  uint8_t *buf = sm + L.off_buf;
+  const WLayout L = wlayout(p.P, NW, NC, F, TALLY_SMEM);
+  uint8_t *wb = sm + warp * L.warp_bytes;
+  uint8_t *buf = wb;
   uint32_t *C = reinterpret_cast<uint32_t *>(buf + kPacketHeader);
-  uint64_t *o_ts = reinterpret_cast<uint64_t *>(sm + L.off_ots);
-  uint64_t *p_ts = reinterpret_cast<uint64_t *>(sm + L.off_pts);
-  uint16_t *o_fn = reinterpret_cast<uint16_t *>(sm + L.off_ofn);
-  uint16_t *o_rank = reinterpret_cast<uint16_t *>(sm + L.off_orank);
-  uint16_t *o_np = reinterpret_cast<uint16_t *>(sm + L.off_onp);
-  uint16_t *p_fn = reinterpret_cast<uint16_t *>(sm + L.off_pfn);
-  uint8_t *o_lvl = sm + L.off_olvl;
-  uint8_t *p_err = sm + L.off_perr;
-  uint32_t *s_base = reinterpret_cast<uint32_t *>(sm + L.off_base);
-  uint32_t *t_cnt = reinterpret_cast<uint32_t *>(sm + L.off_tally);
-  uint32_t *t_err = t_cnt + F;
-  uint32_t *t_mn = t_err + F;
-  uint32_t *t_mx = t_mn + F;
-  unsigned long long *t_tot = reinterpret_cast<unsigned long long *>(sm + L.off_tally + ((F * 16u + 15u) & ~15u));
+  uint64_t *stk_ts = reinterpret_cast<uint64_t *>(wb + L.off_stk);
+  uint64_t *stk_md = stk_ts + kStack * 32;
+  uint16_t *s_off = reinterpret_cast<uint16_t *>(wb + L.off_off);
+  uint32_t *s_bpc = reinterpret_cast<uint32_t *>(wb + L.off_bpc);
+  uint32_t *s_hm = reinterpret_cast<uint32_t *>(wb + L.off_hm);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(wb + L.off_bar);
+  uint32_t *ctab = reinterpret_cast<uint32_t *>(sm + L.off_ctab);
+  uint16_t *cfn = reinterpret_cast<uint16_t *>(sm + L.off_cfn);
+  unsigned long long *t_ce = reinterpret_cast<unsigned long long *>(sm + L.off_tally);  // count | errors << 32
+  unsigned long long *t_tot = t_ce + 2 * F;
+  uint32_t *t_mn = reinterpret_cast<uint32_t *>(t_tot + 2 * F);
+  uint32_t *t_mx = t_mn + 2 * F;
 
   const uint64_t w_begin = (uint64_t)blockIdx.x * p.per_cta;
   const uint64_t w_end = (w_begin + p.per_cta < p.n_order) ? w_begin + p.per_cta : p.n_order;
-  if (w_begin >= w_end) return;
+  if (w_begin >= w_end) return;  // uniform over the CTA
   auto pos_of = [&](uint64_t w) -> uint64_t { return p.poslist ? p.poslist[w] : w; };
 
-  if (TALLY_SMEM)
-    for (uint32_t f = lane; f < F; f += 32) {
-      t_cnt[f] = 0;
-      t_err[f] = 0;
-      t_mn[f] = 0xFFFFFFFFu;
-      t_mx[f] = 0;
-      t_tot[f] = 0;
+  for (uint32_t c = threadIdx.x; c <= NC; c += blockDim.x) {
+    if (c < NC) {
+      const uint64_t r = p.classes[c];
+      ctab[c] = cls_fixedw(r) | (cls_kind(r) << 14) | ((uint32_t)(cls_resw(r) + 1) << 17);
+      cfn[c] = (uint16_t)cls_func(r);
+    } else {
+      ctab[c] = 0;
     }
+  }
+  // tally tables: 0 for the group of the run's first packet, 1 for its last
+  const uint32_t gA = p.desc[pos_of(w_begin)].group, gB = p.desc[pos_of(w_end - 1)].group;
+  if (TALLY_SMEM)
+    for (uint32_t i = threadIdx.x; i < 2 * F; i += blockDim.x) {
+      t_ce[i] = 0;
+      t_tot[i] = 0;
+      t_mn[i] = 0xFFFFFFFFu;
+      t_mx[i] = 0;
+    }
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
   auto issue = [&](const PkDesc &d) {
     const uint32_t bytes = align16(kPacketHeader + d.content);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, bytes);
     bulk_copy_g2s(buf, p.packets + (uint64_t)d.pk * p.P, bytes, bar);
   };
-  PkDesc dcur = load_desc(p.desc + pos_of(w_begin));
-  PkDesc dnext = dcur;
-  if (w_begin + 1 < w_end) dnext = load_desc(p.desc + pos_of(w_begin + 1));
-  if (lane == 0) {
-    mbar_init(bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    issue(dcur);
-  }
-  __syncwarp();
 
   uint64_t fr_base = 0;
   uint32_t fr_left = 0;  // lane 0: current frontier chunk
   unsigned long long n_mismatch = 0, n_other = 0, n_pairs = 0, n_events = 0, n_disc = 0, n_pk = 0, n_slots = 0;
   uint64_t tmin = ~0ull, tmax = 0;
   uint32_t phase = 0;
-  bool issued = true;  // a copy is in flight into buf
+  bool issued = false;  // a copy is in flight into buf
   bool timed_out = false;
 
-  for (uint64_t w = w_begin; w < w_end; ++w) {
+  uint64_t w = w_begin + warp;
+  PkDesc dcur{}, dnext{};
+  if (w < w_end) {
+    dcur = load_desc(p.desc + pos_of(w));
+    dnext = dcur;
+    if (w + NW < w_end) dnext = load_desc(p.desc + pos_of(w + NW));
+    if (lane == 0) issue(dcur);
+    issued = true;
+  }
+  __syncwarp();
+
+  for (; w < w_end; w += NW) {
     const PkDesc d = dcur;
     const uint64_t pos = pos_of(w);
-    const bool has_next = w + 1 < w_end;
-    dcur = dnext;  // next packet's descriptor (issued below once the buffer is free)
-    if (w + 2 < w_end) dnext = load_desc(p.desc + pos_of(w + 2));
+    const bool has_next = w + NW < w_end;
+    dcur = dnext;  // next packet's descriptor (its copy is issued once the buffer is free)
+    if (w + 2 * NW < w_end) dnext = load_desc(p.desc + pos_of(w + 2 * NW));
     const bool ok_wait = mbar_wait_bounded(bar, phase);
     if (__any_sync(0xffffffffu, !ok_wait)) {
       timed_out = true;
@@ -180,13 +224,14 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
     const uint32_t W = d.content >> 2;
     if (lane < 4) C[W + lane] = 0;
     __syncwarp();
+    const int tb = d.group == gA ? 0 : (d.group == gB ? 1 : -1);
 
     // ---- 1. boundaries
     const uint32_t a = (uint32_t)lane * SEGW;
     const uint32_t b = min(a + SEGW, W);
     Bits<BW> spec;
     spec.clear();
-    const uint32_t spec_x = a < b ? walk<BW>(C, a, a, b, nullptr, spec, p.classes, NC) : a;
+    const uint32_t spec_x = a < b ? walk<false, BW>(C, a, a, b, spec, spec, ctab, NC) : a;
     Bits<BW> bits;
     auto resolve = [&](uint32_t y) -> uint32_t {
       if (y == a && a < b) {
@@ -199,7 +244,7 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
       }
       Bits<BW> walked;
       walked.clear();
-      const uint32_t m = walk<BW>(C, y, a, b, &spec, walked, p.classes, NC);
+      const uint32_t m = walk<true, BW>(C, y, a, b, spec, walked, ctab, NC);
       if (m < b) {
         bits = spec;
         bits.keep_from(m - a);
@@ -225,105 +270,121 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
       }
     }
 
-    // ---- 2. validation + lane summaries
+    // ---- 2. compact the event offsets
     const uint32_t cnt = bits.count();
-    uint32_t n_entry = 0;
-    TsM tsum{0, 0};
-    DM dsum{0, 0};
-    int maxh = 0;
-    uint32_t ekey = 0xFFFFFFFFu;  // local index << 3 | code of the first bad event
-    {
-      uint32_t local = 0;
+    uint32_t cinc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, cinc, o);
+      if (lane >= o) cinc += u;
+    }
+    const uint32_t c_tot = __shfl_sync(0xffffffffu, cinc, 31);
+    bool fallback = c_tot > kEvMax || d.nev > kEvMax;
+    bool bad = false;
+    uint32_t e0 = 0, e1 = 0;
+    if (!fallback) {
+      uint32_t idx = cinc - cnt;
 #pragma unroll
       for (int k = 0; k < BW; ++k) {
         uint32_t m = bits.w[k];
         while (m) {
-          const uint32_t oo = a + k * 32 + (__ffs(m) - 1);
+          s_off[idx++] = (uint16_t)(a + k * 32 + (__ffs(m) - 1));
           m &= m - 1;
-          uint32_t code = 0;
-          const uint32_t w0 = C[oo], w1 = C[oo + 1];
-          const uint32_t c = w1 & 0xFFFFu;
-          uint64_t cr = 0;
-          const bool ext = (w0 & kExtBit) != 0;
-          if (oo + 2 > W) {
-            code = THAPI_E_TRUNCATED;
-          } else if ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) {
-            code = THAPI_E_FORMAT;
-          } else {
-            cr = __ldg(p.classes + c);
-            const uint32_t sz = 2 + (ext ? 2 : 0) + cls_fixedw(cr) + (((w1 >> 16) + 3u) >> 2);
-            if (oo + sz > W) code = THAPI_E_TRUNCATED;
-          }
-          if (code) {
-            if (ekey == 0xFFFFFFFFu) ekey = (local << 3) | code;
-          } else {
-            const uint32_t kd = cls_kind(cr);
-            const int e = kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
-            n_entry += kd == kEntry ? 1u : 0u;
-            dsum.s += e;
-            dsum.m = min(dsum.m, dsum.s);
-            maxh = max(maxh, dsum.s - dsum.m);
-            if (ext) {
-              tsum.has = 1;
-              tsum.v = (uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32);
-            } else {
-              tsum.v += w0 & kDeltaMask;
-            }
-          }
-          ++local;
+        }
+      }
+      const uint32_t per = (c_tot + 31u) >> 5;
+      e0 = min((uint32_t)lane * per, c_tot);
+      e1 = min(e0 + per, c_tot);
+    }
+    __syncwarp();
+
+    // ---- 3. validation + lane summaries over events [e0, e1)
+    uint32_t n_entry = 0;
+    TsM tsum{0, 0};
+    DM dsum{0, 0};
+    int slots_used = 0;
+    uint32_t ekey = 0xFFFFFFFFu;  // event index << 3 | code of the first bad event
+    for (uint32_t e = e0; e < e1; ++e) {
+      const uint32_t oo = s_off[e];
+      const uint32_t w0 = C[oo], w1 = C[oo + 1];
+      const uint32_t c = w1 & 0xFFFFu;
+      const bool ext = (w0 & kExtBit) != 0;
+      const uint32_t r = ctab[c < NC ? c : NC];
+      const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+      uint32_t code = 0;
+      if (oo + 2 > W)
+        code = THAPI_E_TRUNCATED;
+      else if ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0))
+        code = THAPI_E_FORMAT;
+      else if (oo + sz > W)
+        code = THAPI_E_TRUNCATED;
+      if (code) {
+        if (ekey == 0xFFFFFFFFu) ekey = (e << 3) | code;
+      } else {
+        const uint32_t kd = row_kind(r);
+        const int dv = kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
+        n_entry += kd == kEntry ? 1u : 0u;
+        dsum.s += dv;
+        dsum.m = min(dsum.m, dsum.s);
+        slots_used = max(slots_used, dsum.s - 2 * dsum.m);  // pending exits + open entries
+        if (ext) {
+          tsum.has = 1;
+          tsum.v = (uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32);
+        } else {
+          tsum.v += w0 & kDeltaMask;
         }
       }
     }
-    // warp scans (exclusive) of counts, timestamps, depth
-    uint32_t ci = cnt | (n_entry << 16);
+    // warp scans (exclusive) of entries, timestamps, depth
+    uint32_t ei = n_entry;
     TsM ti = tsum;
     DM di = dsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t uc = __shfl_up_sync(0xffffffffu, ci, o);
+      const uint32_t ue = __shfl_up_sync(0xffffffffu, ei, o);
       const uint32_t uh = __shfl_up_sync(0xffffffffu, ti.has, o);
       const uint64_t uv = __shfl_up_sync(0xffffffffu, ti.v, o);
       const int us = __shfl_up_sync(0xffffffffu, di.s, o);
       const int um = __shfl_up_sync(0xffffffffu, di.m, o);
       if (lane >= o) {
-        ci += uc;
+        ei += ue;
         ti = ts_op(TsM{uh, uv}, ti);
         di = d_op(DM{us, um}, di);
       }
     }
-    const uint32_t c_tot2 = __shfl_sync(0xffffffffu, ci, 31);
+    const uint32_t e_tot = __shfl_sync(0xffffffffu, ei, 31);
     const int dtot_s = __shfl_sync(0xffffffffu, di.s, 31), dtot_m = __shfl_sync(0xffffffffu, di.m, 31);
-    uint32_t cex2 = __shfl_up_sync(0xffffffffu, ci, 1);
+    uint32_t e_ex = __shfl_up_sync(0xffffffffu, ei, 1);
     uint32_t hex = __shfl_up_sync(0xffffffffu, ti.has, 1);
     uint64_t vex = __shfl_up_sync(0xffffffffu, ti.v, 1);
     int sex = __shfl_up_sync(0xffffffffu, di.s, 1), mex = __shfl_up_sync(0xffffffffu, di.m, 1);
     if (lane == 0) {
-      cex2 = 0;
+      e_ex = 0;
       hex = 0;
       vex = 0;
       sex = 0;
       mex = 0;
     }
-    const uint32_t c_ex = cex2 & 0xFFFFu, e_ex = cex2 >> 16;
-    const uint32_t c_tot = c_tot2 & 0xFFFFu, e_tot = c_tot2 >> 16;
-    const uint32_t gkey = __reduce_min_sync(0xffffffffu, ekey == 0xFFFFFFFFu ? 0xFFFFFFFFu : ekey + (c_ex << 3));
-    const bool counts_ok = c_tot == d.nev;
-    const bool deep = __any_sync(0xffffffffu, maxh > kStack || -dsum.m > kStack);
-    const bool bad = gkey != 0xFFFFFFFFu || !counts_ok;
-    if (bad || deep) {
+    const uint32_t gkey = __reduce_min_sync(0xffffffffu, ekey);
+    if (!fallback) {
+      bad = gkey != 0xFFFFFFFFu || c_tot != d.nev;
+      fallback = !bad && __any_sync(0xffffffffu, slots_used > kStack);
+    }
+    if (bad || fallback) {
       if (lane == 0) {
         if (bad)
           atomicMin(p.content_err, gkey != 0xFFFFFFFFu ? err_key(d.pk, gkey >> 3, gkey & 7u)
                                                        : err_key(d.pk, c_tot, THAPI_E_FORMAT));
-        else  // lane stacks too small for this packet: the CTA kernel takes it
+        else  // the CTA kernel takes it
           p.dense_list[atomicAdd(p.dense_count, 1ull)] = (uint32_t)pos;
       }
       __syncwarp();
       if (lane == 0 && has_next) issue(dcur);
       issued = has_next;
-    } else {
+      continue;
+    }
 
-    // ---- 3. decode with per-lane call stacks
+    // ---- 4. decode with per-lane call stacks
     const uint32_t P_p = (uint32_t)(-dtot_m);
     const uint32_t O_p = (uint32_t)(dtot_s - dtot_m);
     uint64_t fbase = 0;
@@ -346,92 +407,94 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
       }
     }
     fbase = __shfl_sync(0xffffffffu, fbase, 0);
-    const TsM t_ex = TsM{hex, vex};
-    uint64_t t = t_ex.has ? t_ex.v : d.tsb + t_ex.v;
-    int depth = sex;  // packet-relative depth before the next event
+    thapi_interval *const pslots = p.slots ? p.slots + d.evbase : nullptr;
+    Cell *const gcells = p.tally + (uint64_t)d.group * F;
+    auto tally = [&](uint32_t fn, uint64_t dur, uint32_t err) {
+      if (TALLY_SMEM && tb >= 0 && dur < (1ull << 32)) {
+        const uint32_t i = (uint32_t)tb * F + fn;
+        atomicAdd(&t_ce[i], 1ull | ((unsigned long long)err << 32));
+        atomicAdd(&t_tot[i], (unsigned long long)dur);
+        atomicMin(&t_mn[i], (uint32_t)dur);
+        atomicMax(&t_mx[i], (uint32_t)dur);
+      } else {
+        Cell &cell = gcells[fn];
+        atomicAdd(&cell.count, 1ull);
+        atomicAdd(&cell.total, (unsigned long long)dur);
+        atomicMin(&cell.mn, (unsigned long long)dur);
+        atomicMax(&cell.mx, (unsigned long long)dur);
+        if (err) atomicAdd(&cell.err, 1ull);
+      }
+    };
+    uint32_t valid = 0, mism = 0;
+    // one pair: entry (ets, metadata em) closed by an exit (xts, xfn, xerr)
+    auto emit = [&](uint64_t ets, uint64_t em, uint64_t xts, uint32_t xfn, uint32_t xerr) {
+      const uint32_t efn = (uint32_t)(em & 0xFFFFu);
+      uint32_t flags = 0;
+      if (efn == xfn) {
+        ++valid;
+        flags = kIvValid | xerr;
+        tally(xfn, xts - ets, xerr);
+      } else {
+        ++mism;  // mismatched pair: no interval
+      }
+      if (pslots)
+        put_interval(pslots + ((em >> 16) & 0xFFFFu), ets, xts, (uint32_t)((em >> 40) & 0xFFFFu), efn,
+                     (uint32_t)((em >> 32) & 0xFFu), flags);
+    };
+    uint64_t t = hex ? vex : d.tsb + vex;
+    int depth = sex;   // packet-relative depth before the next event
     int runmin = mex;  // packet-relative running minimum of the depth (<= 0)
     uint32_t rank = e_ex;
     uint32_t top = 0, pc = 0;
-    uint32_t valid = 0, mism = 0;
-    const uint32_t sb = (uint32_t)lane;  // stack entry i of this lane lives at i * 32 + lane
-#pragma unroll
-    for (int kk = 0; kk < BW; ++kk) {
-      uint32_t m = bits.w[kk];
-      while (m) {
-        const uint32_t oo = a + kk * 32 + (__ffs(m) - 1);
-        m &= m - 1;
-        const uint32_t w0 = C[oo], w1 = C[oo + 1];
-        const bool ext = (w0 & kExtBit) != 0;
-        const uint64_t cr = __ldg(p.classes + (w1 & 0xFFFFu));
-        const uint32_t kd = cls_kind(cr);
-        const uint32_t fn = cls_func(cr);
-        t = ext ? ((uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32)) : t + (w0 & kDeltaMask);
-        tmin = min(tmin, t);
-        tmax = max(tmax, t);
-        if (kd == kEntry) {
-          o_ts[top * 32 + sb] = t;
-          o_fn[top * 32 + sb] = (uint16_t)fn;
-          o_rank[top * 32 + sb] = (uint16_t)rank;
-          o_lvl[top * 32 + sb] = (uint8_t)min(depth - runmin, 255);
-          o_np[top * 32 + sb] = (uint16_t)(-runmin);
-          ++top;
-          ++rank;
-          ++depth;
-        } else if (kd == kExit) {
-          const int32_t rw = cls_resw(cr);
-          const uint32_t err = (rw >= 0 && C[oo + 2 + (ext ? 2 : 0) + rw] != 0) ? 1u : 0u;
-          --depth;
-          runmin = min(runmin, depth);
-          if (top) {
-            --top;
-            const uint64_t ets = o_ts[top * 32 + sb];
-            const uint32_t efn = o_fn[top * 32 + sb];
-            thapi_interval iv;
-            iv.start_ns = ets;
-            iv.end_ns = t;
-            iv.stream_id = o_np[top * 32 + sb];
-            iv.func_id = (uint16_t)efn;
-            iv.level = o_lvl[top * 32 + sb];
-            if (efn == fn) {
-              ++valid;
-              iv.flags = (uint8_t)(kIvValid | err);
-              const uint64_t dur = t - ets;
-              if (TALLY_SMEM && dur < (1ull << 32)) {
-                atomicAdd(&t_cnt[fn], 1u);
-                atomicAdd(&t_tot[fn], (unsigned long long)dur);
-                atomicMin(&t_mn[fn], (uint32_t)dur);
-                atomicMax(&t_mx[fn], (uint32_t)dur);
-                if (err) atomicAdd(&t_err[fn], 1u);
-              } else {
-                Cell &cell = p.tally[(uint64_t)d.group * F + fn];
-                atomicAdd(&cell.count, 1ull);
-                atomicAdd(&cell.total, (unsigned long long)dur);
-                atomicMin(&cell.mn, (unsigned long long)dur);
-                atomicMax(&cell.mx, (unsigned long long)dur);
-                if (err) atomicAdd(&cell.err, 1ull);
-              }
-            } else {
-              iv.flags = 0;  // mismatched pair: no interval
-              ++mism;
-            }
-            if (p.slots) p.slots[d.evbase + o_rank[top * 32 + sb]] = iv;
-          } else {
-            p_ts[pc * 32 + sb] = t;
-            p_fn[pc * 32 + sb] = (uint16_t)fn;
-            p_err[pc * 32 + sb] = (uint8_t)err;
-            ++pc;
-          }
+    bool first = true;
+    for (uint32_t e = e0; e < e1; ++e) {
+      const uint32_t oo = s_off[e];
+      const uint32_t w0 = C[oo], w1 = C[oo + 1];
+      const uint32_t c = w1 & 0xFFFFu;
+      const bool ext = (w0 & kExtBit) != 0;
+      const uint32_t r = ctab[c];
+      const uint32_t kd = row_kind(r);
+      const uint32_t fn = cfn[c];
+      const uint64_t tn = ext ? ((uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32)) : t + (w0 & kDeltaMask);
+      if (ext || first || tn < t) {  // a new nondecreasing run of timestamps
+        if (!first) tmax = max(tmax, t);
+        tmin = min(tmin, tn);
+        first = false;
+      }
+      t = tn;
+      if (kd == kEntry) {
+        const uint32_t si = (pc + top) * 32 + (uint32_t)lane;
+        stk_ts[si] = t;
+        stk_md[si] = open_meta(fn, rank, (uint32_t)min(depth - runmin, 255), (uint32_t)(-runmin));
+        ++top;
+        ++rank;
+        ++depth;
+      } else if (kd == kExit) {
+        const int32_t rw = row_resw(r);
+        const uint32_t err = (rw >= 0 && C[oo + 2 + (ext ? 2 : 0) + rw] != 0) ? 1u : 0u;
+        --depth;
+        runmin = min(runmin, depth);
+        if (top) {
+          --top;
+          const uint32_t si = (pc + top) * 32 + (uint32_t)lane;
+          emit(stk_ts[si], stk_md[si], t, fn, err);
         } else {
-          ++n_other;
+          const uint32_t si = pc * 32 + (uint32_t)lane;
+          stk_ts[si] = t;
+          stk_md[si] = (uint64_t)fn | ((uint64_t)err << 16);
+          ++pc;
         }
+      } else {
+        ++n_other;
       }
     }
+    if (!first) tmax = max(tmax, t);
     __syncwarp();
     // the packet bytes are no longer needed: stage the next packet now
     if (lane == 0 && has_next) issue(dcur);
     issued = has_next;
 
-    // ---- 4. warp merge of the lane frontiers
+    // ---- 5. warp merge of the lane frontiers
     uint32_t sp = pc, so = top;  // inclusive bracket-monoid scan over lanes
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -450,8 +513,8 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
       A = 0;
     }
     const uint32_t base = A > pc ? A - pc : 0u;
-    s_base[lane] = base;
-    uint32_t later = base;  // min base of the lanes after me
+    s_bpc[lane] = base | (pc << 16);
+    uint32_t later;  // min base of the lanes after me
     {
       uint32_t suf = base;
 #pragma unroll
@@ -462,48 +525,33 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
       later = __shfl_down_sync(0xffffffffu, suf, 1);
       if (lane == 31) later = 0xFFFFFFFFu;
     }
+    // owner masks: bit j of s_hm[h] is set when lane j's base is <= h
+    const uint32_t hq = __reduce_max_sync(0xffffffffu, pc ? A : 0u);
+    const bool masks = hq <= kHMax;
+    if (masks)
+      for (uint32_t h = 0; h < hq; ++h) {
+        const uint32_t m = __ballot_sync(0xffffffffu, base <= h);
+        if (lane == 0) s_hm[h] = m;
+      }
     __syncwarp();
     // my pending exits: pop earlier lanes' opens, the rest leave the packet
     for (uint32_t k = 0; k < pc; ++k) {
-      const uint64_t xts = p_ts[k * 32 + sb];
-      const uint32_t xfn = p_fn[k * 32 + sb];
-      const uint32_t xerr = p_err[k * 32 + sb];
+      const uint32_t si = k * 32 + (uint32_t)lane;
+      const uint64_t xts = stk_ts[si];
+      const uint64_t xm = stk_md[si];
+      const uint32_t xfn = (uint32_t)(xm & 0xFFFFu), xerr = (uint32_t)((xm >> 16) & 1u);
       if (k < A) {
         const uint32_t h = A - 1 - k;
-        int j = lane - 1;
-        while (j > 0 && s_base[j] > h) --j;
-        const uint32_t it = (h - s_base[j]) * 32 + (uint32_t)j;
-        const uint64_t ets = o_ts[it];
-        const uint32_t efn = o_fn[it];
-        thapi_interval iv;
-        iv.start_ns = ets;
-        iv.end_ns = xts;
-        iv.stream_id = o_np[it];
-        iv.func_id = (uint16_t)efn;
-        iv.level = o_lvl[it];
-        if (efn == xfn) {
-          ++valid;
-          iv.flags = (uint8_t)(kIvValid | xerr);
-          const uint64_t dur = xts - ets;
-          if (TALLY_SMEM && dur < (1ull << 32)) {
-            atomicAdd(&t_cnt[xfn], 1u);
-            atomicAdd(&t_tot[xfn], (unsigned long long)dur);
-            atomicMin(&t_mn[xfn], (uint32_t)dur);
-            atomicMax(&t_mx[xfn], (uint32_t)dur);
-            if (xerr) atomicAdd(&t_err[xfn], 1u);
-          } else {
-            Cell &cell = p.tally[(uint64_t)d.group * F + xfn];
-            atomicAdd(&cell.count, 1ull);
-            atomicAdd(&cell.total, (unsigned long long)dur);
-            atomicMin(&cell.mn, (unsigned long long)dur);
-            atomicMax(&cell.mx, (unsigned long long)dur);
-            if (xerr) atomicAdd(&cell.err, 1ull);
-          }
+        int j;
+        if (masks) {
+          j = 31 - __clz(s_hm[h] & ((1u << lane) - 1u));
         } else {
-          iv.flags = 0;
-          ++mism;
+          j = lane - 1;
+          while (j > 0 && (s_bpc[j] & 0xFFFFu) > h) --j;
         }
-        if (p.slots) p.slots[d.evbase + o_rank[it]] = iv;
+        const uint32_t bj = s_bpc[j];
+        const uint32_t it = ((bj >> 16) + h - (bj & 0xFFFFu)) * 32 + (uint32_t)j;
+        emit(stk_ts[it], stk_md[it], xts, xfn, xerr);
       } else if (fbase != ~0ull) {
         Frontier fr;
         fr.ts = xts;
@@ -517,29 +565,25 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
     for (uint32_t i = 0; i < top; ++i) {
       const uint32_t h = base + i;
       if (h >= later) break;
-      const uint32_t it = i * 32 + sb;
+      const uint32_t si = (pc + i) * 32 + (uint32_t)lane;
+      const uint64_t ots = stk_ts[si];
+      const uint64_t om = stk_md[si];
+      const uint32_t orank = (uint32_t)((om >> 16) & 0xFFFFu);
       if (fbase != ~0ull) {
         Frontier fr;
-        fr.ts = o_ts[it];
-        fr.aux = p.slots ? (uint32_t)o_rank[it] : 0xFFFFFFFFu;
-        fr.func = o_fn[it];
+        fr.ts = ots;
+        fr.aux = pslots ? orank : 0xFFFFFFFFu;
+        fr.func = (uint16_t)(om & 0xFFFFu);
         fr.flags = 0;
         p.frontier[fbase + P_p + h] = fr;
       }
-      if (p.slots) {
-        thapi_interval iv;
-        iv.start_ns = o_ts[it];
-        iv.end_ns = 0;
-        iv.stream_id = o_np[it];
-        iv.func_id = o_fn[it];
-        iv.level = o_lvl[it];
-        iv.flags = kIvOpen;
-        p.slots[d.evbase + o_rank[it]] = iv;
-      }
+      if (pslots)
+        put_interval(pslots + orank, ots, 0, (uint32_t)((om >> 40) & 0xFFFFu), (uint32_t)(om & 0xFFFFu),
+                     (uint32_t)((om >> 32) & 0xFFu), kIvOpen);
     }
     n_mismatch += mism;
-    const uint32_t vsum = __reduce_add_sync(0xffffffffu, valid);
     n_pairs += valid;
+    const uint32_t vsum = __reduce_add_sync(0xffffffffu, valid);
     if (lane == 0) {
       p.sum_pend[pos] = P_p;
       p.sum_open[pos] = O_p;
@@ -550,27 +594,6 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
       if (p.slots) n_slots += e_tot;
       n_disc += d.disc;
       n_pk += 1;
-    }
-    }  // analysed in the warp
-    // ---- 5. flush the lane-shared tally when the stream changes
-    if (TALLY_SMEM && (!has_next || dcur.stream != d.stream)) {
-      __syncwarp();
-      for (uint32_t f = lane; f < F; f += 32) {
-        const uint32_t c = t_cnt[f];
-        if (c) {
-          Cell &cell = p.tally[(uint64_t)d.group * F + f];
-          atomicAdd(&cell.count, (unsigned long long)c);
-          atomicAdd(&cell.total, t_tot[f]);
-          atomicMin(&cell.mn, (unsigned long long)t_mn[f]);
-          atomicMax(&cell.mx, (unsigned long long)t_mx[f]);
-          if (t_err[f]) atomicAdd(&cell.err, (unsigned long long)t_err[f]);
-          t_cnt[f] = 0;
-          t_err[f] = 0;
-          t_mn[f] = 0xFFFFFFFFu;
-          t_mx[f] = 0;
-          t_tot[f] = 0;
-        }
-      }
     }
     __syncwarp();
   }
@@ -593,27 +616,42 @@ __global__ void __launch_bounds__(32) k_analyze_warp(AnalyzeParams p, unsigned i
     if (n_pairs) atomicAdd(&p.diag[dPairs], n_pairs);
     if (tmin != ~0ull) atomicMin(&p.tminmax[0], (unsigned long long)tmin);
     if (tmax) atomicMax(&p.tminmax[1], (unsigned long long)tmax);
-    atomicAdd(&p.diag[dEvents], n_events);
-    atomicAdd(&p.diag[dDiscarded], n_disc);
-    atomicAdd(&p.diag[dPackets], n_pk);
+    if (n_events) atomicAdd(&p.diag[dEvents], n_events);
+    if (n_disc) atomicAdd(&p.diag[dDiscarded], n_disc);
+    if (n_pk) atomicAdd(&p.diag[dPackets], n_pk);
     if (n_slots && p.slots_written) atomicAdd(p.slots_written, n_slots);
+  }
+
+  // ---- flush the tally tables of the run's first and last group
+  if (TALLY_SMEM) {
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < 2 * F; i += blockDim.x) {
+      const unsigned long long ce = t_ce[i];
+      const uint32_t c = (uint32_t)ce;
+      if (!c) continue;
+      const uint32_t tbl = i / F, f = i - tbl * F;
+      Cell &cell = p.tally[(uint64_t)(tbl ? gB : gA) * F + f];
+      atomicAdd(&cell.count, (unsigned long long)c);
+      atomicAdd(&cell.total, t_tot[i]);
+      atomicMin(&cell.mn, (unsigned long long)t_mn[i]);
+      atomicMax(&cell.mx, (unsigned long long)t_mx[i]);
+      if (ce >> 32) atomicAdd(&cell.err, ce >> 32);
+    }
   }
 }
 
 template <int BW, bool TS>
-cudaError_t launch_w(const AnalyzeParams &p, uint32_t grid, uint32_t smem, cudaStream_t s, unsigned *status) {
+cudaError_t launch_w(const AnalyzeParams &p, uint32_t nw, uint32_t grid, uint32_t smem, cudaStream_t s,
+                     unsigned *status) {
   auto fn = k_analyze_warp<BW, TS>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, 32, smem, s>>>(p, status);
+  fn<<<grid, nw * 32, smem, s>>>(p, nw, status);
   count_launches(1);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-// Bitmap words per lane for packets of P bytes (0: too large for the warp kernel).
-int analyze_warp_bw(uint32_t P) {
+int warp_bw(uint32_t P) {
   const uint32_t wmax = (P - kPacketHeader) / 4;
   if (wmax <= 32u * 32) return 1;
   if (wmax <= 64u * 32) return 2;
@@ -622,22 +660,46 @@ int analyze_warp_bw(uint32_t P) {
   return 0;
 }
 
-uint32_t analyze_warp_smem_bytes(uint32_t P, uint32_t n_funcs) {
-  return wlayout(P, n_funcs, n_funcs <= kTallySmemMax).total;
+}  // namespace
+
+// Chooses warps per CTA and CTAs per SM for the warp kernel (false: the CTA
+// kernel takes every packet of this trace).
+bool plan_analyze_warp(uint32_t P, uint32_t n_classes, uint32_t n_funcs, int smem_optin, int smem_per_sm,
+                       WarpPlan *out) {
+  if (!warp_bw(P) || n_classes > kClsMax) return false;
+  const bool ts = n_funcs <= kTallyMax;
+  WarpPlan best{};
+  for (uint32_t nw = 1; nw <= kMaxWarps; ++nw) {
+    const uint32_t smem = wlayout(P, nw, n_classes, n_funcs, ts).total;
+    if ((int)smem > smem_optin) break;
+    const uint32_t ctas = std::min<uint32_t>(32u / nw, (uint32_t)(smem_per_sm / (int)(smem + 1024)));
+    if (ctas * nw > best.ctas_per_sm * best.nw) {
+      best.nw = nw;
+      best.ctas_per_sm = ctas;
+      best.smem = smem;
+    }
+  }
+  if (!best.nw) return false;
+  *out = best;
+  return true;
 }
 
-// One warp per CTA; packets the warp kernel cannot take are appended to
-// p.dense_list for the CTA kernel.
-cudaError_t launch_analyze_warp(const AnalyzeParams &p, uint32_t grid, cudaStream_t s, unsigned *status) {
-  const bool ts = p.n_funcs <= kTallySmemMax;
-  const uint32_t smem = analyze_warp_smem_bytes(p.P, p.n_funcs);
-  switch (analyze_warp_bw(p.P)) {
-    case 1: return ts ? launch_w<1, true>(p, grid, smem, s, status) : launch_w<1, false>(p, grid, smem, s, status);
-    case 2: return ts ? launch_w<2, true>(p, grid, smem, s, status) : launch_w<2, false>(p, grid, smem, s, status);
-    case 4: return ts ? launch_w<4, true>(p, grid, smem, s, status) : launch_w<4, false>(p, grid, smem, s, status);
-    case 8: return ts ? launch_w<8, true>(p, grid, smem, s, status) : launch_w<8, false>(p, grid, smem, s, status);
+cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s,
+                                unsigned *status) {
+  const bool ts = p.n_funcs <= kTallyMax;
+  switch (warp_bw(p.P)) {
+    case 1: return ts ? launch_w<1, true>(p, wp.nw, grid, wp.smem, s, status)
+                      : launch_w<1, false>(p, wp.nw, grid, wp.smem, s, status);
+    case 2: return ts ? launch_w<2, true>(p, wp.nw, grid, wp.smem, s, status)
+                      : launch_w<2, false>(p, wp.nw, grid, wp.smem, s, status);
+    case 4: return ts ? launch_w<4, true>(p, wp.nw, grid, wp.smem, s, status)
+                      : launch_w<4, false>(p, wp.nw, grid, wp.smem, s, status);
+    case 8: return ts ? launch_w<8, true>(p, wp.nw, grid, wp.smem, s, status)
+                      : launch_w<8, false>(p, wp.nw, grid, wp.smem, s, status);
     default: return cudaErrorInvalidValue;
   }
 }
+
+uint64_t analyze_warp_frontier_slack(uint64_t warps) { return warps * kChunk; }
 
 }  // namespace thapi

@@ -464,13 +464,12 @@ int Loader::run() {
   const int stages = n ? pick_stages(c_, P, emax_main, L.n_classes, F) : 1;
   if (!stages) return THAPI_E_UNSUPPORTED;
   // warp-per-packet kernel for packets up to 32 KB, the CTA kernel otherwise
-  const bool warp_path = analyze_warp_bw(P) != 0;
+  WarpPlan wplan;
+  const bool warp_path = plan_analyze_warp(P, L.n_classes, F, c_->smem_per_block, c_->smem_per_sm, &wplan);
   uint64_t grid = 1, per = 1;
   if (n) {
     if (warp_path) {
-      const uint32_t smem = analyze_warp_smem_bytes(P, F);
-      const int blocks = std::max(1, std::min(32, c_->smem_per_sm / (int)(smem + 1024)));
-      grid = (uint64_t)c_->num_sms * blocks;
+      grid = (uint64_t)c_->num_sms * wplan.ctas_per_sm;
     } else {
       const uint32_t smem = analyze_smem_bytes(P, emax_main, stages, L.n_classes, F);
       grid = (uint64_t)c_->num_sms * blocks_per_sm(c_, smem);
@@ -478,7 +477,8 @@ int Loader::run() {
     per = (n + grid - 1) / grid;
     grid = (n + per - 1) / per;
   }
-  uint64_t fcap = total_events / 16 + 4096 + analyze_frontier_slack((uint32_t)grid) +
+  uint64_t fcap = total_events / 16 + 4096 +
+                  (warp_path ? analyze_warp_frontier_slack(grid * wplan.nw) : analyze_frontier_slack((uint32_t)grid)) +
                   analyze_frontier_slack((uint32_t)c_->num_sms * 16);
   Frontier *frontier = nullptr;
   unsigned *status = reinterpret_cast<unsigned *>(misc_ + mStatus);
@@ -525,7 +525,7 @@ int Loader::run() {
       ap.per_cta = (uint32_t)per;
       clk_.rec(PhaseClock::kAn0, s_);
       if (warp_path)
-        CK(launch_analyze_warp(ap, (uint32_t)grid, s_, status));
+        CK(launch_analyze_warp(ap, wplan, (uint32_t)grid, s_, status));
       else
         CK(launch_analyze(ap, stages, (uint32_t)grid, s_, status));
       clk_.rec(PhaseClock::kAn1, s_);

@@ -63,17 +63,23 @@ struct Bits {
 #pragma unroll
     for (int i = 0; i < BW; ++i) w[i] = 0;
   }
+  // set/test take a word-relative offset per word (no index select), so that
+  // the words stay in registers
   __device__ __forceinline__ void set(uint32_t i) {
 #pragma unroll
-    for (int k = 0; k < BW; ++k)
-      if ((i >> 5) == (uint32_t)k) w[k] |= 1u << (i & 31);
+    for (int k = 0; k < BW; ++k) {
+      const uint32_t d = i - 32u * k;
+      w[k] |= d < 32u ? 1u << d : 0u;
+    }
   }
   __device__ __forceinline__ bool test(uint32_t i) const {
-    bool r = false;
+    uint32_t r = 0;
 #pragma unroll
-    for (int k = 0; k < BW; ++k)
-      if ((i >> 5) == (uint32_t)k) r = (w[k] >> (i & 31)) & 1u;
-    return r;
+    for (int k = 0; k < BW; ++k) {
+      const uint32_t d = i - 32u * k;
+      r |= d < 32u ? (w[k] >> d) & 1u : 0u;
+    }
+    return r != 0;
   }
   // keep bits with index >= i
   __device__ __forceinline__ void keep_from(uint32_t i) {

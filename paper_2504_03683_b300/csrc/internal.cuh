@@ -182,9 +182,14 @@ void launch_stream_bounds(const uint64_t *skey, const uint32_t *order, const uin
 uint32_t analyze_smem_bytes(uint32_t P, uint32_t emax, int stages, uint32_t n_classes, uint32_t n_funcs);
 uint64_t analyze_frontier_slack(uint32_t grid);
 // analyze_warp.cu: one warp per packet (packets up to 32 KB)
-int analyze_warp_bw(uint32_t P);
-uint32_t analyze_warp_smem_bytes(uint32_t P, uint32_t n_funcs);
-cudaError_t launch_analyze_warp(const AnalyzeParams &p, uint32_t grid, cudaStream_t s, unsigned *status);
+struct WarpPlan {
+  uint32_t nw = 0, ctas_per_sm = 0, smem = 0;  // warps per CTA, resident CTAs per SM, dynamic shared memory
+};
+bool plan_analyze_warp(uint32_t P, uint32_t n_classes, uint32_t n_funcs, int smem_optin, int smem_per_sm,
+                       WarpPlan *out);
+cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s,
+                                unsigned *status);
+uint64_t analyze_warp_frontier_slack(uint64_t warps);
 cudaError_t launch_analyze(const AnalyzeParams &p, int stages, uint32_t grid, cudaStream_t s, unsigned *status);
 // frontier.cu
 void launch_frontier(const FrontierParams &p, cudaStream_t s);
