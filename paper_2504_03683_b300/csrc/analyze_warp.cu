@@ -1,8 +1,10 @@
 // analyze_warp.cu — decode + in-packet pairing + tally, one warp per packet.
 //
-// A CTA holds NW independent warps that share the class table and two tally
-// tables.  The CTA takes a contiguous run of the stream-ordered packet list
-// and its warps take the run's packets in turn.  Each warp stages its packet
+// A CTA holds NW independent warps that share the class table.  The CTA
+// takes a contiguous run of the stream-ordered packet list and its warps take
+// the run's packets in turn.  Pairs are tallied with fire-and-forget global
+// reductions on the (group, function) cells: on this part those cost the SM
+// less than shared-memory atomics, whose latency sits on the decode chain.  Each warp stages its packet
 // with a TMA bulk copy (mbarrier completion) and then works on it alone:
 //
 //  1. boundaries: every lane walks a 32*BW-word segment speculatively from
@@ -11,8 +13,9 @@
 //     speculative exit; the first lane whose exit breaks that assumption
 //     hands its successor the right entry, one ballot round per such lane).
 //     The marks are then exactly the event starts of the chain from offset 0.
-//  2. the event offsets are compacted in order and dealt out in equal runs,
-//     one run per lane, so that every lane decodes the same number of events;
+//  2. the event offsets are compacted and dealt out in equal runs, one run per
+//     lane, so that every lane decodes the same number of events (stored
+//     transposed: the i-th event of every lane's run sits in one 64-byte row);
 //  3. validation and per-lane summaries (entries, timestamp monoid, depth
 //     monoid, stack slots used), then warp shuffle scans of the summaries;
 //  4. decode with a per-lane call stack: entries are pushed, exits pop the
@@ -36,10 +39,9 @@ namespace thapi {
 namespace {
 using namespace dev;
 
-constexpr int kStack = 8;              // lane stack slots (pending exits below open entries)
+constexpr int kStack = 12;             // lane stack slots (pending exits below open entries)
 constexpr uint32_t kEvMax = 1024;      // events of one packet the warp path takes
 constexpr uint32_t kClsMax = 4096;     // class rows held in shared memory
-constexpr uint32_t kTallyMax = 512;    // functions tallied in shared memory
 constexpr uint32_t kHMax = 64;         // heights with a precomputed owner mask
 constexpr uint32_t kChunk = 2048;      // frontier items grabbed per global atomic
 constexpr uint32_t kMaxWarps = 16;     // warps per CTA
@@ -48,10 +50,10 @@ __host__ __device__ inline uint32_t rup(uint32_t v, uint32_t a) { return (v + a 
 
 struct WLayout {
   uint32_t off_stk, off_off, off_bpc, off_hm, off_bar, warp_bytes;  // within one warp's block
-  uint32_t off_ctab, off_cfn, off_tally, total;                     // CTA-wide
+  uint32_t off_ctab, off_cfn, total;                                // CTA-wide
 };
 
-__host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t NW, uint32_t NC, uint32_t F, bool tally_smem) {
+__host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t NW, uint32_t NC) {
   WLayout L;
   uint32_t o = rup(P + 48u, 128u);  // packet (header + content) and a zeroed tail
   L.off_stk = o;
@@ -70,8 +72,6 @@ __host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t NW, uint32_t NC,
   o += rup((NC + 1u) * 4u, 16u);
   L.off_cfn = o;
   o += rup(NC * 2u, 16u);
-  L.off_tally = o;
-  if (tally_smem) o += 2u * F * 24u;
   L.total = rup(o, 128u);
   return L;
 }
@@ -128,7 +128,7 @@ __device__ __forceinline__ uint64_t open_meta(uint32_t fn, uint32_t rank, uint32
   return (uint64_t)fn | ((uint64_t)rank << 16) | ((uint64_t)lvl << 32) | ((uint64_t)np << 40);
 }
 
-template <int BW, bool TALLY_SMEM>
+template <int BW>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p, uint32_t NW, unsigned int *status) {
   extern __shared__ __align__(128) uint8_t sm[];
   constexpr uint32_t SEGW = 32u * BW;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t F = p.n_funcs;
   const uint32_t NC = p.n_classes;
-  const WLayout L = wlayout(p.P, NW, NC, F, TALLY_SMEM);
+  const WLayout L = wlayout(p.P, NW, NC);
   uint8_t *wb = sm + warp * L.warp_bytes;
   uint8_t *buf = wb;
   uint32_t *C = reinterpret_cast<uint32_t *>(buf + kPacketHeader);
@@ -148,10 +148,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   uint64_t *bar = reinterpret_cast<uint64_t *>(wb + L.off_bar);
   uint32_t *ctab = reinterpret_cast<uint32_t *>(sm + L.off_ctab);
   uint16_t *cfn = reinterpret_cast<uint16_t *>(sm + L.off_cfn);
-  unsigned long long *t_ce = reinterpret_cast<unsigned long long *>(sm + L.off_tally);  // count | errors << 32
-  unsigned long long *t_tot = t_ce + 2 * F;
-  uint32_t *t_mn = reinterpret_cast<uint32_t *>(t_tot + 2 * F);
-  uint32_t *t_mx = t_mn + 2 * F;
 
   const uint64_t w_begin = (uint64_t)blockIdx.x * p.per_cta;
   const uint64_t w_end = (w_begin + p.per_cta < p.n_order) ? w_begin + p.per_cta : p.n_order;
@@ -167,15 +163,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       ctab[c] = 0;
     }
   }
-  // tally tables: 0 for the group of the run's first packet, 1 for its last
-  const uint32_t gA = p.desc[pos_of(w_begin)].group, gB = p.desc[pos_of(w_end - 1)].group;
-  if (TALLY_SMEM)
-    for (uint32_t i = threadIdx.x; i < 2 * F; i += blockDim.x) {
-      t_ce[i] = 0;
-      t_tot[i] = 0;
-      t_mn[i] = 0xFFFFFFFFu;
-      t_mx[i] = 0;
-    }
   if (lane == 0) {
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -224,7 +211,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     const uint32_t W = d.content >> 2;
     if (lane < 4) C[W + lane] = 0;
     __syncwarp();
-    const int tb = d.group == gA ? 0 : (d.group == gB ? 1 : -1);
 
     // ---- 1. boundaries
     const uint32_t a = (uint32_t)lane * SEGW;
@@ -283,16 +269,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     bool bad = false;
     uint32_t e0 = 0, e1 = 0;
     if (!fallback) {
-      uint32_t idx = cinc - cnt;
+      // event e is the (e % per)-th of lane e / per's run: s_off[(e % per) * 32 + e / per]
+      const uint32_t per = (c_tot + 31u) >> 5;
+      const uint32_t inv = per ? (65536u + per - 1u) / per : 0u;  // e / per = (e * inv) >> 16 for e < 1024
+      uint32_t e = cinc - cnt;
 #pragma unroll
       for (int k = 0; k < BW; ++k) {
         uint32_t m = bits.w[k];
         while (m) {
-          s_off[idx++] = (uint16_t)(a + k * 32 + (__ffs(m) - 1));
+          const uint32_t q = (e * inv) >> 16;
+          s_off[(e - q * per) * 32 + q] = (uint16_t)(a + k * 32 + (__ffs(m) - 1));
           m &= m - 1;
+          ++e;
         }
       }
-      const uint32_t per = (c_tot + 31u) >> 5;
       e0 = min((uint32_t)lane * per, c_tot);
       e1 = min(e0 + per, c_tot);
     }
@@ -305,7 +295,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     int slots_used = 0;
     uint32_t ekey = 0xFFFFFFFFu;  // event index << 3 | code of the first bad event
     for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t oo = s_off[e];
+      const uint32_t oo = s_off[(e - e0) * 32 + (uint32_t)lane];
       const uint32_t w0 = C[oo], w1 = C[oo + 1];
       const uint32_t c = w1 & 0xFFFFu;
       const bool ext = (w0 & kExtBit) != 0;
@@ -410,20 +400,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     thapi_interval *const pslots = p.slots ? p.slots + d.evbase : nullptr;
     Cell *const gcells = p.tally + (uint64_t)d.group * F;
     auto tally = [&](uint32_t fn, uint64_t dur, uint32_t err) {
-      if (TALLY_SMEM && tb >= 0 && dur < (1ull << 32)) {
-        const uint32_t i = (uint32_t)tb * F + fn;
-        atomicAdd(&t_ce[i], 1ull | ((unsigned long long)err << 32));
-        atomicAdd(&t_tot[i], (unsigned long long)dur);
-        atomicMin(&t_mn[i], (uint32_t)dur);
-        atomicMax(&t_mx[i], (uint32_t)dur);
-      } else {
-        Cell &cell = gcells[fn];
-        atomicAdd(&cell.count, 1ull);
-        atomicAdd(&cell.total, (unsigned long long)dur);
-        atomicMin(&cell.mn, (unsigned long long)dur);
-        atomicMax(&cell.mx, (unsigned long long)dur);
-        if (err) atomicAdd(&cell.err, 1ull);
-      }
+      Cell &cell = gcells[fn];
+      atomicAdd(&cell.count, 1ull);
+      atomicAdd(&cell.total, (unsigned long long)dur);
+      atomicMin(&cell.mn, (unsigned long long)dur);
+      atomicMax(&cell.mx, (unsigned long long)dur);
+      if (err) atomicAdd(&cell.err, 1ull);
     };
     uint32_t valid = 0, mism = 0;
     // one pair: entry (ets, metadata em) closed by an exit (xts, xfn, xerr)
@@ -447,9 +429,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     uint32_t rank = e_ex;
     uint32_t top = 0, pc = 0;
     bool first = true;
-    for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t oo = s_off[e];
-      const uint32_t w0 = C[oo], w1 = C[oo + 1];
+    const uint32_t n_run = e1 - e0;
+    uint32_t oo_n = 0, w0_n = 0, w1_n = 0;  // next event of the run, loaded one step ahead
+    if (n_run) {
+      oo_n = s_off[lane];
+      w0_n = C[oo_n];
+      w1_n = C[oo_n + 1];
+    }
+    for (uint32_t i = 0; i < n_run; ++i) {
+      const uint32_t oo = oo_n, w0 = w0_n, w1 = w1_n;
+      if (i + 1 < n_run) {
+        oo_n = s_off[(i + 1) * 32 + (uint32_t)lane];
+        w0_n = C[oo_n];
+        w1_n = C[oo_n + 1];
+      }
       const uint32_t c = w1 & 0xFFFFu;
       const bool ext = (w0 & kExtBit) != 0;
       const uint32_t r = ctab[c];
@@ -622,31 +615,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     if (n_slots && p.slots_written) atomicAdd(p.slots_written, n_slots);
   }
 
-  // ---- flush the tally tables of the run's first and last group
-  if (TALLY_SMEM) {
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < 2 * F; i += blockDim.x) {
-      const unsigned long long ce = t_ce[i];
-      const uint32_t c = (uint32_t)ce;
-      if (!c) continue;
-      const uint32_t tbl = i / F, f = i - tbl * F;
-      Cell &cell = p.tally[(uint64_t)(tbl ? gB : gA) * F + f];
-      atomicAdd(&cell.count, (unsigned long long)c);
-      atomicAdd(&cell.total, t_tot[i]);
-      atomicMin(&cell.mn, (unsigned long long)t_mn[i]);
-      atomicMax(&cell.mx, (unsigned long long)t_mx[i]);
-      if (ce >> 32) atomicAdd(&cell.err, ce >> 32);
-    }
-  }
 }
 
-template <int BW, bool TS>
-cudaError_t launch_w(const AnalyzeParams &p, uint32_t nw, uint32_t grid, uint32_t smem, cudaStream_t s,
-                     unsigned *status) {
-  auto fn = k_analyze_warp<BW, TS>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int BW>
+cudaError_t launch_w(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s, unsigned *status) {
+  auto fn = k_analyze_warp<BW>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wp.smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, nw * 32, smem, s>>>(p, nw, status);
+  fn<<<grid, wp.nw * 32, wp.smem, s>>>(p, wp.nw, status);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -664,13 +640,11 @@ int warp_bw(uint32_t P) {
 
 // Chooses warps per CTA and CTAs per SM for the warp kernel (false: the CTA
 // kernel takes every packet of this trace).
-bool plan_analyze_warp(uint32_t P, uint32_t n_classes, uint32_t n_funcs, int smem_optin, int smem_per_sm,
-                       WarpPlan *out) {
+bool plan_analyze_warp(uint32_t P, uint32_t n_classes, int smem_optin, int smem_per_sm, WarpPlan *out) {
   if (!warp_bw(P) || n_classes > kClsMax) return false;
-  const bool ts = n_funcs <= kTallyMax;
   WarpPlan best{};
   for (uint32_t nw = 1; nw <= kMaxWarps; ++nw) {
-    const uint32_t smem = wlayout(P, nw, n_classes, n_funcs, ts).total;
+    const uint32_t smem = wlayout(P, nw, n_classes).total;
     if ((int)smem > smem_optin) break;
     const uint32_t ctas = std::min<uint32_t>(32u / nw, (uint32_t)(smem_per_sm / (int)(smem + 1024)));
     if (ctas * nw > best.ctas_per_sm * best.nw) {
@@ -686,16 +660,11 @@ bool plan_analyze_warp(uint32_t P, uint32_t n_classes, uint32_t n_funcs, int sme
 
 cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s,
                                 unsigned *status) {
-  const bool ts = p.n_funcs <= kTallyMax;
   switch (warp_bw(p.P)) {
-    case 1: return ts ? launch_w<1, true>(p, wp.nw, grid, wp.smem, s, status)
-                      : launch_w<1, false>(p, wp.nw, grid, wp.smem, s, status);
-    case 2: return ts ? launch_w<2, true>(p, wp.nw, grid, wp.smem, s, status)
-                      : launch_w<2, false>(p, wp.nw, grid, wp.smem, s, status);
-    case 4: return ts ? launch_w<4, true>(p, wp.nw, grid, wp.smem, s, status)
-                      : launch_w<4, false>(p, wp.nw, grid, wp.smem, s, status);
-    case 8: return ts ? launch_w<8, true>(p, wp.nw, grid, wp.smem, s, status)
-                      : launch_w<8, false>(p, wp.nw, grid, wp.smem, s, status);
+    case 1: return launch_w<1>(p, wp, grid, s, status);
+    case 2: return launch_w<2>(p, wp, grid, s, status);
+    case 4: return launch_w<4>(p, wp, grid, s, status);
+    case 8: return launch_w<8>(p, wp, grid, s, status);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -465,7 +465,7 @@ int Loader::run() {
   if (!stages) return THAPI_E_UNSUPPORTED;
   // warp-per-packet kernel for packets up to 32 KB, the CTA kernel otherwise
   WarpPlan wplan;
-  const bool warp_path = plan_analyze_warp(P, L.n_classes, F, c_->smem_per_block, c_->smem_per_sm, &wplan);
+  const bool warp_path = plan_analyze_warp(P, L.n_classes, c_->smem_per_block, c_->smem_per_sm, &wplan);
   uint64_t grid = 1, per = 1;
   if (n) {
     if (warp_path) {
@@ -616,8 +616,7 @@ int Loader::run() {
 
   // ---- timeline: compact valid slots, sort by start, gather
   thapi_interval *rec = alloc<thapi_interval>(n_iv);
-  uint64_t *k1 = alloc<uint64_t>(n_iv), *k2 = alloc<uint64_t>(n_iv);
-  uint32_t *v1 = alloc<uint32_t>(n_iv), *v2 = alloc<uint32_t>(n_iv);
+  uint64_t *k1 = alloc<uint64_t>(n_iv);
   if (sc_.failed) return THAPI_E_NOMEM;
   const uint64_t tmin = misc_h_[mTmin], tmax = misc_h_[mTmax];
   int bits = 0;
@@ -625,14 +624,25 @@ int Loader::run() {
     const uint64_t span = tmax - tmin;
     while (bits < 64 && (span >> bits)) ++bits;
   }
+  BucketCells bcells;
+  const bool bucket_on = bucket_plan(n_iv, bits, S, sc_, s_, &bcells);
+  if (sc_.failed) return THAPI_E_NOMEM;
   clk_.rec(PhaseClock::kCo0, s_);
   launch_timeline_compact(slots, evbase, sum_nslot, obase, A, order, pk_stream, n, n_iv ? tmin : 0, rec, k1,
-                          bits <= 32, v1, c_->num_sms, s_);
+                          bits <= 32, nullptr, bucket_on ? &bcells : nullptr, c_->num_sms, s_);
   clk_.rec(PhaseClock::kCo1, s_);
   tr_->tl_bytes = std::max<uint64_t>(n_iv, 1) * sizeof(thapi_interval);
   tr_->tl = static_cast<thapi_interval *>(dev_alloc(c_, tr_->tl_bytes, s_));
   if (!tr_->tl) return THAPI_E_NOMEM;
-  radix_sort_gather(k1, v1, k2, v2, n_iv, bits, rec, tr_->tl, sc_, s_);
+  if (!bucket_on || !bucket_run(bcells, tmin, n_iv, rec, tr_->tl, sc_, s_, c_->num_sms)) {
+    if (sc_.failed) return THAPI_E_NOMEM;
+    CK(cudaGetLastError());
+    uint64_t *k2 = alloc<uint64_t>(n_iv);
+    uint32_t *v1 = alloc<uint32_t>(n_iv), *v2 = alloc<uint32_t>(n_iv);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    launch_iota_u32(v1, n_iv, s_);
+    radix_sort_gather(k1, v1, k2, v2, n_iv, bits, rec, tr_->tl, sc_, s_);
+  }
   if (sc_.failed) return THAPI_E_NOMEM;
   clk_.rec(PhaseClock::kSo1, s_);
   clk_.rec(PhaseClock::kGa1, s_);

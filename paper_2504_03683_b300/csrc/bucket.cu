@@ -1,0 +1,274 @@
+// bucket.cu — timeline order by bucketing on start time.
+//
+// The compacted interval records are in (stream, entry position) order and
+// each stream's records are sorted by start, so the records of one stream
+// that fall in one start bucket are a contiguous run.  With B buckets on the
+// high bits of the start offset and S streams, the compaction counts the
+// records of each (bucket, stream) cell and notes the cell's first record
+// (one atomic pair per cell and warp).  Then one CTA per bucket:
+//  1. reads its S cells, then the cells' runs of records (thread per cell,
+//     several loads in flight) into shared memory, in (stream, position)
+//     order;
+//  2. sorts (low key bits, position) stably with an LSD radix in shared
+//     memory (9-bit digits, warp ranks from one ballot per digit bit), so
+//     that equal starts keep the (stream, position) order;
+//  3. writes the records out in that order with coalesced stores, at the
+//     bucket's offset (an exclusive scan of the bucket sizes).
+// The result is the order (start, stream, entry position).  A cell's records
+// are contiguous only while each stream's starts never decrease (an absolute
+// timestamp may go back): every record read is checked to lie in its bucket,
+// which holds exactly when the cell is contiguous.  A failed check, too many
+// cells or a bucket over kCap records make the caller fall back to the radix
+// sort.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace thapi {
+
+namespace {
+
+constexpr uint64_t kCoarse = 4096;          // bucket size aimed at (the mean lands between half and all of it)
+constexpr uint64_t kMaxCells = 1ull << 24;  // (bucket, stream) cells
+constexpr uint32_t kMaxStreams = 2048;      // cells of one bucket held in shared memory
+constexpr uint32_t kCap = 4096;             // records of one bucket sorted in shared memory
+constexpr int kDigit = 9;
+constexpr uint32_t kBins = 1u << kDigit;
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kRounds = kCap / kThreads;  // 32-record rounds per warp and radix pass
+static_assert(kThreads == (int)kBins, "one thread per digit in the digit scan");
+static_assert(kMaxStreams == 4 * kThreads, "four cells per thread in the cell scan");
+
+// Shared memory of k_bucket_sort for item type IT.
+template <class IT>
+constexpr uint32_t sort_smem() {
+  return (uint32_t)(kCap * sizeof(thapi_interval) + 2 * kCap * sizeof(IT) +
+                    (kWarps * kBins + kBins + kWarps + 2 * kMaxStreams + 1) * sizeof(uint32_t));
+}
+
+__global__ void k_bucket_sizes(const uint32_t *cnt, uint32_t nb, uint32_t S, uint64_t *size) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per bucket
+  if (b >= nb) return;
+  uint32_t c = 0;
+  for (uint32_t r = lane; r < S; r += 32) c += cnt[(uint64_t)b * S + r];
+  c = __reduce_add_sync(0xffffffffu, c);
+  if (lane == 0) size[b] = c;
+}
+
+__global__ void k_bucket_max(const uint64_t *size, uint32_t nb, unsigned long long *out) {
+  uint32_t m = 0;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += gridDim.x * blockDim.x)
+    m = max(m, (uint32_t)size[i]);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, (unsigned long long)m);
+}
+
+// One CTA per bucket (strided).  IT items: low key bits << QSH | position.
+template <class IT>
+__global__ void __launch_bounds__(kThreads, 1) k_bucket_sort(const uint32_t *cnt, const uint32_t *first,
+                                                             const uint64_t *bstart, const uint64_t *bsize,
+                                                             uint32_t nb, uint32_t S, int shift, uint64_t t_min,
+                                                             const thapi_interval *__restrict__ rec,
+                                                             thapi_interval *__restrict__ out, unsigned int *fail) {
+  constexpr int QSH = sizeof(IT) == 4 ? 12 : 32;  // position bits (kCap <= 2^12)
+  constexpr IT QMASK = ((IT)1 << QSH) - 1;
+  extern __shared__ __align__(16) uint8_t smem[];
+  thapi_interval *srec = reinterpret_cast<thapi_interval *>(smem);
+  IT *ia = reinterpret_cast<IT *>(smem + kCap * sizeof(thapi_interval));
+  IT *ib = ia + kCap;
+  uint32_t *wcount = reinterpret_cast<uint32_t *>(ib + kCap);  // [kWarps][kBins]
+  uint32_t *dstart = wcount + kWarps * kBins;                  // [kBins]
+  uint32_t *wsum = dstart + kBins;                             // [kWarps]
+  uint32_t *cpre = wsum + kWarps;                              // [S + 1] cell starts in the bucket
+  uint32_t *cfirst = cpre + kMaxStreams + 1;                   // [S] first record of each cell
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint64_t kmask = shift >= 64 ? ~0ull : ((1ull << shift) - 1);
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const uint32_t c = (uint32_t)bsize[b];
+    if (c == 0) continue;
+    const uint64_t st = bstart[b];
+    // cells of this bucket: exclusive scan of the counts (thread t: entries 4t .. 4t+3)
+    {
+      uint32_t loc[4], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t r = tid * 4 + q;
+        loc[q] = r < S ? cnt[(uint64_t)b * S + r] : 0u;
+        if (r < S) cfirst[r] = first[(uint64_t)b * S + r];
+        sum += loc[q];
+      }
+      uint32_t inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += u;
+      }
+      if (lane == 31) wsum[warp] = inc;
+      __syncthreads();
+      uint32_t run = inc - sum;
+      for (uint32_t w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint32_t r = tid * 4 + q;
+        if (r < S) cpre[r] = run;
+        run += loc[q];
+      }
+      if (tid == 0) cpre[S] = c;
+    }
+    __syncthreads();
+    // records of each cell (a contiguous run of rec), thread per cell, four loads in flight
+    auto put = [&](uint32_t q, const thapi_interval &v) {
+      srec[q] = v;
+      const uint64_t key = v.start_ns - t_min;
+      if ((key >> shift) != b && !(b == nb - 1 && (key >> shift) > b)) atomicExch(fail, 1u);  // cell not contiguous
+      const uint64_t kl = (key - ((uint64_t)b << shift)) & kmask;
+      ia[q] = ((IT)kl << QSH) | (IT)q;
+    };
+    for (uint32_t r = tid; r < S; r += kThreads) {
+      const uint32_t off = cpre[r], n_r = cpre[r + 1] - off;
+      const thapi_interval *rr = rec + cfirst[r];
+      uint32_t j = 0;
+      for (; j + 4 <= n_r; j += 4) {
+        const thapi_interval v0 = rr[j], v1 = rr[j + 1], v2 = rr[j + 2], v3 = rr[j + 3];
+        put(off + j, v0);
+        put(off + j + 1, v1);
+        put(off + j + 2, v2);
+        put(off + j + 3, v3);
+      }
+      for (; j < n_r; ++j) put(off + j, rr[j]);
+    }
+    __syncthreads();
+    // stable LSD radix on the key bits above QSH
+    const uint32_t chunk = ((c + kThreads - 1) / kThreads) * 32;  // items per warp
+    const uint32_t lo = warp * chunk, hi = min(lo + chunk, c);
+    IT *src = ia, *dst = ib;
+    for (int sh = QSH; sh < QSH + shift; sh += kDigit) {
+      for (uint32_t d = lane; d < kBins; d += 32) wcount[warp * kBins + d] = 0;
+      __syncwarp();
+      IT v[kRounds];
+      uint32_t loc[kRounds], dg[kRounds];
+#pragma unroll
+      for (uint32_t r = 0; r < kRounds; ++r) {
+        const uint32_t i = lo + r * 32 + lane;
+        const bool in = i < hi;
+        v[r] = in ? src[i] : (IT)0;
+        const uint32_t d = (uint32_t)(v[r] >> sh) & (kBins - 1);
+        // lanes holding the same digit: one ballot per digit bit
+        uint32_t peers = __ballot_sync(0xffffffffu, in);
+#pragma unroll
+        for (int bit = 0; bit < kDigit; ++bit) {
+          const uint32_t m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+          peers &= ((d >> bit) & 1u) ? m : ~m;
+        }
+        const uint32_t before = in ? wcount[warp * kBins + d] : 0u;
+        __syncwarp();
+        if (in && (peers & lt) == 0) wcount[warp * kBins + d] = before + __popc(peers);
+        __syncwarp();
+        loc[r] = before + __popc(peers & lt);
+        dg[r] = d;
+      }
+      __syncthreads();
+      uint32_t tot = 0;  // digit tid: exclusive prefix over warps (in place) and the digit total
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t t = wcount[w * kBins + tid];
+        wcount[w * kBins + tid] = tot;
+        tot += t;
+      }
+      uint32_t inc = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += u;
+      }
+      if (lane == 31) wsum[warp] = inc;
+      __syncthreads();
+      uint32_t wbase = 0;
+      for (uint32_t w = 0; w < warp; ++w) wbase += wsum[w];
+      dstart[tid] = wbase + inc - tot;
+      __syncthreads();
+#pragma unroll
+      for (uint32_t r = 0; r < kRounds; ++r) {
+        const uint32_t i = lo + r * 32 + lane;
+        if (i < hi) dst[dstart[dg[r]] + wcount[warp * kBins + dg[r]] + loc[r]] = v[r];
+      }
+      __syncthreads();
+      IT *t = src;
+      src = dst;
+      dst = t;
+    }
+    for (uint32_t p = tid; p < c; p += kThreads) out[st + p] = srec[(uint32_t)(src[p] & QMASK)];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+bool bucket_plan(uint64_t n, int bits, uint32_t S, Scratch &sc, cudaStream_t s, BucketCells *bc) {
+  *bc = BucketCells{};
+  if (n < 2 || bits <= 0 || n >= 0xFFFFFFFFull || S == 0 || S > kMaxStreams) return false;
+  int k1 = 0;
+  while ((n >> k1) > kCoarse && k1 < bits && ((uint64_t)S << (k1 + 1)) <= kMaxCells) ++k1;
+  if (bits - k1 > 32) k1 = bits - 32;  // the low key bits must fit 32 bits
+  if (((uint64_t)S << k1) > kMaxCells) return false;
+  const uint64_t cells = (uint64_t)S << k1;
+  bc->cnt = static_cast<uint32_t *>(sc.get(cells * sizeof(uint32_t)));
+  bc->first = static_cast<uint32_t *>(sc.get(cells * sizeof(uint32_t)));
+  if (!bc->cnt || !bc->first) return false;
+  cudaMemsetAsync(bc->cnt, 0, cells * sizeof(uint32_t), s);
+  cudaMemsetAsync(bc->first, 0xFF, cells * sizeof(uint32_t), s);
+  bc->shift = bits - k1;
+  bc->nb = 1u << k1;
+  bc->S = S;
+  return true;
+}
+
+bool bucket_run(const BucketCells &bc, uint64_t t_min, uint64_t n, const thapi_interval *rec, thapi_interval *out,
+                Scratch &sc, cudaStream_t s, int num_sms) {
+  if (!bc.cnt) return false;
+  uint64_t *bsize = static_cast<uint64_t *>(sc.get((uint64_t)bc.nb * sizeof(uint64_t)));
+  uint64_t *bstart = static_cast<uint64_t *>(sc.get((uint64_t)bc.nb * sizeof(uint64_t)));
+  unsigned long long *maxv = static_cast<unsigned long long *>(sc.get(2 * sizeof(unsigned long long)));
+  if (!bsize || !bstart || !maxv) return false;
+  unsigned int *fail = reinterpret_cast<unsigned int *>(maxv + 1);
+  cudaMemsetAsync(maxv, 0, 2 * sizeof(unsigned long long), s);
+  k_bucket_sizes<<<(unsigned)(((uint64_t)bc.nb * 32 + 255) / 256), 256, 0, s>>>(bc.cnt, bc.nb, bc.S, bsize);
+  k_bucket_max<<<(unsigned)std::min<uint32_t>((bc.nb + 255) / 256, 1024u), 256, 0, s>>>(bsize, bc.nb, maxv);
+  count_launches(2);
+  if (cudaMemcpyAsync(bstart, bsize, (uint64_t)bc.nb * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return false;
+  scan_exclusive_u64(bstart, bc.nb, nullptr, sc, s);
+  unsigned long long mx = 0;
+  if (cudaMemcpyAsync(&mx, maxv, sizeof(mx), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  if (mx > kCap) return false;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(bc.nb, (uint64_t)num_sms));
+  if (bc.shift + 12 <= 32) {
+    auto fn = k_bucket_sort<uint32_t>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem<uint32_t>()) !=
+        cudaSuccess)
+      return false;
+    fn<<<grid, kThreads, sort_smem<uint32_t>(), s>>>(bc.cnt, bc.first, bstart, bsize, bc.nb, bc.S, bc.shift, t_min,
+                                                      rec, out, fail);
+  } else {
+    auto fn = k_bucket_sort<uint64_t>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem<uint64_t>()) !=
+        cudaSuccess)
+      return false;
+    fn<<<grid, kThreads, sort_smem<uint64_t>(), s>>>(bc.cnt, bc.first, bstart, bsize, bc.nb, bc.S, bc.shift, t_min,
+                                                      rec, out, fail);
+  }
+  count_launches(1);
+  unsigned int failed = 1;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&failed, fail, sizeof(failed), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return false;
+  return failed == 0 && !sc.failed;
+}
+
+}  // namespace thapi

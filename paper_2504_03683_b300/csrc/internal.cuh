@@ -138,6 +138,18 @@ void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32
                       int bits, bool *result_in_alt, Scratch &sc, cudaStream_t s);
 void radix_sort_pairs32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
                         bool *result_in_alt, Scratch &sc, cudaStream_t s);
+// bucket.cu: timeline order by start bucket.  bucket_plan sizes the coarse
+// buckets and clears the (bucket, stream) cells the compaction counts into;
+// bucket_run orders the compacted records (false from either: use
+// radix_sort_gather).
+struct BucketCells {
+  uint32_t *cnt = nullptr, *first = nullptr;  // [nb * S] records and first record index per cell
+  int shift = 0;                              // coarse bucket = key >> shift
+  uint32_t nb = 0, S = 0;
+};
+bool bucket_plan(uint64_t n, int bits, uint32_t S, Scratch &sc, cudaStream_t s, BucketCells *bc);
+bool bucket_run(const BucketCells &bc, uint64_t t_min, uint64_t n, const thapi_interval *rec, thapi_interval *out,
+                Scratch &sc, cudaStream_t s, int num_sms);
 // keys hold u32 values when bits <= 32 (u64 otherwise); rec_out[i] = rec[value of the i-th smallest key]
 void radix_sort_gather(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
                        const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc, cudaStream_t s);
@@ -185,8 +197,7 @@ uint64_t analyze_frontier_slack(uint32_t grid);
 struct WarpPlan {
   uint32_t nw = 0, ctas_per_sm = 0, smem = 0;  // warps per CTA, resident CTAs per SM, dynamic shared memory
 };
-bool plan_analyze_warp(uint32_t P, uint32_t n_classes, uint32_t n_funcs, int smem_optin, int smem_per_sm,
-                       WarpPlan *out);
+bool plan_analyze_warp(uint32_t P, uint32_t n_classes, int smem_optin, int smem_per_sm, WarpPlan *out);
 cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s,
                                 unsigned *status);
 uint64_t analyze_warp_frontier_slack(uint64_t warps);
@@ -201,9 +212,11 @@ void launch_tally_compact(const Cell *cells, uint64_t n, const uint32_t *group_k
 void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
                              const uint64_t *out_base, const uint32_t *A, const uint32_t *order,
                              const uint32_t *pk_stream, uint64_t n_order, uint64_t t_min, thapi_interval *rec,
-                             void *keys, bool key32, uint32_t *vals, int num_sms, cudaStream_t s);
+                             void *keys, bool key32, uint32_t *vals, const BucketCells *cells, int num_sms,
+                             cudaStream_t s);
 void launch_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uint64_t n, thapi_interval *out,
                             cudaStream_t s);
+void launch_iota_u32(uint32_t *v, uint64_t n, cudaStream_t s);
 void launch_window_count(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *hi_dev,
                          uint64_t *flags, uint64_t *n_dev, Scratch &sc, cudaStream_t s, uint64_t hi_host);
 void launch_window_write(const thapi_interval *tl, uint64_t hi, uint64_t t0, uint64_t t1, const uint64_t *pos,

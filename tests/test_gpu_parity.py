@@ -193,6 +193,39 @@ def test_equal_start_ties_across_streams(ctx):
     assert_parity(ctx, tb.build())
 
 
+def test_crowded_start_bucket_takes_radix_sort(ctx):
+    # 5000 zero-length calls starting at one instant fill one start bucket past
+    # its shared-memory capacity: the timeline is ordered by the radix sort.
+    tb, h, ids = _builder(P=4096)
+    s0, s1 = tb.add_stream(h, 1, 1), tb.add_stream(h, 1, 2)
+    evs = []
+    for _ in range(5000):
+        evs += [Ev(ids[0][1], 1000), Ev(ids[0][2], 1000)]
+    tb.place(tb.stream_events(s0, evs, ts_begin=1000))
+    tb.place(tb.stream_events(s1, [Ev(ids[1][1], 999), Ev(ids[1][2], 1000 + 10**6)], ts_begin=999))
+    o = assert_parity(ctx, tb.build())
+    assert len(o.intervals) == 5001
+
+
+def test_spread_starts_many_buckets(ctx):
+    # starts spread over a wide span with jitter and ties across streams: the
+    # bucketed order must equal the oracle's (start, stream, position) order
+    rng = random.Random(5)
+    tb, h, ids = _builder(P=1024)
+    streams = [tb.add_stream(h, 2, 10 + k) for k in range(24)]
+    for s in streams:
+        t, evs = 1 << 20, []
+        for _ in range(900):
+            t += rng.choice([0, 0, 1, 7, 300, 5000])
+            f = rng.randrange(3)
+            d = rng.choice([0, 1, 3, 40])
+            evs += [Ev(ids[f][1], t), Ev(ids[f][2], t + d)]
+            t += d
+        tb.place(tb.stream_events(s, evs, ts_begin=1 << 20))
+    o = assert_parity(ctx, tb.build())
+    assert len(o.intervals) == 24 * 900
+
+
 def test_brute_force_sequences_in_one_trace(ctx):
     rng = random.Random(77)
     tb, h, ids = _builder(P=256, n_funcs=2)
