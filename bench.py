@@ -153,7 +153,7 @@ class ClockSampler:
 
 def profile_traffic(kernel_file):
     """DRAM traffic per launch recorded by the committed ncu summary, if it still matches the kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_analyze_large.md")
+    path = os.path.join(ROOT, "profiles", "k_analyze_warp_large.md")
     try:
         text = open(path).read()
     except OSError:
@@ -302,7 +302,7 @@ def main():
     phase = {k: round(statistics.mean(t[k] for t in timings), 4)
              for k in ("index_ms", "analyze_ms", "frontier_ms", "tally_ms", "compact_ms", "sort_ms", "gather_ms",
                        "total_ms")}
-    traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze.cu"))
+    traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze_warp.cu"))
 
     # end to end through the public API: host bytes in, host results out
     e2e = None
@@ -344,7 +344,7 @@ def main():
                        else "single", "l2": "inputs larger than L2 (8.4 GB trace vs 126 MB L2); no flush"},
             "trace_gbs": meta["nbytes"] / (ms_max / 1e3) / 1e9 * (world if world > 1 else 1),
             "phases_ms": phase,
-            "roofline": {"kernel": "k_analyze (decode+pair+tally, interval slots)", "bound": "hbm",
+            "roofline": {"kernel": "k_analyze_warp (decode+validate+pair+tally, interval slots)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src + " hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                          else "fallback",
