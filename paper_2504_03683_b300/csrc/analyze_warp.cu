@@ -2,33 +2,36 @@
 //
 // A CTA holds NW independent warps that share the class table.  The CTA
 // takes a contiguous run of the stream-ordered packet list and its warps take
-// the run's packets in turn.  Pairs are tallied with fire-and-forget global
-// reductions on the (group, function) cells: on this part those cost the SM
-// less than shared-memory atomics, whose latency sits on the decode chain.  Each warp stages its packet
-// with a TMA bulk copy (mbarrier completion) and then works on it alone:
+// the run's packets in turn.  Each warp stages its packet with a TMA bulk copy
+// (mbarrier completion) and then works on it alone:
 //
-//  1. boundaries: every lane walks a 32*BW-word segment speculatively from
-//     the segment start, marking the offsets it visits; the warp stitches
-//     the segments (a lane assumes its entry offset is its predecessor's
-//     speculative exit; the first lane whose exit breaks that assumption
-//     hands its successor the right entry, one ballot round per such lane).
-//     The marks are then exactly the event starts of the chain from offset 0.
-//  2. the event offsets are compacted and dealt out in equal runs, one run per
-//     lane, so that every lane decodes the same number of events (stored
-//     transposed: the i-th event of every lane's run sits in one 64-byte row);
-//  3. validation and per-lane summaries (entries, timestamp monoid, depth
-//     monoid, stack slots used), then warp shuffle scans of the summaries;
-//  4. decode with a per-lane call stack: entries are pushed, exits pop the
-//     lane's own entries (pairs are tallied and their interval slots written
-//     at once), exits on an empty lane stack are kept as lane-pending;
-//  5. merge of the lane frontiers with the bracket monoid
-//     (p1,o1).(p2,o2) = (p1 + max(p2-o1,0), o2 + max(o1-p2,0)): the k-th
-//     pending exit of lane i pops height A_i-1-k, held by the latest earlier
-//     lane whose base is <= that height (found from per-height ballots);
-//     what no lane of the packet pops is the packet's frontier (pending exits,
-//     open entries), resolved across packets by frontier.cu.
-// Packets with more than kEvMax events, or whose lanes need more than kStack
-// stack slots, are appended to the fallback list for the CTA kernel.
+//  1. boundaries: every lane walks a 32*BW-word segment speculatively from the
+//     segment start, marking the offsets it visits; the warp stitches the
+//     segments (a lane assumes its entry offset is its predecessor's
+//     speculative exit; the first lane whose exit breaks that assumption hands
+//     its successor the right entry, one ballot round per such lane).  The
+//     marks are then exactly the event starts of the chain from offset 0, and
+//     they are compacted into the packet's event offsets, in order.
+//  2. validation, 32 events at a time (one per lane): format checks and a
+//     warp scan of the depth monoid (sum, min-prefix), carried across the
+//     batches, giving the packet's depth range;
+//  3. pairing, 32 events at a time: warp scans of the timestamp monoid
+//     (has_abs, value), the depth monoid and the entry count give each
+//     event's timestamp, depths before/after and entry rank.  An exit at
+//     depth h after it closes the latest earlier entry at height h: in its
+//     batch (the highest earlier lane of the same height, from match-any), or
+//     else the packet's latest entry at h kept in a per-height table (written
+//     by the last entry of each height in each batch).  An exit whose height is
+//     below every depth reached so far pops an entry of an earlier packet: it
+//     is a pending exit.  The table rows left at the end, heights from the
+//     minimum depth up to the final depth, are the packet's open entries.
+//     Pending exits and open entries form the packet's frontier, resolved
+//     across packets by frontier.cu.
+// Every lane runs the same instructions on its event; pairs are tallied with
+// fire-and-forget global reductions on the (group, function) cells and their
+// interval slots are written at once.  Packets with more than kEvMax events or
+// a depth range over kHeights go to the CTA kernel of analyze.cu (appended to
+// the fallback list).
 #include <algorithm>
 
 #include "device_util.cuh"
@@ -39,31 +42,27 @@ namespace thapi {
 namespace {
 using namespace dev;
 
-constexpr int kStack = 12;             // lane stack slots (pending exits below open entries)
-constexpr uint32_t kEvMax = 1024;      // events of one packet the warp path takes
-constexpr uint32_t kClsMax = 4096;     // class rows held in shared memory
-constexpr uint32_t kHMax = 64;         // heights with a precomputed owner mask
-constexpr uint32_t kChunk = 2048;      // frontier items grabbed per global atomic
-constexpr uint32_t kMaxWarps = 16;     // warps per CTA
+constexpr uint32_t kEvMax = 1024;       // events of one packet the warp path takes
+constexpr uint32_t kHeights = 64;       // per-height table rows (depth range of a packet)
+constexpr uint32_t kClsMax = 4096;      // class rows held in shared memory
+constexpr uint32_t kChunk = 2048;       // frontier items grabbed per global atomic
+constexpr uint32_t kMaxWarps = 16;      // warps per CTA
+constexpr uint32_t kFull = 0xffffffffu;
 
 __host__ __device__ inline uint32_t rup(uint32_t v, uint32_t a) { return (v + a - 1u) / a * a; }
 
 struct WLayout {
-  uint32_t off_stk, off_off, off_bpc, off_hm, off_bar, warp_bytes;  // within one warp's block
-  uint32_t off_ctab, off_cfn, total;                                // CTA-wide
+  uint32_t off_off, off_tab, off_bar, warp_bytes;  // within one warp's block
+  uint32_t off_ctab, off_cfn, total;               // CTA-wide
 };
 
 __host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t NW, uint32_t NC) {
   WLayout L;
   uint32_t o = rup(P + 48u, 128u);  // packet (header + content) and a zeroed tail
-  L.off_stk = o;
-  o += kStack * 32u * 16u;  // slot timestamps, slot metadata
+  L.off_tab = o;
+  o += kHeights * 16u;  // per-height table: entry timestamp, entry metadata
   L.off_off = o;
   o += kEvMax * 2u;
-  L.off_bpc = o;
-  o += 32u * 4u;
-  L.off_hm = o;
-  o += kHMax * 4u;
   L.off_bar = o;
   o += 16u;
   L.warp_bytes = rup(o, 128u);
@@ -91,25 +90,45 @@ __device__ __forceinline__ uint32_t step(const uint32_t *C, uint32_t o, const ui
   return o + (ok ? len : 1u);
 }
 
-// Walks from o while o < b, marking the offsets visited; with STOP, returns at
-// the first offset already marked in `stop`.
-template <bool STOP, int BW>
-__device__ __forceinline__ uint32_t walk(const uint32_t *C, uint32_t o, uint32_t a, uint32_t b, const Bits<BW> &stop,
-                                         Bits<BW> &marks, const uint32_t *ctab, uint32_t NC) {
+// Walks from o while o < b, marking the offsets visited; returns at the first
+// offset already marked in `stop`.
+template <int BW>
+__device__ __forceinline__ uint32_t walk_to(const uint32_t *C, uint32_t o, uint32_t a, uint32_t b, const Bits<BW> &stop,
+                                            Bits<BW> &marks, const uint32_t *ctab, uint32_t NC) {
   while (o < b) {
-    if (STOP && stop.test(o - a)) return o;
+    if (stop.test(o - a)) return o;
     marks.set(o - a);
     o = step(C, o, ctab, NC);
   }
   return o;
 }
 
-// (p, o) bracket monoid
-__device__ __forceinline__ void bm(uint32_t &p1, uint32_t &o1, uint32_t p2, uint32_t o2) {
-  const uint32_t np = p1 + (p2 > o1 ? p2 - o1 : 0u);
-  const uint32_t no = o2 + (o1 > p2 ? o1 - p2 : 0u);
-  p1 = np;
-  o1 = no;
+// Event starts of segment [a, b) when its chain enters at y: the speculative
+// marks from where the chain meets them, plus the offsets walked before that.
+// Returns the chain's exit offset.
+template <int BW>
+__device__ __forceinline__ uint32_t resolve_seg(const uint32_t *C, uint32_t y, uint32_t a, uint32_t b,
+                                                const Bits<BW> &spec, uint32_t spec_x, Bits<BW> &bits,
+                                                const uint32_t *ctab, uint32_t NC) {
+  if (y == a && a < b) {
+    bits = spec;
+    return spec_x;
+  }
+  if (y >= b) {
+    bits.clear();
+    return y;
+  }
+  Bits<BW> walked;
+  walked.clear();
+  const uint32_t m = walk_to<BW>(C, y, a, b, spec, walked, ctab, NC);
+  if (m < b) {
+    bits = spec;
+    bits.keep_from(m - a);
+    bits.merge(walked);
+    return spec_x;
+  }
+  bits = walked;
+  return m;
 }
 
 // Interval slot, written as three 8-byte words.
@@ -122,29 +141,47 @@ __device__ __forceinline__ void put_interval(thapi_interval *dst, uint64_t start
          ((unsigned long long)flags << 56);
 }
 
-// Open-entry slot metadata: func | rank << 16 | level << 32 | pending-before << 40.
-// Pending-exit slot metadata: func | error << 16.
-__device__ __forceinline__ uint64_t open_meta(uint32_t fn, uint32_t rank, uint32_t lvl, uint32_t np) {
+// Entry metadata: func | rank << 16 | level << 32 | depth below the packet start << 40.
+__device__ __forceinline__ uint64_t entry_meta(uint32_t fn, uint32_t rank, uint32_t lvl, uint32_t np) {
   return (uint64_t)fn | ((uint64_t)rank << 16) | ((uint64_t)lvl << 32) | ((uint64_t)np << 40);
+}
+
+// Inclusive warp scans.
+__device__ __forceinline__ DM scan_dm(DM x, uint32_t lane) {
+#pragma unroll
+  for (int q = 1; q < 32; q <<= 1) {
+    const int us = __shfl_up_sync(kFull, x.s, q), um = __shfl_up_sync(kFull, x.m, q);
+    if (lane >= (uint32_t)q) x = d_op(DM{us, um}, x);
+  }
+  return x;
+}
+__device__ __forceinline__ TsM scan_ts(TsM x, uint32_t lane) {
+#pragma unroll
+  for (int q = 1; q < 32; q <<= 1) {
+    const uint32_t uh = __shfl_up_sync(kFull, x.has, q);
+    const uint64_t uv = __shfl_up_sync(kFull, x.v, q);
+    if (lane >= (uint32_t)q) x = ts_op(TsM{uh, uv}, x);
+  }
+  return x;
 }
 
 template <int BW>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p, uint32_t NW, unsigned int *status) {
   extern __shared__ __align__(128) uint8_t sm[];
   constexpr uint32_t SEGW = 32u * BW;
-  const int lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t gt = ~((2u << lane) - 1u);
   const uint32_t F = p.n_funcs;
   const uint32_t NC = p.n_classes;
   const WLayout L = wlayout(p.P, NW, NC);
   uint8_t *wb = sm + warp * L.warp_bytes;
   uint8_t *buf = wb;
   uint32_t *C = reinterpret_cast<uint32_t *>(buf + kPacketHeader);
-  uint64_t *stk_ts = reinterpret_cast<uint64_t *>(wb + L.off_stk);
-  uint64_t *stk_md = stk_ts + kStack * 32;
+  uint64_t *tab_ts = reinterpret_cast<uint64_t *>(wb + L.off_tab);  // [height - minimum depth]
+  uint64_t *tab_md = tab_ts + kHeights;
   uint16_t *s_off = reinterpret_cast<uint16_t *>(wb + L.off_off);
-  uint32_t *s_bpc = reinterpret_cast<uint32_t *>(wb + L.off_bpc);
-  uint32_t *s_hm = reinterpret_cast<uint32_t *>(wb + L.off_hm);
   uint64_t *bar = reinterpret_cast<uint64_t *>(wb + L.off_bar);
   uint32_t *ctab = reinterpret_cast<uint32_t *>(sm + L.off_ctab);
   uint16_t *cfn = reinterpret_cast<uint16_t *>(sm + L.off_cfn);
@@ -202,164 +239,92 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     dcur = dnext;  // next packet's descriptor (its copy is issued once the buffer is free)
     if (w + 2 * NW < w_end) dnext = load_desc(p.desc + pos_of(w + 2 * NW));
     const bool ok_wait = mbar_wait_bounded(bar, phase);
-    if (__any_sync(0xffffffffu, !ok_wait)) {
+    if (__any_sync(kFull, !ok_wait)) {
       timed_out = true;
       break;
     }
     phase ^= 1u;
     issued = false;
     const uint32_t W = d.content >> 2;
-    if (lane < 4) C[W + lane] = 0;
+    if (lane < 8) C[W + lane] = 0;
     __syncwarp();
 
     // ---- 1. boundaries
-    const uint32_t a = (uint32_t)lane * SEGW;
+    const uint32_t a = lane * SEGW;
     const uint32_t b = min(a + SEGW, W);
-    Bits<BW> spec;
+    Bits<BW> spec, bits;
     spec.clear();
-    const uint32_t spec_x = a < b ? walk<false, BW>(C, a, a, b, spec, spec, ctab, NC) : a;
-    Bits<BW> bits;
-    auto resolve = [&](uint32_t y) -> uint32_t {
-      if (y == a && a < b) {
-        bits = spec;
-        return spec_x;
-      }
-      if (y >= b) {
-        bits.clear();
-        return y;
-      }
-      Bits<BW> walked;
-      walked.clear();
-      const uint32_t m = walk<true, BW>(C, y, a, b, spec, walked, ctab, NC);
-      if (m < b) {
-        bits = spec;
-        bits.keep_from(m - a);
-        bits.merge(walked);
-        return spec_x;
-      }
-      bits = walked;
-      return m;
-    };
+    uint32_t o = a;
+    while (o < b) {
+      spec.set(o - a);
+      o = step(C, o, ctab, NC);
+    }
+    const uint32_t spec_x = a < b ? o : a;
     const bool succ_live = a + SEGW < W;
-    uint32_t ent = __shfl_up_sync(0xffffffffu, spec_x, 1);
+    uint32_t ent = __shfl_up_sync(kFull, spec_x, 1);
     if (lane == 0) ent = 0;
-    uint32_t x = resolve(ent);
+    uint32_t x = resolve_seg<BW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
     for (int r = 0; r < 32; ++r) {
-      const uint32_t next_ent = __shfl_down_sync(0xffffffffu, ent, 1);
-      const uint32_t bal = __ballot_sync(0xffffffffu, lane < 31 && succ_live && x != next_ent);
+      const uint32_t next_ent = __shfl_down_sync(kFull, ent, 1);
+      const uint32_t bal = __ballot_sync(kFull, lane < 31 && succ_live && x != next_ent);
       if (!bal) break;
       const int k = __ffs(bal) - 1;
-      const uint32_t xk = __shfl_sync(0xffffffffu, x, k);
-      if (lane == k + 1) {
+      const uint32_t xk = __shfl_sync(kFull, x, k);
+      if (lane == (uint32_t)k + 1) {
         ent = xk;
-        x = resolve(ent);
+        x = resolve_seg<BW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
       }
     }
-
-    // ---- 2. compact the event offsets
     const uint32_t cnt = bits.count();
     uint32_t cinc = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, cinc, o);
-      if (lane >= o) cinc += u;
+    for (int q = 1; q < 32; q <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, cinc, q);
+      if (lane >= (uint32_t)q) cinc += u;
     }
-    const uint32_t c_tot = __shfl_sync(0xffffffffu, cinc, 31);
+    const uint32_t c_tot = __shfl_sync(kFull, cinc, 31);
     bool fallback = c_tot > kEvMax || d.nev > kEvMax;
-    bool bad = false;
-    uint32_t e0 = 0, e1 = 0;
     if (!fallback) {
-      // event e is the (e % per)-th of lane e / per's run: s_off[(e % per) * 32 + e / per]
-      const uint32_t per = (c_tot + 31u) >> 5;
-      const uint32_t inv = per ? (65536u + per - 1u) / per : 0u;  // e / per = (e * inv) >> 16 for e < 1024
       uint32_t e = cinc - cnt;
 #pragma unroll
       for (int k = 0; k < BW; ++k) {
         uint32_t m = bits.w[k];
         while (m) {
-          const uint32_t q = (e * inv) >> 16;
-          s_off[(e - q * per) * 32 + q] = (uint16_t)(a + k * 32 + (__ffs(m) - 1));
+          s_off[e++] = (uint16_t)(a + k * 32 + (__ffs(m) - 1));
           m &= m - 1;
-          ++e;
         }
       }
-      e0 = min((uint32_t)lane * per, c_tot);
-      e1 = min(e0 + per, c_tot);
     }
     __syncwarp();
+    const uint32_t nb = fallback ? 0u : (c_tot + 31) >> 5;  // batches of 32 events
 
-    // ---- 3. validation + lane summaries over events [e0, e1)
-    uint32_t n_entry = 0;
-    TsM tsum{0, 0};
-    DM dsum{0, 0};
-    int slots_used = 0;
+    // ---- 2. validation and the packet's depth range
     uint32_t ekey = 0xFFFFFFFFu;  // event index << 3 | code of the first bad event
-    for (uint32_t e = e0; e < e1; ++e) {
-      const uint32_t oo = s_off[(e - e0) * 32 + (uint32_t)lane];
+    DM dc{0, 0};                  // depth monoid of the batches so far
+    int dmax = 0;
+    for (uint32_t bt = 0; bt < nb; ++bt) {
+      const uint32_t e = bt * 32 + lane;
+      const bool act = e < c_tot;
+      const uint32_t oo = act ? s_off[e] : W;
       const uint32_t w0 = C[oo], w1 = C[oo + 1];
       const uint32_t c = w1 & 0xFFFFu;
       const bool ext = (w0 & kExtBit) != 0;
       const uint32_t r = ctab[c < NC ? c : NC];
       const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
-      uint32_t code = 0;
-      if (oo + 2 > W)
-        code = THAPI_E_TRUNCATED;
-      else if ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0))
-        code = THAPI_E_FORMAT;
-      else if (oo + sz > W)
-        code = THAPI_E_TRUNCATED;
-      if (code) {
-        if (ekey == 0xFFFFFFFFu) ekey = (e << 3) | code;
-      } else {
-        const uint32_t kd = row_kind(r);
-        const int dv = kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
-        n_entry += kd == kEntry ? 1u : 0u;
-        dsum.s += dv;
-        dsum.m = min(dsum.m, dsum.s);
-        slots_used = max(slots_used, dsum.s - 2 * dsum.m);  // pending exits + open entries
-        if (ext) {
-          tsum.has = 1;
-          tsum.v = (uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32);
-        } else {
-          tsum.v += w0 & kDeltaMask;
-        }
-      }
+      const uint32_t code = oo + 2 > W ? THAPI_E_TRUNCATED
+                            : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
+                            : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
+      if (act && code) ekey = min(ekey, (e << 3) | code);
+      const uint32_t kd = row_kind(r);
+      const int dv = (!act || code) ? 0 : kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
+      const DM inc = d_op(dc, scan_dm(DM{dv, min(dv, 0)}, lane));
+      dmax = max(dmax, inc.s);
+      dc = DM{__shfl_sync(kFull, inc.s, 31), __shfl_sync(kFull, inc.m, 31)};
     }
-    // warp scans (exclusive) of entries, timestamps, depth
-    uint32_t ei = n_entry;
-    TsM ti = tsum;
-    DM di = dsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t ue = __shfl_up_sync(0xffffffffu, ei, o);
-      const uint32_t uh = __shfl_up_sync(0xffffffffu, ti.has, o);
-      const uint64_t uv = __shfl_up_sync(0xffffffffu, ti.v, o);
-      const int us = __shfl_up_sync(0xffffffffu, di.s, o);
-      const int um = __shfl_up_sync(0xffffffffu, di.m, o);
-      if (lane >= o) {
-        ei += ue;
-        ti = ts_op(TsM{uh, uv}, ti);
-        di = d_op(DM{us, um}, di);
-      }
-    }
-    const uint32_t e_tot = __shfl_sync(0xffffffffu, ei, 31);
-    const int dtot_s = __shfl_sync(0xffffffffu, di.s, 31), dtot_m = __shfl_sync(0xffffffffu, di.m, 31);
-    uint32_t e_ex = __shfl_up_sync(0xffffffffu, ei, 1);
-    uint32_t hex = __shfl_up_sync(0xffffffffu, ti.has, 1);
-    uint64_t vex = __shfl_up_sync(0xffffffffu, ti.v, 1);
-    int sex = __shfl_up_sync(0xffffffffu, di.s, 1), mex = __shfl_up_sync(0xffffffffu, di.m, 1);
-    if (lane == 0) {
-      e_ex = 0;
-      hex = 0;
-      vex = 0;
-      sex = 0;
-      mex = 0;
-    }
-    const uint32_t gkey = __reduce_min_sync(0xffffffffu, ekey);
-    if (!fallback) {
-      bad = gkey != 0xFFFFFFFFu || c_tot != d.nev;
-      fallback = !bad && __any_sync(0xffffffffu, slots_used > kStack);
-    }
+    const uint32_t gkey = __reduce_min_sync(kFull, ekey);
+    dmax = __reduce_max_sync(kFull, dmax);
+    const bool bad = !fallback && (gkey != 0xFFFFFFFFu || c_tot != d.nev);
+    fallback = fallback || (!bad && (uint32_t)(dmax - dc.m) > kHeights);
     if (bad || fallback) {
       if (lane == 0) {
         if (bad)
@@ -374,9 +339,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       continue;
     }
 
-    // ---- 4. decode with per-lane call stacks
-    const uint32_t P_p = (uint32_t)(-dtot_m);
-    const uint32_t O_p = (uint32_t)(dtot_s - dtot_m);
+    // ---- 3. pairing, 32 events at a time
+    const int dmin = dc.m;  // minimum depth (packet-relative, <= 0); heights are indexed from it
+    const uint32_t P_p = (uint32_t)(-dmin);
+    const uint32_t O_p = (uint32_t)(dc.s - dmin);
     uint64_t fbase = 0;
     if (lane == 0) {
       const uint32_t need = P_p + O_p;
@@ -396,171 +362,106 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         }
       }
     }
-    fbase = __shfl_sync(0xffffffffu, fbase, 0);
+    fbase = __shfl_sync(kFull, fbase, 0);
     thapi_interval *const pslots = p.slots ? p.slots + d.evbase : nullptr;
     Cell *const gcells = p.tally + (uint64_t)d.group * F;
-    auto tally = [&](uint32_t fn, uint64_t dur, uint32_t err) {
-      Cell &cell = gcells[fn];
-      atomicAdd(&cell.count, 1ull);
-      atomicAdd(&cell.total, (unsigned long long)dur);
-      atomicMin(&cell.mn, (unsigned long long)dur);
-      atomicMax(&cell.mx, (unsigned long long)dur);
-      if (err) atomicAdd(&cell.err, 1ull);
-    };
     uint32_t valid = 0, mism = 0;
-    // one pair: entry (ets, metadata em) closed by an exit (xts, xfn, xerr)
-    auto emit = [&](uint64_t ets, uint64_t em, uint64_t xts, uint32_t xfn, uint32_t xerr) {
-      const uint32_t efn = (uint32_t)(em & 0xFFFFu);
-      uint32_t flags = 0;
-      if (efn == xfn) {
-        ++valid;
-        flags = kIvValid | xerr;
-        tally(xfn, xts - ets, xerr);
-      } else {
-        ++mism;  // mismatched pair: no interval
-      }
-      if (pslots)
-        put_interval(pslots + ((em >> 16) & 0xFFFFu), ets, xts, (uint32_t)((em >> 40) & 0xFFFFu), efn,
-                     (uint32_t)((em >> 32) & 0xFFu), flags);
-    };
-    uint64_t t = hex ? vex : d.tsb + vex;
-    int depth = sex;   // packet-relative depth before the next event
-    int runmin = mex;  // packet-relative running minimum of the depth (<= 0)
-    uint32_t rank = e_ex;
-    uint32_t top = 0, pc = 0;
-    bool first = true;
-    const uint32_t n_run = e1 - e0;
-    uint32_t oo_n = 0, w0_n = 0, w1_n = 0;  // next event of the run, loaded one step ahead
-    if (n_run) {
-      oo_n = s_off[lane];
-      w0_n = C[oo_n];
-      w1_n = C[oo_n + 1];
-    }
-    for (uint32_t i = 0; i < n_run; ++i) {
-      const uint32_t oo = oo_n, w0 = w0_n, w1 = w1_n;
-      if (i + 1 < n_run) {
-        oo_n = s_off[(i + 1) * 32 + (uint32_t)lane];
-        w0_n = C[oo_n];
-        w1_n = C[oo_n + 1];
-      }
-      const uint32_t c = w1 & 0xFFFFu;
+    TsM tc{0, 0};         // timestamp monoid of the batches so far
+    DM dp{0, 0};          // depth monoid of the batches so far
+    uint32_t rank_c = 0;  // entries so far
+    uint32_t pend_c = 0;  // pending exits so far
+    for (uint32_t bt = 0; bt < nb; ++bt) {
+      const uint32_t e = bt * 32 + lane;
+      const bool act = e < c_tot;
+      const uint32_t oo = act ? s_off[e] : W;
+      const uint32_t w0 = C[oo], w1 = C[oo + 1];
+      const uint32_t c = act ? (w1 & 0xFFFFu) : NC;
       const bool ext = (w0 & kExtBit) != 0;
       const uint32_t r = ctab[c];
-      const uint32_t kd = row_kind(r);
-      const uint32_t fn = cfn[c];
-      const uint64_t tn = ext ? ((uint64_t)C[oo + 2] | ((uint64_t)C[oo + 3] << 32)) : t + (w0 & kDeltaMask);
-      if (ext || first || tn < t) {  // a new nondecreasing run of timestamps
-        if (!first) tmax = max(tmax, t);
-        tmin = min(tmin, tn);
-        first = false;
+      const uint32_t kd = act ? row_kind(r) : kSample;
+      const uint32_t fn = cfn[min(c, NC - 1)];
+      const bool is_entry = kd == kEntry, is_exit = kd == kExit;
+      const uint64_t xts = (uint64_t)C[min(oo + 2, W)] | ((uint64_t)C[min(oo + 3, W)] << 32);
+      const int32_t rw = row_resw(r);
+      const uint32_t err =
+          (is_exit && rw >= 0 && C[min(oo + 2 + (ext ? 2u : 0u) + (uint32_t)max(rw, 0), W)] != 0) ? 1u : 0u;
+      // timestamp, depths and entry rank of every event of the batch
+      const TsM ti = ts_op(tc, scan_ts(TsM{act && ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane));
+      const uint64_t t = ti.has ? ti.v : d.tsb + ti.v;
+      const int dv = is_entry ? 1 : (is_exit ? -1 : 0);
+      const DM din = scan_dm(DM{dv, min(dv, 0)}, lane);
+      DM dex{__shfl_up_sync(kFull, din.s, 1), __shfl_up_sync(kFull, din.m, 1)};
+      if (lane == 0) dex = DM{0, 0};
+      const DM before = d_op(dp, dex);   // depth and running minimum before the event
+      const int post = before.s + dv;    // depth after the event
+      const uint32_t ebal = __ballot_sync(kFull, is_entry);
+      const uint32_t rank = rank_c + __popc(ebal & lt);
+      const uint64_t meta = entry_meta(fn, rank, (uint32_t)min(before.s - before.m, 255), (uint32_t)(-before.m));
+      // matching: the latest earlier entry at the exit's height
+      const uint32_t key = is_entry ? (uint32_t)(before.s - dmin) : is_exit ? (uint32_t)(post - dmin) : (0x80000000u | lane);
+      const uint32_t peers = __match_any_sync(kFull, key);
+      const uint32_t cand = is_exit ? (peers & ebal & lt) : 0u;
+      const int src = cand ? 31 - __clz(cand) : (int)lane;
+      const uint64_t ets_b = __shfl_sync(kFull, t, src), em_b = __shfl_sync(kFull, meta, src);
+      const bool from_tab = is_exit && !cand && post >= before.m;
+      const bool pend = is_exit && !cand && post < before.m;
+      uint64_t ets = ets_b, em = em_b;
+      if (from_tab) {
+        ets = tab_ts[post - dmin];
+        em = tab_md[post - dmin];
       }
-      t = tn;
-      if (kd == kEntry) {
-        const uint32_t si = (pc + top) * 32 + (uint32_t)lane;
-        stk_ts[si] = t;
-        stk_md[si] = open_meta(fn, rank, (uint32_t)min(depth - runmin, 255), (uint32_t)(-runmin));
-        ++top;
-        ++rank;
-        ++depth;
-      } else if (kd == kExit) {
-        const int32_t rw = row_resw(r);
-        const uint32_t err = (rw >= 0 && C[oo + 2 + (ext ? 2 : 0) + rw] != 0) ? 1u : 0u;
-        --depth;
-        runmin = min(runmin, depth);
-        if (top) {
-          --top;
-          const uint32_t si = (pc + top) * 32 + (uint32_t)lane;
-          emit(stk_ts[si], stk_md[si], t, fn, err);
+      if (cand || from_tab) {  // one pair: entry (ets, em) closed by this exit
+        const uint32_t efn = (uint32_t)(em & 0xFFFFu);
+        uint32_t flags = 0;
+        if (efn == fn) {
+          ++valid;
+          flags = kIvValid | err;
+          const uint64_t dur = t - ets;
+          Cell &cell = gcells[fn];
+          atomicAdd(&cell.count, 1ull);
+          atomicAdd(&cell.total, (unsigned long long)dur);
+          atomicMin(&cell.mn, (unsigned long long)dur);
+          atomicMax(&cell.mx, (unsigned long long)dur);
+          if (err) atomicAdd(&cell.err, 1ull);
         } else {
-          const uint32_t si = pc * 32 + (uint32_t)lane;
-          stk_ts[si] = t;
-          stk_md[si] = (uint64_t)fn | ((uint64_t)err << 16);
-          ++pc;
+          ++mism;  // mismatched pair: no interval
         }
-      } else {
-        ++n_other;
+        if (pslots)
+          put_interval(pslots + ((em >> 16) & 0xFFFFu), ets, t, (uint32_t)((em >> 40) & 0xFFFFu), efn,
+                       (uint32_t)((em >> 32) & 0xFFu), flags);
       }
+      const uint32_t pbal = __ballot_sync(kFull, pend);
+      if (pend && fbase != ~0ull) {
+        Frontier fr;
+        fr.ts = t;
+        fr.aux = err;
+        fr.func = (uint16_t)fn;
+        fr.flags = 0;
+        p.frontier[fbase + pend_c + __popc(pbal & lt)] = fr;
+      }
+      __syncwarp();  // the table is read above before the batch's entries update it
+      if (is_entry && (peers & ebal & gt) == 0) {  // the batch's last entry at its height
+        tab_ts[before.s - dmin] = t;
+        tab_md[before.s - dmin] = meta;
+      }
+      __syncwarp();
+      if (act) {
+        tmin = min(tmin, t);
+        tmax = max(tmax, t);
+      }
+      n_other += (act && !is_entry && !is_exit) ? 1u : 0u;
+      tc = TsM{__shfl_sync(kFull, ti.has, 31), __shfl_sync(kFull, ti.v, 31)};
+      dp = d_op(dp, DM{__shfl_sync(kFull, din.s, 31), __shfl_sync(kFull, din.m, 31)});
+      rank_c += __popc(ebal);
+      pend_c += __popc(pbal);
     }
-    if (!first) tmax = max(tmax, t);
     __syncwarp();
     // the packet bytes are no longer needed: stage the next packet now
     if (lane == 0 && has_next) issue(dcur);
     issued = has_next;
-
-    // ---- 5. warp merge of the lane frontiers
-    uint32_t sp = pc, so = top;  // inclusive bracket-monoid scan over lanes
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t up = __shfl_up_sync(0xffffffffu, sp, o);
-      const uint32_t uo = __shfl_up_sync(0xffffffffu, so, o);
-      if (lane >= o) {
-        uint32_t tp = up, to = uo;
-        bm(tp, to, sp, so);
-        sp = tp;
-        so = to;
-      }
-    }
-    uint32_t pb = __shfl_up_sync(0xffffffffu, sp, 1), A = __shfl_up_sync(0xffffffffu, so, 1);
-    if (lane == 0) {
-      pb = 0;
-      A = 0;
-    }
-    const uint32_t base = A > pc ? A - pc : 0u;
-    s_bpc[lane] = base | (pc << 16);
-    uint32_t later;  // min base of the lanes after me
-    {
-      uint32_t suf = base;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_down_sync(0xffffffffu, suf, o);
-        if (lane + o < 32) suf = min(suf, u);
-      }
-      later = __shfl_down_sync(0xffffffffu, suf, 1);
-      if (lane == 31) later = 0xFFFFFFFFu;
-    }
-    // owner masks: bit j of s_hm[h] is set when lane j's base is <= h
-    const uint32_t hq = __reduce_max_sync(0xffffffffu, pc ? A : 0u);
-    const bool masks = hq <= kHMax;
-    if (masks)
-      for (uint32_t h = 0; h < hq; ++h) {
-        const uint32_t m = __ballot_sync(0xffffffffu, base <= h);
-        if (lane == 0) s_hm[h] = m;
-      }
-    __syncwarp();
-    // my pending exits: pop earlier lanes' opens, the rest leave the packet
-    for (uint32_t k = 0; k < pc; ++k) {
-      const uint32_t si = k * 32 + (uint32_t)lane;
-      const uint64_t xts = stk_ts[si];
-      const uint64_t xm = stk_md[si];
-      const uint32_t xfn = (uint32_t)(xm & 0xFFFFu), xerr = (uint32_t)((xm >> 16) & 1u);
-      if (k < A) {
-        const uint32_t h = A - 1 - k;
-        int j;
-        if (masks) {
-          j = 31 - __clz(s_hm[h] & ((1u << lane) - 1u));
-        } else {
-          j = lane - 1;
-          while (j > 0 && (s_bpc[j] & 0xFFFFu) > h) --j;
-        }
-        const uint32_t bj = s_bpc[j];
-        const uint32_t it = ((bj >> 16) + h - (bj & 0xFFFFu)) * 32 + (uint32_t)j;
-        emit(stk_ts[it], stk_md[it], xts, xfn, xerr);
-      } else if (fbase != ~0ull) {
-        Frontier fr;
-        fr.ts = xts;
-        fr.aux = xerr;
-        fr.func = (uint16_t)xfn;
-        fr.flags = 0;
-        p.frontier[fbase + pb + (k - A)] = fr;
-      }
-    }
-    // my opens that no later lane pops leave the packet
-    for (uint32_t i = 0; i < top; ++i) {
-      const uint32_t h = base + i;
-      if (h >= later) break;
-      const uint32_t si = (pc + i) * 32 + (uint32_t)lane;
-      const uint64_t ots = stk_ts[si];
-      const uint64_t om = stk_md[si];
+    // the table rows from the minimum depth up to the final depth are the open entries
+    for (uint32_t k = lane; k < O_p; k += 32) {
+      const uint64_t ots = tab_ts[k], om = tab_md[k];
       const uint32_t orank = (uint32_t)((om >> 16) & 0xFFFFu);
       if (fbase != ~0ull) {
         Frontier fr;
@@ -568,7 +469,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         fr.aux = pslots ? orank : 0xFFFFFFFFu;
         fr.func = (uint16_t)(om & 0xFFFFu);
         fr.flags = 0;
-        p.frontier[fbase + P_p + h] = fr;
+        p.frontier[fbase + P_p + k] = fr;
       }
       if (pslots)
         put_interval(pslots + orank, ots, 0, (uint32_t)((om >> 40) & 0xFFFFu), (uint32_t)(om & 0xFFFFu),
@@ -576,15 +477,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     }
     n_mismatch += mism;
     n_pairs += valid;
-    const uint32_t vsum = __reduce_add_sync(0xffffffffu, valid);
+    const uint32_t vsum = __reduce_add_sync(kFull, valid);
     if (lane == 0) {
       p.sum_pend[pos] = P_p;
       p.sum_open[pos] = O_p;
       p.sum_fbase[pos] = fbase;
-      p.sum_nslot[pos] = e_tot;
+      p.sum_nslot[pos] = rank_c;
       p.sum_nvalid[pos] = vsum;
       n_events += c_tot;
-      if (p.slots) n_slots += e_tot;
+      if (p.slots) n_slots += rank_c;
       n_disc += d.disc;
       n_pk += 1;
     }
@@ -597,11 +498,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   }
 
   for (int off = 16; off > 0; off >>= 1) {
-    n_mismatch += __shfl_down_sync(0xffffffffu, n_mismatch, off);
-    n_other += __shfl_down_sync(0xffffffffu, n_other, off);
-    n_pairs += __shfl_down_sync(0xffffffffu, n_pairs, off);
-    tmin = min(tmin, __shfl_down_sync(0xffffffffu, tmin, off));
-    tmax = max(tmax, __shfl_down_sync(0xffffffffu, tmax, off));
+    n_mismatch += __shfl_down_sync(kFull, n_mismatch, off);
+    n_other += __shfl_down_sync(kFull, n_other, off);
+    n_pairs += __shfl_down_sync(kFull, n_pairs, off);
+    tmin = min(tmin, __shfl_down_sync(kFull, tmin, off));
+    tmax = max(tmax, __shfl_down_sync(kFull, tmax, off));
   }
   if (lane == 0) {
     if (n_mismatch) atomicAdd(&p.diag[dMismatch], n_mismatch);
@@ -614,7 +515,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     if (n_pk) atomicAdd(&p.diag[dPackets], n_pk);
     if (n_slots && p.slots_written) atomicAdd(p.slots_written, n_slots);
   }
-
 }
 
 template <int BW>
@@ -627,6 +527,7 @@ cudaError_t launch_w(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, 
   return cudaGetLastError();
 }
 
+// Bitmap words per lane segment for packets of P bytes (0: too large for the warp kernel).
 int warp_bw(uint32_t P) {
   const uint32_t wmax = (P - kPacketHeader) / 4;
   if (wmax <= 32u * 32) return 1;
