@@ -284,45 +284,52 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     }
     const uint32_t c_tot = __shfl_sync(kFull, cinc, 31);
     bool fallback = c_tot > kEvMax || d.nev > kEvMax;
+    // ---- 2. compaction and validation: each lane stores its events' offsets
+    // in order and checks them, folding the depth monoid (sum, min-prefix) and
+    // the highest depth of its events
+    uint32_t ekey = 0xFFFFFFFFu;  // event index << 3 | code of the first bad event
+    DM ld{0, 0};
+    int lmax = 0;
     if (!fallback) {
       uint32_t e = cinc - cnt;
 #pragma unroll
       for (int k = 0; k < BW; ++k) {
         uint32_t m = bits.w[k];
         while (m) {
-          s_off[e++] = (uint16_t)(a + k * 32 + (__ffs(m) - 1));
+          const uint32_t oo = a + k * 32 + (__ffs(m) - 1);
           m &= m - 1;
+          s_off[e] = (uint16_t)oo;
+          const uint32_t w0 = C[oo], w1 = C[oo + 1];
+          const uint32_t c = w1 & 0xFFFFu;
+          const bool ext = (w0 & kExtBit) != 0;
+          const uint32_t r = ctab[c < NC ? c : NC];
+          const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+          const uint32_t code = oo + 2 > W ? THAPI_E_TRUNCATED
+                                : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
+                                : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
+          if (code) ekey = min(ekey, (e << 3) | code);
+          const uint32_t kd = row_kind(r);
+          const int dv = code ? 0 : kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
+          ld.s += dv;
+          ld.m = min(ld.m, ld.s);
+          lmax = max(lmax, ld.s);
+          ++e;
         }
       }
     }
     __syncwarp();
     const uint32_t nb = fallback ? 0u : (c_tot + 31) >> 5;  // batches of 32 events
-
-    // ---- 2. validation and the packet's depth range
-    uint32_t ekey = 0xFFFFFFFFu;  // event index << 3 | code of the first bad event
-    DM dc{0, 0};                  // depth monoid of the batches so far
-    int dmax = 0;
-    for (uint32_t bt = 0; bt < nb; ++bt) {
-      const uint32_t e = bt * 32 + lane;
-      const bool act = e < c_tot;
-      const uint32_t oo = act ? s_off[e] : W;
-      const uint32_t w0 = C[oo], w1 = C[oo + 1];
-      const uint32_t c = w1 & 0xFFFFu;
-      const bool ext = (w0 & kExtBit) != 0;
-      const uint32_t r = ctab[c < NC ? c : NC];
-      const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
-      const uint32_t code = oo + 2 > W ? THAPI_E_TRUNCATED
-                            : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
-                            : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
-      if (act && code) ekey = min(ekey, (e << 3) | code);
-      const uint32_t kd = row_kind(r);
-      const int dv = (!act || code) ? 0 : kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
-      const DM inc = d_op(dc, scan_dm(DM{dv, min(dv, 0)}, lane));
-      dmax = max(dmax, inc.s);
+    // the packet's depth range: exclusive scan of the lanes' depth monoids
+    DM dc;
+    int dmax;
+    {
+      DM inc = scan_dm(ld, lane);
+      DM ex{__shfl_up_sync(kFull, inc.s, 1), __shfl_up_sync(kFull, inc.m, 1)};
+      if (lane == 0) ex = DM{0, 0};
       dc = DM{__shfl_sync(kFull, inc.s, 31), __shfl_sync(kFull, inc.m, 31)};
+      dmax = __reduce_max_sync(kFull, ex.s + lmax);
     }
     const uint32_t gkey = __reduce_min_sync(kFull, ekey);
-    dmax = __reduce_max_sync(kFull, dmax);
     const bool bad = !fallback && (gkey != 0xFFFFFFFFu || c_tot != d.nev);
     fallback = fallback || (!bad && (uint32_t)(dmax - dc.m) > kHeights);
     if (bad || fallback) {
@@ -366,8 +373,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     thapi_interval *const pslots = p.slots ? p.slots + d.evbase : nullptr;
     Cell *const gcells = p.tally + (uint64_t)d.group * F;
     uint32_t valid = 0, mism = 0;
-    TsM tc{0, 0};         // timestamp monoid of the batches so far
-    DM dp{0, 0};          // depth monoid of the batches so far
+    uint64_t tcur = d.tsb;  // timestamp of the last event so far
+    DM dp{0, 0};            // depth monoid of the batches so far
     uint32_t rank_c = 0;  // entries so far
     uint32_t pend_c = 0;  // pending exits so far
     for (uint32_t bt = 0; bt < nb; ++bt) {
@@ -385,16 +392,35 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       const int32_t rw = row_resw(r);
       const uint32_t err =
           (is_exit && rw >= 0 && C[min(oo + 2 + (ext ? 2u : 0u) + (uint32_t)max(rw, 0), W)] != 0) ? 1u : 0u;
-      // timestamp, depths and entry rank of every event of the batch
-      const TsM ti = ts_op(tc, scan_ts(TsM{act && ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane));
-      const uint64_t t = ti.has ? ti.v : d.tsb + ti.v;
+      // timestamp: 32-bit delta scan, or the (has_abs, value) monoid when the
+      // batch holds an absolute timestamp
+      uint64_t t;
+      if (__any_sync(kFull, act && ext)) {
+        t = ts_op(TsM{1u, tcur}, scan_ts(TsM{act && ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane)).v;
+      } else {
+        uint32_t x = act ? (w0 & kDeltaMask) : 0u;
+#pragma unroll
+        for (int q = 1; q < 32; q <<= 1) {
+          const uint32_t u = __shfl_up_sync(kFull, x, q);
+          if (lane >= (uint32_t)q) x += u;
+        }
+        t = tcur + x;
+      }
+      // depths: the prefix sum from entry/exit ballots, the running minimum by a min-scan
       const int dv = is_entry ? 1 : (is_exit ? -1 : 0);
-      const DM din = scan_dm(DM{dv, min(dv, 0)}, lane);
-      DM dex{__shfl_up_sync(kFull, din.s, 1), __shfl_up_sync(kFull, din.m, 1)};
-      if (lane == 0) dex = DM{0, 0};
-      const DM before = d_op(dp, dex);   // depth and running minimum before the event
-      const int post = before.s + dv;    // depth after the event
-      const uint32_t ebal = __ballot_sync(kFull, is_entry);
+      const uint32_t ebal = __ballot_sync(kFull, is_entry), xbal = __ballot_sync(kFull, is_exit);
+      const uint32_t le = lt | (1u << lane);
+      const int s_in = (int)__popc(ebal & le) - (int)__popc(xbal & le);
+      int m_in = min(s_in, 0);
+#pragma unroll
+      for (int q = 1; q < 32; q <<= 1) {
+        const int u = __shfl_up_sync(kFull, m_in, q);
+        if (lane >= (uint32_t)q) m_in = min(m_in, u);
+      }
+      int m_ex = __shfl_up_sync(kFull, m_in, 1);
+      if (lane == 0) m_ex = 0;
+      const DM before{dp.s + s_in - dv, min(dp.m, dp.s + m_ex)};  // depth and running minimum before the event
+      const int post = before.s + dv;                              // depth after the event
       const uint32_t rank = rank_c + __popc(ebal & lt);
       const uint64_t meta = entry_meta(fn, rank, (uint32_t)min(before.s - before.m, 255), (uint32_t)(-before.m));
       // matching: the latest earlier entry at the exit's height
@@ -450,8 +476,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         tmax = max(tmax, t);
       }
       n_other += (act && !is_entry && !is_exit) ? 1u : 0u;
-      tc = TsM{__shfl_sync(kFull, ti.has, 31), __shfl_sync(kFull, ti.v, 31)};
-      dp = d_op(dp, DM{__shfl_sync(kFull, din.s, 31), __shfl_sync(kFull, din.m, 31)});
+      tcur = __shfl_sync(kFull, t, 31);
+      dp = d_op(dp, DM{(int)__popc(ebal) - (int)__popc(xbal), __shfl_sync(kFull, m_in, 31)});
       rank_c += __popc(ebal);
       pend_c += __popc(pbal);
     }
