@@ -80,14 +80,19 @@ __device__ __forceinline__ uint32_t row_fixedw(uint32_t r) { return r & 0x3FFFu;
 __device__ __forceinline__ uint32_t row_kind(uint32_t r) { return (r >> 14) & 7u; }
 __device__ __forceinline__ int32_t row_resw(uint32_t r) { return (int32_t)(r >> 17) - 1; }
 
-// Event chain step from word offset o; class ids out of range step one word.
+// Event chain step from word offset o.  An offset whose class id is out of
+// range is no event start: the chain moves to the next offset whose class id
+// is in range, at most four words on (the offsets a one-word-at-a-time walk
+// would pass through and land on, so every in-range offset it reaches is the
+// same).  Reads up to C[o + 4].
 __device__ __forceinline__ uint32_t step(const uint32_t *C, uint32_t o, const uint32_t *ctab, uint32_t NC) {
-  const uint32_t w0 = C[o], w1 = C[o + 1];
+  const uint32_t w0 = C[o], w1 = C[o + 1], w2 = C[o + 2], w3 = C[o + 3], w4 = C[o + 4];
   const uint32_t c = w1 & 0xFFFFu;
   const bool ok = c < NC;
   const uint32_t r = ctab[ok ? c : NC];
   const uint32_t len = 2u + ((w0 >> 26) & 2u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
-  return o + (ok ? len : 1u);
+  const uint32_t skip = (w2 & 0xFFFFu) < NC ? 1u : (w3 & 0xFFFFu) < NC ? 2u : (w4 & 0xFFFFu) < NC ? 3u : 4u;
+  return o + (ok ? len : skip);
 }
 
 // Walks from o while o < b, marking the offsets visited; returns at the first
@@ -377,45 +382,64 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     DM dp{0, 0};            // depth monoid of the batches so far
     uint32_t rank_c = 0;  // entries so far
     uint32_t pend_c = 0;  // pending exits so far
+    // the next batch's offsets, header words and class row are loaded one batch ahead
+    uint32_t n_oo, n_w0, n_w1, n_r;
+    auto prefetch = [&](uint32_t bt) {
+      const uint32_t e = bt * 32 + lane;
+      n_oo = e < c_tot ? s_off[min(e, c_tot - 1)] : W;
+      n_w0 = C[n_oo];
+      n_w1 = C[n_oo + 1];
+      n_r = ctab[e < c_tot ? (n_w1 & 0xFFFFu) : NC];
+    };
+    if (nb) prefetch(0);
     for (uint32_t bt = 0; bt < nb; ++bt) {
       const uint32_t e = bt * 32 + lane;
       const bool act = e < c_tot;
-      const uint32_t oo = act ? s_off[e] : W;
-      const uint32_t w0 = C[oo], w1 = C[oo + 1];
+      const uint32_t oo = n_oo, w0 = n_w0, w1 = n_w1, r = n_r;
+      if (bt + 1 < nb) prefetch(bt + 1);
       const uint32_t c = act ? (w1 & 0xFFFFu) : NC;
       const bool ext = (w0 & kExtBit) != 0;
-      const uint32_t r = ctab[c];
       const uint32_t kd = act ? row_kind(r) : kSample;
       const uint32_t fn = cfn[min(c, NC - 1)];
       const bool is_entry = kd == kEntry, is_exit = kd == kExit;
-      const uint64_t xts = (uint64_t)C[min(oo + 2, W)] | ((uint64_t)C[min(oo + 3, W)] << 32);
       const int32_t rw = row_resw(r);
       const uint32_t err =
           (is_exit && rw >= 0 && C[min(oo + 2 + (ext ? 2u : 0u) + (uint32_t)max(rw, 0), W)] != 0) ? 1u : 0u;
-      // timestamp: 32-bit delta scan, or the (has_abs, value) monoid when the
-      // batch holds an absolute timestamp
-      uint64_t t;
-      if (__any_sync(kFull, act && ext)) {
-        t = ts_op(TsM{1u, tcur}, scan_ts(TsM{act && ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane)).v;
-      } else {
-        uint32_t x = act ? (w0 & kDeltaMask) : 0u;
-#pragma unroll
-        for (int q = 1; q < 32; q <<= 1) {
-          const uint32_t u = __shfl_up_sync(kFull, x, q);
-          if (lane >= (uint32_t)q) x += u;
-        }
-        t = tcur + x;
-      }
-      // depths: the prefix sum from entry/exit ballots, the running minimum by a min-scan
+      // depths from the entry/exit ballots, relative to the batch start; the
+      // match on batch-relative heights (equal iff the heights are) needs nothing else
       const int dv = is_entry ? 1 : (is_exit ? -1 : 0);
       const uint32_t ebal = __ballot_sync(kFull, is_entry), xbal = __ballot_sync(kFull, is_exit);
       const uint32_t le = lt | (1u << lane);
       const int s_in = (int)__popc(ebal & le) - (int)__popc(xbal & le);
+      const uint32_t key =
+          is_entry ? (uint32_t)(s_in - dv + 64) : is_exit ? (uint32_t)(s_in + 64) : (0x80000000u | lane);
+      const uint32_t peers = __match_any_sync(kFull, key);
+      // timestamps (32-bit deltas) and the running minimum depth in one set of scan rounds
+      const bool any_ext = __any_sync(kFull, act && ext);
+      uint32_t x = act ? (w0 & kDeltaMask) : 0u;
       int m_in = min(s_in, 0);
 #pragma unroll
       for (int q = 1; q < 32; q <<= 1) {
-        const int u = __shfl_up_sync(kFull, m_in, q);
-        if (lane >= (uint32_t)q) m_in = min(m_in, u);
+        const uint32_t u = __shfl_up_sync(kFull, x, q);
+        const int um = __shfl_up_sync(kFull, m_in, q);
+        if (lane >= (uint32_t)q) {
+          x += u;
+          m_in = min(m_in, um);
+        }
+      }
+      uint64_t t;
+      if (any_ext) {  // an absolute timestamp in the batch: the (has_abs, value) monoid
+        const uint64_t xts = (uint64_t)C[min(oo + 2, W)] | ((uint64_t)C[min(oo + 3, W)] << 32);
+        t = ts_op(TsM{1u, tcur}, scan_ts(TsM{act && ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane)).v;
+        if (act) {
+          tmin = min(tmin, t);
+          tmax = max(tmax, t);
+        }
+      } else {
+        t = tcur + x;
+        // nondecreasing over the batch (lane 0 holds an event): its ends bound it
+        tmin = min(tmin, __shfl_sync(kFull, t, 0));
+        tmax = max(tmax, __shfl_sync(kFull, t, 31));
       }
       int m_ex = __shfl_up_sync(kFull, m_in, 1);
       if (lane == 0) m_ex = 0;
@@ -423,9 +447,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       const int post = before.s + dv;                              // depth after the event
       const uint32_t rank = rank_c + __popc(ebal & lt);
       const uint64_t meta = entry_meta(fn, rank, (uint32_t)min(before.s - before.m, 255), (uint32_t)(-before.m));
-      // matching: the latest earlier entry at the exit's height
-      const uint32_t key = is_entry ? (uint32_t)(before.s - dmin) : is_exit ? (uint32_t)(post - dmin) : (0x80000000u | lane);
-      const uint32_t peers = __match_any_sync(kFull, key);
       const uint32_t cand = is_exit ? (peers & ebal & lt) : 0u;
       const int src = cand ? 31 - __clz(cand) : (int)lane;
       const uint64_t ets_b = __shfl_sync(kFull, t, src), em_b = __shfl_sync(kFull, meta, src);
@@ -471,10 +492,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         tab_md[before.s - dmin] = meta;
       }
       __syncwarp();
-      if (act) {
-        tmin = min(tmin, t);
-        tmax = max(tmax, t);
-      }
       n_other += (act && !is_entry && !is_exit) ? 1u : 0u;
       tcur = __shfl_sync(kFull, t, 31);
       dp = d_op(dp, DM{(int)__popc(ebal) - (int)__popc(xbal), __shfl_sync(kFull, m_in, 31)});
