@@ -297,28 +297,43 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     int lmax = 0;
     if (!fallback) {
       uint32_t e = cinc - cnt;
+      // one event: its error code (0 if none) and depth step
+      auto check = [&](uint32_t oo, uint32_t &code, int &dv) {
+        const uint32_t w0 = C[oo], w1 = C[oo + 1];
+        const uint32_t c = w1 & 0xFFFFu;
+        const bool ext = (w0 & kExtBit) != 0;
+        const uint32_t r = ctab[c < NC ? c : NC];
+        const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+        code = oo + 2 > W ? THAPI_E_TRUNCATED
+               : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
+               : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
+        const uint32_t kd = row_kind(r);
+        dv = code ? 0 : kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
+      };
+      auto fold = [&](uint32_t code, int dv) {
+        if (code) ekey = min(ekey, (e << 3) | code);
+        ld.s += dv;
+        ld.m = min(ld.m, ld.s);
+        lmax = max(lmax, ld.s);
+        ++e;
+      };
 #pragma unroll
       for (int k = 0; k < BW; ++k) {
         uint32_t m = bits.w[k];
-        while (m) {
-          const uint32_t oo = a + k * 32 + (__ffs(m) - 1);
+        while (m) {  // two events per iteration: their loads overlap
+          const uint32_t oo0 = a + k * 32 + (__ffs(m) - 1);
           m &= m - 1;
-          s_off[e] = (uint16_t)oo;
-          const uint32_t w0 = C[oo], w1 = C[oo + 1];
-          const uint32_t c = w1 & 0xFFFFu;
-          const bool ext = (w0 & kExtBit) != 0;
-          const uint32_t r = ctab[c < NC ? c : NC];
-          const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
-          const uint32_t code = oo + 2 > W ? THAPI_E_TRUNCATED
-                                : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
-                                : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
-          if (code) ekey = min(ekey, (e << 3) | code);
-          const uint32_t kd = row_kind(r);
-          const int dv = code ? 0 : kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
-          ld.s += dv;
-          ld.m = min(ld.m, ld.s);
-          lmax = max(lmax, ld.s);
-          ++e;
+          const bool two = m != 0;
+          const uint32_t oo1 = two ? a + k * 32 + (__ffs(m) - 1) : oo0;
+          m &= m - 1;  // (no-op when m is 0)
+          s_off[e] = (uint16_t)oo0;
+          if (two) s_off[e + 1] = (uint16_t)oo1;
+          uint32_t c0, c1;
+          int d0, d1;
+          check(oo0, c0, d0);
+          check(oo1, c1, d1);
+          fold(c0, d0);
+          if (two) fold(c1, d1);
         }
       }
     }
@@ -427,7 +442,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           m_in = min(m_in, um);
         }
       }
-      uint64_t t;
+      uint64_t t, t_last;
       if (any_ext) {  // an absolute timestamp in the batch: the (has_abs, value) monoid
         const uint64_t xts = (uint64_t)C[min(oo + 2, W)] | ((uint64_t)C[min(oo + 3, W)] << 32);
         t = ts_op(TsM{1u, tcur}, scan_ts(TsM{act && ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane)).v;
@@ -435,11 +450,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           tmin = min(tmin, t);
           tmax = max(tmax, t);
         }
+        t_last = __shfl_sync(kFull, t, 31);
       } else {
         t = tcur + x;
         // nondecreasing over the batch (lane 0 holds an event): its ends bound it
-        tmin = min(tmin, __shfl_sync(kFull, t, 0));
-        tmax = max(tmax, __shfl_sync(kFull, t, 31));
+        t_last = tcur + __shfl_sync(kFull, x, 31);
+        tmin = min(tmin, tcur + __shfl_sync(kFull, x, 0));
+        tmax = max(tmax, t_last);
       }
       int m_ex = __shfl_up_sync(kFull, m_in, 1);
       if (lane == 0) m_ex = 0;
@@ -493,7 +510,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       }
       __syncwarp();
       n_other += (act && !is_entry && !is_exit) ? 1u : 0u;
-      tcur = __shfl_sync(kFull, t, 31);
+      tcur = t_last;
       dp = d_op(dp, DM{(int)__popc(ebal) - (int)__popc(xbal), __shfl_sync(kFull, m_in, 31)});
       rank_c += __popc(ebal);
       pend_c += __popc(pbal);
