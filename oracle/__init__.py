@@ -1,8 +1,8 @@
 """THPT trace-analysis oracle (TEST INFRASTRUCTURE ONLY).
 
 A plain sequential CPU statement of the analysis path (decode, per-thread
-call-stack pairing, ordered-map tally, time-ordered timeline), compiled from
-``oracle.cpp``.  Only the tests, ``__graft_entry__.smoke()`` and the CPU
+call-stack pairing, ordered-map tally, device-activity pairing by command id,
+time-ordered timeline), compiled from ``oracle.cpp``.  Only the tests, ``__graft_entry__.smoke()`` and the CPU
 baseline leg of ``bench.py`` may import this package; the CUDA library never
 does and shares no code with it.
 """
@@ -33,6 +33,9 @@ EVENT_DTYPE = np.dtype([("ts", "<u8"), ("cmd", "<u8"), ("stream_id", "<u4"), ("c
                         ("func_id", "<u2")])
 DIAG_FIELDS = ("events", "pairs", "unmatched_entries", "unmatched_exits", "mismatched_pairs",
                "other_events", "discarded", "packets")
+DEV_DIAG_FIELDS = ("dev_events", "dev_pairs", "dev_intervals", "dev_unpaired", "dev_unjoined", "dev_ambiguous",
+                   "host_cmd_entries", "host_unjoined")
+IV_ERR, IV_DEVICE = 1, 4
 assert ROW_DTYPE.itemsize == 56 and INTERVAL_DTYPE.itemsize == 24 and EVENT_DTYPE.itemsize == 32
 
 
@@ -43,6 +46,10 @@ class _Opts(ctypes.Structure):
 
 class _Diag(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in DIAG_FIELDS]
+
+
+class _DevDiag(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in DEV_DIAG_FIELDS]
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +83,12 @@ def _load():
     lib.orc_intervals.restype = vp
     lib.orc_get_diag.argtypes = [vp, ctypes.POINTER(_Diag)]
     lib.orc_get_diag.restype = None
+    lib.orc_n_dev_rows.argtypes = [vp]
+    lib.orc_n_dev_rows.restype = u64
+    lib.orc_dev_rows.argtypes = [vp]
+    lib.orc_dev_rows.restype = vp
+    lib.orc_get_dev_diag.argtypes = [vp, ctypes.POINTER(_DevDiag)]
+    lib.orc_get_dev_diag.restype = None
     lib.orc_error_location.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(u64), ctypes.POINTER(u64)]
     lib.orc_error_location.restype = None
     lib.orc_free.argtypes = [vp]
@@ -95,12 +108,14 @@ def _ptr(buf):
 
 
 class Result:
-    def __init__(self, code, loc, rows, intervals, diag):
+    def __init__(self, code, loc, rows, intervals, diag, dev_rows, dev_diag):
         self.code = code
         self.loc = loc            # (level, packet, event): 0 file, 1 packet header, 2 packet content
         self.rows = rows          # ROW_DTYPE, ordered by (host_id, pid, tid, func_id)
-        self.intervals = intervals  # INTERVAL_DTYPE, timeline order
+        self.intervals = intervals  # INTERVAL_DTYPE, timeline order (host and device intervals)
         self.diag = diag          # dict of DIAG_FIELDS
+        self.dev_rows = dev_rows  # ROW_DTYPE: device intervals per (device stream's host, pid, tid; host function)
+        self.dev_diag = dev_diag  # dict of DEV_DIAG_FIELDS
 
 
 def run(trace, streams=None, t0: int = 0, t1: int = 2**64 - 1, want_intervals: bool = True) -> Result:
@@ -135,10 +150,17 @@ def run(trace, streams=None, t0: int = 0, t1: int = 2**64 - 1, want_intervals: b
         d = _Diag()
         lib.orc_get_diag(h, ctypes.byref(d))
         diag = {f: int(getattr(d, f)) for f in DIAG_FIELDS}
+        nd = lib.orc_n_dev_rows(h)
+        dev_rows = np.zeros(nd, dtype=ROW_DTYPE)
+        if nd:
+            ctypes.memmove(dev_rows.ctypes.data, lib.orc_dev_rows(h), nd * ROW_DTYPE.itemsize)
+        dd = _DevDiag()
+        lib.orc_get_dev_diag(h, ctypes.byref(dd))
+        dev_diag = {f: int(getattr(dd, f)) for f in DEV_DIAG_FIELDS}
     finally:
         lib.orc_free(h)
     del keep, sub
-    return Result(code, (lvl.value, pk.value, ev.value), rows, ivs, diag)
+    return Result(code, (lvl.value, pk.value, ev.value), rows, ivs, diag, dev_rows, dev_diag)
 
 
 def decode(trace) -> np.ndarray:

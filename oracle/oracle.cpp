@@ -36,6 +36,25 @@
 //    at 255;
 //  * timeline order = (start ts, stream id, entry position in the stream);
 //    window [t0, t1) keeps intervals with start < t1 and end >= t0.
+//
+// Device activity (the paper's GPU profiling code records device start and
+// end times of the commands a host API call submits, Sec. 3.3, and the
+// timeline shows device rows beside the host rows, Sec. 3.6).  Readings:
+//  * a command is named by a u64 command id carried by DEV_BEGIN / DEV_END
+//    events and by the ENTRY of the host call that submitted it (classes
+//    with a command offset);
+//  * per command id c, let B, E, H count its DEV_BEGIN, DEV_END and host
+//    ENTRY events.  c is a device pair when B = E = 1 and the end ts is not
+//    below the begin ts; a device pair with H = 1 is joined and becomes a
+//    device interval [begin ts, end ts] on the begin's stream, labelled with
+//    the host call's function, level 0, flags bit 2; H = 0 leaves the pair
+//    unjoined and H > 1 ambiguous (both excluded);
+//  * device intervals are tallied apart from the host calls, per (host, pid,
+//    tid of the device stream, function of the host call); they have no
+//    result, so their error count is 0;
+//  * in the timeline a device interval sits at the position of its DEV_BEGIN
+//    in its stream;
+//  * the same ns clock for host and device events.
 
 #include <algorithm>
 #include <cstdint>
@@ -231,12 +250,23 @@ typedef struct orc_interval {
   uint32_t stream_id;
   uint16_t func_id;
   uint8_t level;
-  uint8_t flags;  // bit0 err
+  uint8_t flags;  // bit0 err, bit2 device interval
 } orc_interval;
 
 typedef struct orc_diag {
   uint64_t events, pairs, unmatched_entries, unmatched_exits, mismatched_pairs, other_events, discarded, packets;
 } orc_diag;
+
+typedef struct orc_dev_diag {
+  uint64_t dev_events;       // DEV_BEGIN and DEV_END events
+  uint64_t dev_pairs;        // commands with one begin and one end, end >= begin
+  uint64_t dev_intervals;    // device pairs joined to exactly one host entry
+  uint64_t dev_unpaired;     // device events not in a device pair
+  uint64_t dev_unjoined;     // device pairs with no host entry
+  uint64_t dev_ambiguous;    // device pairs with several host entries
+  uint64_t host_cmd_entries; // host entries carrying a command id
+  uint64_t host_unjoined;    // of those, entries whose command is no device pair
+} orc_dev_diag;
 
 typedef struct orc_event {
   uint64_t ts;
@@ -268,6 +298,20 @@ struct Result {
   std::vector<orc_interval> intervals;
   orc_diag diag{};
   std::vector<orc_event> events;
+  std::vector<orc_row> dev_rows;
+  orc_dev_diag dev{};
+};
+
+// Everything one command id gathered over the trace.
+struct DevBegin {
+  uint64_t ts;
+  uint32_t stream;
+  uint64_t seq;
+};
+struct Command {
+  std::vector<DevBegin> begins;
+  std::vector<uint64_t> ends;
+  std::vector<uint16_t> host_funcs;
 };
 
 struct Open {
@@ -338,6 +382,7 @@ std::vector<std::vector<uint64_t>> packets_by_stream(const Trace &t, const std::
 void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, Result &r, bool collect_events) {
   auto by = packets_by_stream(t, keep);
   std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, orc_row> tally;
+  std::map<uint64_t, Command> commands;
   std::vector<Keyed> ivs;
   orc_diag &d = r.diag;
   for (uint32_t s = 0; s < t.n_streams; ++s) {
@@ -378,6 +423,19 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
           e.kind = ci.kind;
           e.func_id = ci.func;
           r.events.push_back(e);
+        }
+        if (ci.kind == KIND_ENTRY && ci.cmd_off >= 0) {
+          r.dev.host_cmd_entries += 1;
+          commands[cmd].host_funcs.push_back(ci.func);
+        }
+        if (ci.kind == KIND_DEV_BEGIN || ci.kind == KIND_DEV_END) {
+          r.dev.dev_events += 1;
+          if (ci.cmd_off >= 0) {
+            if (ci.kind == KIND_DEV_BEGIN)
+              commands[cmd].begins.push_back({ts, s, seq_in_stream});
+            else
+              commands[cmd].ends.push_back(ts);
+          }
         }
         if (ci.kind == KIND_ENTRY) {
           stack.push_back({ci.func, ts, seq_in_stream});
@@ -426,6 +484,53 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
     d.unmatched_entries += stack.size();
   }
   for (auto &kv : tally) r.rows.push_back(kv.second);
+
+  // device activity: one pass over the commands, in command-id order
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, orc_row> dev_tally;
+  for (auto &kv : commands) {
+    const Command &c = kv.second;
+    const bool pair = c.begins.size() == 1 && c.ends.size() == 1 && c.ends[0] >= c.begins[0].ts;
+    if (!pair) {
+      r.dev.host_unjoined += c.host_funcs.size();
+      continue;
+    }
+    r.dev.dev_pairs += 1;
+    if (c.host_funcs.empty()) {
+      r.dev.dev_unjoined += 1;
+      continue;
+    }
+    if (c.host_funcs.size() > 1) {
+      r.dev.dev_ambiguous += 1;
+      continue;
+    }
+    r.dev.dev_intervals += 1;
+    const DevBegin &b = c.begins[0];
+    const uint64_t te = c.ends[0];
+    const uint16_t f = c.host_funcs[0];
+    const Stream &st = t.streams[b.stream];
+    const uint64_t dur = te - b.ts;
+    auto key = std::make_tuple(st.host, st.pid, st.tid, (uint32_t)f);
+    auto it = dev_tally.find(key);
+    if (it == dev_tally.end()) it = dev_tally.emplace(key, orc_row{st.host, st.pid, st.tid, f, 0, 0, UINT64_MAX, 0, 0}).first;
+    orc_row &row = it->second;
+    row.count += 1;
+    row.total_ns += dur;
+    row.min_ns = std::min(row.min_ns, dur);
+    row.max_ns = std::max(row.max_ns, dur);
+    if (o.want_intervals && b.ts < o.t1 && te >= o.t0) {
+      orc_interval iv{};
+      iv.start_ns = b.ts;
+      iv.end_ns = te;
+      iv.stream_id = b.stream;
+      iv.func_id = f;
+      iv.level = 0;
+      iv.flags = 4;
+      ivs.push_back({b.ts, b.stream, b.seq, iv});
+    }
+  }
+  r.dev.dev_unpaired = r.dev.dev_events - 2 * r.dev.dev_pairs;
+  for (auto &kv : dev_tally) r.dev_rows.push_back(kv.second);
+
   std::sort(ivs.begin(), ivs.end(), [](const Keyed &a, const Keyed &b) {
     if (a.start != b.start) return a.start < b.start;
     if (a.stream != b.stream) return a.stream < b.stream;
@@ -485,6 +590,9 @@ const orc_interval *orc_intervals(const orc_result *r) {
   return reinterpret_cast<const Result *>(r)->intervals.data();
 }
 void orc_get_diag(const orc_result *r, orc_diag *d) { *d = reinterpret_cast<const Result *>(r)->diag; }
+uint64_t orc_n_dev_rows(const orc_result *r) { return reinterpret_cast<const Result *>(r)->dev_rows.size(); }
+const orc_row *orc_dev_rows(const orc_result *r) { return reinterpret_cast<const Result *>(r)->dev_rows.data(); }
+void orc_get_dev_diag(const orc_result *r, orc_dev_diag *d) { *d = reinterpret_cast<const Result *>(r)->dev; }
 void orc_error_location(const orc_result *r, int *level, uint64_t *packet, uint64_t *event) {
   const Result *x = reinterpret_cast<const Result *>(r);
   *level = x->loc.level;

@@ -129,3 +129,55 @@ def rows_equal(a, b) -> bool:
 
 def intervals_equal(a, b) -> bool:
     return len(a) == len(b) and all(np.array_equal(a[f], b[f]) for f in INTERVAL_DTYPE.names)
+
+
+def expected_device_from_truth(trace, calls: np.ndarray):
+    """Device tally rows, device intervals (timeline order) and the device
+    diagnostics implied by the generator's ground truth of a device-model
+    trace, drops included.
+
+    In that model every host call issues one command with a unique id, so a
+    truth record of a device command (flag 8) is a device interval exactly
+    when neither its DEV_BEGIN (flag 2) nor its DEV_END (flag 4) nor the
+    issuing call's ENTRY (flag 16) was dropped.
+    """
+    st = stream_table(trace)
+    dev_all = calls[(calls["flags"] & 8) != 0]
+    host = calls[(calls["flags"] & 8) == 0]
+    seq = np.flatnonzero((calls["flags"] & 8) != 0)  # stream-major truth order = stream order
+    paired = (dev_all["flags"] & 6) == 0
+    joined = paired & ((dev_all["flags"] & 16) == 0)
+    dev = dev_all[joined]
+    dev_seq = seq[joined]
+    dev_events = 2 * len(dev_all) - int(((dev_all["flags"] & 2) != 0).sum()) - int(((dev_all["flags"] & 4) != 0).sum())
+    host_cmd_entries = int(((host["flags"] & 2) == 0).sum())
+    diag = dict(dev_events=dev_events, dev_pairs=int(paired.sum()), dev_intervals=int(joined.sum()),
+                dev_unpaired=dev_events - 2 * int(paired.sum()), dev_unjoined=int((paired & ~joined).sum()),
+                dev_ambiguous=0, host_cmd_entries=host_cmd_entries,
+                host_unjoined=host_cmd_entries - int(joined.sum()))
+    acc = defaultdict(lambda: [0, 0, U64, 0, 0])
+    for r in dev:
+        sid = int(r["stream_id"])
+        d = int(r["end_ns"]) - int(r["start_ns"])
+        a = acc[(int(st[sid][0]), int(st[sid][1]), int(st[sid][2]), int(r["func_id"]))]
+        a[0] += 1
+        a[1] += d
+        a[2] = min(a[2], d)
+        a[3] = max(a[3], d)
+    keys = sorted(acc)
+    rows = np.zeros(len(keys), dtype=ROW_DTYPE)
+    for i, k in enumerate(keys):
+        rows[i] = (*k, *acc[k])
+    ivs = np.zeros(len(dev), dtype=INTERVAL_DTYPE)
+    ivs["start_ns"], ivs["end_ns"] = dev["start_ns"], dev["end_ns"]
+    ivs["stream_id"], ivs["func_id"] = dev["stream_id"], dev["func_id"]
+    ivs["flags"] = 4
+    order = np.lexsort((dev_seq, dev["stream_id"], dev["start_ns"]))
+    return rows, ivs[order], diag
+
+
+def merge_timelines(a: np.ndarray, a_seq: np.ndarray, b: np.ndarray, b_seq: np.ndarray) -> np.ndarray:
+    """Two timelines over disjoint streams merged in (start, stream, position) order."""
+    allv = np.concatenate([a, b])
+    seq = np.concatenate([a_seq, b_seq])
+    return allv[np.lexsort((seq, allv["stream_id"], allv["start_ns"]))]

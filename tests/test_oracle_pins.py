@@ -23,7 +23,8 @@ import pytest
 import oracle
 import tracegen as tg
 from tracegen.handbuilt import DEV_BEGIN, ENTRY, EXIT, SAMPLE, Ev, TraceBuilder
-from tests._util import (brute_force_stream, expected_from_truth, intervals_equal, rows_equal,
+from tests._util import (brute_force_stream, expected_device_from_truth, expected_from_truth, intervals_equal,
+                         merge_timelines, rows_equal,
                          stream_table, tally_from_pairs)
 
 
@@ -426,3 +427,85 @@ def test_error_seq_and_header_fields():
     tb, e, x, s0, s1 = _good_builder()
     tb.raw_packet(s0, 0, [tb.encode_event(e, 1)], n_events=2)
     _expect(tb.build(), oracle.E_FORMAT, (1, 0, 0))
+
+
+# ------------------------------------------------ device-activity pairing
+def test_device_pairing_handbuilt_cases():
+    from tests import _device_trace as dt
+    b, ids = dt.build()
+    r = oracle.run(b)
+    assert r.code == oracle.OK
+    assert r.dev_diag == dt.EXPECTED_DEV_DIAG
+    assert dt.as_tuples(r.dev_rows) == dt.expected_dev_rows(ids)
+    dev = r.intervals[(r.intervals["flags"] & oracle.IV_DEVICE) != 0]
+    assert dt.as_tuples(dev) == dt.expected_dev_intervals(ids)
+    # the host calls themselves are ordinary intervals; device events are other events
+    assert r.diag["pairs"] == 9 and r.diag["other_events"] == 17
+    assert len(r.intervals) == 9 + 3
+    # the host tally has no device rows
+    assert set(int(x) for x in r.rows["pid"]) == {7}
+
+
+@pytest.mark.parametrize("over", [
+    dict(total_calls=20_000, n_hosts=1, pids_per_host=2, tids_per_pid=2, n_device_streams=3),
+    dict(total_calls=30_000, n_hosts=2, pids_per_host=2, tids_per_pid=2, n_device_streams=5, packet_bytes=1024,
+         p_ext=0.01, seed=5),
+])
+def test_device_pairing_matches_ground_truth(over):
+    b, calls, _ev = tg.generate(tg.preset("device", **over), truth=True)
+    r = oracle.run(b)
+    assert r.code == oracle.OK
+    rows, ivs, diag = expected_device_from_truth(b, calls)
+    assert r.dev_diag == diag
+    assert rows_equal(r.dev_rows, rows)
+    # whole timeline = host calls and device intervals merged by (start, stream, position)
+    host_rows, host_ivs = expected_from_truth(b, calls)
+    assert rows_equal(r.rows, host_rows)
+    host_seq = np.flatnonzero((calls["flags"] & 8) == 0)
+    dev_seq = np.flatnonzero((calls["flags"] & 8) != 0)
+    host_ivs_seq = host_seq[np.lexsort((host_seq, calls["stream_id"][host_seq], calls["start_ns"][host_seq]))]
+    dev_ivs_seq = dev_seq[np.lexsort((dev_seq, calls["stream_id"][dev_seq], calls["start_ns"][dev_seq]))]
+    merged = merge_timelines(host_ivs, host_ivs_seq, ivs, dev_ivs_seq)
+    assert intervals_equal(r.intervals, merged)
+
+
+@pytest.mark.parametrize("seed", [6, 7])
+def test_device_pairing_with_drops_matches_ground_truth(seed):
+    cfg = tg.preset("device", total_calls=30_000, n_hosts=1, pids_per_host=2, tids_per_pid=3, n_device_streams=4,
+                    p_drop=0.01, seed=seed, packet_bytes=1024)
+    b, calls, _ev = tg.generate(cfg, truth=True)
+    r = oracle.run(b)
+    rows, ivs, diag = expected_device_from_truth(b, calls)
+    assert diag["dev_unpaired"] > 0 and diag["dev_unjoined"] > 0 and diag["host_unjoined"] > 0
+    assert r.dev_diag == diag
+    assert rows_equal(r.dev_rows, rows)
+    assert intervals_equal(r.intervals[(r.intervals["flags"] & oracle.IV_DEVICE) != 0], ivs)
+
+
+def test_device_invariants():
+    cfg = tg.preset("device", total_calls=40_000, n_hosts=1, pids_per_host=2, tids_per_pid=2, n_device_streams=6,
+                    p_drop=0.005, seed=9, packet_bytes=512)
+    b, _c, _e = tg.generate(cfg)
+    r = oracle.run(b)
+    dd = r.dev_diag
+    assert dd["dev_events"] == 2 * dd["dev_pairs"] + dd["dev_unpaired"]
+    assert dd["dev_pairs"] == dd["dev_intervals"] + dd["dev_unjoined"] + dd["dev_ambiguous"]
+    dev = r.intervals[(r.intervals["flags"] & oracle.IV_DEVICE) != 0]
+    assert int(r.dev_rows["count"].sum()) == dd["dev_intervals"] == len(dev)
+    durs = (dev["end_ns"] - dev["start_ns"]).astype(object)
+    assert int(r.dev_rows["total_ns"].astype(object).sum()) == int(durs.sum())
+    assert np.all(dev["level"] == 0) and np.all(r.dev_rows["err_count"] == 0)
+    s = r.intervals["start_ns"]
+    assert np.all(s[1:] >= s[:-1])
+    # device events are the other events of this model (no samples)
+    assert r.diag["other_events"] == dd["dev_events"]
+
+
+def test_device_window_keeps_overlapping_device_intervals():
+    from tests import _device_trace as dt
+    b, ids = dt.build()
+    full = oracle.run(b)
+    w = oracle.run(b, t0=dt.T0 + 150, t1=dt.T0 + 131)
+    keep = (full.intervals["start_ns"] < dt.T0 + 131) & (full.intervals["end_ns"] >= dt.T0 + 150)
+    assert intervals_equal(w.intervals, full.intervals[keep])
+    assert dt.as_tuples(w.intervals[(w.intervals["flags"] & 4) != 0])[0][:2] == (dt.T0 + 100, dt.T0 + 150)

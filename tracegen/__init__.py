@@ -88,6 +88,7 @@ CALL_ERR = 1
 CALL_ENTRY_DROPPED = 2
 CALL_EXIT_DROPPED = 4
 CALL_DEVICE = 8
+CALL_HOST_DROPPED = 16  # device interval whose issuing host call lost its ENTRY event
 
 
 def build(force: bool = False) -> str:

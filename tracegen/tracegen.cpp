@@ -134,7 +134,9 @@ typedef struct tg_call {
   uint32_t stream_id;
   uint16_t func_id;
   uint8_t level;
-  uint8_t flags;  // bit0 err result, bit1 entry dropped, bit2 exit dropped, bit3 device interval
+  // bit0 err result, bit1 entry (or DEV_BEGIN) dropped, bit2 exit (or DEV_END) dropped,
+  // bit3 device interval (func = the issuing host call's function), bit4 that host call's ENTRY dropped
+  uint8_t flags;
 } tg_call;
 
 // Ground-truth record of one written (not dropped) event, in stream order.
@@ -273,6 +275,14 @@ Model build_model(const tg_config &c) {
 }
 
 // ------------------------------------------------------- packet writer
+// A command issued by a host call (device model): id, submit time (the call's
+// exit), the call's function and whether its ENTRY event was dropped.
+struct IssuedCmd {
+  uint64_t cmd, submit;
+  uint32_t func;
+  bool entry_dropped;
+};
+
 struct PacketSink {
   // Pass 1 (bytes == nullptr): records ts_begin per packet.
   // Pass 2: writes packets at bytes + packets_off + file_index[seq] * P.
@@ -400,8 +410,8 @@ struct HostStreamGen {
   uint32_t stream;
   uint64_t budget;  // calls left
   uint64_t t;
-  // device model: commands issued by this stream (cmd, submit time)
-  std::vector<std::pair<uint64_t, uint64_t>> *cmds = nullptr;
+  // device model: commands issued by this stream
+  std::vector<IssuedCmd> *cmds = nullptr;
   uint64_t cmd_counter = 0;
 
   HostStreamGen(const tg_config &c_, const Model &m_, PacketSink &s, std::vector<tg_call> *tr, uint32_t st, uint64_t b)
@@ -508,7 +518,7 @@ struct HostStreamGen {
       if (ex.dropped) tc.flags |= 4;
     }
     sink.put(ex);
-    if (kind == 4 && cmds) cmds->push_back({cmd, t});
+    if (kind == 4 && cmds) cmds->push_back({cmd, t, f, en.dropped});
   }
 
   void run(uint64_t t0) {
@@ -546,8 +556,13 @@ struct Plan {
   std::vector<uint64_t> t0;
   std::vector<std::vector<uint64_t>> file_index;  // [stream][seq]
   uint64_t n_packets = 0;
-  // device model: per device stream, (cmd, begin, end) triples in time order
-  std::vector<std::vector<std::array<uint64_t, 3>>> dev_work;
+  // device model: per device stream, its commands in time order
+  struct DevWork {
+    uint64_t cmd, begin, end;
+    uint32_t func;
+    bool host_dropped;
+  };
+  std::vector<std::vector<DevWork>> dev_work;
 };
 
 void for_streams(uint32_t n, uint32_t threads, const std::function<void(uint32_t)> &fn) {
@@ -576,16 +591,20 @@ uint64_t stream_seed(uint64_t seed, uint32_t stream, uint32_t role) {
 // Device model: the host streams' command lists are turned into device work.
 // Each command goes to device stream (cmd mod D) and starts after its submit
 // time and after the previous command of that device stream ends.
-void plan_device_work(Plan &pl, const std::vector<std::vector<std::pair<uint64_t, uint64_t>>> &cmds) {
+void plan_device_work(Plan &pl, const std::vector<std::vector<IssuedCmd>> &cmds) {
   const tg_config &c = pl.c;
   uint32_t D = c.n_device_streams;
   pl.dev_work.assign(D, {});
-  std::vector<std::vector<std::pair<uint64_t, uint64_t>>> per_dev(D);  // (submit, cmd)
+  std::vector<std::vector<std::pair<uint64_t, const IssuedCmd *>>> per_dev(D);  // (submit, command)
   for (auto &lst : cmds)
-    for (auto &pc : lst) per_dev[(uint32_t)(pc.first % D)].push_back({pc.second, pc.first});
+    for (auto &ic : lst) per_dev[(uint32_t)(ic.cmd % D)].push_back({ic.submit, &ic});
   for (uint32_t d = 0; d < D; ++d) {
     auto &v = per_dev[d];
-    std::sort(v.begin(), v.end());
+    std::sort(v.begin(), v.end(), [](const std::pair<uint64_t, const IssuedCmd *> &a,
+                                     const std::pair<uint64_t, const IssuedCmd *> &b) {
+      if (a.first != b.first) return a.first < b.first;
+      return a.second->cmd < b.second->cmd;
+    });
     Xoshiro256ss r;
     r.seed(stream_seed(c.seed, 0x40000000u + d, 2));
     uint64_t free_at = 0;
@@ -593,7 +612,7 @@ void plan_device_work(Plan &pl, const std::vector<std::vector<std::pair<uint64_t
       uint64_t begin = std::max(free_at, sc.first + (uint64_t)std::llround(r.expo(c.gap_mean_ns)));
       double dv = c.dur_median_ns * std::exp(c.dur_sigma * r.normal());
       uint64_t dur = (uint64_t)std::llround(dv > 1e12 ? 1e12 : (dv < 0 ? 0 : dv));
-      pl.dev_work[d].push_back({sc.second, begin, begin + dur});
+      pl.dev_work[d].push_back({sc.second->cmd, begin, begin + dur, sc.second->func, sc.second->entry_dropped});
       free_at = begin + dur;
     }
   }
@@ -605,7 +624,7 @@ struct DeviceStreamGen {
   PacketSink &sink;
   std::vector<tg_call> *truth;
   uint32_t stream;
-  const std::vector<std::array<uint64_t, 3>> &work;
+  const std::vector<Plan::DevWork> &work;
   Xoshiro256ss rng;
   void run(uint64_t t0) {
     sink.start(t0);
@@ -613,21 +632,21 @@ struct DeviceStreamGen {
       Ev b{};
       b.cls = (uint16_t)m.dev_begin_cls;
       b.var_len = 0;
-      b.cmd = w[0];
-      b.ts = w[1];
+      b.cmd = w.cmd;
+      b.ts = w.begin;
       b.dropped = rng.uniform() < c.p_drop;
       Ev e = b;
       e.cls = (uint16_t)m.dev_end_cls;
-      e.ts = w[2];
+      e.ts = w.end;
       e.dropped = rng.uniform() < c.p_drop;
-      if (truth) {
+      if (truth) {  // the device interval, labelled with the issuing host call's function
         tg_call tc{};
-        tc.start_ns = w[1];
-        tc.end_ns = w[2];
+        tc.start_ns = w.begin;
+        tc.end_ns = w.end;
         tc.stream_id = stream;
-        tc.func_id = m.classes[m.dev_begin_cls].func;
+        tc.func_id = (uint16_t)w.func;
         tc.level = 0;
-        tc.flags = (uint8_t)(8 | (b.dropped ? 2 : 0) | (e.dropped ? 4 : 0));
+        tc.flags = (uint8_t)(8 | (b.dropped ? 2 : 0) | (e.dropped ? 4 : 0) | (w.host_dropped ? 16 : 0));
         truth->push_back(tc);
       }
       sink.put(b);
@@ -637,8 +656,7 @@ struct DeviceStreamGen {
   }
 };
 
-void run_stream(Plan &pl, uint32_t s, PacketSink &sink, std::vector<tg_call> *truth,
-                std::vector<std::pair<uint64_t, uint64_t>> *cmds) {
+void run_stream(Plan &pl, uint32_t s, PacketSink &sink, std::vector<tg_call> *truth, std::vector<IssuedCmd> *cmds) {
   const tg_config &c = pl.c;
   sink.P = c.packet_bytes;
   sink.stream = s;
@@ -728,7 +746,7 @@ tg_plan *tg_plan_create(const tg_config *cfg) {
   }
   // sizing pass
   std::vector<std::vector<uint64_t>> ts_begins(S);
-  std::vector<std::vector<std::pair<uint64_t, uint64_t>>> cmds(HS);
+  std::vector<std::vector<IssuedCmd>> cmds(HS);
   for_streams(HS, c.n_threads, [&](uint32_t s) {
     PacketSink sink;
     run_stream(*pl, s, sink, nullptr, c.model == MODEL_DEVICE ? &cmds[s] : nullptr);
@@ -736,6 +754,10 @@ tg_plan *tg_plan_create(const tg_config *cfg) {
   });
   if (c.model == MODEL_DEVICE) {
     plan_device_work(*pl, cmds);
+    // a device stream's first packet starts no later than its first event, so
+    // its packets' ts_begin (and with it the file order) follow its seq order
+    for (uint32_t d = 0; d < S - HS; ++d)
+      if (!pl->dev_work[d].empty()) pl->t0[HS + d] = std::min(pl->t0[HS + d], pl->dev_work[d][0].begin);
     for_streams(S - HS, c.n_threads, [&](uint32_t d) {
       PacketSink sink;
       run_stream(*pl, HS + d, sink, nullptr, nullptr);
@@ -862,7 +884,7 @@ int tg_plan_write(tg_plan *p, void *out, tg_call *calls, uint64_t calls_cap, uin
     rb.seed(stream_seed(c.seed, s, 1));
     sink.rng_bytes = &rb;
     sink.events = want_truth ? &tevents[s] : nullptr;
-    std::vector<std::pair<uint64_t, uint64_t>> cmds;
+    std::vector<IssuedCmd> cmds;
     run_stream(pl, s, sink, want_truth ? &tcalls[s] : nullptr, c.model == MODEL_DEVICE ? &cmds : nullptr);
   };
   for_streams(S, c.n_threads, body);
