@@ -37,6 +37,9 @@ WORKLOADS = {
                                        "100M calls = 200M events; depth<=6; 1% errors; 16 KB packets"),
     "tiny": dict(preset="tiny", desc="1 host x 1 pid x 4 threads; one API of 40 functions; 100k calls; "
                                      "depth<=3; 4 KB packets"),
+    "device": dict(preset="device", desc="512 host streams (8x8x8) of launch/memcpy calls (16 fns) carrying unique "
+                                         "random 64-bit command ids; 64 device streams of begin/end events; 50M "
+                                         "commands = 200M events; device pairing + merged timeline; 16 KB packets"),
 }
 
 
@@ -300,8 +303,8 @@ def main():
     achieved = an_bytes / (an_ms / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6400.0))
     phase = {k: round(statistics.mean(t[k] for t in timings), 4)
-             for k in ("index_ms", "analyze_ms", "frontier_ms", "tally_ms", "compact_ms", "sort_ms", "gather_ms",
-                       "total_ms")}
+             for k in ("index_ms", "analyze_ms", "frontier_ms", "join_ms", "tally_ms", "compact_ms", "sort_ms",
+                       "gather_ms", "total_ms")}
     traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze_warp.cu"))
 
     # end to end through the public API: host bytes in, host results out
@@ -341,7 +344,8 @@ def main():
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                        "calls": int(cfg.total_calls), "events_per_rank": events, "trace_bytes": meta["nbytes"],
                        "packets": meta["n_packets"], "seed": int(cfg.seed), "parallelism": "replicas" if world > 1
-                       else "single", "l2": "inputs larger than L2 (8.4 GB trace vs 126 MB L2); no flush"},
+                       else "single",
+                       "l2": "inputs larger than L2 (%.1f GB trace vs 126 MB L2); no flush" % (meta["nbytes"] / 1e9)},
             "trace_gbs": meta["nbytes"] / (ms_max / 1e3) / 1e9 * (world if world > 1 else 1),
             "phases_ms": phase,
             "roofline": {"kernel": "k_analyze_warp (decode+validate+pair+tally, interval slots)", "bound": "hbm",

@@ -45,6 +45,18 @@
  * be dropped by the tracer, Sec. 3.1).  DEV_BEGIN / DEV_END / SAMPLE events are
  * decoded and counted as other events.
  *
+ * Device activity (GPU timings of the commands a host call submits, Sec. 3.3;
+ * device rows of the timeline, Sec. 3.6): a class with a command offset
+ * carries a u64 command id.  Per command id c, with B, E, H the numbers of
+ * its DEV_BEGIN, DEV_END and host ENTRY events, c is a device pair when
+ * B = E = 1 and end ts >= begin ts.  A device pair with H = 1 is a device
+ * interval [begin ts, end ts] on the begin's stream, labelled with the host
+ * call's function, level 0, flags THAPI_IV_DEVICE; it joins the timeline at
+ * the begin's position in its stream and is tallied apart from the host calls
+ * (thapi_device_tally), per (host, pid, tid of its stream, function).  Pairs
+ * with H = 0 (unjoined) or H > 1 (ambiguous), and device events outside a
+ * pair, are counted in thapi_device_diag.
+ *
  * Threading: a context may be used from one host thread at a time.
  * Errors: every call returns a THAPI_* status; nothing falls back to the CPU.
  */
@@ -79,7 +91,9 @@ typedef struct thapi_tally_row {
 } thapi_tally_row;
 
 /* One timeline interval (24 B).  Timeline order is (start_ns, stream_id,
- * position of the entry in its stream).  flags bit 0 = error result. */
+ * position of the entry, or of the DEV_BEGIN, in its stream). */
+#define THAPI_IV_ERR 1u    /* the call's exit result was nonzero */
+#define THAPI_IV_DEVICE 4u /* a device interval (device-activity pairing) */
 typedef struct thapi_interval {
   uint64_t start_ns, end_ns;
   uint32_t stream_id;
@@ -101,11 +115,26 @@ typedef struct thapi_diag {
   uint64_t packets;
 } thapi_diag;
 
-/* Facts about a loaded trace. */
+/* Device-activity diagnostics of one trace (64 B).
+ * dev_events = 2*dev_pairs + dev_unpaired;
+ * dev_pairs = dev_intervals + dev_unjoined + dev_ambiguous. */
+typedef struct thapi_device_diag {
+  uint64_t dev_events;        /* DEV_BEGIN and DEV_END events */
+  uint64_t dev_pairs;         /* command ids with one begin and one end, end >= begin */
+  uint64_t dev_intervals;     /* device pairs joined to exactly one host ENTRY */
+  uint64_t dev_unpaired;      /* device events outside a device pair */
+  uint64_t dev_unjoined;      /* device pairs with no host ENTRY */
+  uint64_t dev_ambiguous;     /* device pairs with several host ENTRY events */
+  uint64_t host_cmd_entries;  /* host ENTRY events carrying a command id */
+  uint64_t host_unjoined;     /* of those, entries whose command id is no device pair */
+} thapi_device_diag;
+
+/* Facts about a loaded trace.  intervals counts host and device intervals. */
 typedef struct thapi_trace_info {
   uint64_t nbytes, n_packets, events, intervals, tally_rows, device_bytes;
   uint32_t n_streams, n_classes, n_funcs, n_hosts, packet_bytes, reserved;
   uint64_t t_min, t_max;      /* smallest / largest event timestamp */
+  uint64_t device_rows, device_intervals;  /* device tally rows; device intervals */
 } thapi_trace_info;
 
 /* Optional device allocator.  alloc returns device memory of at least `bytes`
@@ -152,6 +181,13 @@ int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id);
 int thapi_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
                 thapi_diag *diag);
 
+/* Copies the device tally rows (device intervals per (host_id, pid, tid of
+ * the device stream, function of the submitting host call), ordered by those
+ * keys; err_count is 0) to HOST memory `rows` and the device diagnostics to
+ * `diag` (may be NULL).  cap semantics as thapi_tally. */
+int thapi_device_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                       thapi_device_diag *diag);
+
 /* Copies the timeline intervals with start_ns < t1 and end_ns >= t0 (t0 = 0,
  * t1 = UINT64_MAX: all), in timeline order, to HOST memory `out` (capacity
  * `cap`).  *n_out = number selected; cap semantics as thapi_tally. */
@@ -195,6 +231,8 @@ typedef struct thapi_load_timing {
   uint64_t analyze_write_bytes;  /* interval slots written by the analysis (24 B each) */
   uint64_t analyze_launches;     /* analysis kernel launches of the load */
   uint64_t launches;             /* all kernel launches of the load */
+  float join_ms;                 /* device-activity pairing (includes one host wait) */
+  float reserved_ms;
 } thapi_load_timing;
 
 /* Enables (1) or disables (0) per-phase timing of subsequent loads. */

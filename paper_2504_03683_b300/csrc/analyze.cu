@@ -238,6 +238,8 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
 
   unsigned long long n_mismatch = 0, n_other = 0, n_pairs = 0;
   unsigned long long n_events = 0, n_disc = 0, n_pk = 0, n_slots = 0;
+  unsigned long long n_dev = 0;  // DEV_BEGIN / DEV_END events (device pairing on)
+  const bool dev_on = p.cmd.counts != nullptr;  // device-activity records wanted
   uint64_t tmin = ~0ull, tmax = 0;
   uint32_t phase = 0;  // bit s = parity expected next on bar[s]
   uint32_t pending_mask = 1u;
@@ -396,7 +398,8 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
             } else {
               const uint32_t kd = cls_kind(cr);
               const int e = kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
-              n_entry += kd == kEntry ? 1u : 0u;
+              // interval slot owners: entries, and DEV_BEGINs carrying a command id
+              n_entry += (kd == kEntry || (dev_on && kd == kDevBegin && cls_cmdw(cr) >= 0)) ? 1u : 0u;
               dsum.s += e;
               dsum.m = min(dsum.m, dsum.s);
               if (ext) {
@@ -448,6 +451,7 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
         int depth = d_ex.s;
         int segmin = 0x7FFFFFFF;
         uint32_t k = c_ex;
+        uint32_t orank = e_ex;  // slot of the next slot owner
 #pragma unroll
         for (int kk = 0; kk < BW; ++kk) {
           uint32_t m = bits.w[kk];
@@ -465,8 +469,33 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
             uint32_t err = 0;
             const int32_t rw = cls_resw(cr);
             if (kd == kExit && rw >= 0 && base + (uint32_t)rw < W) err = C[base + rw] != 0 ? 1u : 0u;
+            // device-activity record of an event carrying a command id
+            uint32_t dev_slot = 0;
+            if (dev_on && cls_cmdw(cr) >= 0 && (kd == kEntry || kd == kDevBegin || kd == kDevEnd)) {
+              const uint32_t q = min(base + (uint32_t)cls_cmdw(cr), W);
+              const uint64_t id = (uint64_t)C[q] | ((uint64_t)C[min(q + 1u, W)] << 32);
+              if (kd == kDevBegin) {
+                const unsigned long long at = atomicAdd(&p.cmd.counts[0], 1ull);
+                if (at < p.cmd.cap_b) p.cmd.b[at] = CmdBegin{id, t, d.evbase + orank, d.group, (uint32_t)pos};
+                if (p.slots) {  // invalid until the device join fills it
+                  thapi_interval iv{};
+                  iv.start_ns = t;
+                  iv.stream_id = 0xFFFFFFFFu;
+                  p.slots[d.evbase + orank] = iv;
+                }
+                dev_slot = 1;
+              } else if (kd == kDevEnd) {
+                const unsigned long long at = atomicAdd(&p.cmd.counts[1], 1ull);
+                if (at < p.cmd.cap_e) p.cmd.e[at] = CmdEnd{id, t};
+              } else {
+                const unsigned long long at = atomicAdd(&p.cmd.counts[2], 1ull);
+                if (at < p.cmd.cap_h) p.cmd.h[at] = CmdHost{id, cls_func(cr), 0u};
+              }
+            }
+            if (dev_on && (kd == kDevBegin || kd == kDevEnd)) ++n_dev;
+            if (kd == kEntry || dev_slot) ++orank;
             s_ts[k] = t;
-            s_dk[k] = ((uint32_t)depth & 0xFFFFu) | (kd << 16) | (err << 19);
+            s_dk[k] = ((uint32_t)depth & 0xFFFFu) | (kd << 16) | (err << 19) | (dev_slot << 20);
             s_fn[k] = (uint16_t)cls_func(cr);
             segmin = min(segmin, depth);
             tmin = min(tmin, t);
@@ -602,6 +631,7 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
             }
           } else {
             ++n_other;
+            if (dk & (1u << 20)) ++rank;  // a DEV_BEGIN's slot, written above
           }
           mrun = min(mrun, post);
         }
@@ -666,6 +696,7 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
     n_mismatch += __shfl_down_sync(0xffffffffu, n_mismatch, off);
     n_other += __shfl_down_sync(0xffffffffu, n_other, off);
     n_pairs += __shfl_down_sync(0xffffffffu, n_pairs, off);
+    n_dev += __shfl_down_sync(0xffffffffu, n_dev, off);
     tmin = min(tmin, __shfl_down_sync(0xffffffffu, tmin, off));
     tmax = max(tmax, __shfl_down_sync(0xffffffffu, tmax, off));
   }
@@ -673,6 +704,7 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
     if (n_mismatch) atomicAdd(&p.diag[dMismatch], n_mismatch);
     if (n_other) atomicAdd(&p.diag[dOther], n_other);
     if (n_pairs) atomicAdd(&p.diag[dPairs], n_pairs);
+    if (n_dev) atomicAdd(&p.diag[dDevEvents], n_dev);
     if (tmin != ~0ull) atomicMin(&p.tminmax[0], (unsigned long long)tmin);
     if (tmax) atomicMax(&p.tminmax[1], (unsigned long long)tmax);
   }

@@ -75,10 +75,11 @@ __host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t NW, uint32_t NC)
   return L;
 }
 
-// Shared-memory class row: fixed words (14 bits) | kind << 14 (3) | (result word + 1) << 17 (15).
+// Shared-memory class row: fixed words (14 bits) | kind << 14 (3) | (result word + 1) << 17 (14)
+//   | carries a command id (device pairing on) << 31.
 __device__ __forceinline__ uint32_t row_fixedw(uint32_t r) { return r & 0x3FFFu; }
 __device__ __forceinline__ uint32_t row_kind(uint32_t r) { return (r >> 14) & 7u; }
-__device__ __forceinline__ int32_t row_resw(uint32_t r) { return (int32_t)(r >> 17) - 1; }
+__device__ __forceinline__ int32_t row_resw(uint32_t r) { return (int32_t)((r >> 17) & 0x3FFFu) - 1; }
 
 // Event chain step from word offset o.  An offset whose class id is out of
 // range is no event start: the chain moves to the next offset whose class id
@@ -196,10 +197,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   if (w_begin >= w_end) return;  // uniform over the CTA
   auto pos_of = [&](uint64_t w) -> uint64_t { return p.poslist ? p.poslist[w] : w; };
 
+  const bool dev_on = p.cmd.counts != nullptr;  // device-activity records wanted
   for (uint32_t c = threadIdx.x; c <= NC; c += blockDim.x) {
     if (c < NC) {
       const uint64_t r = p.classes[c];
-      ctab[c] = cls_fixedw(r) | (cls_kind(r) << 14) | ((uint32_t)(cls_resw(r) + 1) << 17);
+      const uint32_t k = cls_kind(r);
+      const bool carries = dev_on && cls_cmdw(r) >= 0 && (k == kEntry || k == kDevBegin || k == kDevEnd);
+      ctab[c] = cls_fixedw(r) | (k << 14) | ((uint32_t)(cls_resw(r) + 1) << 17) | (carries ? 1u << 31 : 0u);
       cfn[c] = (uint16_t)cls_func(r);
     } else {
       ctab[c] = 0;
@@ -221,6 +225,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   uint64_t fr_base = 0;
   uint32_t fr_left = 0;  // lane 0: current frontier chunk
   unsigned long long n_mismatch = 0, n_other = 0, n_pairs = 0, n_events = 0, n_disc = 0, n_pk = 0, n_slots = 0;
+  unsigned long long n_dev = 0;  // DEV_BEGIN / DEV_END events (device pairing on)
   uint64_t tmin = ~0ull, tmax = 0;
   uint32_t phase = 0;
   bool issued = false;  // a copy is in flight into buf
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     uint32_t valid = 0, mism = 0;
     uint64_t tcur = d.tsb;  // timestamp of the last event so far
     DM dp{0, 0};            // depth monoid of the batches so far
-    uint32_t rank_c = 0;  // entries so far
+    uint32_t rank_c = 0;  // slot owners so far: entries, and command-carrying DEV_BEGINs
     uint32_t pend_c = 0;  // pending exits so far
     // the next batch's offsets, header words and class row are loaded one batch ahead
     uint32_t n_oo, n_w0, n_w1, n_r;
@@ -462,7 +467,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       if (lane == 0) m_ex = 0;
       const DM before{dp.s + s_in - dv, min(dp.m, dp.s + m_ex)};  // depth and running minimum before the event
       const int post = before.s + dv;                              // depth after the event
-      const uint32_t rank = rank_c + __popc(ebal & lt);
+      // a DEV_BEGIN with a command id owns an interval slot too (its device interval)
+      const bool hcmd = (r >> 31) != 0;
+      const bool rec_b = hcmd && kd == kDevBegin;
+      const uint32_t bbal = dev_on ? __ballot_sync(kFull, rec_b) : 0u;
+      const uint32_t obal = ebal | bbal;
+      const uint32_t rank = rank_c + __popc(obal & lt);
       const uint64_t meta = entry_meta(fn, rank, (uint32_t)min(before.s - before.m, 255), (uint32_t)(-before.m));
       const uint32_t cand = is_exit ? (peers & ebal & lt) : 0u;
       const int src = cand ? 31 - __clz(cand) : (int)lane;
@@ -503,6 +513,37 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         fr.flags = 0;
         p.frontier[fbase + pend_c + __popc(pbal & lt)] = fr;
       }
+      if (dev_on) {  // device-activity records of the batch
+        n_dev += (kd == kDevBegin || kd == kDevEnd) ? 1u : 0u;
+        const bool rec_e = hcmd && kd == kDevEnd, rec_h = hcmd && is_entry;
+        const uint32_t xb = __ballot_sync(kFull, rec_e), hb = __ballot_sync(kFull, rec_h);
+        if (bbal | xb | hb) {
+          unsigned long long o_b = 0, o_e = 0, o_h = 0;
+          if (lane == 0) {
+            if (bbal) o_b = atomicAdd(&p.cmd.counts[0], (unsigned long long)__popc(bbal));
+            if (xb) o_e = atomicAdd(&p.cmd.counts[1], (unsigned long long)__popc(xb));
+            if (hb) o_h = atomicAdd(&p.cmd.counts[2], (unsigned long long)__popc(hb));
+          }
+          o_b = __shfl_sync(kFull, o_b, 0);
+          o_e = __shfl_sync(kFull, o_e, 0);
+          o_h = __shfl_sync(kFull, o_h, 0);
+          if (rec_b || rec_e || rec_h) {
+            const uint32_t q = min(oo + 2u + (ext ? 2u : 0u) + (uint32_t)cls_cmdw(p.classes[c]), W);
+            const uint64_t id = (uint64_t)C[q] | ((uint64_t)C[min(q + 1u, W)] << 32);
+            if (rec_b) {
+              const uint64_t k = o_b + __popc(bbal & lt);
+              if (k < p.cmd.cap_b) p.cmd.b[k] = CmdBegin{id, t, d.evbase + rank, d.group, (uint32_t)pos};
+              if (pslots) put_interval(pslots + rank, t, 0, 0xFFFFFFFFu, 0, 0, 0);  // invalid until joined
+            } else if (rec_e) {
+              const uint64_t k = o_e + __popc(xb & lt);
+              if (k < p.cmd.cap_e) p.cmd.e[k] = CmdEnd{id, t};
+            } else {
+              const uint64_t k = o_h + __popc(hb & lt);
+              if (k < p.cmd.cap_h) p.cmd.h[k] = CmdHost{id, fn, 0u};
+            }
+          }
+        }
+      }
       __syncwarp();  // the table is read above before the batch's entries update it
       if (is_entry && (peers & ebal & gt) == 0) {  // the batch's last entry at its height
         tab_ts[before.s - dmin] = t;
@@ -512,7 +553,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       n_other += (act && !is_entry && !is_exit) ? 1u : 0u;
       tcur = t_last;
       dp = d_op(dp, DM{(int)__popc(ebal) - (int)__popc(xbal), __shfl_sync(kFull, m_in, 31)});
-      rank_c += __popc(ebal);
+      rank_c += __popc(obal);
       pend_c += __popc(pbal);
     }
     __syncwarp();
@@ -561,6 +602,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     n_mismatch += __shfl_down_sync(kFull, n_mismatch, off);
     n_other += __shfl_down_sync(kFull, n_other, off);
     n_pairs += __shfl_down_sync(kFull, n_pairs, off);
+    n_dev += __shfl_down_sync(kFull, n_dev, off);
     tmin = min(tmin, __shfl_down_sync(kFull, tmin, off));
     tmax = max(tmax, __shfl_down_sync(kFull, tmax, off));
   }
@@ -568,6 +610,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     if (n_mismatch) atomicAdd(&p.diag[dMismatch], n_mismatch);
     if (n_other) atomicAdd(&p.diag[dOther], n_other);
     if (n_pairs) atomicAdd(&p.diag[dPairs], n_pairs);
+    if (n_dev) atomicAdd(&p.diag[dDevEvents], n_dev);
     if (tmin != ~0ull) atomicMin(&p.tminmax[0], (unsigned long long)tmin);
     if (tmax) atomicMax(&p.tminmax[1], (unsigned long long)tmax);
     if (n_events) atomicAdd(&p.diag[dEvents], n_events);

@@ -24,6 +24,9 @@ struct TraceRec {
   uint64_t rows_bytes = 0;
   thapi_interval *tl = nullptr;
   uint64_t tl_bytes = 0;
+  thapi_tally_row *dev_rows = nullptr;
+  uint64_t dev_rows_bytes = 0;
+  thapi_device_diag dev_diag{};
   std::vector<char> strings;
   std::vector<uint32_t> host_name, func_name;
   thapi_load_timing timing{};
@@ -54,7 +57,7 @@ uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // CUDA events bracketing the phases of one load (only when timing is on).
 struct PhaseClock {
-  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kTa1, kCo0, kCo1, kSo1, kGa1, kN };
+  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kJo0, kJo1, kTa1, kCo0, kCo1, kSo1, kGa1, kN };
   cudaEvent_t ev[kN] = {};
   bool on = false, dense = false;
   void init(bool enable) {
@@ -280,6 +283,9 @@ enum Misc {
   mIv,
   mReadBytes,
   mSlots,
+  mCmdCount0,                 // device-activity records: begin, end, host
+  mJoin0 = mCmdCount0 + 3,    // join results: pairs, intervals, unjoined, ambiguous, host entries of pairs, overflow
+  mDevRows = mJoin0 + 6,
   mCount
 };
 
@@ -303,6 +309,7 @@ class Loader {
     if (tr_) {
       dev_free(c_, tr_->rows, tr_->rows_bytes, s_);
       dev_free(c_, tr_->tl, tr_->tl_bytes, s_);
+      dev_free(c_, tr_->dev_rows, tr_->dev_rows_bytes, s_);
       delete tr_;
     }
     cudaStreamSynchronize(s_);
@@ -378,7 +385,14 @@ int Loader::run() {
 
   // admission: coarse peak of this load (packets, index, table, slots, sort)
   const uint64_t est_events = n * (uint64_t)((P - kPacketHeader) / 8);
-  const uint64_t est = (host_ ? n * (uint64_t)P : 0) + n * 128 + cells * 80 + est_events * 24;
+  // device-activity pairing: records of events carrying a command id, their table, a device tally
+  bool dev_on = false;
+  for (uint64_t c : L.cls) {
+    const uint32_t k = cls_kind(c);
+    dev_on = dev_on || k == kDevBegin || k == kDevEnd || (k == kEntry && cls_cmdw(c) >= 0);
+  }
+  const uint64_t est = (host_ ? n * (uint64_t)P : 0) + n * 128 + cells * 80 + est_events * 24 +
+                       (dev_on ? est_events * 48 + cells * 80 : 0);
   if (c_->cap && c_->used + est > c_->cap) return THAPI_E_NOMEM;
 
   tr_ = new (std::nothrow) TraceRec();
@@ -482,7 +496,20 @@ int Loader::run() {
                   analyze_frontier_slack((uint32_t)c_->num_sms * 16);
   Frontier *frontier = nullptr;
   unsigned *status = reinterpret_cast<unsigned *>(misc_ + mStatus);
+  CmdOut cmd;
+  uint64_t cap_b = dev_on ? total_events / 2 + 1024 : 0, cap_e = cap_b, cap_h = cap_b;
   for (int attempt = 0;; ++attempt) {
+    if (dev_on) {  // (re)sized per attempt: a second attempt knows the exact counts
+      cmd.b = alloc<CmdBegin>(cap_b);
+      cmd.e = alloc<CmdEnd>(cap_e);
+      cmd.h = alloc<CmdHost>(cap_h);
+      if (sc_.failed) return THAPI_E_NOMEM;
+      cmd.cap_b = cap_b;
+      cmd.cap_e = cap_e;
+      cmd.cap_h = cap_h;
+      cmd.counts = reinterpret_cast<unsigned long long *>(misc_ + mCmdCount0);
+      CK(cudaMemsetAsync(misc_ + mCmdCount0, 0, 3 * sizeof(uint64_t), s_));
+    }
     frontier = static_cast<Frontier *>(dev_alloc(c_, fcap * sizeof(Frontier), s_));
     if (!frontier) return THAPI_E_NOMEM;
     sc_.adopt(frontier, fcap * sizeof(Frontier));
@@ -521,6 +548,7 @@ int Loader::run() {
     ap.dense_list = dense_list;
     ap.dense_count = reinterpret_cast<unsigned long long *>(misc_ + mDense);
     ap.slots_written = reinterpret_cast<unsigned long long *>(misc_ + mSlots);
+    ap.cmd = cmd;
     if (n) {
       ap.per_cta = (uint32_t)per;
       clk_.rec(PhaseClock::kAn0, s_);
@@ -561,10 +589,18 @@ int Loader::run() {
       c_->err_event = (k >> 3) & 0x1FFFFu;
       return (int)(k & 7u);
     }
-    if (misc_h_[mFrontTop] <= fcap || attempt >= 1) break;
-    fcap = misc_h_[mFrontTop];  // retry once with the exact frontier size
+    const uint64_t nb = misc_h_[mCmdCount0], ne = misc_h_[mCmdCount0 + 1], nh = misc_h_[mCmdCount0 + 2];
+    const bool cmd_over = dev_on && (nb > cap_b || ne > cap_e || nh > cap_h);
+    if ((misc_h_[mFrontTop] <= fcap && !cmd_over) || attempt >= 1) break;
+    // retry once with the exact frontier size and record counts
+    fcap = std::max(fcap, (uint64_t)misc_h_[mFrontTop]);
+    cap_b = std::max(cap_b, nb);
+    cap_e = std::max(cap_e, ne);
+    cap_h = std::max(cap_h, nh);
   }
   if (misc_h_[mFrontTop] > fcap) return THAPI_E_NOMEM;
+  if (dev_on && (misc_h_[mCmdCount0] > cap_b || misc_h_[mCmdCount0 + 1] > cap_e || misc_h_[mCmdCount0 + 2] > cap_h))
+    return THAPI_E_NOMEM;
 
   // ---- pairing across packets
   {
@@ -593,12 +629,58 @@ int Loader::run() {
     clk_.rec(PhaseClock::kFr1, s_);
   }
 
-  // ---- tally rows and interval offsets
+  // ---- device-activity pairing: command table, then device intervals and tally
+  Cell *dcells = nullptr;
+  if (dev_on) {
+    const uint64_t nb = misc_h_[mCmdCount0], ne = misc_h_[mCmdCount0 + 1], nh = misc_h_[mCmdCount0 + 2];
+    if (nb + ne + nh >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;  // 32-bit counts per table entry
+    dcells = alloc<Cell>(cells);
+    if (!dcells) return THAPI_E_NOMEM;
+    launch_tally_init(dcells, cells, s_);
+    CK(cudaMemsetAsync(misc_ + mJoin0, 0, 6 * sizeof(uint64_t), s_));
+    JoinParams jp{};
+    jp.b = cmd.b;
+    jp.e = cmd.e;
+    jp.h = cmd.h;
+    jp.nb = nb;
+    jp.ne = ne;
+    jp.nh = nh;
+    jp.slots = slots;
+    jp.sum_nvalid = sum_nvalid;
+    jp.dcells = dcells;
+    jp.n_funcs = F;
+    jp.out = reinterpret_cast<unsigned long long *>(misc_ + mJoin0);
+    clk_.rec(PhaseClock::kJo0, s_);
+    // first table: room for twice the largest record kind, short probes; if an
+    // insert runs out of probes, a table with room for twice every record
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const uint64_t want = attempt == 0 ? 2 * std::max(nb, std::max(ne, nh)) : 2 * (nb + ne + nh);
+      uint64_t cap = 1024;
+      while (cap < want) cap <<= 1;
+      jp.tab = alloc<CmdEntry>(cap + 1);
+      if (!jp.tab) return THAPI_E_NOMEM;
+      jp.mask = cap - 1;
+      jp.probe_limit = attempt == 0 ? 4096 : cap;
+      CK(cudaMemsetAsync(jp.tab, 0, (cap + 1) * sizeof(CmdEntry), s_));
+      launch_cmd_insert(jp, c_->num_sms, s_);
+      if (attempt == 1) break;
+      CK(cudaGetLastError());
+      if ((rc = sync_misc()) != THAPI_OK) return rc;
+      if (!misc_h_[mJoin0 + 5]) break;
+      CK(cudaMemsetAsync(misc_ + mJoin0 + 5, 0, sizeof(uint64_t), s_));
+    }
+    launch_cmd_emit(jp, c_->num_sms, s_);
+    clk_.rec(PhaseClock::kJo1, s_);
+  }
+
+  // ---- tally rows (host calls; device intervals apart) and interval offsets
   uint64_t *flags = alloc<uint64_t>(cells);
   thapi_tally_row *rows_tmp = alloc<thapi_tally_row>(cells);
+  thapi_tally_row *drows_tmp = dev_on ? alloc<thapi_tally_row>(cells) : nullptr;
   uint64_t *obase = alloc<uint64_t>(n);
   if (sc_.failed) return THAPI_E_NOMEM;
   launch_tally_compact(tally, cells, d_gkeys, F, flags, rows_tmp, misc_ + mRows, sc_, s_);
+  if (dev_on) launch_tally_compact(dcells, cells, d_gkeys, F, flags, drows_tmp, misc_ + mDevRows, sc_, s_);
   launch_widen_u32(sum_nvalid, obase, n, s_);
   scan_exclusive_u64(obase, n, misc_ + mIv, sc_, s_);
   if (sc_.failed) return THAPI_E_NOMEM;
@@ -606,6 +688,7 @@ int Loader::run() {
   CK(cudaGetLastError());
   if ((rc = sync_misc()) != THAPI_OK) return rc;
   const uint64_t n_rows = cells ? misc_h_[mRows] : 0;
+  const uint64_t n_dev_rows = dev_on && cells ? misc_h_[mDevRows] : 0;
   const uint64_t n_iv = n ? misc_h_[mIv] : 0;
   if (n_iv >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
   tr_->rows_bytes = std::max<uint64_t>(n_rows, 1) * sizeof(thapi_tally_row);
@@ -613,6 +696,14 @@ int Loader::run() {
   if (!tr_->rows) return THAPI_E_NOMEM;
   if (n_rows)
     CK(cudaMemcpyAsync(tr_->rows, rows_tmp, n_rows * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice, s_));
+  if (dev_on) {
+    tr_->dev_rows_bytes = std::max<uint64_t>(n_dev_rows, 1) * sizeof(thapi_tally_row);
+    tr_->dev_rows = static_cast<thapi_tally_row *>(dev_alloc(c_, tr_->dev_rows_bytes, s_));
+    if (!tr_->dev_rows) return THAPI_E_NOMEM;
+    if (n_dev_rows)
+      CK(cudaMemcpyAsync(tr_->dev_rows, drows_tmp, n_dev_rows * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice,
+                         s_));
+  }
 
   // ---- timeline: compact valid slots, sort by start, gather
   thapi_interval *rec = alloc<thapi_interval>(n_iv);
@@ -659,7 +750,8 @@ int Loader::run() {
       t.analyze_ms = clk_.ms(PhaseClock::kAn0, PhaseClock::kAn1) +
                      (clk_.dense ? clk_.ms(PhaseClock::kDn0, PhaseClock::kDn1) : 0.f);
       t.frontier_ms = clk_.ms(PhaseClock::kFr0, PhaseClock::kFr1);
-      t.tally_ms = clk_.ms(PhaseClock::kFr1, PhaseClock::kTa1);
+      t.join_ms = dev_on ? clk_.ms(PhaseClock::kJo0, PhaseClock::kJo1) : 0.f;
+      t.tally_ms = clk_.ms(dev_on ? PhaseClock::kJo1 : PhaseClock::kFr1, PhaseClock::kTa1);
       t.compact_ms = clk_.ms(PhaseClock::kCo0, PhaseClock::kCo1);
       t.sort_ms = clk_.ms(PhaseClock::kCo1, PhaseClock::kSo1);
       t.gather_ms = clk_.ms(PhaseClock::kSo1, PhaseClock::kGa1);
@@ -677,6 +769,17 @@ int Loader::run() {
   d.other_events = misc_h_[mDiag0 + dOther];
   d.discarded = misc_h_[mDiag0 + dDiscarded];
   d.packets = misc_h_[mDiag0 + dPackets];
+  thapi_device_diag &dd = tr_->dev_diag;
+  dd.dev_events = misc_h_[mDiag0 + dDevEvents];
+  if (dev_on) {
+    dd.dev_pairs = misc_h_[mJoin0];
+    dd.dev_intervals = misc_h_[mJoin0 + 1];
+    dd.dev_unjoined = misc_h_[mJoin0 + 2];
+    dd.dev_ambiguous = misc_h_[mJoin0 + 3];
+    dd.host_cmd_entries = misc_h_[mCmdCount0 + 2];
+    dd.host_unjoined = dd.host_cmd_entries - misc_h_[mJoin0 + 4];
+  }
+  dd.dev_unpaired = dd.dev_events - 2 * dd.dev_pairs;
   thapi_trace_info &inf = tr_->info;
   inf.nbytes = nbytes_;
   inf.n_packets = n;
@@ -690,7 +793,9 @@ int Loader::run() {
   inf.packet_bytes = P;
   inf.t_min = tmin == ~0ull ? 0 : tmin;
   inf.t_max = tmax;
-  inf.device_bytes = tr_->rows_bytes + tr_->tl_bytes;
+  inf.device_bytes = tr_->rows_bytes + tr_->tl_bytes + tr_->dev_rows_bytes;
+  inf.device_rows = n_dev_rows;
+  inf.device_intervals = dd.dev_intervals;
   tr_->strings.assign(L.strings.begin(), L.strings.end());
   tr_->host_name = L.host_name;
   tr_->func_name = L.func_name;
@@ -822,6 +927,24 @@ static int tally_impl(thapi_ctx *c, thapi_trace_id id, thapi_tally_row *rows, ui
   return THAPI_OK;
 }
 
+static int device_tally_impl(thapi_ctx *c, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                             thapi_device_diag *diag) {
+  TraceRec *tr = find(c, id);
+  if (!tr || !n_rows || (cap && !rows)) return THAPI_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
+  const uint64_t n = tr->info.device_rows;
+  *n_rows = n;
+  if (diag) *diag = tr->dev_diag;
+  if (cap == 0) return THAPI_OK;
+  if (cap < n) return THAPI_E_RANGE;
+  if (!n) return THAPI_OK;
+  if (cudaMemcpyAsync(rows, tr->dev_rows, n * sizeof(thapi_tally_row), cudaMemcpyDeviceToHost, tr->stream) !=
+      cudaSuccess)
+    return THAPI_E_CUDA;
+  if (cudaStreamSynchronize(tr->stream) != cudaSuccess) return THAPI_E_CUDA;
+  return THAPI_OK;
+}
+
 }  // namespace thapi
 
 using namespace thapi;
@@ -867,6 +990,7 @@ int thapi_ctx_destroy(thapi_ctx *ctx) {
     TraceRec *t = kv.second;
     dev_free(ctx, t->rows, t->rows_bytes, t->stream);
     dev_free(ctx, t->tl, t->tl_bytes, t->stream);
+    dev_free(ctx, t->dev_rows, t->dev_rows_bytes, t->stream);
     cudaStreamSynchronize(t->stream);
     delete t;
   }
@@ -893,6 +1017,7 @@ int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id) {
   cudaSetDevice(ctx->device);
   dev_free(ctx, t->rows, t->rows_bytes, t->stream);
   dev_free(ctx, t->tl, t->tl_bytes, t->stream);
+  dev_free(ctx, t->dev_rows, t->dev_rows_bytes, t->stream);
   cudaStreamSynchronize(t->stream);
   ctx->used -= std::min(ctx->used, t->info.device_bytes);
   ctx->traces.erase(id);
@@ -909,6 +1034,11 @@ int thapi_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64
 int thapi_tally_device(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
                        thapi_diag *diag, void *cuda_stream) {
   return tally_impl(ctx, id, rows, cap, n_rows, diag, true, static_cast<cudaStream_t>(cuda_stream));
+}
+
+int thapi_device_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
+                       thapi_device_diag *diag) {
+  return device_tally_impl(ctx, id, rows, cap, n_rows, diag);
 }
 
 int thapi_timeline(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out, uint64_t cap,

@@ -34,8 +34,9 @@ __host__ __device__ inline uint32_t cls_func(uint64_t c) { return (uint32_t)((c 
 __host__ __device__ inline int32_t cls_resw(uint64_t c) { return (int32_t)((c >> 33) & 0x7FFFu) - 1; }
 __host__ __device__ inline int32_t cls_cmdw(uint64_t c) { return (int32_t)((c >> 48) & 0x7FFFu) - 1; }
 
-// Interval slot flags (the output keeps bit 0 only).
+// Interval slot flags (the output keeps bits 0 and 2).
 constexpr uint8_t kIvErr = 1u;
+constexpr uint8_t kIvDevice = 1u << 2;  // device interval (device-activity pairing)
 constexpr uint8_t kIvOpen = 1u << 6;
 constexpr uint8_t kIvValid = 1u << 7;
 
@@ -59,7 +60,32 @@ __host__ __device__ inline unsigned long long err_key(uint64_t packet, uint32_t 
 }
 
 // Diagnostic counters (device), same order as thapi_diag.
-enum Diag { dEvents = 0, dPairs, dUnEntry, dUnExit, dMismatch, dOther, dDiscarded, dPackets, dCount };
+// dDevEvents: DEV_BEGIN / DEV_END events (device-activity diagnostics).
+enum Diag { dEvents = 0, dPairs, dUnEntry, dUnExit, dMismatch, dOther, dDiscarded, dPackets, dDevEvents, dCount };
+
+// Device-activity records, one per event that carries a command id, written
+// by the analysis kernels in no particular order (join.cu pairs them).
+struct __align__(16) CmdBegin {  // DEV_BEGIN
+  uint64_t cmd, ts;
+  uint64_t slot;                 // its interval slot (global index)
+  uint32_t group, pos;           // its stream's (host, pid, tid) group; its packet's order position
+};
+struct __align__(16) CmdEnd {    // DEV_END
+  uint64_t cmd, ts;
+};
+struct __align__(16) CmdHost {   // ENTRY of the host call that submitted the command
+  uint64_t cmd;
+  uint32_t func, pad;
+};
+// Where the analysis writes them: counts[k] grows past cap[k] without writing
+// past it (the host then retries with the exact counts).
+struct CmdOut {
+  CmdBegin *b = nullptr;
+  CmdEnd *e = nullptr;
+  CmdHost *h = nullptr;
+  uint64_t cap_b = 0, cap_e = 0, cap_h = 0;
+  unsigned long long *counts = nullptr;  // [3]: begin, end, host records; null = no device pairing
+};
 
 // ------------------------------------------------------ kernel params
 struct IndexParams {
@@ -103,6 +129,7 @@ struct AnalyzeParams {
   uint32_t *dense_list;          // packets with more events than emax (order positions)
   unsigned long long *dense_count;
   uint32_t per_cta;              // work items per CTA
+  CmdOut cmd;                    // device-activity records (counts null: none)
 };
 
 struct FrontierParams {
@@ -208,6 +235,29 @@ void launch_frontier(const FrontierParams &p, cudaStream_t s);
 void launch_tally_init(Cell *cells, uint64_t n, cudaStream_t s);
 void launch_tally_compact(const Cell *cells, uint64_t n, const uint32_t *group_keys, uint32_t n_funcs,
                           uint64_t *flags, thapi_tally_row *rows, uint64_t *n_rows_dev, Scratch &sc, cudaStream_t s);
+// join.cu: device-activity pairing over the command records.  The command
+// table has a power-of-two capacity plus one entry (for the zero id) and must
+// be zeroed before launch_cmd_insert.
+struct __align__(32) CmdEntry {
+  unsigned long long key, te;     // command id; ts of its (first) DEV_END
+  unsigned nb, ne, nh, func;      // begin / end / host records seen; host call's function (first one)
+};
+struct JoinParams {
+  const CmdBegin *b;
+  const CmdEnd *e;
+  const CmdHost *h;
+  uint64_t nb, ne, nh;
+  CmdEntry *tab;
+  uint64_t mask;                  // capacity - 1
+  uint64_t probe_limit;           // entries one insert may probe before it reports overflow
+  thapi_interval *slots;
+  uint32_t *sum_nvalid;           // per order position
+  Cell *dcells;                   // device tally [groups * n_funcs]
+  uint32_t n_funcs;
+  unsigned long long *out;        // [0..4]: pairs, intervals, unjoined, ambiguous, host entries of pairs; [5]: overflow
+};
+void launch_cmd_insert(const JoinParams &jp, int num_sms, cudaStream_t s);
+void launch_cmd_emit(const JoinParams &jp, int num_sms, cudaStream_t s);
 // timeline.cu
 void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
                              const uint64_t *out_base, const uint32_t *A, const uint32_t *order,

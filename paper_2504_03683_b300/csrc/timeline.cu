@@ -45,7 +45,7 @@ __global__ void k_timeline_compact(const thapi_interval *slots, const uint64_t *
         uint32_t lvl = above + iv.level;
         iv.level = (uint8_t)(lvl > 255u ? 255u : lvl);
         iv.stream_id = stream;
-        iv.flags &= kIvErr;
+        iv.flags &= (uint8_t)(kIvErr | kIvDevice);
         rec[at] = iv;
         key = iv.start_ns - t_min;
         if (key32)

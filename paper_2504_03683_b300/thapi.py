@@ -25,13 +25,16 @@ INTERVAL_DTYPE = np.dtype([("start_ns", "<u8"), ("end_ns", "<u8"), ("stream_id",
                            ("func_id", "<u2"), ("level", "u1"), ("flags", "u1")])
 DIAG_FIELDS = ("events", "pairs", "unmatched_entries", "unmatched_exits", "mismatched_pairs",
                "other_events", "discarded", "packets")
+DEVICE_DIAG_FIELDS = ("dev_events", "dev_pairs", "dev_intervals", "dev_unpaired", "dev_unjoined", "dev_ambiguous",
+                      "host_cmd_entries", "host_unjoined")
+IV_ERR, IV_DEVICE = 1, 4  # interval flags
 
 EXPORTED = (
     "thapi_ctx_create", "thapi_ctx_set_allocator", "thapi_ctx_destroy", "thapi_trace_load",
     "thapi_trace_load_device", "thapi_trace_free", "thapi_tally", "thapi_timeline", "thapi_tally_device",
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
-    "thapi_tally_static",
+    "thapi_tally_static", "thapi_device_tally",
 )
 
 
@@ -42,12 +45,20 @@ class Diag(ctypes.Structure):
         return {f: int(getattr(self, f)) for f in DIAG_FIELDS}
 
 
+class DeviceDiag(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in DEVICE_DIAG_FIELDS]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f in DEVICE_DIAG_FIELDS}
+
+
 class TraceInfo(ctypes.Structure):
     _fields_ = [("nbytes", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("events", ctypes.c_uint64),
                 ("intervals", ctypes.c_uint64), ("tally_rows", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("n_streams", ctypes.c_uint32), ("n_classes", ctypes.c_uint32), ("n_funcs", ctypes.c_uint32),
                 ("n_hosts", ctypes.c_uint32), ("packet_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("t_min", ctypes.c_uint64), ("t_max", ctypes.c_uint64)]
+                ("t_min", ctypes.c_uint64), ("t_max", ctypes.c_uint64),
+                ("device_rows", ctypes.c_uint64), ("device_intervals", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -57,7 +68,8 @@ class LoadTiming(ctypes.Structure):
     _fields_ = [(f, ctypes.c_float) for f in ("index_ms", "analyze_ms", "frontier_ms", "tally_ms", "compact_ms",
                                                "sort_ms", "gather_ms", "total_ms")] + \
                [(f, ctypes.c_uint64) for f in ("analyze_read_bytes", "analyze_write_bytes", "analyze_launches",
-                                                "launches")]
+                                                "launches")] + \
+               [(f, ctypes.c_float) for f in ("join_ms", "reserved_ms")]
 
     def as_dict(self):
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
@@ -107,6 +119,7 @@ def library():
         "thapi_trace_timing": ([vp, u64, P(LoadTiming)], i32),
         "thapi_kernel_launches": ([], u64),
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
+        "thapi_device_tally": ([vp, u64, vp, u64, P(u64), P(DeviceDiag)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -192,6 +205,19 @@ def thapi_tally(ctx: int, trace_id: int):
     if n.value:
         _check(lib.thapi_tally(ctx, trace_id, rows.ctypes.data, n.value, ctypes.byref(n), ctypes.byref(d)),
                "thapi_tally")
+    return rows, d.as_dict()
+
+
+def thapi_device_tally(ctx: int, trace_id: int):
+    """Returns (device tally rows as ROW_DTYPE array, device diag dict)."""
+    lib = library()
+    n = ctypes.c_uint64()
+    d = DeviceDiag()
+    _check(lib.thapi_device_tally(ctx, trace_id, None, 0, ctypes.byref(n), ctypes.byref(d)), "thapi_device_tally")
+    rows = np.zeros(n.value, dtype=ROW_DTYPE)
+    if n.value:
+        _check(lib.thapi_device_tally(ctx, trace_id, rows.ctypes.data, n.value, ctypes.byref(n), ctypes.byref(d)),
+               "thapi_device_tally")
     return rows, d.as_dict()
 
 
@@ -325,6 +351,9 @@ class Context:
 
     def tally(self, trace_id: int):
         return thapi_tally(self.handle, trace_id)
+
+    def device_tally(self, trace_id: int):
+        return thapi_device_tally(self.handle, trace_id)
 
     def timeline(self, trace_id: int, t0: int = 0, t1: int = 2**64 - 1):
         return thapi_timeline(self.handle, trace_id, t0, t1)

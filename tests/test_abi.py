@@ -40,5 +40,6 @@ def test_struct_sizes_match_header():
     assert thapi.ROW_DTYPE.itemsize == 56
     assert thapi.INTERVAL_DTYPE.itemsize == 24
     assert ctypes.sizeof(thapi.Diag) == 64
-    assert ctypes.sizeof(thapi.TraceInfo) == 8 * 6 + 4 * 6 + 16
-    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4
+    assert ctypes.sizeof(thapi.DeviceDiag) == 64
+    assert ctypes.sizeof(thapi.TraceInfo) == 8 * 6 + 4 * 6 + 16 + 16
+    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4 + 4 * 2

@@ -32,22 +32,25 @@ def ctx():
     c.close()
 
 
-def gpu_run(ctx, trace, windows=()):
+def gpu_run(ctx, trace, windows=(), device=False):
     tid = ctx.load(trace)
     try:
         rows, diag = ctx.tally(tid)
         ivs = ctx.timeline(tid)
         win = [ctx.timeline(tid, t0, t1) for (t0, t1) in windows]
         info = ctx.info(tid)
+        dev = ctx.device_tally(tid)
     finally:
         ctx.free(tid)
+    if device:
+        return rows, diag, ivs, win, info, dev
     return rows, diag, ivs, win, info
 
 
 def assert_parity(ctx, trace, windows=()):
     o = oracle.run(trace)
     assert o.code == oracle.OK
-    rows, diag, ivs, win, info = gpu_run(ctx, trace, windows)
+    rows, diag, ivs, win, info, (dev_rows, dev_diag) = gpu_run(ctx, trace, windows, device=True)
     for k in oracle.DIAG_FIELDS:
         assert diag[k] == o.diag[k], (k, diag[k], o.diag[k])
     assert rows_equal(rows, o.rows)
@@ -56,6 +59,10 @@ def assert_parity(ctx, trace, windows=()):
         ow = oracle.run(trace, t0=t0, t1=t1)
         assert intervals_equal(w, ow.intervals), (t0, t1)
     assert info["intervals"] == len(o.intervals) and info["tally_rows"] == len(o.rows)
+    # device-activity pairing
+    assert dev_diag == o.dev_diag, (dev_diag, o.dev_diag)
+    assert rows_equal(dev_rows, o.dev_rows)
+    assert info["device_rows"] == len(o.dev_rows) and info["device_intervals"] == o.dev_diag["dev_intervals"]
     return o
 
 
@@ -99,6 +106,59 @@ def test_device_workload_counts_other_events(ctx):
                                       n_device_streams=3))
     o = assert_parity(ctx, b)
     assert o.diag["other_events"] > 0
+
+
+# ------------------------------------------------ device-activity pairing
+@pytest.mark.parametrize("packet_bytes", [256, 4096, 65536])
+def test_device_pairing_handbuilt_cases(ctx, packet_bytes):
+    from tests import _device_trace as dt
+    b, ids = dt.build(packet_bytes=packet_bytes)
+    o = assert_parity(ctx, b, [(0, U64MAX), (dt.T0 + 150, dt.T0 + 131), (dt.T0 + 138, dt.T0 + 139)])
+    assert o.dev_diag == dt.EXPECTED_DEV_DIAG
+
+
+@pytest.mark.parametrize("over", [
+    # device streams with ~1000 events per 16 KB packet (warp kernel), drops, EXT timestamps
+    dict(total_calls=120_000, n_hosts=1, pids_per_host=4, tids_per_pid=4, n_device_streams=8, seed=3),
+    dict(total_calls=80_000, n_hosts=2, pids_per_host=2, tids_per_pid=2, n_device_streams=5, packet_bytes=1024,
+         p_drop=0.01, p_ext=0.01, seed=4),
+    # 32 KB packets: device packets hold ~2000 events, past the warp kernel's limit (the CTA kernel takes them)
+    dict(total_calls=60_000, n_hosts=1, pids_per_host=2, tids_per_pid=2, n_device_streams=3, packet_bytes=32768,
+         p_drop=0.002, seed=5),
+    # 64 KB packets: every packet goes to the CTA kernel
+    dict(total_calls=60_000, n_hosts=1, pids_per_host=2, tids_per_pid=2, n_device_streams=4, packet_bytes=65536,
+         seed=6),
+])
+def test_device_workloads(ctx, over):
+    b, calls, _e = tg.generate(tg.preset("device", **over), truth=True)
+    o = oracle.run(b)
+    assert_parity(ctx, b, _windows(o, seed=over["seed"]))
+    assert o.dev_diag["dev_intervals"] > 0
+
+
+def test_device_table_rebuilt_when_ids_do_not_repeat(ctx):
+    """Every record has its own id (no begin, end or host record shares one), so the
+    first command table (room for twice the largest record kind) overflows and the
+    join rebuilds it for every record."""
+    tb = TraceBuilder(packet_bytes=4096)
+    h = tb.add_host("h")
+    f = tb.add_func("launch")
+    fd = tb.add_func("dev", 3)
+    en = tb.add_class(f, ENTRY, 16, cmd_off=8)
+    ex = tb.add_class(f, EXIT, 4, result_off=0)
+    cb = tb.add_class(fd, DEV_BEGIN, 8, cmd_off=0)
+    from tracegen.handbuilt import DEV_END
+    ce = tb.add_class(fd, DEV_END, 8, cmd_off=0)
+    sh, sd = tb.add_stream(h, 1, 1), tb.add_stream(h, 2, 2, 1)
+    n = 3000
+    host, dev = [], []
+    for i in range(n):
+        host += [Ev(en, 10_000 + 10 * i, cmd=3 * i + 1), Ev(ex, 10_000 + 10 * i + 5, result=0)]
+        dev += [Ev(cb, 10_000 + 10 * i, cmd=3 * i + 2), Ev(ce, 10_000 + 10 * i + 3, cmd=3 * i + 3)]
+    tb.place(tb.stream_events(sh, host, ts_begin=10_000))
+    tb.place(tb.stream_events(sd, dev, ts_begin=10_000))
+    o = assert_parity(ctx, tb.build())
+    assert o.dev_diag["dev_unpaired"] == 2 * n and o.dev_diag["host_unjoined"] == n
 
 
 def test_ground_truth_through_gpu(ctx):
