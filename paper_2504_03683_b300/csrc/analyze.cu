@@ -474,6 +474,9 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
             if (dev_on && cls_cmdw(cr) >= 0 && (kd == kEntry || kd == kDevBegin || kd == kDevEnd)) {
               const uint32_t q = min(base + (uint32_t)cls_cmdw(cr), W);
               const uint64_t id = (uint64_t)C[q] | ((uint64_t)C[min(q + 1u, W)] << 32);
+              atomicAdd(&p.cmd.hist[((kd == kDevBegin ? 0u : kd == kDevEnd ? 1u : 2u) << p.cmd.part_bits) +
+                                    cmd_part(id, p.cmd.part_bits)],
+                        1u);
               if (kd == kDevBegin) {
                 const unsigned long long at = atomicAdd(&p.cmd.counts[0], 1ull);
                 if (at < p.cmd.cap_b) p.cmd.b[at] = CmdBegin{id, t, d.evbase + orank, d.group, (uint32_t)pos};

@@ -171,7 +171,9 @@ __device__ __forceinline__ TsM scan_ts(TsM x, uint32_t lane) {
   return x;
 }
 
-template <int BW>
+// DEV: device-activity records wanted (p.cmd.counts set); the kernel without
+// them carries none of that code.
+template <int BW, bool DEV>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p, uint32_t NW, unsigned int *status) {
   extern __shared__ __align__(128) uint8_t sm[];
   constexpr uint32_t SEGW = 32u * BW;
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   if (w_begin >= w_end) return;  // uniform over the CTA
   auto pos_of = [&](uint64_t w) -> uint64_t { return p.poslist ? p.poslist[w] : w; };
 
-  const bool dev_on = p.cmd.counts != nullptr;  // device-activity records wanted
+  constexpr bool dev_on = DEV;
   for (uint32_t c = threadIdx.x; c <= NC; c += blockDim.x) {
     if (c < NC) {
       const uint64_t r = p.classes[c];
@@ -300,10 +302,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     uint32_t ekey = 0xFFFFFFFFu;  // event index << 3 | code of the first bad event
     DM ld{0, 0};
     int lmax = 0;
+    uint32_t nrec = 0;  // device-activity records of the lane's events: begin | end << 10 | host << 20
     if (!fallback) {
       uint32_t e = cinc - cnt;
       // one event: its error code (0 if none) and depth step
-      auto check = [&](uint32_t oo, uint32_t &code, int &dv) {
+      // (rec: its device-activity record, counted in nrec's fields)
+      auto check = [&](uint32_t oo, uint32_t &code, int &dv, uint32_t &rec) {
         const uint32_t w0 = C[oo], w1 = C[oo + 1];
         const uint32_t c = w1 & 0xFFFFu;
         const bool ext = (w0 & kExtBit) != 0;
@@ -314,8 +318,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
                : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
         const uint32_t kd = row_kind(r);
         dv = code ? 0 : kd == kEntry ? 1 : (kd == kExit ? -1 : 0);
+        rec = (dev_on && !code && (r >> 31))
+                  ? (kd == kDevBegin ? 1u : kd == kDevEnd ? (1u << 10) : kd == kEntry ? (1u << 20) : 0u)
+                  : 0u;
       };
-      auto fold = [&](uint32_t code, int dv) {
+      auto fold = [&](uint32_t code, int dv, uint32_t rec) {
+        nrec += rec;
         if (code) ekey = min(ekey, (e << 3) | code);
         ld.s += dv;
         ld.m = min(ld.m, ld.s);
@@ -333,12 +341,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           m &= m - 1;  // (no-op when m is 0)
           s_off[e] = (uint16_t)oo0;
           if (two) s_off[e + 1] = (uint16_t)oo1;
-          uint32_t c0, c1;
+          uint32_t c0, c1, r0, r1;
           int d0, d1;
-          check(oo0, c0, d0);
-          check(oo1, c1, d1);
-          fold(c0, d0);
-          if (two) fold(c1, d1);
+          check(oo0, c0, d0, r0);
+          check(oo1, c1, d1, r1);
+          fold(c0, d0, r0);
+          if (two) fold(c1, d1, r1);
         }
       }
     }
@@ -375,6 +383,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     const int dmin = dc.m;  // minimum depth (packet-relative, <= 0); heights are indexed from it
     const uint32_t P_p = (uint32_t)(-dmin);
     const uint32_t O_p = (uint32_t)(dc.s - dmin);
+    // the packet's device-activity records, reserved at once (bases per kind)
+    unsigned long long rbase_b = 0, rbase_e = 0, rbase_h = 0;
+    if (dev_on) {
+      const uint32_t nb_p = __reduce_add_sync(kFull, nrec & 0x3FFu);
+      const uint32_t ne_p = __reduce_add_sync(kFull, (nrec >> 10) & 0x3FFu);
+      const uint32_t nh_p = __reduce_add_sync(kFull, nrec >> 20);
+      if (lane == 0) {
+        if (nb_p) rbase_b = atomicAdd(&p.cmd.counts[0], (unsigned long long)nb_p);
+        if (ne_p) rbase_e = atomicAdd(&p.cmd.counts[1], (unsigned long long)ne_p);
+        if (nh_p) rbase_h = atomicAdd(&p.cmd.counts[2], (unsigned long long)nh_p);
+      }
+    }
     uint64_t fbase = 0;
     if (lane == 0) {
       const uint32_t need = P_p + O_p;
@@ -395,6 +415,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       }
     }
     fbase = __shfl_sync(kFull, fbase, 0);
+    if (dev_on) {
+      rbase_b = __shfl_sync(kFull, rbase_b, 0);
+      rbase_e = __shfl_sync(kFull, rbase_e, 0);
+      rbase_h = __shfl_sync(kFull, rbase_h, 0);
+    }
     thapi_interval *const pslots = p.slots ? p.slots + d.evbase : nullptr;
     Cell *const gcells = p.tally + (uint64_t)d.group * F;
     uint32_t valid = 0, mism = 0;
@@ -513,36 +538,30 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         fr.flags = 0;
         p.frontier[fbase + pend_c + __popc(pbal & lt)] = fr;
       }
-      if (dev_on) {  // device-activity records of the batch
+      if (dev_on) {  // device-activity records of the batch, at the packet's reserved bases
         n_dev += (kd == kDevBegin || kd == kDevEnd) ? 1u : 0u;
         const bool rec_e = hcmd && kd == kDevEnd, rec_h = hcmd && is_entry;
         const uint32_t xb = __ballot_sync(kFull, rec_e), hb = __ballot_sync(kFull, rec_h);
-        if (bbal | xb | hb) {
-          unsigned long long o_b = 0, o_e = 0, o_h = 0;
-          if (lane == 0) {
-            if (bbal) o_b = atomicAdd(&p.cmd.counts[0], (unsigned long long)__popc(bbal));
-            if (xb) o_e = atomicAdd(&p.cmd.counts[1], (unsigned long long)__popc(xb));
-            if (hb) o_h = atomicAdd(&p.cmd.counts[2], (unsigned long long)__popc(hb));
-          }
-          o_b = __shfl_sync(kFull, o_b, 0);
-          o_e = __shfl_sync(kFull, o_e, 0);
-          o_h = __shfl_sync(kFull, o_h, 0);
-          if (rec_b || rec_e || rec_h) {
-            const uint32_t q = min(oo + 2u + (ext ? 2u : 0u) + (uint32_t)cls_cmdw(p.classes[c]), W);
-            const uint64_t id = (uint64_t)C[q] | ((uint64_t)C[min(q + 1u, W)] << 32);
-            if (rec_b) {
-              const uint64_t k = o_b + __popc(bbal & lt);
-              if (k < p.cmd.cap_b) p.cmd.b[k] = CmdBegin{id, t, d.evbase + rank, d.group, (uint32_t)pos};
-              if (pslots) put_interval(pslots + rank, t, 0, 0xFFFFFFFFu, 0, 0, 0);  // invalid until joined
-            } else if (rec_e) {
-              const uint64_t k = o_e + __popc(xb & lt);
-              if (k < p.cmd.cap_e) p.cmd.e[k] = CmdEnd{id, t};
-            } else {
-              const uint64_t k = o_h + __popc(hb & lt);
-              if (k < p.cmd.cap_h) p.cmd.h[k] = CmdHost{id, fn, 0u};
-            }
+        if (rec_b || rec_e || rec_h) {
+          const uint32_t q = min(oo + 2u + (ext ? 2u : 0u) + (uint32_t)cls_cmdw(p.classes[c]), W);
+          const uint64_t id = (uint64_t)C[q] | ((uint64_t)C[min(q + 1u, W)] << 32);
+          atomicAdd(&p.cmd.hist[((rec_b ? 0u : rec_e ? 1u : 2u) << p.cmd.part_bits) + cmd_part(id, p.cmd.part_bits)],
+                    1u);
+          if (rec_b) {
+            const uint64_t k = rbase_b + __popc(bbal & lt);
+            if (k < p.cmd.cap_b) p.cmd.b[k] = CmdBegin{id, t, d.evbase + rank, d.group, (uint32_t)pos};
+            if (pslots) put_interval(pslots + rank, t, 0, 0xFFFFFFFFu, 0, 0, 0);  // invalid until joined
+          } else if (rec_e) {
+            const uint64_t k = rbase_e + __popc(xb & lt);
+            if (k < p.cmd.cap_e) p.cmd.e[k] = CmdEnd{id, t};
+          } else {
+            const uint64_t k = rbase_h + __popc(hb & lt);
+            if (k < p.cmd.cap_h) p.cmd.h[k] = CmdHost{id, fn, 0u};
           }
         }
+        rbase_b += __popc(bbal);
+        rbase_e += __popc(xb);
+        rbase_h += __popc(hb);
       }
       __syncwarp();  // the table is read above before the batch's entries update it
       if (is_entry && (peers & ebal & gt) == 0) {  // the batch's last entry at its height
@@ -622,7 +641,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
 
 template <int BW>
 cudaError_t launch_w(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s, unsigned *status) {
-  auto fn = k_analyze_warp<BW>;
+  auto fn = p.cmd.counts ? k_analyze_warp<BW, true> : k_analyze_warp<BW, false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wp.smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, wp.nw * 32, wp.smem, s>>>(p, wp.nw, status);

@@ -286,6 +286,7 @@ enum Misc {
   mCmdCount0,                 // device-activity records: begin, end, host
   mJoin0 = mCmdCount0 + 3,    // join results: pairs, intervals, unjoined, ambiguous, host entries of pairs, overflow
   mDevRows = mJoin0 + 6,
+  mPartMax,                   // records of the largest command-id partition
   mCount
 };
 
@@ -497,7 +498,14 @@ int Loader::run() {
   Frontier *frontier = nullptr;
   unsigned *status = reinterpret_cast<unsigned *>(misc_ + mStatus);
   CmdOut cmd;
+  if (dev_on && total_events >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;  // 32-bit record indexes
   uint64_t cap_b = dev_on ? total_events / 2 + 1024 : 0, cap_e = cap_b, cap_h = cap_b;
+  // command-id partitions: about 1.5k records each at most (the records are at most the events)
+  int part_bits = 1;
+  while (part_bits < 18 && (total_events >> part_bits) > 1536) ++part_bits;
+  const uint64_t n_part = 1ull << part_bits;
+  uint32_t *part_hist = dev_on ? alloc<uint32_t>(3 * n_part) : nullptr;
+  if (dev_on && !part_hist) return THAPI_E_NOMEM;
   for (int attempt = 0;; ++attempt) {
     if (dev_on) {  // (re)sized per attempt: a second attempt knows the exact counts
       cmd.b = alloc<CmdBegin>(cap_b);
@@ -508,7 +516,10 @@ int Loader::run() {
       cmd.cap_e = cap_e;
       cmd.cap_h = cap_h;
       cmd.counts = reinterpret_cast<unsigned long long *>(misc_ + mCmdCount0);
+      cmd.hist = part_hist;
+      cmd.part_bits = part_bits;
       CK(cudaMemsetAsync(misc_ + mCmdCount0, 0, 3 * sizeof(uint64_t), s_));
+      CK(cudaMemsetAsync(part_hist, 0, 3 * n_part * sizeof(uint32_t), s_));
     }
     frontier = static_cast<Frontier *>(dev_alloc(c_, fcap * sizeof(Frontier), s_));
     if (!frontier) return THAPI_E_NOMEM;
@@ -651,25 +662,48 @@ int Loader::run() {
     jp.n_funcs = F;
     jp.out = reinterpret_cast<unsigned long long *>(misc_ + mJoin0);
     clk_.rec(PhaseClock::kJo0, s_);
-    // first table: room for twice the largest record kind, short probes; if an
-    // insert runs out of probes, a table with room for twice every record
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      const uint64_t want = attempt == 0 ? 2 * std::max(nb, std::max(ne, nh)) : 2 * (nb + ne + nh);
-      uint64_t cap = 1024;
-      while (cap < want) cap <<= 1;
-      jp.tab = alloc<CmdEntry>(cap + 1);
-      if (!jp.tab) return THAPI_E_NOMEM;
-      jp.mask = cap - 1;
-      jp.probe_limit = attempt == 0 ? 4096 : cap;
-      CK(cudaMemsetAsync(jp.tab, 0, (cap + 1) * sizeof(CmdEntry), s_));
-      launch_cmd_insert(jp, c_->num_sms, s_);
-      if (attempt == 1) break;
-      CK(cudaGetLastError());
-      if ((rc = sync_misc()) != THAPI_OK) return rc;
-      if (!misc_h_[mJoin0 + 5]) break;
-      CK(cudaMemsetAsync(misc_ + mJoin0 + 5, 0, sizeof(uint64_t), s_));
+    // partitioned join when every partition fits a shared-memory table
+    PartPlan pp{};
+    pp.part_bits = part_bits;
+    pp.hist = part_hist;
+    pp.base = alloc<uint64_t>(3 * n_part + 1);
+    pp.cursor = reinterpret_cast<unsigned long long *>(alloc<uint64_t>(3 * n_part));
+    pp.max_records = reinterpret_cast<unsigned long long *>(misc_ + mPartMax);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    CK(cudaMemsetAsync(misc_ + mPartMax, 0, sizeof(uint64_t), s_));
+    launch_part_prep(pp, s_);
+    scan_exclusive_u64(pp.base, 3 * n_part, pp.base + 3 * n_part, sc_, s_);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    CK(cudaGetLastError());
+    if ((rc = sync_misc()) != THAPI_OK) return rc;
+    if (misc_h_[mPartMax] <= kPartMaxRecords) {
+      pp.pb = alloc<CmdBegin>(nb);
+      pp.pe = alloc<CmdEnd>(ne);
+      pp.ph = alloc<CmdHost>(nh);
+      if (sc_.failed) return THAPI_E_NOMEM;
+      launch_part_scatter(jp, pp, c_->num_sms, s_);
+      launch_part_join(jp, pp, s_);
+    } else {
+      // one global table: room for twice the largest record kind, short probes;
+      // if an insert runs out of probes, a table with room for twice every record
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        const uint64_t want = attempt == 0 ? 2 * std::max(nb, std::max(ne, nh)) : 2 * (nb + ne + nh);
+        uint64_t cap = 1024;
+        while (cap < want) cap <<= 1;
+        jp.tab = alloc<CmdEntry>(cap + 1);
+        if (!jp.tab) return THAPI_E_NOMEM;
+        jp.mask = cap - 1;
+        jp.probe_limit = attempt == 0 ? 4096 : cap;
+        CK(cudaMemsetAsync(jp.tab, 0, (cap + 1) * sizeof(CmdEntry), s_));
+        launch_cmd_insert(jp, c_->num_sms, s_);
+        if (attempt == 1) break;
+        CK(cudaGetLastError());
+        if ((rc = sync_misc()) != THAPI_OK) return rc;
+        if (!misc_h_[mJoin0 + 5]) break;
+        CK(cudaMemsetAsync(misc_ + mJoin0 + 5, 0, sizeof(uint64_t), s_));
+      }
+      launch_cmd_emit(jp, c_->num_sms, s_);
     }
-    launch_cmd_emit(jp, c_->num_sms, s_);
     clk_.rec(PhaseClock::kJo1, s_);
   }
 
@@ -691,6 +725,7 @@ int Loader::run() {
   const uint64_t n_dev_rows = dev_on && cells ? misc_h_[mDevRows] : 0;
   const uint64_t n_iv = n ? misc_h_[mIv] : 0;
   if (n_iv >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+  if (dev_on && misc_h_[mJoin0 + 5]) return THAPI_E_CUDA;  // a join table without room: not reached
   tr_->rows_bytes = std::max<uint64_t>(n_rows, 1) * sizeof(thapi_tally_row);
   tr_->rows = static_cast<thapi_tally_row *>(dev_alloc(c_, tr_->rows_bytes, s_));
   if (!tr_->rows) return THAPI_E_NOMEM;

@@ -29,7 +29,7 @@ namespace thapi {
 namespace {
 
 constexpr uint64_t kCoarse = 4096;          // bucket size aimed at (the mean lands between half and all of it)
-constexpr uint64_t kMaxCells = 1ull << 24;  // (bucket, stream) cells
+constexpr uint64_t kMaxCells = 1ull << 26;  // (bucket, stream) cells
 constexpr uint32_t kMaxStreams = 2048;      // cells of one bucket held in shared memory
 constexpr uint32_t kCap = 4096;             // records of one bucket sorted in shared memory
 constexpr int kDigit = 9;

@@ -78,14 +78,30 @@ struct __align__(16) CmdHost {   // ENTRY of the host call that submitted the co
   uint32_t func, pad;
 };
 // Where the analysis writes them: counts[k] grows past cap[k] without writing
-// past it (the host then retries with the exact counts).
+// past it (the host then retries with the exact counts).  hist counts the
+// records of each kind per hash partition of the command id (join.cu).
 struct CmdOut {
   CmdBegin *b = nullptr;
   CmdEnd *e = nullptr;
   CmdHost *h = nullptr;
   uint64_t cap_b = 0, cap_e = 0, cap_h = 0;
   unsigned long long *counts = nullptr;  // [3]: begin, end, host records; null = no device pairing
+  uint32_t *hist = nullptr;              // [3][1 << part_bits]
+  int part_bits = 1;                     // partition = top part_bits bits of cmd_hash(id), 1..18
 };
+
+// Finaliser of SplitMix64 (Steele, Lea & Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014): a bijective mix of a
+// command id.  Its top bits choose the id's partition, its low bits the
+// entry in a partition's table.
+__host__ __device__ __forceinline__ uint64_t cmd_hash(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint32_t cmd_part(uint64_t id, int part_bits) {
+  return (uint32_t)(cmd_hash(id) >> (64 - part_bits));
+}
 
 // ------------------------------------------------------ kernel params
 struct IndexParams {
@@ -239,8 +255,10 @@ void launch_tally_compact(const Cell *cells, uint64_t n, const uint32_t *group_k
 // table has a power-of-two capacity plus one entry (for the zero id) and must
 // be zeroed before launch_cmd_insert.
 struct __align__(32) CmdEntry {
-  unsigned long long key, te;     // command id; ts of its (first) DEV_END
-  unsigned nb, ne, nh, func;      // begin / end / host records seen; host call's function (first one)
+  unsigned long long key;         // command id (0: free, except in the zero id's own entry)
+  unsigned long long nbe;         // begin records | end records << 32
+  unsigned long long te;          // sum of its DEV_END timestamps (the timestamp when there is one)
+  unsigned long long nhf;         // host records | sum of their functions << 32 (the function when one)
 };
 struct JoinParams {
   const CmdBegin *b;
@@ -258,6 +276,25 @@ struct JoinParams {
 };
 void launch_cmd_insert(const JoinParams &jp, int num_sms, cudaStream_t s);
 void launch_cmd_emit(const JoinParams &jp, int num_sms, cudaStream_t s);
+// Partitioned join: records grouped by partition (hist from the analysis),
+// then one CTA per partition with its table in shared memory.
+constexpr uint32_t kPartMaxRecords = 3072;  // records of one partition the shared-memory table takes
+struct PartPlan {
+  int part_bits;
+  const uint32_t *hist;           // [3][P] records per kind and partition
+  uint64_t *base;                 // [3P + 1] exclusive prefix of hist (kind-major), then the total
+  unsigned long long *cursor;     // [3P] scatter cursors
+  unsigned long long *max_records;  // largest partition (all kinds)
+  CmdBegin *pb;                   // partitioned copies
+  CmdEnd *pe;
+  CmdHost *ph;
+};
+// Widens hist into base and finds the largest partition (before the scan of base).
+void launch_part_prep(const PartPlan &pp, cudaStream_t s);
+// Cursors from the scanned base, then every record to its partition.
+void launch_part_scatter(const JoinParams &jp, const PartPlan &pp, int num_sms, cudaStream_t s);
+// One CTA per partition: pairs, joins, emits (needs max_records <= kPartMaxRecords).
+void launch_part_join(const JoinParams &jp, const PartPlan &pp, cudaStream_t s);
 // timeline.cu
 void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase, const uint32_t *nslot,
                              const uint64_t *out_base, const uint32_t *A, const uint32_t *order,

@@ -424,3 +424,37 @@ def test_hbm_cap_admission():
         with pytest.raises(thapi.ThapiError) as ei:
             c.load(b)
         assert ei.value.code == thapi.E_NOMEM
+
+
+def test_device_join_global_table_for_a_heavy_id(ctx):
+    """3100 host calls share one command id, so that id's partition holds more
+    records than a shared-memory partition table takes and the join uses one
+    global table instead.  4096 begins and 4096 ends with ids of their own, and
+    500 more host ids, overflow that table's first size (twice the largest record
+    kind, 8192 entries, for 8693 ids), so it is rebuilt for every record."""
+    from tracegen.handbuilt import DEV_END
+    tb = TraceBuilder(packet_bytes=4096)
+    h = tb.add_host("h")
+    f = tb.add_func("launch")
+    fd = tb.add_func("dev", 3)
+    en = tb.add_class(f, ENTRY, 16, cmd_off=8)
+    ex = tb.add_class(f, EXIT, 4, result_off=0)
+    cb = tb.add_class(fd, DEV_BEGIN, 8, cmd_off=0)
+    ce = tb.add_class(fd, DEV_END, 8, cmd_off=0)
+    sh, sd = tb.add_stream(h, 1, 1), tb.add_stream(h, 2, 2, 1)
+    host, dev = [], []
+    t = 10_000
+    for i in range(3100):
+        host += [Ev(en, t, cmd=0xABCDEF), Ev(ex, t + 5, result=0)]
+        t += 10
+    for i in range(500):
+        host += [Ev(en, t, cmd=(1 << 40) + i), Ev(ex, t + 5, result=0)]
+        t += 10
+    t = 10_000
+    for i in range(4096):
+        dev += [Ev(cb, t, cmd=(2 << 40) + i), Ev(ce, t + 3, cmd=(3 << 40) + i)]
+        t += 10
+    tb.place(tb.stream_events(sh, host, ts_begin=10_000))
+    tb.place(tb.stream_events(sd, dev, ts_begin=10_000))
+    o = assert_parity(ctx, tb.build())
+    assert o.dev_diag["dev_unpaired"] == 2 * 4096 and o.dev_diag["host_unjoined"] == 3600

@@ -16,8 +16,12 @@ paper's analysis inputs are traces of intercepted API entry/exit events
               over vendor (120 fns) plus a message-passing layer (30 fns);
               100M calls (200M events, ~8 GB); depth <= 6; median 5 us;
               1 % error results; 16 KB packets.
-* ``device``  launch/memcpy calls carrying 64-bit command ids plus device
-              streams of begin/end events (device-activity pairing).
+* ``device``  8 hosts x 8 pids x 8 threads (512 host streams) of launch /
+              memcpy calls (16 fns) carrying unique random 64-bit command
+              ids; 64 device streams run each command after its submit
+              (log-normal device time, median 400 ns, so the 8 host streams
+              feeding one device stream keep it about half busy) and log
+              DEV_BEGIN / DEV_END with the id; 50M commands = 200M events.
 """
 from __future__ import annotations
 
@@ -67,6 +71,7 @@ class TgConfig(ctypes.Structure):
         ("p_ext", ctypes.c_double),
         ("p_nest", ctypes.c_double),
         ("p_sample", ctypes.c_double),
+        ("dev_dur_median_ns", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -161,7 +166,7 @@ def preset(name: str, **overrides) -> TgConfig:
         base = dict(seed=2, total_calls=50_000_000, n_hosts=8, pids_per_host=8, tids_per_pid=8,
                     packet_bytes=16384, model=MODEL_DEVICE, max_depth=1, n_flat=16,
                     n_device_streams=64, dur_median_ns=5000.0, dur_sigma=1.0,
-                    gap_mean_ns=1000.0, var_min=0, var_max=48, p_err=0.01)
+                    gap_mean_ns=1000.0, var_min=0, var_max=48, p_err=0.01, dev_dur_median_ns=400.0)
     else:
         raise KeyError(name)
     base.update(overrides)

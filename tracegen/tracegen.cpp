@@ -125,6 +125,7 @@ typedef struct tg_config {
   double p_ext;             // probability an event uses EXT although its delta fits
   double p_nest;            // probability that a nestable call has children
   double p_sample;          // probability of an extra SAMPLE event after a call
+  double dev_dur_median_ns; // device model: log-normal median of a command's device time (0 = dur_median_ns)
 } tg_config;
 
 // Ground-truth record of one generated call (entry and exit as written, before drops).
@@ -610,7 +611,8 @@ void plan_device_work(Plan &pl, const std::vector<std::vector<IssuedCmd>> &cmds)
     uint64_t free_at = 0;
     for (auto &sc : v) {
       uint64_t begin = std::max(free_at, sc.first + (uint64_t)std::llround(r.expo(c.gap_mean_ns)));
-      double dv = c.dur_median_ns * std::exp(c.dur_sigma * r.normal());
+      const double med = c.dev_dur_median_ns > 0 ? c.dev_dur_median_ns : c.dur_median_ns;
+      double dv = med * std::exp(c.dur_sigma * r.normal());
       uint64_t dur = (uint64_t)std::llround(dv > 1e12 ? 1e12 : (dv < 0 ? 0 : dv));
       pl.dev_work[d].push_back({sc.second->cmd, begin, begin + dur, sc.second->func, sc.second->entry_dropped});
       free_at = begin + dur;
@@ -710,6 +712,7 @@ void tg_default_config(tg_config *c) {
   c->p_ext = 0.0;
   c->p_nest = 0.3;
   c->p_sample = 0.0;
+  c->dev_dur_median_ns = 0.0;
 }
 
 // Validates the config and runs the sizing pass.  Returns nullptr on a bad config.
