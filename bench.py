@@ -154,9 +154,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profile_traffic(kernel_file):
+def profile_traffic(kernel_file, workload):
     """DRAM traffic per launch recorded by the committed ncu summary, if it still matches the kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_analyze_warp_large.md")
+    path = os.path.join(ROOT, "profiles", "k_analyze_warp_%s.md" % workload)
     try:
         text = open(path).read()
     except OSError:
@@ -305,7 +305,7 @@ def main():
     phase = {k: round(statistics.mean(t[k] for t in timings), 4)
              for k in ("index_ms", "analyze_ms", "frontier_ms", "join_ms", "tally_ms", "compact_ms", "sort_ms",
                        "gather_ms", "total_ms")}
-    traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze_warp.cu"))
+    traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze_warp.cu"), args.workload)
 
     # end to end through the public API: host bytes in, host results out
     e2e = None
@@ -348,7 +348,8 @@ def main():
                        "l2": "inputs larger than L2 (%.1f GB trace vs 126 MB L2); no flush" % (meta["nbytes"] / 1e9)},
             "trace_gbs": meta["nbytes"] / (ms_max / 1e3) / 1e9 * (world if world > 1 else 1),
             "phases_ms": phase,
-            "roofline": {"kernel": "k_analyze_warp (decode+validate+pair+tally, interval slots)", "bound": "hbm",
+            "roofline": {"kernel": "k_analyze_warp (decode+validate+pair+tally, interval slots%s)" % (
+                             ", command records" if args.workload == "device" else ""), "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": peak_src + " hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
                          else "fallback",

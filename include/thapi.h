@@ -228,7 +228,9 @@ typedef struct thapi_load_timing {
   float gather_ms;    /* timeline gather */
   float total_ms;     /* first to last event of the load (includes host waits) */
   uint64_t analyze_read_bytes;   /* sum over packets of 32 + content_bytes (what the analysis must read) */
-  uint64_t analyze_write_bytes;  /* interval slots written by the analysis (24 B each) */
+  uint64_t analyze_write_bytes;  /* written by the analysis: interval slots (24 B each) and
+                                    device-activity records (32 B per DEV_BEGIN, 16 B per DEV_END
+                                    and per host ENTRY carrying a command id) */
   uint64_t analyze_launches;     /* analysis kernel launches of the load */
   uint64_t launches;             /* all kernel launches of the load */
   float join_ms;                 /* device-activity pairing (includes one host wait) */

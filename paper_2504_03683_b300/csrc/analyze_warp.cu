@@ -194,8 +194,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   uint32_t *ctab = reinterpret_cast<uint32_t *>(sm + L.off_ctab);
   uint16_t *cfn = reinterpret_cast<uint16_t *>(sm + L.off_cfn);
 
-  const uint64_t w_begin = (uint64_t)blockIdx.x * p.per_cta;
-  const uint64_t w_end = (w_begin + p.per_cta < p.n_order) ? w_begin + p.per_cta : p.n_order;
+  uint64_t w_begin = (uint64_t)blockIdx.x * p.per_cta;
+  uint64_t w_end = (w_begin + p.per_cta < p.n_order) ? w_begin + p.per_cta : p.n_order;
+  if (p.run_start) {  // runs of about equal cost
+    w_begin = p.run_start[blockIdx.x];
+    w_end = p.run_start[blockIdx.x + 1];
+  }
   if (w_begin >= w_end) return;  // uniform over the CTA
   auto pos_of = [&](uint64_t w) -> uint64_t { return p.poslist ? p.poslist[w] : w; };
 
@@ -693,5 +697,40 @@ cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint
 }
 
 uint64_t analyze_warp_frontier_slack(uint64_t warps) { return warps * kChunk; }
+
+namespace {
+
+// A packet's cost in events: its events plus the boundary walk, stitch and
+// compaction, which take about as long as pairing kPacketCost events.
+constexpr uint64_t kPacketCost = 384;
+
+__global__ void k_cost_split(const uint64_t *evbase, uint64_t n, uint64_t total_events, uint32_t grid,
+                             uint32_t *run_start) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > grid) return;
+  if (c == grid) {
+    run_start[c] = (uint32_t)n;
+    return;
+  }
+  const uint64_t total = total_events + kPacketCost * n;
+  const uint64_t target = total / grid * c + total % grid * c / grid;
+  uint64_t lo = 0, hi = n;  // first i with evbase[i] + kPacketCost * i >= target
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) / 2;
+    if (evbase[mid] + kPacketCost * mid < target)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  run_start[c] = (uint32_t)lo;
+}
+
+}  // namespace
+
+void launch_cost_split(const uint64_t *evbase, uint64_t n, uint64_t total_events, uint32_t grid, uint32_t *run_start,
+                       cudaStream_t s) {
+  k_cost_split<<<(grid + 1 + 127) / 128, 128, 0, s>>>(evbase, n, total_events, grid, run_start);
+  count_launches(1);
+}
 
 }  // namespace thapi

@@ -497,6 +497,8 @@ int Loader::run() {
                   analyze_frontier_slack((uint32_t)c_->num_sms * 16);
   Frontier *frontier = nullptr;
   unsigned *status = reinterpret_cast<unsigned *>(misc_ + mStatus);
+  uint32_t *run_start = alloc<uint32_t>(grid + 1);
+  if (!run_start) return THAPI_E_NOMEM;
   CmdOut cmd;
   if (dev_on && total_events >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;  // 32-bit record indexes
   uint64_t cap_b = dev_on ? total_events / 2 + 1024 : 0, cap_e = cap_b, cap_h = cap_b;
@@ -560,6 +562,11 @@ int Loader::run() {
     ap.dense_count = reinterpret_cast<unsigned long long *>(misc_ + mDense);
     ap.slots_written = reinterpret_cast<unsigned long long *>(misc_ + mSlots);
     ap.cmd = cmd;
+    ap.run_start = nullptr;
+    if (n && warp_path) {
+      ap.run_start = run_start;
+      launch_cost_split(evbase, n, total_events, (uint32_t)grid, run_start, s_);
+    }
     if (n) {
       ap.per_cta = (uint32_t)per;
       clk_.rec(PhaseClock::kAn0, s_);
@@ -572,6 +579,7 @@ int Loader::run() {
       if ((rc = sync_misc()) != THAPI_OK) return rc;
       if (misc_h_[mDense]) {
         AnalyzeParams dp = ap;
+        dp.run_start = nullptr;
         dp.emax = ((P - kPacketHeader) / 4) / 2 + 1;
         dp.n_order = misc_h_[mDense];
         dp.poslist = dense_list;
@@ -779,7 +787,10 @@ int Loader::run() {
     t.launches = launches_total() - launches0;
     t.analyze_launches = analyze_launches;
     t.analyze_read_bytes = misc_h_[mReadBytes];
-    t.analyze_write_bytes = misc_h_[mSlots] * sizeof(thapi_interval);
+    t.analyze_write_bytes = misc_h_[mSlots] * sizeof(thapi_interval) +
+                            (dev_on ? misc_h_[mCmdCount0] * sizeof(CmdBegin) + misc_h_[mCmdCount0 + 1] * sizeof(CmdEnd) +
+                                          misc_h_[mCmdCount0 + 2] * sizeof(CmdHost)
+                                    : 0);
     if (clk_.on && n) {
       t.index_ms = clk_.ms(PhaseClock::kIdx0, PhaseClock::kIdx1);
       t.analyze_ms = clk_.ms(PhaseClock::kAn0, PhaseClock::kAn1) +

@@ -145,6 +145,7 @@ struct AnalyzeParams {
   uint32_t *dense_list;          // packets with more events than emax (order positions)
   unsigned long long *dense_count;
   uint32_t per_cta;              // work items per CTA
+  const uint32_t *run_start;     // warp kernel: CTA c takes work items [run_start[c], run_start[c + 1])
   CmdOut cmd;                    // device-activity records (counts null: none)
 };
 
@@ -244,6 +245,10 @@ bool plan_analyze_warp(uint32_t P, uint32_t n_classes, int smem_optin, int smem_
 cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s,
                                 unsigned *status);
 uint64_t analyze_warp_frontier_slack(uint64_t warps);
+// Splits the stream-ordered packets into `grid` contiguous runs of about equal
+// cost (events + a per-packet constant): run_start[0..grid].
+void launch_cost_split(const uint64_t *evbase, uint64_t n, uint64_t total_events, uint32_t grid, uint32_t *run_start,
+                       cudaStream_t s);
 cudaError_t launch_analyze(const AnalyzeParams &p, int stages, uint32_t grid, cudaStream_t s, unsigned *status);
 // frontier.cu
 void launch_frontier(const FrontierParams &p, cudaStream_t s);

@@ -427,11 +427,11 @@ def test_hbm_cap_admission():
 
 
 def test_device_join_global_table_for_a_heavy_id(ctx):
-    """3100 host calls share one command id, so that id's partition holds more
-    records than a shared-memory partition table takes and the join uses one
-    global table instead.  4096 begins and 4096 ends with ids of their own, and
-    500 more host ids, overflow that table's first size (twice the largest record
-    kind, 8192 entries, for 8693 ids), so it is rebuilt for every record."""
+    """6200 host calls share one command id, so that id's partition holds more
+    records than a shared-memory partition table takes (3072) and the join uses
+    one global table instead.  8192 begins and 8192 ends with ids of their own,
+    and 100 more host ids, overflow that table's first size (twice the largest
+    record kind, 16384 entries, for 16485 ids), so it is rebuilt for every record."""
     from tracegen.handbuilt import DEV_END
     tb = TraceBuilder(packet_bytes=4096)
     h = tb.add_host("h")
@@ -444,17 +444,17 @@ def test_device_join_global_table_for_a_heavy_id(ctx):
     sh, sd = tb.add_stream(h, 1, 1), tb.add_stream(h, 2, 2, 1)
     host, dev = [], []
     t = 10_000
-    for i in range(3100):
+    for i in range(6200):
         host += [Ev(en, t, cmd=0xABCDEF), Ev(ex, t + 5, result=0)]
         t += 10
-    for i in range(500):
+    for i in range(100):
         host += [Ev(en, t, cmd=(1 << 40) + i), Ev(ex, t + 5, result=0)]
         t += 10
     t = 10_000
-    for i in range(4096):
+    for i in range(8192):
         dev += [Ev(cb, t, cmd=(2 << 40) + i), Ev(ce, t + 3, cmd=(3 << 40) + i)]
         t += 10
     tb.place(tb.stream_events(sh, host, ts_begin=10_000))
     tb.place(tb.stream_events(sd, dev, ts_begin=10_000))
     o = assert_parity(ctx, tb.build())
-    assert o.dev_diag["dev_unpaired"] == 2 * 4096 and o.dev_diag["host_unjoined"] == 3600
+    assert o.dev_diag["dev_unpaired"] == 2 * 8192 and o.dev_diag["host_unjoined"] == 6300
