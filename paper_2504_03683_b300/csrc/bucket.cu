@@ -6,9 +6,9 @@
 // high bits of the start offset and S streams, the compaction counts the
 // records of each (bucket, stream) cell and notes the cell's first record
 // (one atomic pair per cell and warp).  Then one CTA per bucket:
-//  1. reads its S cells, then the cells' runs of records (thread per cell,
-//     several loads in flight) into shared memory, in (stream, position)
-//     order;
+//  1. reads its S cells, then the cells' runs of records into shared memory
+//     in (stream, position) order, a thread per record (its cell from a
+//     binary search of the cell starts), four loads in flight;
 //  2. sorts (low key bits, position) stably with an LSD radix in shared
 //     memory (9-bit digits, warp ranks from one ballot per digit bit), so
 //     that equal starts keep the (stream, position) order;
@@ -119,7 +119,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_bucket_sort(const uint32_t *cnt
       if (tid == 0) cpre[S] = c;
     }
     __syncthreads();
-    // records of each cell (a contiguous run of rec), thread per cell, four loads in flight
+    // records of the bucket in (cell, position) order: thread per record, its
+    // cell found by a binary search of the cell starts (the largest cell start
+    // not above it belongs to a non-empty cell), so that neighbouring threads
+    // read neighbouring records of a cell; four records in flight per thread
     auto put = [&](uint32_t q, const thapi_interval &v) {
       srec[q] = v;
       const uint64_t key = v.start_ns - t_min;
@@ -127,18 +130,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_bucket_sort(const uint32_t *cnt
       const uint64_t kl = (key - ((uint64_t)b << shift)) & kmask;
       ia[q] = ((IT)kl << QSH) | (IT)q;
     };
-    for (uint32_t r = tid; r < S; r += kThreads) {
-      const uint32_t off = cpre[r], n_r = cpre[r + 1] - off;
-      const thapi_interval *rr = rec + cfirst[r];
-      uint32_t j = 0;
-      for (; j + 4 <= n_r; j += 4) {
-        const thapi_interval v0 = rr[j], v1 = rr[j + 1], v2 = rr[j + 2], v3 = rr[j + 3];
-        put(off + j, v0);
-        put(off + j + 1, v1);
-        put(off + j + 2, v2);
-        put(off + j + 3, v3);
+    auto src_of = [&](uint32_t q) -> uint64_t {
+      uint32_t lo = 0, hi = S;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cpre[mid] <= q)
+          lo = mid;
+        else
+          hi = mid;
       }
-      for (; j < n_r; ++j) put(off + j, rr[j]);
+      return (uint64_t)cfirst[lo] + (q - cpre[lo]);
+    };
+    for (uint32_t q0 = tid; q0 < c; q0 += 4 * kThreads) {
+      uint64_t g[4];
+      thapi_interval v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t q = q0 + u * kThreads;
+        g[u] = q < c ? src_of(q) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u * kThreads < c) v[u] = rec[g[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u * kThreads < c) put(q0 + u * kThreads, v[u]);
     }
     __syncthreads();
     // stable LSD radix on the key bits above QSH
