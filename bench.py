@@ -173,16 +173,33 @@ def profile_traffic(kernel_file, workload):
     return rec["traffic"]
 
 
-def cpu_sample(host_np, n_streams, max_streams):
-    """The oracle, as it stands, on the first k streams of the same trace (1 core)."""
+def sample_streams(workload, n_streams, cpu_streams):
+    """Streams of the bounded CPU sample (about 10-20 s of oracle time on one core)."""
+    if workload == "device":  # the first host streams and the first device streams (ids 512..575)
+        k = cpu_streams or 32
+        return list(range(min(k, 512))) + list(range(512, min(n_streams, 514)))
+    k = cpu_streams or (200 if workload == "large" else 64)
+    return list(range(max(1, min(n_streams, k))))
+
+
+def cpu_sample(host_np, n_streams, streams):
+    """The oracle, as it stands, on a subset of the streams of the same trace (1 core)."""
     import oracle
-    k = max(1, min(n_streams, max_streams))
     t = time.perf_counter()
-    r = oracle.run(host_np, streams=list(range(k)))
+    r = oracle.run(host_np, streams=streams)
     dt = time.perf_counter() - t
+    ranges, i = [], 0
+    while i < len(streams):
+        j = i
+        while j + 1 < len(streams) and streams[j + 1] == streams[j] + 1:
+            j += 1
+        ranges.append("%d..%d" % (streams[i], streams[j]))
+        i = j + 1
     return dict(value=r.diag["events"] / dt, unit="events/s", cores=1, kind="oracle",
-                sample="streams 0..%d of %d of the same trace (%d events), decode+pair+tally+timeline, "
-                       "one thread" % (k - 1, n_streams, r.diag["events"]), seconds=round(dt, 3))
+                sample="streams %s of %d of the same trace (%d events), decode+pair+tally%s+timeline, "
+                       "one thread" % (", ".join(ranges), n_streams, r.diag["events"],
+                                       "+device pairing" if r.dev_diag["dev_events"] else ""),
+                seconds=round(dt, 3))
 
 
 def run_reference(args, rank, world):
@@ -195,10 +212,10 @@ def run_reference(args, rank, world):
     plan = tg.Plan(cfg)
     n_streams = plan.n_streams
     plan.close()
-    max_streams = args.cpu_streams or (64 if args.workload == "large" else n_streams)
+    streams = sample_streams(args.workload, n_streams, args.cpu_streams or {"large": 64, "device": 16}.get(args.workload, 0))
     samples = []
     for i in range(args.warmup + args.steps):
-        s = cpu_sample(host, n_streams, max_streams)
+        s = cpu_sample(host, n_streams, streams)
         if i >= args.warmup:
             samples.append(s)
     value = statistics.median(x["value"] for x in samples)
@@ -334,7 +351,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
         host_np = host.numpy()
-        cpu = cpu_sample(host_np, meta["n_streams"], args.cpu_streams or (200 if args.workload == "large" else 10**9))
+        cpu = cpu_sample(host_np, meta["n_streams"], sample_streams(args.workload, meta["n_streams"], args.cpu_streams))
 
     if rank == 0:
         line = {
