@@ -188,6 +188,20 @@ int thapi_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64
 int thapi_device_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
                        thapi_device_diag *diag);
 
+/* Merges tally rows of several traces or ranks (the paper's local -> global
+ * aggregation, Sec. 3.4).  `rows`: n rows in HOST memory, in any order (for
+ * example the concatenated results of thapi_tally of several traces, or of
+ * several ranks; the 56-byte little-endian row is also the exchange format).
+ * Rows with equal (host_id, pid, tid, func_id) combine exactly: count,
+ * total_ns and err_count add (total_ns in u64), min_ns / max_ns take the
+ * minimum / maximum.  The merged rows go to HOST memory `out` (capacity
+ * `cap`), ordered by that key; *n_out = their number (at most n).  cap = 0 is
+ * a size query (the merge still runs); 0 < cap < *n_out gives E_RANGE.  Runs
+ * on the context's device on `cuda_stream`; blocks until done.
+ * Errors: E_INVALID, E_UNSUPPORTED (n >= 2^32), E_NOMEM, E_RANGE, E_CUDA. */
+int thapi_tally_merge(thapi_ctx *ctx, const thapi_tally_row *rows, uint64_t n, thapi_tally_row *out, uint64_t cap,
+                      uint64_t *n_out, void *cuda_stream);
+
 /* Copies the timeline intervals with start_ns < t1 and end_ns >= t0 (t0 = 0,
  * t1 = UINT64_MAX: all), in timeline order, to HOST memory `out` (capacity
  * `cap`).  *n_out = number selected; cap semantics as thapi_tally. */

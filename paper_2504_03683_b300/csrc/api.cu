@@ -1087,6 +1087,53 @@ int thapi_device_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows,
   return device_tally_impl(ctx, id, rows, cap, n_rows, diag);
 }
 
+int thapi_tally_merge(thapi_ctx *ctx, const thapi_tally_row *rows, uint64_t n, thapi_tally_row *out, uint64_t cap,
+                      uint64_t *n_out, void *cuda_stream) {
+  if (!ctx || !n_out || (n && !rows) || (cap && !out)) return THAPI_E_INVALID;
+  if (n >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return THAPI_E_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  Scratch sc;
+  sc.ctx = ctx;
+  sc.stream = s;
+  int rc = THAPI_OK;
+  uint64_t m = 0;
+  do {
+    thapi_tally_row *d_in = static_cast<thapi_tally_row *>(sc.get(std::max<uint64_t>(n, 1) * sizeof(thapi_tally_row)));
+    thapi_tally_row *d_out = static_cast<thapi_tally_row *>(sc.get(std::max<uint64_t>(n, 1) * sizeof(thapi_tally_row)));
+    uint64_t *d_m = static_cast<uint64_t *>(sc.get(sizeof(uint64_t)));
+    if (sc.failed) {
+      rc = THAPI_E_NOMEM;
+      break;
+    }
+    if (n && cudaMemcpyAsync(d_in, rows, n * sizeof(thapi_tally_row), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      rc = THAPI_E_CUDA;
+      break;
+    }
+    if (!tally_merge_device(d_in, n, d_out, d_m, sc, s)) {
+      rc = sc.failed ? THAPI_E_NOMEM : THAPI_E_CUDA;
+      break;
+    }
+    if (cudaMemcpyAsync(&m, d_m, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = THAPI_E_CUDA;
+      break;
+    }
+    *n_out = m;
+    if (cap == 0) break;
+    if (cap < m) {
+      rc = THAPI_E_RANGE;
+      break;
+    }
+    if (m && (cudaMemcpyAsync(out, d_out, m * sizeof(thapi_tally_row), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+              cudaStreamSynchronize(s) != cudaSuccess))
+      rc = THAPI_E_CUDA;
+  } while (false);
+  sc.release_all();
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
 int thapi_timeline(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out, uint64_t cap,
                    uint64_t *n_out) {
   TraceRec *t = find(ctx, id);

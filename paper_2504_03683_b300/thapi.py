@@ -34,7 +34,7 @@ EXPORTED = (
     "thapi_trace_load_device", "thapi_trace_free", "thapi_tally", "thapi_timeline", "thapi_tally_device",
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
-    "thapi_tally_static", "thapi_device_tally",
+    "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge",
 )
 
 
@@ -120,6 +120,7 @@ def library():
         "thapi_kernel_launches": ([], u64),
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
         "thapi_device_tally": ([vp, u64, vp, u64, P(u64), P(DeviceDiag)], i32),
+        "thapi_tally_merge": ([vp, vp, u64, vp, u64, P(u64), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -219,6 +220,18 @@ def thapi_device_tally(ctx: int, trace_id: int):
         _check(lib.thapi_device_tally(ctx, trace_id, rows.ctypes.data, n.value, ctypes.byref(n), ctypes.byref(d)),
                "thapi_device_tally")
     return rows, d.as_dict()
+
+
+def thapi_tally_merge(ctx: int, rows, stream=None):
+    """Merges tally rows (ROW_DTYPE, any order; e.g. several traces' or ranks' rows
+    concatenated) into one row per key, in key order."""
+    lib = library()
+    rows = np.ascontiguousarray(rows, dtype=ROW_DTYPE)
+    n = ctypes.c_uint64()
+    out = np.zeros(max(1, len(rows)), dtype=ROW_DTYPE)
+    _check(lib.thapi_tally_merge(ctx, rows.ctypes.data if len(rows) else None, len(rows), out.ctypes.data, len(out),
+                                 ctypes.byref(n), ctypes.c_void_p(_stream_ptr(stream))), "thapi_tally_merge")
+    return out[: n.value].copy()
 
 
 def thapi_tally_device(ctx: int, trace_id: int, dev_ptr: int, cap: int, stream=None):
@@ -354,6 +367,9 @@ class Context:
 
     def device_tally(self, trace_id: int):
         return thapi_device_tally(self.handle, trace_id)
+
+    def tally_merge(self, rows, stream=None):
+        return thapi_tally_merge(self.handle, rows, stream)
 
     def timeline(self, trace_id: int, t0: int = 0, t1: int = 2**64 - 1):
         return thapi_timeline(self.handle, trace_id, t0, t1)
