@@ -1,0 +1,92 @@
+"""Text rendering of tally rows, in the layout of the paper's summary table
+(arxiv 2504.03683, Sec. 4.3: Name | Time | Time(%) | Calls | Average | Min |
+Max, rows by Time descending, durations with s / ms / us / ns units and two
+decimals).
+
+Rendering is display only: Time(%) and Average are floating-point views of the
+exact integer rows (total_ns / sum of all rows' totals, total_ns / count),
+outside the bit-exact contract of the tally itself.  Names come from the
+trace's string table (thapi_trace_strings).
+"""
+from __future__ import annotations
+
+from collections import OrderedDict
+
+import numpy as np
+
+
+def fmt_ns(v) -> str:
+    """A duration in the paper's format: two decimals in s, ms or us; ns as an integer when exact."""
+    if v >= 1e9:
+        return "%.2fs" % (v / 1e9)
+    if v >= 1e6:
+        return "%.2fms" % (v / 1e6)
+    if v >= 1e3:
+        return "%.2fus" % (v / 1e3)
+    if isinstance(v, (int, np.integer)) or float(v).is_integer():
+        return "%dns" % int(v)
+    return "%.2fns" % v
+
+
+def fmt_pct(v: float) -> str:
+    return "%.2f%%" % v
+
+
+def summarize(rows, func_names, by_group: bool = False):
+    """Rows combined per function (or per (host_id, pid, tid, function) with by_group),
+    as dicts of exact integers, ordered by total time descending then name."""
+    acc = OrderedDict()
+    for r in np.asarray(rows).tolist():
+        host, pid, tid, func, count, total, mn, mx, err = r
+        key = (host, pid, tid, func) if by_group else (func,)
+        a = acc.get(key)
+        if a is None:
+            acc[key] = [count, total, mn, mx, err]
+        else:
+            a[0] += count
+            a[1] = (a[1] + total) & ((1 << 64) - 1)
+            a[2] = min(a[2], mn)
+            a[3] = max(a[3], mx)
+            a[4] += err
+    out = []
+    for key, (count, total, mn, mx, err) in acc.items():
+        out.append(dict(key=key, name=func_names[key[-1]], count=count, total=total, min=mn, max=mx, err=err))
+    out.sort(key=lambda d: (-d["total"], d["name"]))
+    return out
+
+
+def tally_table(rows, func_names, title: str | None = None, by_group: bool = False, host_names=None) -> str:
+    """The summary table as text; Time(%) of each row against the sum over all rows shown."""
+    items = summarize(rows, func_names, by_group)
+    grand = float(sum(d["total"] for d in items)) or 1.0
+    header = ["Name", "Time", "Time(%)", "Calls", "Average", "Min", "Max"]
+    if by_group:
+        header = ["Hostname", "Process", "Thread"] + header
+    body = []
+    for d in items:
+        cells = [d["name"], fmt_ns(d["total"]), fmt_pct(100.0 * d["total"] / grand), str(d["count"]),
+                 fmt_ns(d["total"] / d["count"]) if d["count"] else "-", fmt_ns(d["min"]), fmt_ns(d["max"])]
+        if by_group:
+            host, pid, tid = d["key"][:3]
+            hname = host_names[host] if host_names is not None else str(host)
+            cells = [hname, str(pid), str(tid)] + cells
+        body.append(cells)
+    widths = [max(len(header[i]), *(len(b[i]) for b in body)) if body else len(header[i]) for i in range(len(header))]
+    lines = []
+    if title:
+        lines.append(title)
+    lines.append(" | ".join(h.rjust(w) for h, w in zip(header, widths)) + " |")
+    lines.append("-|-".join("-" * w for w in widths) + "-|")
+    for b in body:
+        lines.append(" | ".join(c.rjust(w) for c, w in zip(b, widths)) + " |")
+    return "\n".join(lines) + "\n"
+
+
+def trace_names(ctx, trace_id: int):
+    """(function names, host names) of a loaded trace, from its string table."""
+    from .thapi import thapi_trace_info_get, thapi_trace_strings
+    h = ctx.handle if hasattr(ctx, "handle") else ctx
+    info = thapi_trace_info_get(h, trace_id)
+    funcs = [thapi_trace_strings(h, trace_id, 1, i) for i in range(info["n_funcs"])]
+    hosts = [thapi_trace_strings(h, trace_id, 0, i) for i in range(info["n_hosts"])]
+    return funcs, hosts

@@ -15,3 +15,27 @@ def test_paper_hiplz_table_reproduced():
     shown = [g["name"] for g in golden]
     by_time = sorted(shown, key=lambda n: -int(r.rows[[names[int(f)] == n for f in r.rows["func_id"]]][0]["total_ns"]))
     assert by_time == shown
+
+
+def _parse_table(text):
+    """{name: (Time, Time%, Calls, Average, Min, Max)} from a rendered table."""
+    out = {}
+    for line in text.splitlines()[2:]:
+        cells = [c.strip() for c in line.strip(" |").split("|")]
+        if len(cells) == 7:
+            out[cells[0]] = tuple(cells[1:])
+    return out
+
+
+def test_product_renderer_reproduces_paper_table_from_rows():
+    """The package's table renderer, fed the oracle's rows, prints the paper's values
+    in the paper's order (Time descending)."""
+    from paper_2504_03683_b300.render import tally_table
+    trace, golden, names = pt.build()
+    r = oracle.run(trace, want_intervals=False)
+    text = tally_table(r.rows, names)
+    got = _parse_table(text)
+    for g in golden:
+        assert got[g["name"]] == (g["time"], g["pct"], str(g["calls"]), g["avg"], g["min"], g["max"]), g["name"]
+    order = [ln.split("|")[0].strip() for ln in text.splitlines()[2:]]
+    assert order[:len(golden)] == [g["name"] for g in golden]
