@@ -102,6 +102,19 @@ typedef struct thapi_interval {
   uint8_t flags;
 } thapi_interval;
 
+/* One decoded event (32 B), as thapi_decode returns it. */
+typedef struct thapi_event {
+  uint64_t ts;        /* rebuilt timestamp (ns) */
+  uint64_t cmd;       /* command id (0 if the class has none) */
+  uint32_t stream_id;
+  uint16_t class_id;
+  uint16_t var_len;   /* payload bytes */
+  int32_t result;     /* i32 at the class's result offset (0 if none) */
+  uint8_t ext;        /* 1: the event carried an absolute timestamp */
+  uint8_t kind;       /* class kind (0 ENTRY, 1 EXIT, 2 DEV_BEGIN, 3 DEV_END, 4 SAMPLE) */
+  uint16_t func_id;
+} thapi_event;
+
 /* Diagnostics of one trace (64 B).
  * events = 2*(pairs + mismatched_pairs) + unmatched_entries + unmatched_exits + other_events. */
 typedef struct thapi_diag {
@@ -171,6 +184,21 @@ int thapi_trace_load(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, void *c
  * caller-owned, read during the call only; not copied). */
 int thapi_trace_load_device(thapi_ctx *ctx, const void *dev_bytes, uint64_t nbytes, void *cuda_stream,
                             thapi_trace_id *out);
+
+/* Decodes every event of a trace in HOST memory (caller-owned, copied to the
+ * device during the call) and writes one thapi_event per event to HOST
+ * memory `out` (capacity `cap`), in stream order (streams by id, packets by
+ * seq, events in packet order); *n_out = the trace's event count.  The
+ * records are the decode step of the analysis (event boundaries, timestamps
+ * rebuilt from deltas and absolute values, class, result, command id) made
+ * visible, for tools and text output.  cap = 0 is a size query (checks the
+ * headers only); 0 < cap < events gives E_RANGE.  Validation as
+ * thapi_trace_load (locations through thapi_last_error_location); nothing is
+ * kept on the device.  Packets up to 32 KB.
+ * Errors: E_INVALID, E_FORMAT / E_TRUNCATED, E_RANGE, E_NOMEM, E_UNSUPPORTED,
+ * E_CUDA. */
+int thapi_decode(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, thapi_event *out, uint64_t cap, uint64_t *n_out,
+                 void *cuda_stream);
 
 /* Releases a loaded trace's device results.  Errors: E_INVALID (unknown id). */
 int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id);

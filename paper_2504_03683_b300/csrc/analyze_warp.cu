@@ -663,6 +663,160 @@ int warp_bw(uint32_t P) {
   return 0;
 }
 
+// ---------------------------------------------------------------- decode
+// Every event of every packet as a record (thapi_event) at its global event
+// index: the same boundary walk, stitch and checks as the analysis, then 32
+// events per batch with the timestamp monoid scanned across the batches.  No
+// pairing.  Plain coalesced loads stage the packet (one warp per packet).
+constexpr uint32_t kDecodeWarps = 8;
+
+__host__ __device__ inline uint32_t decode_warp_bytes(uint32_t P) {
+  return rup(P + 48u, 128u) + rup(((P - kPacketHeader) / 8u + 1u) * 2u, 128u);
+}
+
+template <int BW>
+__global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams p, uint32_t NW) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  constexpr uint32_t SEGW = 32u * BW;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t NC = p.n_classes;
+  const uint32_t wbytes = decode_warp_bytes(p.P);
+  uint8_t *buf = sm + warp * wbytes;
+  uint32_t *C = reinterpret_cast<uint32_t *>(buf + kPacketHeader);
+  uint16_t *s_off = reinterpret_cast<uint16_t *>(buf + rup(p.P + 48u, 128u));
+  uint32_t *ctab = reinterpret_cast<uint32_t *>(sm + NW * wbytes);
+  for (uint32_t c = threadIdx.x; c <= NC; c += blockDim.x) {
+    if (c < NC) {
+      const uint64_t r = p.classes[c];
+      ctab[c] = cls_fixedw(r) | (cls_kind(r) << 14) | ((uint32_t)(cls_resw(r) + 1) << 17);
+    } else {
+      ctab[c] = 0;
+    }
+  }
+  __syncthreads();
+  for (uint64_t w = (uint64_t)blockIdx.x * NW + warp; w < p.n_order; w += (uint64_t)gridDim.x * NW) {
+    const PkDesc d = load_desc(p.desc + w);
+    const uint32_t W = d.content >> 2;
+    {  // stage header + content
+      const uint4 *src = reinterpret_cast<const uint4 *>(p.packets + (uint64_t)d.pk * p.P);
+      uint4 *dst = reinterpret_cast<uint4 *>(buf);
+      const uint32_t n16 = align16(kPacketHeader + d.content) / 16u;
+      for (uint32_t k = lane; k < n16; k += 32) dst[k] = src[k];
+    }
+    __syncwarp();
+    if (lane < 8) C[W + lane] = 0;
+    __syncwarp();
+    // boundaries (as in the analysis kernel)
+    const uint32_t a = lane * SEGW;
+    const uint32_t b = min(a + SEGW, W);
+    Bits<BW> spec, bits;
+    spec.clear();
+    uint32_t o = a;
+    while (o < b) {
+      spec.set(o - a);
+      o = step(C, o, ctab, NC);
+    }
+    const uint32_t spec_x = a < b ? o : a;
+    const bool succ_live = a + SEGW < W;
+    uint32_t ent = __shfl_up_sync(kFull, spec_x, 1);
+    if (lane == 0) ent = 0;
+    uint32_t x = resolve_seg<BW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
+    for (int r = 0; r < 32; ++r) {
+      const uint32_t next_ent = __shfl_down_sync(kFull, ent, 1);
+      const uint32_t bal = __ballot_sync(kFull, lane < 31 && succ_live && x != next_ent);
+      if (!bal) break;
+      const int k = __ffs(bal) - 1;
+      const uint32_t xk = __shfl_sync(kFull, x, k);
+      if (lane == (uint32_t)k + 1) {
+        ent = xk;
+        x = resolve_seg<BW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
+      }
+    }
+    const uint32_t cnt = bits.count();
+    uint32_t cinc = cnt;
+#pragma unroll
+    for (int q = 1; q < 32; q <<= 1) {
+      const uint32_t u = __shfl_up_sync(kFull, cinc, q);
+      if (lane >= (uint32_t)q) cinc += u;
+    }
+    const uint32_t c_tot = __shfl_sync(kFull, cinc, 31);
+    // offsets in order, with the format and truncation checks
+    uint32_t ekey = 0xFFFFFFFFu;
+    {
+      uint32_t e = cinc - cnt;
+#pragma unroll
+      for (int k = 0; k < BW; ++k) {
+        uint32_t m = bits.w[k];
+        while (m) {
+          const uint32_t oo = a + k * 32 + (__ffs(m) - 1);
+          m &= m - 1;
+          s_off[e] = (uint16_t)oo;
+          const uint32_t w0 = C[oo], w1 = C[oo + 1];
+          const uint32_t c = w1 & 0xFFFFu;
+          const bool ext = (w0 & kExtBit) != 0;
+          const uint32_t r = ctab[c < NC ? c : NC];
+          const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+          const uint32_t code = oo + 2 > W ? THAPI_E_TRUNCATED
+                                : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
+                                : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
+          if (code) ekey = min(ekey, (e << 3) | code);
+          ++e;
+        }
+      }
+    }
+    __syncwarp();
+    const uint32_t gkey = __reduce_min_sync(kFull, ekey);
+    if (gkey != 0xFFFFFFFFu || c_tot != d.nev) {
+      if (lane == 0)
+        atomicMin(p.content_err, gkey != 0xFFFFFFFFu ? err_key(d.pk, gkey >> 3, gkey & 7u)
+                                                     : err_key(d.pk, c_tot, THAPI_E_FORMAT));
+      __syncwarp();
+      continue;
+    }
+    // records, 32 events at a time
+    uint64_t tcur = d.tsb;
+    for (uint32_t e0 = 0; e0 < c_tot; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const bool act = e < c_tot;
+      const uint32_t oo = act ? s_off[e] : W;
+      const uint32_t w0 = C[oo], w1 = C[oo + 1];
+      const bool ext = act && (w0 & kExtBit) != 0;
+      const uint32_t c = act ? (w1 & 0xFFFFu) : 0u;
+      const uint64_t xts = (uint64_t)C[min(oo + 2, W)] | ((uint64_t)C[min(oo + 3, W)] << 32);
+      const TsM tm = ts_op(TsM{1u, tcur}, scan_ts(TsM{ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane));
+      const uint64_t t = tm.v;
+      tcur = __shfl_sync(kFull, t, 31);
+      if (act) {
+        const uint64_t r = p.classes[c];
+        const uint32_t base = oo + 2u + (ext ? 2u : 0u);
+        const int32_t rw = cls_resw(r), cw = cls_cmdw(r);
+        thapi_event ev;
+        ev.ts = t;
+        ev.cmd = cw >= 0 ? ((uint64_t)C[min(base + cw, W)] | ((uint64_t)C[min(base + cw + 1, W)] << 32)) : 0ull;
+        ev.stream_id = d.stream;
+        ev.class_id = (uint16_t)c;
+        ev.var_len = (uint16_t)(w1 >> 16);
+        ev.result = rw >= 0 ? (int32_t)C[min(base + rw, W)] : 0;
+        ev.ext = ext ? 1 : 0;
+        ev.kind = (uint8_t)cls_kind(r);
+        ev.func_id = (uint16_t)cls_func(r);
+        p.out[d.evbase + e] = ev;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int BW>
+cudaError_t launch_dw(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {
+  const uint32_t smem = nw * decode_warp_bytes(p.P) + rup((p.n_classes + 1u) * 4u, 16u);
+  cudaError_t e = cudaFuncSetAttribute(k_decode_warp<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_decode_warp<BW><<<grid, nw * 32, smem, s>>>(p, nw);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 // Chooses warps per CTA and CTAs per SM for the warp kernel (false: the CTA
@@ -697,6 +851,24 @@ cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint
 }
 
 uint64_t analyze_warp_frontier_slack(uint64_t warps) { return warps * kChunk; }
+
+// Warps per CTA of the decode kernel (0: not supported for this packet size).
+uint32_t decode_warps(uint32_t P, uint32_t n_classes, int smem_optin) {
+  if (!warp_bw(P) || n_classes > kClsMax) return 0;
+  const uint32_t fixed = rup((n_classes + 1u) * 4u, 16u), per = decode_warp_bytes(P);
+  if ((uint32_t)smem_optin < fixed + per) return 0;
+  return std::min<uint32_t>(kDecodeWarps, ((uint32_t)smem_optin - fixed) / per);
+}
+
+cudaError_t launch_decode_warp(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {
+  switch (warp_bw(p.P)) {
+    case 1: return launch_dw<1>(p, nw, grid, s);
+    case 2: return launch_dw<2>(p, nw, grid, s);
+    case 4: return launch_dw<4>(p, nw, grid, s);
+    case 8: return launch_dw<8>(p, nw, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 namespace {
 

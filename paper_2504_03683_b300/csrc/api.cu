@@ -316,6 +316,12 @@ class Loader {
     cudaStreamSynchronize(s_);
   }
   int run();
+  // decode only: every event to HOST `out` (capacity cap), *n = events; no trace is kept
+  void set_decode(thapi_event *out, uint64_t cap, uint64_t *n) {
+    dec_out_ = out;
+    dec_cap_ = cap;
+    dec_n_ = n;
+  }
   TraceRec *take() {
     TraceRec *t = tr_;
     tr_ = nullptr;
@@ -342,7 +348,54 @@ class Loader {
   uint64_t *misc_ = nullptr;
   unsigned long long misc_h_[mCount];
   PhaseClock clk_;
+  thapi_event *dec_out_ = nullptr;
+  uint64_t dec_cap_ = 0, *dec_n_ = nullptr;
+  int decode(const HostLayout &L, uint64_t n, uint64_t total_events, const uint8_t *packets, const uint32_t *order,
+             const uint32_t *pk_stream, const uint32_t *pk_nev, const uint32_t *pk_content, const uint32_t *pk_disc,
+             const uint64_t *pk_tsb, const uint32_t *d_group, const uint64_t *evbase, const uint64_t *d_cls);
 };
+
+// Decode-only tail of a load: descriptors, the decode kernel, the records to the host.
+int Loader::decode(const HostLayout &L, uint64_t n, uint64_t total_events, const uint8_t *packets,
+                   const uint32_t *order, const uint32_t *pk_stream, const uint32_t *pk_nev, const uint32_t *pk_content,
+                   const uint32_t *pk_disc, const uint64_t *pk_tsb, const uint32_t *d_group, const uint64_t *evbase,
+                   const uint64_t *d_cls) {
+  *dec_n_ = total_events;
+  if (dec_cap_ == 0) return THAPI_OK;
+  if (dec_cap_ < total_events) return THAPI_E_RANGE;
+  if (!total_events) return THAPI_OK;
+  const uint32_t nw = decode_warps(L.P, L.n_classes, c_->smem_per_block);
+  if (!nw) return THAPI_E_UNSUPPORTED;
+  int rc;
+  thapi_event *d_ev = alloc<thapi_event>(total_events);
+  PkDesc *desc = alloc<PkDesc>(n);
+  if (sc_.failed) return THAPI_E_NOMEM;
+  launch_build_desc(order, pk_stream, pk_nev, pk_content, pk_disc, pk_tsb, d_group, evbase, n, desc, s_);
+  misc_h_[mContentErr] = ~0ull;
+  CK(cudaMemcpyAsync(misc_ + mContentErr, misc_h_ + mContentErr, sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
+  DecodeParams dp{};
+  dp.packets = packets;
+  dp.P = L.P;
+  dp.n_classes = L.n_classes;
+  dp.n_order = n;
+  dp.desc = desc;
+  dp.classes = d_cls;
+  dp.out = d_ev;
+  dp.content_err = reinterpret_cast<unsigned long long *>(misc_ + mContentErr);
+  const uint64_t grid = std::min<uint64_t>((n + nw - 1) / nw, (uint64_t)c_->num_sms * 4);
+  CK(launch_decode_warp(dp, nw, (uint32_t)std::max<uint64_t>(grid, 1), s_));
+  if ((rc = sync_misc()) != THAPI_OK) return rc;
+  if (misc_h_[mContentErr] != ~0ull) {
+    const unsigned long long k = misc_h_[mContentErr];
+    c_->err_level = 2;
+    c_->err_packet = k >> 20;
+    c_->err_event = (k >> 3) & 0x1FFFFu;
+    return (int)(k & 7u);
+  }
+  CK(cudaMemcpyAsync(dec_out_, d_ev, total_events * sizeof(thapi_event), cudaMemcpyDeviceToHost, s_));
+  CK(cudaStreamSynchronize(s_));
+  return THAPI_OK;
+}
 
 // Double-buffered packets when they fit the per-CTA shared memory, else single.
 static int pick_stages(thapi_ctx *c, uint32_t P, uint32_t emax, uint32_t n_classes, uint32_t n_funcs) {
@@ -463,6 +516,9 @@ int Loader::run() {
     return THAPI_E_FORMAT;
   }
   const uint64_t total_events = n ? misc_h_[mEvents] : 0;
+  if (dec_n_)
+    return decode(L, n, total_events, packets, order, pk_stream, pk_nev, pk_content, pk_disc, pk_tsb, d_group, evbase,
+                  d_cls);
 
   // ---- decode + pair + tally per packet
   Cell *tally = alloc<Cell>(cells);
@@ -870,6 +926,17 @@ static int load_common(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, ui
   return THAPI_OK;
 }
 
+static int decode_common(thapi_ctx *c, const uint8_t *host, uint64_t nbytes, thapi_event *out, uint64_t cap,
+                         uint64_t *n_out, void *stream) {
+  if (!c || !host || !n_out || (cap && !out)) return THAPI_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
+  c->err_level = 0;
+  c->err_packet = c->err_event = 0;
+  Loader ld(c, host, nullptr, nbytes, static_cast<cudaStream_t>(stream));
+  ld.set_decode(out, cap, n_out);
+  return ld.run();
+}
+
 static TraceRec *find(thapi_ctx *c, thapi_trace_id id) {
   if (!c) return nullptr;
   auto it = c->traces.find(id);
@@ -1055,6 +1122,11 @@ int thapi_trace_load_device(thapi_ctx *ctx, const void *dev_bytes, uint64_t nbyt
   if (!dev_bytes) return THAPI_E_INVALID;
   if (reinterpret_cast<uintptr_t>(dev_bytes) % 16 != 0) return THAPI_E_INVALID;
   return load_common(ctx, nullptr, static_cast<const uint8_t *>(dev_bytes), nbytes, cuda_stream, out);
+}
+
+int thapi_decode(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, thapi_event *out, uint64_t cap, uint64_t *n_out,
+                 void *cuda_stream) {
+  return decode_common(ctx, static_cast<const uint8_t *>(bytes), nbytes, out, cap, n_out, cuda_stream);
 }
 
 int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id) {

@@ -245,6 +245,18 @@ bool plan_analyze_warp(uint32_t P, uint32_t n_classes, int smem_optin, int smem_
 cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s,
                                 unsigned *status);
 uint64_t analyze_warp_frontier_slack(uint64_t warps);
+// Decode of every event (thapi_decode): one warp per packet, packets up to 32 KB.
+struct DecodeParams {
+  const uint8_t *packets;
+  uint32_t P, n_classes;
+  uint64_t n_order;
+  const PkDesc *desc;            // per order position
+  const uint64_t *classes;       // packed class rows
+  thapi_event *out;              // at desc.evbase + event index
+  unsigned long long *content_err;
+};
+uint32_t decode_warps(uint32_t P, uint32_t n_classes, int smem_optin);  // warps per CTA, 0 = unsupported
+cudaError_t launch_decode_warp(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s);
 // Splits the stream-ordered packets into `grid` contiguous runs of about equal
 // cost (events + a per-packet constant): run_start[0..grid].
 void launch_cost_split(const uint64_t *evbase, uint64_t n, uint64_t total_events, uint32_t grid, uint32_t *run_start,

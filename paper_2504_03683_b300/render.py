@@ -90,3 +90,30 @@ def trace_names(ctx, trace_id: int):
     funcs = [thapi_trace_strings(h, trace_id, 1, i) for i in range(info["n_funcs"])]
     hosts = [thapi_trace_strings(h, trace_id, 0, i) for i in range(info["n_hosts"])]
     return funcs, hosts
+
+
+_KIND = {0: "entry", 1: "exit", 2: "device_begin", 3: "device_end", 4: "sample"}
+
+
+def event_lines(events, func_names, host_names, stream_table, limit: int | None = None):
+    """Decoded events (thapi_decode records) as text, one line per event, in the
+    spirit of the paper's pretty-printed trace (Sec. 3.2: timestamp, hostname,
+    process and thread, event name, then its fields).  The payload bytes are
+    opaque in this layout, so the fields shown are the ones every class has:
+    result, command id and payload size.  stream_table: (n_streams, 4) rows of
+    host_id, pid, tid, flags."""
+    out = []
+    n = len(events) if limit is None else min(limit, len(events))
+    ev = np.asarray(events)[:n]
+    for r in ev.tolist():
+        ts, cmd, sid, cls, var_len, result, ext, kind, func = r
+        host, pid, tid = (int(v) for v in stream_table[sid][:3])
+        fields = []
+        if kind == 1:
+            fields.append("result: %d" % result)
+        if cmd:
+            fields.append("cmd: 0x%016x" % cmd)
+        fields.append("payload_bytes: %d" % var_len)
+        out.append("%d %s vpid: %d, vtid: %d - %s_%s: { %s }" % (
+            ts, host_names[host], pid, tid, func_names[func], _KIND.get(kind, "event"), ", ".join(fields)))
+    return out

@@ -23,6 +23,8 @@ ROW_DTYPE = np.dtype([("host_id", "<u4"), ("pid", "<u4"), ("tid", "<u4"), ("func
                       ("err_count", "<u8")])
 INTERVAL_DTYPE = np.dtype([("start_ns", "<u8"), ("end_ns", "<u8"), ("stream_id", "<u4"),
                            ("func_id", "<u2"), ("level", "u1"), ("flags", "u1")])
+EVENT_DTYPE = np.dtype([("ts", "<u8"), ("cmd", "<u8"), ("stream_id", "<u4"), ("class_id", "<u2"),
+                        ("var_len", "<u2"), ("result", "<i4"), ("ext", "u1"), ("kind", "u1"), ("func_id", "<u2")])
 DIAG_FIELDS = ("events", "pairs", "unmatched_entries", "unmatched_exits", "mismatched_pairs",
                "other_events", "discarded", "packets")
 DEVICE_DIAG_FIELDS = ("dev_events", "dev_pairs", "dev_intervals", "dev_unpaired", "dev_unjoined", "dev_ambiguous",
@@ -34,7 +36,7 @@ EXPORTED = (
     "thapi_trace_load_device", "thapi_trace_free", "thapi_tally", "thapi_timeline", "thapi_tally_device",
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
-    "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge",
+    "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode",
 )
 
 
@@ -121,6 +123,7 @@ def library():
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
         "thapi_device_tally": ([vp, u64, vp, u64, P(u64), P(DeviceDiag)], i32),
         "thapi_tally_merge": ([vp, vp, u64, vp, u64, P(u64), vp], i32),
+        "thapi_decode": ([vp, vp, u64, vp, u64, P(u64), vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -190,6 +193,23 @@ def thapi_trace_load_device(ctx: int, dev_ptr: int, nbytes: int, stream=None) ->
                                            ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(tid))
     _check(rc, "thapi_trace_load_device", ctx)
     return tid.value
+
+
+def thapi_decode(ctx: int, trace, stream=None) -> np.ndarray:
+    """Every event of a trace in host memory as an EVENT_DTYPE array (stream order)."""
+    lib = library()
+    arr = trace if isinstance(trace, np.ndarray) else np.frombuffer(trace, dtype=np.uint8)
+    arr = np.ascontiguousarray(arr)
+    n = ctypes.c_uint64()
+    sp = ctypes.c_void_p(_stream_ptr(stream))
+    code = lib.thapi_decode(ctx, arr.ctypes.data, arr.nbytes, None, 0, ctypes.byref(n), sp)
+    if code != 0:
+        _check(code, "thapi_decode", ctx)
+    out = np.zeros(n.value, dtype=EVENT_DTYPE)
+    if n.value:
+        _check(lib.thapi_decode(ctx, arr.ctypes.data, arr.nbytes, out.ctypes.data, n.value, ctypes.byref(n), sp),
+               "thapi_decode", ctx)
+    return out
 
 
 def thapi_trace_free(ctx: int, trace_id: int) -> None:
@@ -364,6 +384,9 @@ class Context:
 
     def tally(self, trace_id: int):
         return thapi_tally(self.handle, trace_id)
+
+    def decode(self, trace, stream=None):
+        return thapi_decode(self.handle, trace, stream)
 
     def device_tally(self, trace_id: int):
         return thapi_device_tally(self.handle, trace_id)

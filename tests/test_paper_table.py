@@ -39,3 +39,21 @@ def test_product_renderer_reproduces_paper_table_from_rows():
         assert got[g["name"]] == (g["time"], g["pct"], str(g["calls"]), g["avg"], g["min"], g["max"]), g["name"]
     order = [ln.split("|")[0].strip() for ln in text.splitlines()[2:]]
     assert order[:len(golden)] == [g["name"] for g in golden]
+
+
+def test_event_lines_render_decoded_events():
+    """The pretty-printer turns decoded events into one line each: timestamp,
+    hostname, vpid / vtid, function_kind and the fields every class has."""
+    from paper_2504_03683_b300.render import event_lines
+    from tests._device_trace import build
+    from tests._util import stream_table
+    b, ids = build()
+    ev = oracle.decode(b)
+    st = stream_table(b)
+    names = ["launchKernel", "memcpyAsync", "deviceWork"]
+    lines = event_lines(ev, names, ["n0"], st)
+    assert len(lines) == len(ev)
+    assert lines[0].startswith("1000000 n0 vpid: 7, vtid: 7 - launchKernel_entry: { cmd: 0x000000000000000a")
+    assert lines[1] == "1000010 n0 vpid: 7, vtid: 7 - launchKernel_exit: { result: 0, payload_bytes: 0 }"
+    dev = [ln for ln in lines if "deviceWork_device_begin" in ln]
+    assert dev[0].startswith("1000100 n0 vpid: 900, vtid: 1 - deviceWork_device_begin: { cmd: 0x000000000000000a")
