@@ -5,7 +5,7 @@
 // the run's packets in turn.  Each warp stages its packet with a TMA bulk copy
 // (mbarrier completion) and then works on it alone:
 //
-//  1. boundaries: every lane walks a 32*BW-word segment speculatively from the
+//  1. boundaries: every lane walks a 32*(BW-1)+1-word segment speculatively from the
 //     segment start, marking the offsets it visits; the warp stitches the
 //     segments (a lane assumes its entry offset is its predecessor's
 //     speculative exit; the first lane whose exit breaks that assumption hands
@@ -176,7 +176,7 @@ __device__ __forceinline__ TsM scan_ts(TsM x, uint32_t lane) {
 template <int BW, bool DEV>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p, uint32_t NW, unsigned int *status) {
   extern __shared__ __align__(128) uint8_t sm[];
-  constexpr uint32_t SEGW = 32u * BW;
+  constexpr uint32_t SEGW = 32u * (BW - 1) + 1;  // odd: lane k's segment starts in shared-memory bank k
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
@@ -653,13 +653,17 @@ cudaError_t launch_w(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, 
   return cudaGetLastError();
 }
 
-// Bitmap words per lane segment for packets of P bytes (0: too large for the warp kernel).
+// Bitmap words per lane segment for packets of P bytes (0: too large for the
+// warp kernel).  A lane's segment is 32 * (BW - 1) + 1 words: an odd length,
+// so that the 32 segments start in 32 different shared-memory banks (with
+// 32 * k words they would all start in bank 0, and lanes walking events of
+// one size would stay in the same bank in lock step).
 int warp_bw(uint32_t P) {
   const uint32_t wmax = (P - kPacketHeader) / 4;
-  if (wmax <= 32u * 32) return 1;
-  if (wmax <= 64u * 32) return 2;
-  if (wmax <= 128u * 32) return 4;
-  if (wmax <= 256u * 32) return 8;
+  if (wmax <= 32u * 33) return 2;
+  if (wmax <= 32u * 65) return 3;
+  if (wmax <= 32u * 129) return 5;
+  if (wmax <= 32u * 257) return 9;
   return 0;
 }
 
@@ -677,7 +681,7 @@ __host__ __device__ inline uint32_t decode_warp_bytes(uint32_t P) {
 template <int BW>
 __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams p, uint32_t NW) {
   extern __shared__ __align__(128) uint8_t sm[];
-  constexpr uint32_t SEGW = 32u * BW;
+  constexpr uint32_t SEGW = 32u * (BW - 1) + 1;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t NC = p.n_classes;
   const uint32_t wbytes = decode_warp_bytes(p.P);
@@ -842,10 +846,10 @@ bool plan_analyze_warp(uint32_t P, uint32_t n_classes, int smem_optin, int smem_
 cudaError_t launch_analyze_warp(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s,
                                 unsigned *status) {
   switch (warp_bw(p.P)) {
-    case 1: return launch_w<1>(p, wp, grid, s, status);
     case 2: return launch_w<2>(p, wp, grid, s, status);
-    case 4: return launch_w<4>(p, wp, grid, s, status);
-    case 8: return launch_w<8>(p, wp, grid, s, status);
+    case 3: return launch_w<3>(p, wp, grid, s, status);
+    case 5: return launch_w<5>(p, wp, grid, s, status);
+    case 9: return launch_w<9>(p, wp, grid, s, status);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -862,10 +866,10 @@ uint32_t decode_warps(uint32_t P, uint32_t n_classes, int smem_optin) {
 
 cudaError_t launch_decode_warp(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {
   switch (warp_bw(p.P)) {
-    case 1: return launch_dw<1>(p, nw, grid, s);
     case 2: return launch_dw<2>(p, nw, grid, s);
-    case 4: return launch_dw<4>(p, nw, grid, s);
-    case 8: return launch_dw<8>(p, nw, grid, s);
+    case 3: return launch_dw<3>(p, nw, grid, s);
+    case 5: return launch_dw<5>(p, nw, grid, s);
+    case 9: return launch_dw<9>(p, nw, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
