@@ -55,6 +55,20 @@
 //  * in the timeline a device interval sits at the position of its DEV_BEGIN
 //    in its stream;
 //  * the same ns clock for host and device events.
+//
+// Per-CPU buffers (LTTng keeps one ring buffer per CPU, Sec. 3.1, so one
+// buffer interleaves the events of many threads, each event carrying the
+// thread's vpid / vtid context, Sec. 3.2).  Readings:
+//  * a stream whose flags have bit 1 set is a per-CPU buffer; each of its
+//    events has a 16-byte header: tsw, class, var_len, then u32 vpid, u32 vtid
+//    (before the EXT timestamp);
+//  * a thread is (host of the buffer, vpid, vtid); its events from all the
+//    per-CPU buffers are ordered by (ts, stream id, position in the stream)
+//    and paired with one call stack, as a per-thread stream would be; tally
+//    rows are keyed by (host, vpid, vtid, function) and merge with rows of
+//    per-thread streams of the same key; an interval belongs to its entry's
+//    stream and takes the entry's position in the timeline order;
+//  * device activity is paired over per-thread and device streams only.
 
 #include <algorithm>
 #include <cstdint>
@@ -74,6 +88,7 @@ enum {
 };
 
 enum { KIND_ENTRY = 0, KIND_EXIT = 1, KIND_DEV_BEGIN = 2, KIND_DEV_END = 3, KIND_SAMPLE = 4 };
+const uint32_t STREAM_PER_CPU = 2u;  // stream flags bit 1: a per-CPU buffer
 
 const uint32_t TRACE_MAGIC = 0x54504854u;   // "THPT"
 const uint32_t PACKET_MAGIC = 0x31544B50u;  // "PKT1"
@@ -213,12 +228,14 @@ const uint8_t *packet_at(const Trace &t, uint64_t i) { return t.b + t.packets_of
 int check_content(const Trace &t, const uint8_t *pk, uint64_t *bad_event) {
   uint32_t content = rd32(pk + 16);
   uint32_t n_events = rd32(pk + 20);
+  const uint32_t sid = rd32(pk + 4);
+  const uint32_t hdr = (t.streams[sid].flags & STREAM_PER_CPU) ? 16 : 8;  // per-CPU: + vpid, vtid
   const uint8_t *c = pk + 32;
   uint64_t off = 0;
   uint64_t k = 0;
   while (off < content) {
     *bad_event = k;
-    if (off + 8 > content) return ORC_E_TRUNCATED;
+    if (off + hdr > content) return ORC_E_TRUNCATED;
     uint32_t tsw = rd32(c + off);
     uint16_t cls = rd16(c + off + 4);
     uint16_t var_len = rd16(c + off + 6);
@@ -226,7 +243,7 @@ int check_content(const Trace &t, const uint8_t *pk, uint64_t *bad_event) {
     if (cls >= t.n_classes) return ORC_E_FORMAT;
     bool ext = (tsw & EXT) != 0;
     if (ext && (tsw & DELTA_MASK) != 0) return ORC_E_FORMAT;
-    uint64_t size = 8 + (ext ? 8 : 0) + t.classes[cls].fixed + ((var_len + 3u) & ~3u);
+    uint64_t size = hdr + (ext ? 8 : 0) + t.classes[cls].fixed + ((var_len + 3u) & ~3u);
     if (off + size > content) return ORC_E_TRUNCATED;
     off += size;
     ++k;
@@ -278,6 +295,7 @@ typedef struct orc_event {
   uint8_t ext;
   uint8_t kind;
   uint16_t func_id;
+  uint32_t vpid, vtid;  // the event's context in a per-CPU buffer, else the stream's pid / tid
 } orc_event;
 
 typedef struct orc_opts {
@@ -317,8 +335,20 @@ struct Command {
 struct Open {
   uint16_t func;
   uint64_t ts;
-  uint64_t seq;  // entry position in the stream
+  uint64_t seq;     // entry position in its stream
+  uint32_t stream;  // entry's stream
 };
+
+// One ENTRY / EXIT event of a per-CPU buffer, kept until its thread is paired.
+struct ThreadEvent {
+  uint64_t ts;
+  uint32_t stream;
+  uint64_t seq;
+  uint8_t kind;
+  uint16_t func;
+  int32_t result;
+};
+
 
 struct Keyed {
   uint64_t start;
@@ -383,11 +413,57 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
   auto by = packets_by_stream(t, keep);
   std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, orc_row> tally;
   std::map<uint64_t, Command> commands;
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<ThreadEvent>> threads;  // per-CPU buffers
   std::vector<Keyed> ivs;
   orc_diag &d = r.diag;
+  // One ENTRY or EXIT of the thread (host, pid, tid) whose call stack is `stack`.
+  auto pair = [&](std::vector<Open> &stack, uint32_t host, uint32_t pid, uint32_t tid, uint8_t kind, uint16_t func,
+                  uint64_t ts, int32_t result, uint32_t stream, uint64_t seq) {
+    if (kind == KIND_ENTRY) {
+      stack.push_back({func, ts, seq, stream});
+      return;
+    }
+    if (stack.empty()) {
+      d.unmatched_exits += 1;
+      return;
+    }
+    Open en = stack.back();
+    stack.pop_back();
+    if (en.func != func) {
+      d.mismatched_pairs += 1;
+      return;
+    }
+    uint64_t dur = ts - en.ts;
+    bool err = result != 0;
+    d.pairs += 1;
+    auto key = std::make_tuple(host, pid, tid, (uint32_t)func);
+    auto it = tally.find(key);
+    if (it == tally.end()) {
+      orc_row row{host, pid, tid, func, 0, 0, UINT64_MAX, 0, 0};
+      it = tally.emplace(key, row).first;
+    }
+    orc_row &row = it->second;
+    row.count += 1;
+    row.total_ns += dur;
+    row.min_ns = std::min(row.min_ns, dur);
+    row.max_ns = std::max(row.max_ns, dur);
+    row.err_count += err ? 1 : 0;
+    if (o.want_intervals && en.ts < o.t1 && ts >= o.t0) {
+      orc_interval iv{};
+      iv.start_ns = en.ts;
+      iv.end_ns = ts;
+      iv.stream_id = en.stream;
+      iv.func_id = func;
+      iv.level = (uint8_t)std::min<size_t>(stack.size(), 255);
+      iv.flags = err ? 1 : 0;
+      ivs.push_back({en.ts, en.stream, en.seq, iv});
+    }
+  };
   for (uint32_t s = 0; s < t.n_streams; ++s) {
     if (keep && !(*keep)[s]) continue;
     const Stream &st = t.streams[s];
+    const bool per_cpu = (st.flags & STREAM_PER_CPU) != 0;
+    const uint32_t hdr = per_cpu ? 16 : 8;
     std::vector<Open> stack;
     uint64_t seq_in_stream = 0;
     for (uint64_t pi : by[s]) {
@@ -402,14 +478,15 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
         uint32_t tsw = rd32(c + off);
         uint16_t cls = rd16(c + off + 4);
         uint16_t var_len = rd16(c + off + 6);
+        const uint32_t vpid = per_cpu ? rd32(c + off + 8) : st.pid, vtid = per_cpu ? rd32(c + off + 12) : st.tid;
         bool ext = (tsw & EXT) != 0;
-        uint64_t ts = ext ? rd64(c + off + 8) : ts_prev + (uint64_t)(tsw & DELTA_MASK);
+        uint64_t ts = ext ? rd64(c + off + hdr) : ts_prev + (uint64_t)(tsw & DELTA_MASK);
         ts_prev = ts;
         const Class &ci = t.classes[cls];
-        const uint8_t *fixed = c + off + 8 + (ext ? 8 : 0);
+        const uint8_t *fixed = c + off + hdr + (ext ? 8 : 0);
         int32_t result = ci.result_off >= 0 ? rd32s(fixed + ci.result_off) : 0;
         uint64_t cmd = ci.cmd_off >= 0 ? rd64(fixed + ci.cmd_off) : 0;
-        off += 8 + (ext ? 8 : 0) + ci.fixed + ((var_len + 3u) & ~3u);
+        off += hdr + (ext ? 8 : 0) + ci.fixed + ((var_len + 3u) & ~3u);
         d.events += 1;
         if (collect_events) {
           orc_event e{};
@@ -422,65 +499,48 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
           e.ext = ext ? 1 : 0;
           e.kind = ci.kind;
           e.func_id = ci.func;
+          e.vpid = vpid;
+          e.vtid = vtid;
           r.events.push_back(e);
         }
-        if (ci.kind == KIND_ENTRY && ci.cmd_off >= 0) {
+        if (!per_cpu && ci.kind == KIND_ENTRY && ci.cmd_off >= 0) {
           r.dev.host_cmd_entries += 1;
           commands[cmd].host_funcs.push_back(ci.func);
         }
         if (ci.kind == KIND_DEV_BEGIN || ci.kind == KIND_DEV_END) {
           r.dev.dev_events += 1;
-          if (ci.cmd_off >= 0) {
+          if (!per_cpu && ci.cmd_off >= 0) {
             if (ci.kind == KIND_DEV_BEGIN)
               commands[cmd].begins.push_back({ts, s, seq_in_stream});
             else
               commands[cmd].ends.push_back(ts);
           }
         }
-        if (ci.kind == KIND_ENTRY) {
-          stack.push_back({ci.func, ts, seq_in_stream});
-        } else if (ci.kind == KIND_EXIT) {
-          if (stack.empty()) {
-            d.unmatched_exits += 1;
-          } else {
-            Open en = stack.back();
-            stack.pop_back();
-            if (en.func != ci.func) {
-              d.mismatched_pairs += 1;
-            } else {
-              uint64_t dur = ts - en.ts;
-              bool err = result != 0;
-              d.pairs += 1;
-              auto key = std::make_tuple(st.host, st.pid, st.tid, (uint32_t)ci.func);
-              auto it = tally.find(key);
-              if (it == tally.end()) {
-                orc_row row{st.host, st.pid, st.tid, ci.func, 0, 0, UINT64_MAX, 0, 0};
-                it = tally.emplace(key, row).first;
-              }
-              orc_row &row = it->second;
-              row.count += 1;
-              row.total_ns += dur;
-              row.min_ns = std::min(row.min_ns, dur);
-              row.max_ns = std::max(row.max_ns, dur);
-              row.err_count += err ? 1 : 0;
-              if (o.want_intervals && en.ts < o.t1 && ts >= o.t0) {
-                orc_interval iv{};
-                iv.start_ns = en.ts;
-                iv.end_ns = ts;
-                iv.stream_id = s;
-                iv.func_id = ci.func;
-                iv.level = (uint8_t)std::min<size_t>(stack.size(), 255);
-                iv.flags = err ? 1 : 0;
-                ivs.push_back({en.ts, s, en.seq, iv});
-              }
-            }
-          }
+        if (ci.kind == KIND_ENTRY || ci.kind == KIND_EXIT) {
+          if (per_cpu)
+            threads[std::make_tuple(st.host, vpid, vtid)].push_back(
+                {ts, s, seq_in_stream, ci.kind, ci.func, result});
+          else
+            pair(stack, st.host, st.pid, st.tid, ci.kind, ci.func, ts, result, s, seq_in_stream);
         } else {
           d.other_events += 1;
         }
         ++seq_in_stream;
       }
     }
+    d.unmatched_entries += stack.size();
+  }
+  // threads of the per-CPU buffers: their events in (ts, stream, position) order, one stack each
+  for (auto &kv : threads) {
+    std::vector<ThreadEvent> &ev = kv.second;
+    std::stable_sort(ev.begin(), ev.end(), [](const ThreadEvent &a, const ThreadEvent &b) {
+      if (a.ts != b.ts) return a.ts < b.ts;
+      if (a.stream != b.stream) return a.stream < b.stream;
+      return a.seq < b.seq;
+    });
+    std::vector<Open> stack;
+    const uint32_t host = std::get<0>(kv.first), pid = std::get<1>(kv.first), tid = std::get<2>(kv.first);
+    for (const ThreadEvent &e : ev) pair(stack, host, pid, tid, e.kind, e.func, e.ts, e.result, e.stream, e.seq);
     d.unmatched_entries += stack.size();
   }
   for (auto &kv : tally) r.rows.push_back(kv.second);

@@ -101,19 +101,26 @@ def event_lines(events, func_names, host_names, stream_table, limit: int | None 
     process and thread, event name, then its fields).  The payload bytes are
     opaque in this layout, so the fields shown are the ones every class has:
     result, command id and payload size.  stream_table: (n_streams, 4) rows of
-    host_id, pid, tid, flags."""
+    host_id, pid, tid, flags; the thread is the record's vpid / vtid when it has
+    them (per-CPU buffers), else its stream's pid / tid."""
     out = []
-    n = len(events) if limit is None else min(limit, len(events))
-    ev = np.asarray(events)[:n]
-    for r in ev.tolist():
-        ts, cmd, sid, cls, var_len, result, ext, kind, func = r
+    ev = np.asarray(events)
+    n = len(ev) if limit is None else min(limit, len(ev))
+    has_ctx = ev.dtype.names is not None and "vtid" in ev.dtype.names
+    for i in range(n):
+        r = ev[i]
+        sid = int(r["stream_id"])
         host, pid, tid = (int(v) for v in stream_table[sid][:3])
+        if has_ctx:
+            pid, tid = int(r["vpid"]), int(r["vtid"])
+        kind, cmd = int(r["kind"]), int(r["cmd"])
         fields = []
         if kind == 1:
-            fields.append("result: %d" % result)
+            fields.append("result: %d" % int(r["result"]))
         if cmd:
             fields.append("cmd: 0x%016x" % cmd)
-        fields.append("payload_bytes: %d" % var_len)
+        fields.append("payload_bytes: %d" % int(r["var_len"]))
         out.append("%d %s vpid: %d, vtid: %d - %s_%s: { %s }" % (
-            ts, host_names[host], pid, tid, func_names[func], _KIND.get(kind, "event"), ", ".join(fields)))
+            int(r["ts"]), host_names[host], pid, tid, func_names[int(r["func_id"])], _KIND.get(kind, "event"),
+            ", ".join(fields)))
     return out

@@ -509,3 +509,63 @@ def test_device_window_keeps_overlapping_device_intervals():
     keep = (full.intervals["start_ns"] < dt.T0 + 131) & (full.intervals["end_ns"] >= dt.T0 + 150)
     assert intervals_equal(w.intervals, full.intervals[keep])
     assert dt.as_tuples(w.intervals[(w.intervals["flags"] & 4) != 0])[0][:2] == (dt.T0 + 100, dt.T0 + 150)
+
+
+# --------------------------------------------------------- per-CPU buffers
+def _iv_key(ivs):
+    return sorted((int(v["start_ns"]), int(v["end_ns"]), int(v["func_id"]), int(v["level"]), int(v["flags"]))
+                  for v in ivs)
+
+
+@pytest.mark.parametrize("over,n_cpus", [
+    (dict(total_calls=20_000, n_hosts=2, pids_per_host=2, tids_per_pid=2, seed=3, p_drop=0.005), 3),
+    (dict(total_calls=15_000, n_hosts=1, pids_per_host=2, tids_per_pid=4, seed=4, p_ext=0.02, packet_bytes=512), 2),
+])
+def test_per_cpu_buffers_give_the_per_thread_results(over, n_cpus):
+    """The same calls written per thread and per CPU (threads migrating between
+    CPUs) give the same tally, the same pairing diagnostics and the same
+    intervals up to the stream they belong to."""
+    from tests._percpu import to_per_cpu
+    b, _c, _e = tg.generate(tg.preset("large", **over))
+    pc = to_per_cpu(b, n_cpus=n_cpus, seed=over["seed"])
+    r1, r2 = oracle.run(b), oracle.run(pc)
+    assert r2.code == oracle.OK
+    assert rows_equal(r1.rows, r2.rows)
+    for k in ("events", "pairs", "unmatched_entries", "unmatched_exits", "mismatched_pairs", "other_events"):
+        assert r1.diag[k] == r2.diag[k], k
+    assert _iv_key(r1.intervals) == _iv_key(r2.intervals)
+    s = r2.intervals["start_ns"]
+    assert np.all(s[1:] >= s[:-1])
+
+
+def test_per_cpu_thread_migrates_inside_a_call():
+    """Thread (pid 5, tid 7) enters f on CPU 0 and g inside it, then migrates: g and f exit on CPU 1.
+    Thread (5, 8) interleaves on CPU 0 with its own call.  Written out by hand."""
+    tb = TraceBuilder(packet_bytes=256)
+    h = tb.add_host("h")
+    f, ef, xf = tb.add_call_func("f")
+    g, eg, xg = tb.add_call_func("g")
+    c0, c1 = tb.add_stream(h, 0, 0, 2), tb.add_stream(h, 0, 1, 2)
+    A, B = (5, 7), (5, 8)
+    cpu0 = [Ev(ef, 100, ctx=A), Ev(ef, 105, ctx=B), Ev(eg, 110, ctx=A), Ev(xf, 130, result=3, ctx=B)]
+    cpu1 = [Ev(xg, 140, result=0, ctx=A), Ev(xf, 170, result=0, ctx=A)]
+    tb.place(tb.stream_events(c0, cpu0, ts_begin=100))
+    tb.place(tb.stream_events(c1, cpu1, ts_begin=100))
+    r = oracle.run(tb.build())
+    assert r.code == oracle.OK and r.diag["pairs"] == 3
+    rows = [tuple(int(v) for v in x) for x in r.rows.tolist()]
+    assert rows == [(0, 5, 7, f, 1, 70, 70, 70, 0), (0, 5, 7, g, 1, 30, 30, 30, 0), (0, 5, 8, f, 1, 25, 25, 25, 1)]
+    ivs = [tuple(int(v) for v in x) for x in r.intervals.tolist()]
+    # (start, end, stream of the entry, func, level, flags), by start
+    assert ivs == [(100, 170, c0, f, 0, 0), (105, 130, c0, f, 0, 1), (110, 140, c0, g, 1, 0)]
+
+
+def test_per_cpu_header_truncated():
+    tb = TraceBuilder(packet_bytes=256)
+    h = tb.add_host("h")
+    f, e, x = tb.add_call_func("f")
+    c0 = tb.add_stream(h, 0, 0, 2)
+    ok = tb.encode_event(e, 1, ctx=(1, 1))
+    tb.raw_packet(c0, 0, [ok, ok[:12]], n_events=2)  # the second event's 16-byte header is cut
+    r = oracle.run(tb.build())
+    assert r.code == oracle.E_TRUNCATED and r.loc == (2, 0, 1)

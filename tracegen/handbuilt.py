@@ -10,7 +10,8 @@ Two levels:
   and pre-encoded event byte strings, for malformed-input cases.
 
 Layout (little-endian): 128-byte file header; stream rows {host_id, pid, tid,
-flags}; class rows {func_id u16, kind u8, 0, fixed_bytes u16, result_off i16,
+flags (bit 1: a per-CPU buffer, whose events carry u32 vpid, u32 vtid after the
+8-byte header)}; class rows {func_id u16, kind u8, 0, fixed_bytes u16, result_off i16,
 cmd_off i16, 0 x6}; function rows {name_off u32, layer u16, 0}; host rows
 {name_off u32, 0}; NUL-terminated strings; fixed-size packets at a 256-aligned
 offset, each a 32-byte header {magic "PKT1", stream_id, ts_begin u64,
@@ -38,6 +39,7 @@ class Ev:
     result: int | None = None
     cmd: int | None = None
     force_ext: bool = False
+    ctx: tuple | None = None  # (vpid, vtid) of an event of a per-CPU buffer
 
 
 @dataclass
@@ -85,8 +87,10 @@ class TraceBuilder:
     # ------------------------------------------------------------ events
     def encode_event(self, cls: int, delta: int = 0, ext_ts: int | None = None, payload: bytes = b"",
                      result: int | None = None, cmd: int | None = None, raw_tsw: int | None = None,
-                     var_len: int | None = None, fixed_override: bytes | None = None) -> bytes:
-        """Encodes one event.  ``raw_tsw``/``var_len``/``fixed_override`` allow malformed encodings."""
+                     var_len: int | None = None, fixed_override: bytes | None = None,
+                     ctx: tuple | None = None) -> bytes:
+        """Encodes one event.  ``raw_tsw``/``var_len``/``fixed_override`` allow malformed encodings;
+        ``ctx`` = (vpid, vtid) adds the per-CPU context after the 8-byte header."""
         c = self.classes[cls] if cls < len(self.classes) else _Class(0, ENTRY, 0, -1, -1)
         if raw_tsw is not None:
             tsw = raw_tsw
@@ -97,6 +101,8 @@ class TraceBuilder:
             tsw = delta
         vl = len(payload) if var_len is None else var_len
         out = struct.pack("<IHH", tsw, cls, vl)
+        if ctx is not None:
+            out += struct.pack("<II", ctx[0] & 0xFFFFFFFF, ctx[1] & 0xFFFFFFFF)
         if ext_ts is not None:
             out += struct.pack("<Q", ext_ts & 0xFFFFFFFFFFFFFFFF)
         if fixed_override is not None:
@@ -144,8 +150,10 @@ class TraceBuilder:
             def enc(prev_ts):
                 d = ev.ts - prev_ts
                 if ev.force_ext or d < 0 or d >= DELTA_LIMIT:
-                    return self.encode_event(ev.cls, ext_ts=ev.ts, payload=ev.payload, result=ev.result, cmd=ev.cmd)
-                return self.encode_event(ev.cls, delta=d, payload=ev.payload, result=ev.result, cmd=ev.cmd)
+                    return self.encode_event(ev.cls, ext_ts=ev.ts, payload=ev.payload, result=ev.result, cmd=ev.cmd,
+                                             ctx=ev.ctx)
+                return self.encode_event(ev.cls, delta=d, payload=ev.payload, result=ev.result, cmd=ev.cmd,
+                                         ctx=ev.ctx)
             b = enc(prev)
             if used + len(b) > cap:
                 pkts.append((begin, cur))
