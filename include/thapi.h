@@ -35,6 +35,16 @@
  * header in file order; every packet's events in file order.  See
  * thapi_last_error_location.
  *
+ * Per-CPU buffers: a stream whose flags have bit 1 set is a per-CPU buffer
+ * (one ring buffer per CPU, Sec. 3.1): each of its events has a 16-byte header
+ * {u32 tsw, u16 class_id, u16 var_len, u32 vpid, u32 vtid} (then [u64 ts],
+ * fixed part, payload).  Its events belong to the thread (host of the
+ * buffer, vpid, vtid); a thread's events from all per-CPU buffers are paired
+ * like one stream's, in (ts, stream id, position) order; tally rows are keyed
+ * by (host, vpid, vtid, function) and combine with per-thread rows of the same
+ * key; an interval belongs to its entry's stream.  Per-CPU buffers take no
+ * part in device-activity pairing, and need packets of at most 32 KB.
+ *
  * Semantics: one stream = one thread.  Per stream, events are paired with a
  * call stack: an EXIT pops the latest open ENTRY; equal functions make an
  * interval [entry ts, exit ts] (level = depth of the entry, 0 outermost,
@@ -102,7 +112,7 @@ typedef struct thapi_interval {
   uint8_t flags;
 } thapi_interval;
 
-/* One decoded event (32 B), as thapi_decode returns it. */
+/* One decoded event (40 B), as thapi_decode returns it. */
 typedef struct thapi_event {
   uint64_t ts;        /* rebuilt timestamp (ns) */
   uint64_t cmd;       /* command id (0 if the class has none) */
@@ -113,6 +123,7 @@ typedef struct thapi_event {
   uint8_t ext;        /* 1: the event carried an absolute timestamp */
   uint8_t kind;       /* class kind (0 ENTRY, 1 EXIT, 2 DEV_BEGIN, 3 DEV_END, 4 SAMPLE) */
   uint16_t func_id;
+  uint32_t vpid, vtid; /* the event's thread: its context in a per-CPU buffer, else its stream's pid / tid */
 } thapi_event;
 
 /* Diagnostics of one trace (64 B).
@@ -301,8 +312,8 @@ uint64_t thapi_kernel_launches(void);
  * followed by thapi_tally.  Working memory is one 32 MiB array in device
  * global memory that belongs to the library (every GPU that loads the library
  * holds it until the process exits).  Limits: at most 4096 packets, 2^20
- * events, 2^16 (host, pid, tid) groups x functions, and a cross-packet pairing
- * frontier that fits what the array has left; beyond them the call returns
+ * events, 2^16 (host, pid, tid) groups x functions, no per-CPU buffers, and a
+ * cross-packet pairing frontier that fits what the array has left; beyond them the call returns
  * E_UNSUPPORTED.  The first call on a device looks up the array's device
  * address, so make that first call before any stream capture.  Calls share
  * the array: host calls are serialised, each returns after its GPU work is

@@ -85,26 +85,28 @@ __device__ __forceinline__ int32_t row_resw(uint32_t r) { return (int32_t)((r >>
 // range is no event start: the chain moves to the next offset whose class id
 // is in range, at most four words on (the offsets a one-word-at-a-time walk
 // would pass through and land on, so every in-range offset it reaches is the
-// same).  Reads up to C[o + 4].
+// same).  Reads up to C[o + 4].  HW: header words (2; 4 in per-CPU buffers,
+// whose events carry vpid / vtid).
+template <uint32_t HW = 2>
 __device__ __forceinline__ uint32_t step(const uint32_t *C, uint32_t o, const uint32_t *ctab, uint32_t NC) {
   const uint32_t w0 = C[o], w1 = C[o + 1], w2 = C[o + 2], w3 = C[o + 3], w4 = C[o + 4];
   const uint32_t c = w1 & 0xFFFFu;
   const bool ok = c < NC;
   const uint32_t r = ctab[ok ? c : NC];
-  const uint32_t len = 2u + ((w0 >> 26) & 2u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+  const uint32_t len = HW + ((w0 >> 26) & 2u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
   const uint32_t skip = (w2 & 0xFFFFu) < NC ? 1u : (w3 & 0xFFFFu) < NC ? 2u : (w4 & 0xFFFFu) < NC ? 3u : 4u;
   return o + (ok ? len : skip);
 }
 
 // Walks from o while o < b, marking the offsets visited; returns at the first
 // offset already marked in `stop`.
-template <int BW>
+template <int BW, uint32_t HW = 2>
 __device__ __forceinline__ uint32_t walk_to(const uint32_t *C, uint32_t o, uint32_t a, uint32_t b, const Bits<BW> &stop,
                                             Bits<BW> &marks, const uint32_t *ctab, uint32_t NC) {
   while (o < b) {
     if (stop.test(o - a)) return o;
     marks.set(o - a);
-    o = step(C, o, ctab, NC);
+    o = step<HW>(C, o, ctab, NC);
   }
   return o;
 }
@@ -112,7 +114,7 @@ __device__ __forceinline__ uint32_t walk_to(const uint32_t *C, uint32_t o, uint3
 // Event starts of segment [a, b) when its chain enters at y: the speculative
 // marks from where the chain meets them, plus the offsets walked before that.
 // Returns the chain's exit offset.
-template <int BW>
+template <int BW, uint32_t HW = 2>
 __device__ __forceinline__ uint32_t resolve_seg(const uint32_t *C, uint32_t y, uint32_t a, uint32_t b,
                                                 const Bits<BW> &spec, uint32_t spec_x, Bits<BW> &bits,
                                                 const uint32_t *ctab, uint32_t NC) {
@@ -126,7 +128,7 @@ __device__ __forceinline__ uint32_t resolve_seg(const uint32_t *C, uint32_t y, u
   }
   Bits<BW> walked;
   walked.clear();
-  const uint32_t m = walk_to<BW>(C, y, a, b, spec, walked, ctab, NC);
+  const uint32_t m = walk_to<BW, HW>(C, y, a, b, spec, walked, ctab, NC);
   if (m < b) {
     bits = spec;
     bits.keep_from(m - a);
@@ -243,8 +245,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     dcur = load_desc(p.desc + pos_of(w));
     dnext = dcur;
     if (w + NW < w_end) dnext = load_desc(p.desc + pos_of(w + NW));
-    if (lane == 0) issue(dcur);
-    issued = true;
+    issued = dcur.group != kPerCpuGroup;  // per-CPU buffers are not staged here (percpu.cu takes them)
+    if (lane == 0 && issued) issue(dcur);
   }
   __syncwarp();
 
@@ -254,6 +256,19 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     const bool has_next = w + NW < w_end;
     dcur = dnext;  // next packet's descriptor (its copy is issued once the buffer is free)
     if (w + 2 * NW < w_end) dnext = load_desc(p.desc + pos_of(w + 2 * NW));
+    if (d.group == kPerCpuGroup) {  // a per-CPU buffer: no copy was issued; percpu.cu pairs its threads
+      if (lane == 0) {
+        p.sum_pend[pos] = 0;
+        p.sum_open[pos] = 0;
+        p.sum_fbase[pos] = 0;
+        p.sum_nslot[pos] = 0;
+        p.sum_nvalid[pos] = 0;
+        if (has_next && dcur.group != kPerCpuGroup) issue(dcur);
+      }
+      issued = has_next && dcur.group != kPerCpuGroup;
+      __syncwarp();
+      continue;
+    }
     const bool ok_wait = mbar_wait_bounded(bar, phase);
     if (__any_sync(kFull, !ok_wait)) {
       timed_out = true;
@@ -378,8 +393,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           p.dense_list[atomicAdd(p.dense_count, 1ull)] = (uint32_t)pos;
       }
       __syncwarp();
-      if (lane == 0 && has_next) issue(dcur);
-      issued = has_next;
+      if (lane == 0 && has_next && dcur.group != kPerCpuGroup) issue(dcur);
+      issued = has_next && dcur.group != kPerCpuGroup;
       continue;
     }
 
@@ -581,8 +596,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     }
     __syncwarp();
     // the packet bytes are no longer needed: stage the next packet now
-    if (lane == 0 && has_next) issue(dcur);
-    issued = has_next;
+    if (lane == 0 && has_next && dcur.group != kPerCpuGroup) issue(dcur);
+    issued = has_next && dcur.group != kPerCpuGroup;
     // the table rows from the minimum depth up to the final depth are the open entries
     for (uint32_t k = lane; k < O_p; k += 32) {
       const uint64_t ots = tab_ts[k], om = tab_md[k];
@@ -678,11 +693,178 @@ __host__ __device__ inline uint32_t decode_warp_bytes(uint32_t P) {
   return rup(P + 48u, 128u) + rup(((P - kPacketHeader) / 8u + 1u) * 2u, 128u);
 }
 
+// One packet of the decode (HW header words: 2, or 4 in per-CPU buffers).
+template <int BW, uint32_t HW>
+__device__ __forceinline__ void decode_packet(const DecodeParams &p, const PkDesc &d, uint8_t *buf, uint16_t *s_off,
+                                              const uint32_t *ctab, uint32_t lane) {
+  constexpr uint32_t SEGW = 32u * (BW - 1) + 1;
+  const uint32_t NC = p.n_classes;
+  uint32_t *C = reinterpret_cast<uint32_t *>(buf + kPacketHeader);
+  const uint32_t W = d.content >> 2;
+  {  // stage header + content
+    const uint4 *src = reinterpret_cast<const uint4 *>(p.packets + (uint64_t)d.pk * p.P);
+    uint4 *dst = reinterpret_cast<uint4 *>(buf);
+    const uint32_t n16 = align16(kPacketHeader + d.content) / 16u;
+    for (uint32_t k = lane; k < n16; k += 32) dst[k] = src[k];
+  }
+  __syncwarp();
+  if (lane < 8) C[W + lane] = 0;
+  __syncwarp();
+  // boundaries (as in the analysis kernel)
+  const uint32_t a = lane * SEGW;
+  const uint32_t b = min(a + SEGW, W);
+  Bits<BW> spec, bits;
+  spec.clear();
+  uint32_t o = a;
+  while (o < b) {
+    spec.set(o - a);
+    o = step<HW>(C, o, ctab, NC);
+  }
+  const uint32_t spec_x = a < b ? o : a;
+  const bool succ_live = a + SEGW < W;
+  uint32_t ent = __shfl_up_sync(kFull, spec_x, 1);
+  if (lane == 0) ent = 0;
+  uint32_t x = resolve_seg<BW, HW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
+  for (int r = 0; r < 32; ++r) {
+    const uint32_t next_ent = __shfl_down_sync(kFull, ent, 1);
+    const uint32_t bal = __ballot_sync(kFull, lane < 31 && succ_live && x != next_ent);
+    if (!bal) break;
+    const int k = __ffs(bal) - 1;
+    const uint32_t xk = __shfl_sync(kFull, x, k);
+    if (lane == (uint32_t)k + 1) {
+      ent = xk;
+      x = resolve_seg<BW, HW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
+    }
+  }
+  const uint32_t cnt = bits.count();
+  uint32_t cinc = cnt;
+#pragma unroll
+  for (int q = 1; q < 32; q <<= 1) {
+    const uint32_t u = __shfl_up_sync(kFull, cinc, q);
+    if (lane >= (uint32_t)q) cinc += u;
+  }
+  const uint32_t c_tot = __shfl_sync(kFull, cinc, 31);
+  // offsets in order, with the format and truncation checks
+  uint32_t ekey = 0xFFFFFFFFu;
+  {
+    uint32_t e = cinc - cnt;
+#pragma unroll
+    for (int k = 0; k < BW; ++k) {
+      uint32_t m = bits.w[k];
+      while (m) {
+        const uint32_t oo = a + k * 32 + (__ffs(m) - 1);
+        m &= m - 1;
+        s_off[e] = (uint16_t)oo;
+        const uint32_t w0 = C[oo], w1 = C[oo + 1];
+        const uint32_t c = w1 & 0xFFFFu;
+        const bool ext = (w0 & kExtBit) != 0;
+        const uint32_t r = ctab[c < NC ? c : NC];
+        const uint32_t sz = HW + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+        const uint32_t code = oo + HW > W ? THAPI_E_TRUNCATED
+                              : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
+                              : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
+        if (code) ekey = min(ekey, (e << 3) | code);
+        ++e;
+      }
+    }
+  }
+  __syncwarp();
+  const uint32_t gkey = __reduce_min_sync(kFull, ekey);
+  if (gkey != 0xFFFFFFFFu || c_tot != d.nev) {
+    if (lane == 0)
+      atomicMin(p.content_err, gkey != 0xFFFFFFFFu ? err_key(d.pk, gkey >> 3, gkey & 7u)
+                                                   : err_key(d.pk, c_tot, THAPI_E_FORMAT));
+    __syncwarp();
+    return;
+  }
+  // the stream's pid / tid (per-thread streams) or each event's vpid / vtid (per-CPU buffers)
+  const uint32_t spid = HW == 2 ? p.group_keys[3ull * d.group + 1] : 0u;
+  const uint32_t stid = HW == 2 ? p.group_keys[3ull * d.group + 2] : 0u;
+  // records, 32 events at a time
+  uint64_t tcur = d.tsb;
+  for (uint32_t e0 = 0; e0 < c_tot; e0 += 32) {
+    const uint32_t e = e0 + lane;
+    const bool act = e < c_tot;
+    const uint32_t oo = act ? s_off[e] : W;
+    const uint32_t w0 = C[oo], w1 = C[oo + 1];
+    const bool ext = act && (w0 & kExtBit) != 0;
+    const uint32_t c = act ? (w1 & 0xFFFFu) : 0u;
+    const uint64_t xts = (uint64_t)C[min(oo + HW, W)] | ((uint64_t)C[min(oo + HW + 1, W)] << 32);
+    const TsM tm = ts_op(TsM{1u, tcur}, scan_ts(TsM{ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane));
+    const uint64_t t = tm.v;
+    tcur = __shfl_sync(kFull, t, 31);
+    if (act) {
+      const uint64_t r = p.classes[c];
+      const uint32_t base = oo + HW + (ext ? 2u : 0u);
+      const int32_t rw = cls_resw(r), cw = cls_cmdw(r);
+      thapi_event ev;
+      ev.ts = t;
+      ev.cmd = cw >= 0 ? ((uint64_t)C[min(base + cw, W)] | ((uint64_t)C[min(base + cw + 1, W)] << 32)) : 0ull;
+      ev.stream_id = d.stream;
+      ev.class_id = (uint16_t)c;
+      ev.var_len = (uint16_t)(w1 >> 16);
+      ev.result = rw >= 0 ? (int32_t)C[min(base + rw, W)] : 0;
+      ev.ext = ext ? 1 : 0;
+      ev.kind = (uint8_t)cls_kind(r);
+      ev.func_id = (uint16_t)cls_func(r);
+      ev.vpid = HW == 2 ? spid : C[oo + 2];
+      ev.vtid = HW == 2 ? stid : C[oo + 3];
+      p.out[d.evbase + e] = ev;
+    }
+  }
+  __syncwarp();
+}
+
 template <int BW>
 __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams p, uint32_t NW) {
   extern __shared__ __align__(128) uint8_t sm[];
-  constexpr uint32_t SEGW = 32u * (BW - 1) + 1;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t NC = p.n_classes;
+  const uint32_t wbytes = decode_warp_bytes(p.P);
+  uint8_t *buf = sm + warp * wbytes;
+  uint16_t *s_off = reinterpret_cast<uint16_t *>(buf + rup(p.P + 48u, 128u));
+  uint32_t *ctab = reinterpret_cast<uint32_t *>(sm + NW * wbytes);
+  for (uint32_t c = threadIdx.x; c <= NC; c += blockDim.x) {
+    if (c < NC) {
+      const uint64_t r = p.classes[c];
+      ctab[c] = cls_fixedw(r) | (cls_kind(r) << 14) | ((uint32_t)(cls_resw(r) + 1) << 17);
+    } else {
+      ctab[c] = 0;
+    }
+  }
+  __syncthreads();
+  for (uint64_t w = (uint64_t)blockIdx.x * NW + warp; w < p.n_order; w += (uint64_t)gridDim.x * NW) {
+    const PkDesc d = load_desc(p.desc + w);
+    if (d.group == kPerCpuGroup)
+      decode_packet<BW, 4>(p, d, buf, s_off, ctab, lane);
+    else
+      decode_packet<BW, 2>(p, d, buf, s_off, ctab, lane);
+  }
+}
+
+template <int BW>
+cudaError_t launch_dw(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {
+  const uint32_t smem = nw * decode_warp_bytes(p.P) + rup((p.n_classes + 1u) * 4u, 16u);
+  cudaError_t e = cudaFuncSetAttribute(k_decode_warp<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_decode_warp<BW><<<grid, nw * 32, smem, s>>>(p, nw);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ per-CPU decode
+// The events of per-CPU buffers (16-byte headers: tsw, class, var_len, vpid,
+// vtid): the same boundary walk, stitch and checks with 4 header words, then
+// 32 events per batch: every ENTRY and EXIT becomes a PcRec (at a range
+// reserved once per packet), every ENTRY owns an interval slot (written
+// invalid; percpu.cu fills the paired ones).
+template <int BW>
+__global__ void __launch_bounds__(kDecodeWarps * 32) k_percpu_decode(PcParams p, uint32_t NW) {
+  extern __shared__ __align__(128) uint8_t sm[];
+  constexpr uint32_t SEGW = 32u * (BW - 1) + 1;
+  constexpr uint32_t HW = 4;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
   const uint32_t NC = p.n_classes;
   const uint32_t wbytes = decode_warp_bytes(p.P);
   uint8_t *buf = sm + warp * wbytes;
@@ -698,10 +880,13 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
     }
   }
   __syncthreads();
+  unsigned long long n_ev = 0, n_pk = 0, n_disc = 0, n_other = 0;
+  uint64_t tmin = ~0ull, tmax = 0;
   for (uint64_t w = (uint64_t)blockIdx.x * NW + warp; w < p.n_order; w += (uint64_t)gridDim.x * NW) {
     const PkDesc d = load_desc(p.desc + w);
+    if (d.group != kPerCpuGroup) continue;  // uniform over the warp
     const uint32_t W = d.content >> 2;
-    {  // stage header + content
+    {
       const uint4 *src = reinterpret_cast<const uint4 *>(p.packets + (uint64_t)d.pk * p.P);
       uint4 *dst = reinterpret_cast<uint4 *>(buf);
       const uint32_t n16 = align16(kPacketHeader + d.content) / 16u;
@@ -710,7 +895,6 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
     __syncwarp();
     if (lane < 8) C[W + lane] = 0;
     __syncwarp();
-    // boundaries (as in the analysis kernel)
     const uint32_t a = lane * SEGW;
     const uint32_t b = min(a + SEGW, W);
     Bits<BW> spec, bits;
@@ -718,13 +902,13 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
     uint32_t o = a;
     while (o < b) {
       spec.set(o - a);
-      o = step(C, o, ctab, NC);
+      o = step<HW>(C, o, ctab, NC);
     }
     const uint32_t spec_x = a < b ? o : a;
     const bool succ_live = a + SEGW < W;
     uint32_t ent = __shfl_up_sync(kFull, spec_x, 1);
     if (lane == 0) ent = 0;
-    uint32_t x = resolve_seg<BW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
+    uint32_t x = resolve_seg<BW, HW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
     for (int r = 0; r < 32; ++r) {
       const uint32_t next_ent = __shfl_down_sync(kFull, ent, 1);
       const uint32_t bal = __ballot_sync(kFull, lane < 31 && succ_live && x != next_ent);
@@ -733,7 +917,7 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
       const uint32_t xk = __shfl_sync(kFull, x, k);
       if (lane == (uint32_t)k + 1) {
         ent = xk;
-        x = resolve_seg<BW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
+        x = resolve_seg<BW, HW>(C, ent, a, b, spec, spec_x, bits, ctab, NC);
       }
     }
     const uint32_t cnt = bits.count();
@@ -744,8 +928,7 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
       if (lane >= (uint32_t)q) cinc += u;
     }
     const uint32_t c_tot = __shfl_sync(kFull, cinc, 31);
-    // offsets in order, with the format and truncation checks
-    uint32_t ekey = 0xFFFFFFFFu;
+    uint32_t ekey = 0xFFFFFFFFu, nrec = 0;
     {
       uint32_t e = cinc - cnt;
 #pragma unroll
@@ -759,11 +942,13 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
           const uint32_t c = w1 & 0xFFFFu;
           const bool ext = (w0 & kExtBit) != 0;
           const uint32_t r = ctab[c < NC ? c : NC];
-          const uint32_t sz = 2u + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
-          const uint32_t code = oo + 2 > W ? THAPI_E_TRUNCATED
+          const uint32_t sz = HW + (ext ? 2u : 0u) + row_fixedw(r) + (((w1 >> 16) + 3u) >> 2);
+          const uint32_t code = oo + HW > W ? THAPI_E_TRUNCATED
                                 : ((w0 >> 28) != 0 || c >= NC || (ext && (w0 & kDeltaMask) != 0)) ? THAPI_E_FORMAT
                                 : oo + sz > W ? THAPI_E_TRUNCATED : 0u;
           if (code) ekey = min(ekey, (e << 3) | code);
+          const uint32_t kd = row_kind(r);
+          nrec += (!code && (kd == kEntry || kd == kExit)) ? 1u : 0u;
           ++e;
         }
       }
@@ -777,8 +962,13 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
       __syncwarp();
       continue;
     }
-    // records, 32 events at a time
+    const uint32_t nrec_p = __reduce_add_sync(kFull, nrec);
+    unsigned long long rbase = 0;
+    if (lane == 0 && nrec_p) rbase = atomicAdd(p.count, (unsigned long long)nrec_p);
+    rbase = __shfl_sync(kFull, rbase, 0);
+    const uint32_t host = p.stream_host[d.stream];
     uint64_t tcur = d.tsb;
+    uint32_t rank_e = 0, rank_r = 0;
     for (uint32_t e0 = 0; e0 < c_tot; e0 += 32) {
       const uint32_t e = e0 + lane;
       const bool act = e < c_tot;
@@ -786,37 +976,74 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_decode_warp(DecodeParams 
       const uint32_t w0 = C[oo], w1 = C[oo + 1];
       const bool ext = act && (w0 & kExtBit) != 0;
       const uint32_t c = act ? (w1 & 0xFFFFu) : 0u;
-      const uint64_t xts = (uint64_t)C[min(oo + 2, W)] | ((uint64_t)C[min(oo + 3, W)] << 32);
-      const TsM tm = ts_op(TsM{1u, tcur}, scan_ts(TsM{ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane));
-      const uint64_t t = tm.v;
+      const uint64_t xts = (uint64_t)C[min(oo + HW, W)] | ((uint64_t)C[min(oo + HW + 1, W)] << 32);
+      const uint64_t t =
+          ts_op(TsM{1u, tcur}, scan_ts(TsM{ext ? 1u : 0u, !act ? 0ull : ext ? xts : (w0 & kDeltaMask)}, lane)).v;
       tcur = __shfl_sync(kFull, t, 31);
+      const uint64_t r = act ? p.classes[c] : 0ull;
+      const uint32_t kd = act ? cls_kind(r) : kSample;
+      const bool is_e = kd == kEntry, is_x = kd == kExit;
+      const uint32_t eb = __ballot_sync(kFull, is_e), rb = __ballot_sync(kFull, is_e || is_x);
       if (act) {
-        const uint64_t r = p.classes[c];
-        const uint32_t base = oo + 2u + (ext ? 2u : 0u);
-        const int32_t rw = cls_resw(r), cw = cls_cmdw(r);
-        thapi_event ev;
-        ev.ts = t;
-        ev.cmd = cw >= 0 ? ((uint64_t)C[min(base + cw, W)] | ((uint64_t)C[min(base + cw + 1, W)] << 32)) : 0ull;
-        ev.stream_id = d.stream;
-        ev.class_id = (uint16_t)c;
-        ev.var_len = (uint16_t)(w1 >> 16);
-        ev.result = rw >= 0 ? (int32_t)C[min(base + rw, W)] : 0;
-        ev.ext = ext ? 1 : 0;
-        ev.kind = (uint8_t)cls_kind(r);
-        ev.func_id = (uint16_t)cls_func(r);
-        p.out[d.evbase + e] = ev;
+        tmin = min(tmin, t);
+        tmax = max(tmax, t);
+        if (!is_e && !is_x) ++n_other;
       }
+      if (is_e || is_x) {
+        const uint32_t base = oo + HW + (ext ? 2u : 0u);
+        const int32_t rw = cls_resw(r);
+        PcRec rec;
+        rec.ts = t;
+        rec.thread = ((uint64_t)C[oo + 2] << 32) | C[oo + 3];
+        rec.host = host;
+        rec.gpos = (uint32_t)(d.evbase + e);
+        rec.slot = (uint32_t)(d.evbase + rank_e + __popc(eb & lt));
+        rec.pos = (uint32_t)w;
+        rec.func = (uint16_t)cls_func(r);
+        rec.kind = (uint8_t)kd;
+        rec.err = (is_x && rw >= 0 && C[min(base + rw, W)] != 0) ? 1 : 0;
+        rec.pad = 0;
+        const uint64_t at = rbase + rank_r + __popc(rb & lt);
+        if (at < p.cap) p.rec[at] = rec;
+        if (is_e && p.slots) {  // the entry's slot, invalid until paired
+          unsigned long long *q = reinterpret_cast<unsigned long long *>(p.slots + rec.slot);
+          q[0] = t;
+          q[1] = 0;
+          q[2] = 0xFFFFFFFFull;
+        }
+      }
+      rank_e += __popc(eb);
+      rank_r += __popc(rb);
+    }
+    if (lane == 0) {
+      p.sum_nslot[w] = rank_e;
+      n_ev += c_tot;
+      n_pk += 1;
+      n_disc += d.disc;
     }
     __syncwarp();
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    n_other += __shfl_down_sync(kFull, n_other, off);
+    tmin = min(tmin, __shfl_down_sync(kFull, tmin, off));
+    tmax = max(tmax, __shfl_down_sync(kFull, tmax, off));
+  }
+  if (lane == 0) {
+    if (n_ev) atomicAdd(&p.diag[dEvents], n_ev);
+    if (n_pk) atomicAdd(&p.diag[dPackets], n_pk);
+    if (n_disc) atomicAdd(&p.diag[dDiscarded], n_disc);
+    if (n_other) atomicAdd(&p.diag[dOther], n_other);
+    if (tmin != ~0ull) atomicMin(&p.tminmax[0], (unsigned long long)tmin);
+    if (tmax) atomicMax(&p.tminmax[1], (unsigned long long)tmax);
   }
 }
 
 template <int BW>
-cudaError_t launch_dw(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {
+cudaError_t launch_pc(const PcParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {
   const uint32_t smem = nw * decode_warp_bytes(p.P) + rup((p.n_classes + 1u) * 4u, 16u);
-  cudaError_t e = cudaFuncSetAttribute(k_decode_warp<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_percpu_decode<BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_decode_warp<BW><<<grid, nw * 32, smem, s>>>(p, nw);
+  k_percpu_decode<BW><<<grid, nw * 32, smem, s>>>(p, nw);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -862,6 +1089,16 @@ uint32_t decode_warps(uint32_t P, uint32_t n_classes, int smem_optin) {
   const uint32_t fixed = rup((n_classes + 1u) * 4u, 16u), per = decode_warp_bytes(P);
   if ((uint32_t)smem_optin < fixed + per) return 0;
   return std::min<uint32_t>(kDecodeWarps, ((uint32_t)smem_optin - fixed) / per);
+}
+
+cudaError_t launch_percpu_decode(const PcParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {
+  switch (warp_bw(p.P)) {
+    case 2: return launch_pc<2>(p, nw, grid, s);
+    case 3: return launch_pc<3>(p, nw, grid, s);
+    case 5: return launch_pc<5>(p, nw, grid, s);
+    case 9: return launch_pc<9>(p, nw, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_decode_warp(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s) {

@@ -240,6 +240,8 @@ int describe_device_trace(const uint8_t *dev, uint64_t nbytes, cudaStream_t s, T
   const Reader r{nullptr, dev, nbytes, s};
   const int rc = parse_layout(r, L);
   if (rc != THAPI_OK) return rc;
+  for (uint32_t i = 0; i < L.n_streams; ++i)  // per-CPU buffers need the allocating path
+    if (L.srow[4ull * i + 3] & kStreamPerCpu) return THAPI_E_UNSUPPORTED;
   td.P = L.P;
   td.n_streams = L.n_streams;
   td.n_classes = L.n_classes;
@@ -287,6 +289,11 @@ enum Misc {
   mJoin0 = mCmdCount0 + 3,    // join results: pairs, intervals, unjoined, ambiguous, host entries of pairs, overflow
   mDevRows = mJoin0 + 6,
   mPartMax,                   // records of the largest command-id partition
+  mPcCount,                   // per-CPU records
+  mPcWord,                    // per-CPU pairing: threads
+  mPcLevel,                   // per-CPU pairing: largest call level (follows mPcWord)
+  mPcRows,                    // per-CPU thread tally rows
+  mMerged,                    // tally rows after merging the thread rows
   mCount
 };
 
@@ -352,14 +359,15 @@ class Loader {
   uint64_t dec_cap_ = 0, *dec_n_ = nullptr;
   int decode(const HostLayout &L, uint64_t n, uint64_t total_events, const uint8_t *packets, const uint32_t *order,
              const uint32_t *pk_stream, const uint32_t *pk_nev, const uint32_t *pk_content, const uint32_t *pk_disc,
-             const uint64_t *pk_tsb, const uint32_t *d_group, const uint64_t *evbase, const uint64_t *d_cls);
+             const uint64_t *pk_tsb, const uint32_t *d_group, const uint64_t *evbase, const uint64_t *d_cls,
+             const uint32_t *d_gkeys);
 };
 
 // Decode-only tail of a load: descriptors, the decode kernel, the records to the host.
 int Loader::decode(const HostLayout &L, uint64_t n, uint64_t total_events, const uint8_t *packets,
                    const uint32_t *order, const uint32_t *pk_stream, const uint32_t *pk_nev, const uint32_t *pk_content,
                    const uint32_t *pk_disc, const uint64_t *pk_tsb, const uint32_t *d_group, const uint64_t *evbase,
-                   const uint64_t *d_cls) {
+                   const uint64_t *d_cls, const uint32_t *d_gkeys) {
   *dec_n_ = total_events;
   if (dec_cap_ == 0) return THAPI_OK;
   if (dec_cap_ < total_events) return THAPI_E_RANGE;
@@ -382,6 +390,7 @@ int Loader::decode(const HostLayout &L, uint64_t n, uint64_t total_events, const
   dp.classes = d_cls;
   dp.out = d_ev;
   dp.content_err = reinterpret_cast<unsigned long long *>(misc_ + mContentErr);
+  dp.group_keys = d_gkeys;
   const uint64_t grid = std::min<uint64_t>((n + nw - 1) / nw, (uint64_t)c_->num_sms * 4);
   CK(launch_decode_warp(dp, nw, (uint32_t)std::max<uint64_t>(grid, 1), s_));
   if ((rc = sync_misc()) != THAPI_OK) return rc;
@@ -418,13 +427,22 @@ int Loader::run() {
   const uint32_t P = L.P, S = L.n_streams, F = L.n_funcs;
 
   // (host, pid, tid) groups numbered in order
-  std::vector<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>> keyed(S);
-  for (uint32_t i = 0; i < S; ++i)
-    keyed[i] = std::make_tuple(L.srow[4ull * i], L.srow[4ull * i + 1], L.srow[4ull * i + 2], i);
-  std::sort(keyed.begin(), keyed.end());
-  std::vector<uint32_t> stream_group(S ? S : 1, 0), group_keys;
-  uint32_t G = 0;
+  // per-thread streams numbered in (host, pid, tid) order; per-CPU buffers
+  // (stream flags bit 1) form no group: their events name their threads
+  std::vector<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>> keyed;
+  bool has_pc = false;
+  std::vector<uint32_t> stream_host(S ? S : 1, 0);
   for (uint32_t i = 0; i < S; ++i) {
+    stream_host[i] = L.srow[4ull * i];
+    if (L.srow[4ull * i + 3] & kStreamPerCpu)
+      has_pc = true;
+    else
+      keyed.push_back(std::make_tuple(L.srow[4ull * i], L.srow[4ull * i + 1], L.srow[4ull * i + 2], i));
+  }
+  std::sort(keyed.begin(), keyed.end());
+  std::vector<uint32_t> stream_group(S ? S : 1, kPerCpuGroup), group_keys;
+  uint32_t G = 0;
+  for (size_t i = 0; i < keyed.size(); ++i) {
     if (i == 0 || std::get<0>(keyed[i]) != std::get<0>(keyed[i - 1]) ||
         std::get<1>(keyed[i]) != std::get<1>(keyed[i - 1]) || std::get<2>(keyed[i]) != std::get<2>(keyed[i - 1])) {
       group_keys.push_back(std::get<0>(keyed[i]));
@@ -518,7 +536,7 @@ int Loader::run() {
   const uint64_t total_events = n ? misc_h_[mEvents] : 0;
   if (dec_n_)
     return decode(L, n, total_events, packets, order, pk_stream, pk_nev, pk_content, pk_disc, pk_tsb, d_group, evbase,
-                  d_cls);
+                  d_cls, d_gkeys);
 
   // ---- decode + pair + tally per packet
   Cell *tally = alloc<Cell>(cells);
@@ -537,6 +555,9 @@ int Loader::run() {
   // warp-per-packet kernel for packets up to 32 KB, the CTA kernel otherwise
   WarpPlan wplan;
   const bool warp_path = plan_analyze_warp(P, L.n_classes, c_->smem_per_block, c_->smem_per_sm, &wplan);
+  // per-CPU buffers: packets up to 32 KB (the warp kernels), 32-bit event indexes
+  if (has_pc && (!warp_path || total_events >= 0xFFFFFFFFull || !decode_warps(P, L.n_classes, c_->smem_per_block)))
+    return THAPI_E_UNSUPPORTED;
   uint64_t grid = 1, per = 1;
   if (n) {
     if (warp_path) {
@@ -704,6 +725,50 @@ int Loader::run() {
     clk_.rec(PhaseClock::kFr1, s_);
   }
 
+  // ---- per-CPU buffers: their events' records, then their threads paired
+  PcPairOut pco;
+  if (has_pc) {
+    uint32_t *d_shost = alloc<uint32_t>(S);
+    PcRec *pcrec = alloc<PcRec>(total_events);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    CK(cudaMemcpyAsync(d_shost, stream_host.data(), 4ull * S, cudaMemcpyHostToDevice, s_));
+    CK(cudaMemsetAsync(misc_ + mPcCount, 0, sizeof(uint64_t), s_));
+    PcParams pp{};
+    pp.packets = packets;
+    pp.P = P;
+    pp.n_classes = L.n_classes;
+    pp.n_order = n;
+    pp.desc = desc;
+    pp.classes = d_cls;
+    pp.stream_host = d_shost;
+    pp.rec = pcrec;
+    pp.cap = total_events;
+    pp.count = reinterpret_cast<unsigned long long *>(misc_ + mPcCount);
+    pp.slots = slots;
+    pp.sum_nslot = sum_nslot;
+    pp.content_err = reinterpret_cast<unsigned long long *>(misc_ + mContentErr);
+    pp.diag = reinterpret_cast<unsigned long long *>(misc_ + mDiag0);
+    pp.tminmax = reinterpret_cast<unsigned long long *>(misc_ + mTmin);
+    const uint32_t nw = decode_warps(P, L.n_classes, c_->smem_per_block);
+    const uint64_t g = std::min<uint64_t>((n + nw - 1) / nw, (uint64_t)c_->num_sms * 4);
+    CK(launch_percpu_decode(pp, nw, (uint32_t)std::max<uint64_t>(g, 1), s_));
+    if ((rc = sync_misc()) != THAPI_OK) return rc;
+    if (misc_h_[mContentErr] != ~0ull) {
+      const unsigned long long k = misc_h_[mContentErr];
+      c_->err_level = 2;
+      c_->err_packet = k >> 20;
+      c_->err_event = (k >> 3) & 0x1FFFFu;
+      return (int)(k & 7u);
+    }
+    const uint64_t m = misc_h_[mPcCount];
+    const uint64_t t0 = misc_h_[mTmin], t1 = misc_h_[mTmax];
+    int tb = 1;
+    while (tb < 64 && t1 > t0 && ((t1 - t0) >> tb)) ++tb;
+    rc = percpu_pair(pcrec, m, m ? t0 : 0, tb, F, slots, sum_nvalid, reinterpret_cast<unsigned long long *>(misc_ + mDiag0),
+                     misc_ + mPcWord, sc_, s_, &pco);
+    if (rc != THAPI_OK) return rc;
+  }
+
   // ---- device-activity pairing: command table, then device intervals and tally
   Cell *dcells = nullptr;
   if (dev_on) {
@@ -779,14 +844,36 @@ int Loader::run() {
   if (sc_.failed) return THAPI_E_NOMEM;
   launch_tally_compact(tally, cells, d_gkeys, F, flags, rows_tmp, misc_ + mRows, sc_, s_);
   if (dev_on) launch_tally_compact(dcells, cells, d_gkeys, F, flags, drows_tmp, misc_ + mDevRows, sc_, s_);
+  const uint64_t pc_cells = pco.threads * F;
+  thapi_tally_row *pcrows = nullptr;
+  if (pc_cells) {  // the threads of the per-CPU buffers, compacted like the per-thread rows
+    uint64_t *pcflags = alloc<uint64_t>(pc_cells);
+    pcrows = alloc<thapi_tally_row>(pc_cells);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    launch_tally_compact(pco.cells, pc_cells, pco.keys, F, pcflags, pcrows, misc_ + mPcRows, sc_, s_);
+  }
   launch_widen_u32(sum_nvalid, obase, n, s_);
   scan_exclusive_u64(obase, n, misc_ + mIv, sc_, s_);
   if (sc_.failed) return THAPI_E_NOMEM;
   clk_.rec(PhaseClock::kTa1, s_);
   CK(cudaGetLastError());
   if ((rc = sync_misc()) != THAPI_OK) return rc;
-  const uint64_t n_rows = cells ? misc_h_[mRows] : 0;
+  uint64_t n_rows = cells ? misc_h_[mRows] : 0;
   const uint64_t n_dev_rows = dev_on && cells ? misc_h_[mDevRows] : 0;
+  if (pc_cells && misc_h_[mPcRows]) {  // merge them into the per-thread rows (equal keys combine)
+    const uint64_t n_pc = misc_h_[mPcRows];
+    thapi_tally_row *both = alloc<thapi_tally_row>(n_rows + n_pc);
+    thapi_tally_row *merged = alloc<thapi_tally_row>(n_rows + n_pc);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    if (n_rows)
+      CK(cudaMemcpyAsync(both, rows_tmp, n_rows * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice, s_));
+    CK(cudaMemcpyAsync(both + n_rows, pcrows, n_pc * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice, s_));
+    if (!tally_merge_device(both, n_rows + n_pc, merged, misc_ + mMerged, sc_, s_))
+      return sc_.failed ? THAPI_E_NOMEM : THAPI_E_CUDA;
+    if ((rc = sync_misc()) != THAPI_OK) return rc;
+    n_rows = misc_h_[mMerged];
+    rows_tmp = merged;
+  }
   const uint64_t n_iv = n ? misc_h_[mIv] : 0;
   if (n_iv >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
   if (dev_on && misc_h_[mJoin0 + 5]) return THAPI_E_CUDA;  // a join table without room: not reached

@@ -115,6 +115,11 @@ struct IndexParams {
   unsigned long long *hdr_err;  // min packet index with a header error
 };
 
+// Stream group of a per-CPU buffer (stream flags bit 1): its events belong to
+// the threads named in each event, paired by percpu.cu.
+constexpr uint32_t kPerCpuGroup = 0xFFFFFFFFu;
+constexpr uint32_t kStreamPerCpu = 2u;
+
 // What the analysis needs of one packet, gathered per order position.
 struct __align__(16) PkDesc {
   uint32_t pk, content, nev, stream;  // file index, content bytes, events, stream id
@@ -254,8 +259,54 @@ struct DecodeParams {
   const uint64_t *classes;       // packed class rows
   thapi_event *out;              // at desc.evbase + event index
   unsigned long long *content_err;
+  const uint32_t *group_keys;    // host, pid, tid per group (per-thread streams' pid / tid)
 };
 uint32_t decode_warps(uint32_t P, uint32_t n_classes, int smem_optin);  // warps per CTA, 0 = unsupported
+
+// Per-CPU buffers (percpu.cu): one record per ENTRY / EXIT of a per-CPU
+// buffer, written by k_percpu_decode (analyze_warp.cu).
+struct __align__(8) PcRec {
+  uint64_t ts;
+  uint64_t thread;     // vpid << 32 | vtid
+  uint32_t host;       // the buffer's host
+  uint32_t gpos;       // global event index (stream order): ties of equal timestamps
+  uint32_t slot;       // ENTRY: its interval slot (global index)
+  uint32_t pos;        // order position of its packet
+  uint16_t func;
+  uint8_t kind, err;   // kEntry / kExit; EXIT result != 0
+  uint32_t pad;
+};
+struct PcParams {
+  const uint8_t *packets;
+  uint32_t P, n_classes;
+  uint64_t n_order;
+  const PkDesc *desc;
+  const uint64_t *classes;
+  const uint32_t *stream_host;   // host id per stream
+  PcRec *rec;
+  uint64_t cap;
+  unsigned long long *count;     // records written (may pass cap: then nothing past it is written)
+  thapi_interval *slots;
+  uint32_t *sum_nslot;
+  unsigned long long *content_err;
+  unsigned long long *diag;
+  unsigned long long *tminmax;
+};
+cudaError_t launch_percpu_decode(const PcParams &p, uint32_t nw, uint32_t grid, cudaStream_t s);
+// Pairs the threads of the per-CPU records: sorts them by (host, vpid, vtid,
+// ts, position), scans the depth monoid per thread, matches each entry with
+// its exit by (thread, level); tallies into per-thread cells, writes the
+// entries' interval slots and raises their packets' interval counts.
+// *n_threads (host) = threads; cells / keys are allocated here (sc).
+struct PcPairOut {
+  Cell *cells = nullptr;           // [threads * n_funcs]
+  uint32_t *keys = nullptr;        // [threads * 3] host, vpid, vtid
+  uint64_t threads = 0;
+};
+// word: two device words (threads; largest level).
+int percpu_pair(PcRec *rec, uint64_t m, uint64_t t_min, int ts_bits, uint32_t n_funcs, thapi_interval *slots,
+                uint32_t *sum_nvalid, unsigned long long *diag, uint64_t *word, Scratch &sc, cudaStream_t s,
+                PcPairOut *out);
 cudaError_t launch_decode_warp(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s);
 // Splits the stream-ordered packets into `grid` contiguous runs of about equal
 // cost (events + a per-packet constant): run_start[0..grid].

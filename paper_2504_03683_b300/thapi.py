@@ -24,7 +24,8 @@ ROW_DTYPE = np.dtype([("host_id", "<u4"), ("pid", "<u4"), ("tid", "<u4"), ("func
 INTERVAL_DTYPE = np.dtype([("start_ns", "<u8"), ("end_ns", "<u8"), ("stream_id", "<u4"),
                            ("func_id", "<u2"), ("level", "u1"), ("flags", "u1")])
 EVENT_DTYPE = np.dtype([("ts", "<u8"), ("cmd", "<u8"), ("stream_id", "<u4"), ("class_id", "<u2"),
-                        ("var_len", "<u2"), ("result", "<i4"), ("ext", "u1"), ("kind", "u1"), ("func_id", "<u2")])
+                        ("var_len", "<u2"), ("result", "<i4"), ("ext", "u1"), ("kind", "u1"), ("func_id", "<u2"),
+                        ("vpid", "<u4"), ("vtid", "<u4")])
 DIAG_FIELDS = ("events", "pairs", "unmatched_entries", "unmatched_exits", "mismatched_pairs",
                "other_events", "discarded", "packets")
 DEVICE_DIAG_FIELDS = ("dev_events", "dev_pairs", "dev_intervals", "dev_unpaired", "dev_unjoined", "dev_ambiguous",
