@@ -87,6 +87,10 @@ def _load():
     lib.orc_n_dev_rows.restype = u64
     lib.orc_dev_rows.argtypes = [vp]
     lib.orc_dev_rows.restype = vp
+    lib.orc_n_self_rows.argtypes = [vp]
+    lib.orc_n_self_rows.restype = u64
+    lib.orc_self_rows.argtypes = [vp]
+    lib.orc_self_rows.restype = vp
     lib.orc_get_dev_diag.argtypes = [vp, ctypes.POINTER(_DevDiag)]
     lib.orc_get_dev_diag.restype = None
     lib.orc_error_location.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(u64), ctypes.POINTER(u64)]
@@ -108,7 +112,7 @@ def _ptr(buf):
 
 
 class Result:
-    def __init__(self, code, loc, rows, intervals, diag, dev_rows, dev_diag):
+    def __init__(self, code, loc, rows, intervals, diag, dev_rows, dev_diag, self_rows):
         self.code = code
         self.loc = loc            # (level, packet, event): 0 file, 1 packet header, 2 packet content
         self.rows = rows          # ROW_DTYPE, ordered by (host_id, pid, tid, func_id)
@@ -116,6 +120,7 @@ class Result:
         self.diag = diag          # dict of DIAG_FIELDS
         self.dev_rows = dev_rows  # ROW_DTYPE: device intervals per (device stream's host, pid, tid; host function)
         self.dev_diag = dev_diag  # dict of DEV_DIAG_FIELDS
+        self.self_rows = self_rows  # ROW_DTYPE, the rows' keys and counts; total / min / max of self time
 
 
 def run(trace, streams=None, t0: int = 0, t1: int = 2**64 - 1, want_intervals: bool = True) -> Result:
@@ -154,13 +159,17 @@ def run(trace, streams=None, t0: int = 0, t1: int = 2**64 - 1, want_intervals: b
         dev_rows = np.zeros(nd, dtype=ROW_DTYPE)
         if nd:
             ctypes.memmove(dev_rows.ctypes.data, lib.orc_dev_rows(h), nd * ROW_DTYPE.itemsize)
+        ns = lib.orc_n_self_rows(h)
+        self_rows = np.zeros(ns, dtype=ROW_DTYPE)
+        if ns:
+            ctypes.memmove(self_rows.ctypes.data, lib.orc_self_rows(h), ns * ROW_DTYPE.itemsize)
         dd = _DevDiag()
         lib.orc_get_dev_diag(h, ctypes.byref(dd))
         dev_diag = {f: int(getattr(dd, f)) for f in DEV_DIAG_FIELDS}
     finally:
         lib.orc_free(h)
     del keep, sub
-    return Result(code, (lvl.value, pk.value, ev.value), rows, ivs, diag, dev_rows, dev_diag)
+    return Result(code, (lvl.value, pk.value, ev.value), rows, ivs, diag, dev_rows, dev_diag, self_rows)
 
 
 def decode(trace) -> np.ndarray:

@@ -69,6 +69,19 @@
 //    per-thread streams of the same key; an interval belongs to its entry's
 //    stream and takes the entry's position in the timeline order;
 //  * device activity is paired over per-thread and device streams only.
+//
+// Self (exclusive) time, for the layering analysis of Sec. 4.3 (how much of
+// hipDeviceSynchronize is its own time and how much the nested
+// zeEventHostSynchronize calls).  Readings:
+//  * a call's self time = its duration minus the durations of the calls that
+//    are paired directly inside it (the entries pushed right above its entry
+//    on the same stack and closed by an exit of the same function), in u64
+//    arithmetic; calls deeper down count only toward their own parent;
+//  * a mismatched or unmatched call has no duration: it takes nothing off
+//    its parent's self time, and the paired calls directly inside it take
+//    nothing off any call's self time;
+//  * self rows have the tally's keys, counts and error counts; total / min /
+//    max are over self times.
 
 #include <algorithm>
 #include <cstdint>
@@ -318,6 +331,7 @@ struct Result {
   std::vector<orc_event> events;
   std::vector<orc_row> dev_rows;
   orc_dev_diag dev{};
+  std::vector<orc_row> self_rows;
 };
 
 // Everything one command id gathered over the trace.
@@ -337,6 +351,7 @@ struct Open {
   uint64_t ts;
   uint64_t seq;     // entry position in its stream
   uint32_t stream;  // entry's stream
+  uint64_t child;   // sum of the durations of the calls paired directly inside
 };
 
 // One ENTRY / EXIT event of a per-CPU buffer, kept until its thread is paired.
@@ -411,7 +426,7 @@ std::vector<std::vector<uint64_t>> packets_by_stream(const Trace &t, const std::
 
 void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, Result &r, bool collect_events) {
   auto by = packets_by_stream(t, keep);
-  std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, orc_row> tally;
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, orc_row> tally, self_tally;
   std::map<uint64_t, Command> commands;
   std::map<std::tuple<uint32_t, uint32_t, uint32_t>, std::vector<ThreadEvent>> threads;  // per-CPU buffers
   std::vector<Keyed> ivs;
@@ -420,7 +435,7 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
   auto pair = [&](std::vector<Open> &stack, uint32_t host, uint32_t pid, uint32_t tid, uint8_t kind, uint16_t func,
                   uint64_t ts, int32_t result, uint32_t stream, uint64_t seq) {
     if (kind == KIND_ENTRY) {
-      stack.push_back({func, ts, seq, stream});
+      stack.push_back({func, ts, seq, stream, 0});
       return;
     }
     if (stack.empty()) {
@@ -448,6 +463,18 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
     row.min_ns = std::min(row.min_ns, dur);
     row.max_ns = std::max(row.max_ns, dur);
     row.err_count += err ? 1 : 0;
+    // self time: this call's duration less its direct children's; then its own
+    // duration goes to its parent, the entry now on top of the stack
+    const uint64_t self = dur - en.child;
+    auto st = self_tally.find(key);
+    if (st == self_tally.end()) st = self_tally.emplace(key, orc_row{host, pid, tid, func, 0, 0, UINT64_MAX, 0, 0}).first;
+    orc_row &srow = st->second;
+    srow.count += 1;
+    srow.total_ns += self;
+    srow.min_ns = std::min(srow.min_ns, self);
+    srow.max_ns = std::max(srow.max_ns, self);
+    srow.err_count += err ? 1 : 0;
+    if (!stack.empty()) stack.back().child += dur;
     if (o.want_intervals && en.ts < o.t1 && ts >= o.t0) {
       orc_interval iv{};
       iv.start_ns = en.ts;
@@ -544,6 +571,7 @@ void analyse(const Trace &t, const orc_opts &o, const std::vector<char> *keep, R
     d.unmatched_entries += stack.size();
   }
   for (auto &kv : tally) r.rows.push_back(kv.second);
+  for (auto &kv : self_tally) r.self_rows.push_back(kv.second);
 
   // device activity: one pass over the commands, in command-id order
   std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, orc_row> dev_tally;
@@ -652,6 +680,8 @@ const orc_interval *orc_intervals(const orc_result *r) {
 void orc_get_diag(const orc_result *r, orc_diag *d) { *d = reinterpret_cast<const Result *>(r)->diag; }
 uint64_t orc_n_dev_rows(const orc_result *r) { return reinterpret_cast<const Result *>(r)->dev_rows.size(); }
 const orc_row *orc_dev_rows(const orc_result *r) { return reinterpret_cast<const Result *>(r)->dev_rows.data(); }
+uint64_t orc_n_self_rows(const orc_result *r) { return reinterpret_cast<const Result *>(r)->self_rows.size(); }
+const orc_row *orc_self_rows(const orc_result *r) { return reinterpret_cast<const Result *>(r)->self_rows.data(); }
 void orc_get_dev_diag(const orc_result *r, orc_dev_diag *d) { *d = reinterpret_cast<const Result *>(r)->dev; }
 void orc_error_location(const orc_result *r, int *level, uint64_t *packet, uint64_t *event) {
   const Result *x = reinterpret_cast<const Result *>(r);

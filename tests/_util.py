@@ -105,6 +105,54 @@ def brute_force_stream(events):
     return pairs, mismatched, un_entry, un_exit
 
 
+def brute_force_self(events):
+    """Self time of each pair of brute_force_stream, by brute force.
+
+    Returns (i, j, level, self) per pair: the pair's duration less the
+    durations of the pairs whose direct parent it is.  The direct parent of an
+    entry at depth L > 0 is the last earlier entry at depth L - 1 (the one
+    open at that depth when it is pushed); it takes the child's duration only
+    when it is itself a pair.  Depths by the clamped running sum, as in
+    brute_force_stream; O(n^2) on purpose.
+    """
+    pairs, _mm, _ue, _ux = brute_force_stream(events)
+    n = len(events)
+    s = [0]
+    for (k, _f, _t, _r) in events:
+        s.append(s[-1] + (1 if k == ENTRY else (-1 if k == EXIT else 0)))
+    pre = [s[j] - min(s[: j + 1]) for j in range(n)]
+    paired = {i for (i, _j, _l) in pairs}
+    child = defaultdict(int)
+    for (i, j, lvl) in pairs:
+        if lvl == 0:
+            continue
+        k = max(k for k in range(i) if events[k][0] == ENTRY and pre[k] == lvl - 1)
+        if k in paired:
+            child[k] += (events[j][2] - events[i][2]) & U64
+    return [(i, j, lvl, ((events[j][2] - events[i][2]) - child[i]) & U64) for (i, j, lvl) in pairs]
+
+
+def self_from_truth(trace, calls: np.ndarray):
+    """Self-time rows implied by the ground-truth calls of a drop-free trace: per
+    stream, in entry order, a call's parent is the last earlier call one level up."""
+    st = stream_table(trace)
+    host = calls[(calls["flags"] & 8) == 0]
+    out = []
+    for sid in np.unique(host["stream_id"]):
+        cs = host[host["stream_id"] == sid]
+        dur = [(int(c["end_ns"]) - int(c["start_ns"])) & U64 for c in cs]
+        child = [0] * len(cs)
+        last_at = {}
+        for k, c in enumerate(cs):
+            lvl = int(c["level"])
+            if lvl > 0:
+                child[last_at[lvl - 1]] += dur[k]
+            last_at[lvl] = k
+        for k, c in enumerate(cs):
+            out.append((int(sid), int(c["func_id"]), (dur[k] - child[k]) & U64, int(c["flags"]) & 1))
+    return tally_from_pairs(out, st)
+
+
 def tally_from_pairs(pairs_by_stream, st):
     """Group-by over (host, pid, tid, func) of (stream, func, dur, err) tuples."""
     acc = defaultdict(lambda: [0, 0, U64, 0, 0])

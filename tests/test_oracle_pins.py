@@ -569,3 +569,122 @@ def test_per_cpu_header_truncated():
     tb.raw_packet(c0, 0, [ok, ok[:12]], n_events=2)  # the second event's 16-byte header is cut
     r = oracle.run(tb.build())
     assert r.code == oracle.E_TRUNCATED and r.loc == (2, 0, 1)
+
+
+# ------------------------------------------------------------ self time
+def test_self_time_layered_worked_case():
+    """The layering of Sec. 4.3 by hand: hipDeviceSynchronize [0, 100] waits in
+    two zeEventHostSynchronize calls [10, 40] and [50, 95]; the first of them
+    makes a leaf call [12, 20].  A call's self time loses only its direct
+    children: hip 100 - 30 - 45 = 25, ze 30 - 8 = 22 and 45, the leaf 8."""
+    tb = TraceBuilder(packet_bytes=256)
+    h = tb.add_host("h")
+    hip, eh, xh = tb.add_call_func("hipDeviceSynchronize", layer=0)
+    ze, ez, xz = tb.add_call_func("zeEventHostSynchronize", layer=1)
+    lf, el, xl = tb.add_call_func("leaf", layer=1)
+    s = tb.add_stream(h, 1, 1)
+    evs = [Ev(eh, 1000), Ev(ez, 1010), Ev(el, 1012), Ev(xl, 1020, result=0), Ev(xz, 1040, result=0),
+           Ev(ez, 1050), Ev(xz, 1095, result=0), Ev(xh, 1100, result=2)]
+    tb.place(tb.stream_events(s, evs, ts_begin=1000))
+    r = oracle.run(tb.build())
+    assert r.code == oracle.OK
+    got = {int(x["func_id"]): tuple(int(x[k]) for k in ("count", "total_ns", "min_ns", "max_ns", "err_count"))
+           for x in r.self_rows}
+    assert got == {hip: (1, 25, 25, 25, 1), ze: (2, 22 + 45, 22, 45, 0), lf: (1, 8, 8, 8, 0)}
+    incl = {int(x["func_id"]): int(x["total_ns"]) for x in r.rows}
+    assert incl == {hip: 100, ze: 75, lf: 8}
+
+
+def test_self_time_invalid_parents_take_nothing():
+    """A mismatched call (entry f, exit g) and a call never closed have no
+    duration: the paired calls directly inside them take nothing off any
+    call, and the mismatched call takes nothing off its own parent."""
+    tb = TraceBuilder(packet_bytes=256)
+    h = tb.add_host("h")
+    f, ef, xf = tb.add_call_func("f")
+    g, eg, xg = tb.add_call_func("g")
+    c, ec, xc = tb.add_call_func("c")
+    s = tb.add_stream(h, 1, 1)
+    evs = [Ev(ef, 100),                                   # f [100, 200]
+           Ev(eg, 110), Ev(ec, 120), Ev(xc, 130, result=0), Ev(xf, 140, result=0),  # g..f mismatched, c inside
+           Ev(ec, 150), Ev(xc, 155, result=0),            # c directly in f: 5
+           Ev(xf, 200, result=0),
+           Ev(eg, 300), Ev(ec, 310), Ev(xc, 330, result=0)]  # g never closed, c inside it
+    tb.place(tb.stream_events(s, evs, ts_begin=100))
+    r = oracle.run(tb.build())
+    assert r.diag["mismatched_pairs"] == 1 and r.diag["unmatched_entries"] == 1
+    got = {int(x["func_id"]): (int(x["count"]), int(x["total_ns"])) for x in r.self_rows}
+    assert got == {f: (1, 100 - 5), c: (3, 10 + 5 + 20)}
+
+
+@pytest.mark.parametrize("over", [
+    dict(total_calls=20_000, seed=11),
+    dict(total_calls=20_000, seed=12, n_hosts=2, pids_per_host=2, tids_per_pid=2, packet_bytes=512, p_ext=0.02),
+])
+def test_self_time_from_truth(over):
+    b, calls, _e = tg.generate(tg.preset("large", p_drop=0.0, **over), truth=True)
+    r = oracle.run(b)
+    from tests._util import self_from_truth
+    exp = self_from_truth(b, calls)
+    assert rows_equal(r.self_rows, exp)
+    # keys, counts and error counts are the tally's
+    for k in ("host_id", "pid", "tid", "func_id", "count", "err_count"):
+        assert np.array_equal(r.self_rows[k], r.rows[k]), k
+    # every call's time is counted once: as self time of itself or of its ancestors
+    lvl0 = r.intervals[r.intervals["level"] == 0]
+    total0 = int((lvl0["end_ns"] - lvl0["start_ns"]).astype(np.uint64).sum(dtype=np.uint64))
+    assert int(r.self_rows["total_ns"].sum(dtype=np.uint64)) == total0
+
+
+def test_self_time_flat_calls_equal_inclusive():
+    b, _c, _e = tg.generate(tg.preset("tiny", seed=5))
+    r = oracle.run(b)
+    if int(r.intervals["level"].max()) == 0:
+        assert rows_equal(r.self_rows, r.rows)
+    assert np.all(r.self_rows["total_ns"] <= r.rows["total_ns"])
+
+
+def _brute_self_rows(trace, events_by_stream):
+    from tests._util import brute_force_self
+    st = stream_table(trace)
+    flat = []
+    for sid, evs in enumerate(events_by_stream):
+        for (i, j, _lvl, self_ns) in brute_force_self(evs):
+            flat.append((sid, evs[i][1], self_ns, 1 if evs[j][3] != 0 else 0))
+    return tally_from_pairs(flat, st)
+
+
+def test_self_time_brute_force_short_sequences():
+    for length in range(1, 7):
+        for seq in itertools.product(SYMBOLS, repeat=length):
+            trace, evs = _trace_from_sequence([list(seq), list(reversed(seq))])
+            r = oracle.run(trace)
+            assert rows_equal(r.self_rows, _brute_self_rows(trace, evs)), seq
+
+
+def test_self_time_brute_force_random():
+    rng = random.Random(77)
+    for _ in range(300):
+        length = rng.choice([12, 25, 60])
+        seq, stack = [], []
+        for _j in range(length):
+            if stack and rng.random() < 0.45:
+                f = stack.pop() if rng.random() > 0.1 else rng.randrange(2)
+                seq.append((EXIT, f))
+            elif rng.random() < 0.05:
+                seq.append((EXIT, rng.randrange(2)))
+            else:
+                f = rng.randrange(2)
+                stack.append(f)
+                seq.append((ENTRY, f))
+        trace, evs = _trace_from_sequence([seq])
+        r = oracle.run(trace)
+        assert rows_equal(r.self_rows, _brute_self_rows(trace, evs))
+
+
+def test_self_time_per_cpu_equals_per_thread():
+    from tests._percpu import to_per_cpu
+    b, _c, _e = tg.generate(tg.preset("large", total_calls=15_000, n_hosts=1, pids_per_host=2, tids_per_pid=3,
+                                      seed=21, p_drop=0.01))
+    pc = to_per_cpu(b, n_cpus=3, seed=21)
+    assert rows_equal(oracle.run(b).self_rows, oracle.run(pc).self_rows)
