@@ -156,7 +156,8 @@ typedef struct thapi_device_diag {
 /* Facts about a loaded trace.  intervals counts host and device intervals. */
 typedef struct thapi_trace_info {
   uint64_t nbytes, n_packets, events, intervals, tally_rows, device_bytes;
-  uint32_t n_streams, n_classes, n_funcs, n_hosts, packet_bytes, reserved;
+  uint32_t n_streams, n_classes, n_funcs, n_hosts, packet_bytes;
+  uint32_t self_time;         /* 1: loaded with self time on (thapi_self_tally) */
   uint64_t t_min, t_max;      /* smallest / largest event timestamp */
   uint64_t device_rows, device_intervals;  /* device tally rows; device intervals */
 } thapi_trace_info;
@@ -287,11 +288,32 @@ typedef struct thapi_load_timing {
   uint64_t analyze_launches;     /* analysis kernel launches of the load */
   uint64_t launches;             /* all kernel launches of the load */
   float join_ms;                 /* device-activity pairing (includes one host wait) */
-  float reserved_ms;
+  float self_ms;                 /* self time (when on; includes host waits) */
 } thapi_load_timing;
 
 /* Enables (1) or disables (0) per-phase timing of subsequent loads. */
 int thapi_ctx_set_timing(thapi_ctx *ctx, int enable);
+
+/* Enables (1) or disables (0) self time for subsequent loads (off by default).
+ *
+ * Self (exclusive) time separates what a call spends itself from what the
+ * calls it makes take: the layering analysis of the paper (Sec. 4.3), where
+ * hipDeviceSynchronize is built on the zeEventHostSynchronize spin.  A call's
+ * self time is its duration less the durations of the calls paired directly
+ * inside it (the entries pushed right above its entry on its stack and closed
+ * with the same function), in u64 arithmetic.  A mismatched or unmatched call
+ * has no duration: it takes nothing off its parent, and the calls directly
+ * inside it take nothing off any call.  Per-CPU buffers follow their threads'
+ * stacks.  Device intervals take no part.  A load with self time on keeps, per
+ * event, a 24-byte side record during the load and per interval about 72 bytes
+ * more; traces of 2^31 events or more return E_UNSUPPORTED. */
+int thapi_ctx_set_self_time(thapi_ctx *ctx, int enable);
+
+/* Copies the self-time rows of a trace loaded with self time on to HOST
+ * memory `rows`: the tally's keys, order, counts and error counts, with
+ * total_ns / min_ns / max_ns over the calls' self times.  cap semantics as
+ * thapi_tally; E_INVALID if the trace was loaded with self time off. */
+int thapi_self_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows);
 
 /* Timing of a loaded trace (zeros if timing was off when it was loaded). */
 int thapi_trace_timing(thapi_ctx *ctx, thapi_trace_id id, thapi_load_timing *out);

@@ -597,6 +597,11 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
               }
             } else if (s_fn[j] == s_fn[i]) {
               ++valid;
+              if (p.side) {  // self time: the exit's position and the entry's exact packet-relative depth
+                SelfSlot &ss = p.side[d.evbase + rank];
+                ss.exit_pos = d.evbase + (uint32_t)j;
+                ss.level = (uint32_t)(r - mrun);
+              }
               const uint64_t dur = s_ts[j] - s_ts[i];
               const uint32_t err = (s_dk[j] >> 19) & 1u;
               const uint32_t f = s_fn[i];
@@ -622,14 +627,15 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
               ++n_mismatch;
             }
             if (p.slots) p.slots[d.evbase + rank] = iv;
+            if (p.side) p.side[d.evbase + rank].entry_pos = d.evbase + i;
             ++rank;
           } else if (kd == kExit) {
             if (post < mrun && fbase != ~0ull) {
               Frontier fr;
               fr.ts = s_ts[i];
-              fr.aux = (dk >> 19) & 1u;
+              fr.aux = i;
               fr.func = s_fn[i];
-              fr.flags = 0;
+              fr.flags = (uint16_t)((dk >> 19) & 1u);
               p.frontier[fbase + (uint32_t)(-post - 1)] = fr;
             }
           } else {

@@ -541,6 +541,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           atomicMin(&cell.mn, (unsigned long long)dur);
           atomicMax(&cell.mx, (unsigned long long)dur);
           if (err) atomicAdd(&cell.err, 1ull);
+          if (p.side) {  // self time: the exit's position and the entry's exact packet-relative depth
+            SelfSlot &ss = p.side[d.evbase + ((em >> 16) & 0xFFFFu)];
+            ss.exit_pos = d.evbase + e;
+            ss.level = (uint32_t)(post - before.m);
+          }
         } else {
           ++mism;  // mismatched pair: no interval
         }
@@ -548,13 +553,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           put_interval(pslots + ((em >> 16) & 0xFFFFu), ets, t, (uint32_t)((em >> 40) & 0xFFFFu), efn,
                        (uint32_t)((em >> 32) & 0xFFu), flags);
       }
+      if (p.side && is_entry) p.side[d.evbase + rank].entry_pos = d.evbase + e;
       const uint32_t pbal = __ballot_sync(kFull, pend);
       if (pend && fbase != ~0ull) {
         Frontier fr;
         fr.ts = t;
-        fr.aux = err;
+        fr.aux = e;
         fr.func = (uint16_t)fn;
-        fr.flags = 0;
+        fr.flags = (uint16_t)err;
         p.frontier[fbase + pend_c + __popc(pbal & lt)] = fr;
       }
       if (dev_on) {  // device-activity records of the batch, at the packet's reserved bases

@@ -27,6 +27,8 @@ struct TraceRec {
   thapi_tally_row *dev_rows = nullptr;
   uint64_t dev_rows_bytes = 0;
   thapi_device_diag dev_diag{};
+  thapi_tally_row *self_rows = nullptr;  // self-time rows (loaded with self time on)
+  uint64_t self_rows_bytes = 0, n_self_rows = 0;
   std::vector<char> strings;
   std::vector<uint32_t> host_name, func_name;
   thapi_load_timing timing{};
@@ -47,6 +49,7 @@ struct thapi_ctx {
   int err_level = 0;
   uint64_t err_packet = 0, err_event = 0;
   int timing = 0;
+  int self_time = 0;
 };
 
 namespace thapi {
@@ -57,7 +60,7 @@ uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // CUDA events bracketing the phases of one load (only when timing is on).
 struct PhaseClock {
-  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kJo0, kJo1, kTa1, kCo0, kCo1, kSo1, kGa1, kN };
+  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kJo0, kJo1, kTa1, kSe0, kSe1, kCo0, kCo1, kSo1, kGa1, kN };
   cudaEvent_t ev[kN] = {};
   bool on = false, dense = false;
   void init(bool enable) {
@@ -294,6 +297,10 @@ enum Misc {
   mPcLevel,                   // per-CPU pairing: largest call level (follows mPcWord)
   mPcRows,                    // per-CPU thread tally rows
   mMerged,                    // tally rows after merging the thread rows
+  mSelfWord,                  // self time: largest level
+  mSelfRows,                  // self-time rows of per-thread streams
+  mSelfPcRows,                // self-time rows of per-CPU threads
+  mSelfMerged,                // self-time rows after merging
   mCount
 };
 
@@ -318,6 +325,7 @@ class Loader {
       dev_free(c_, tr_->rows, tr_->rows_bytes, s_);
       dev_free(c_, tr_->tl, tr_->tl_bytes, s_);
       dev_free(c_, tr_->dev_rows, tr_->dev_rows_bytes, s_);
+      dev_free(c_, tr_->self_rows, tr_->self_rows_bytes, s_);
       delete tr_;
     }
     cudaStreamSynchronize(s_);
@@ -463,8 +471,10 @@ int Loader::run() {
     const uint32_t k = cls_kind(c);
     dev_on = dev_on || k == kDevBegin || k == kDevEnd || (k == kEntry && cls_cmdw(c) >= 0);
   }
+  // self time: a side record per slot, then per interval its record, sort keys and children's sum
+  const bool self_on = c_->self_time != 0;
   const uint64_t est = (host_ ? n * (uint64_t)P : 0) + n * 128 + cells * 80 + est_events * 24 +
-                       (dev_on ? est_events * 48 + cells * 80 : 0);
+                       (dev_on ? est_events * 48 + cells * 80 : 0) + (self_on ? est_events * 96 + cells * 120 : 0);
   if (c_->cap && c_->used + est > c_->cap) return THAPI_E_NOMEM;
 
   tr_ = new (std::nothrow) TraceRec();
@@ -545,6 +555,8 @@ int Loader::run() {
   uint32_t *A = alloc<uint32_t>(n), *base = alloc<uint32_t>(n);
   uint64_t *sum_fbase = alloc<uint64_t>(n);
   thapi_interval *slots = alloc<thapi_interval>(total_events);
+  if (self_on && total_events >= 0x80000000ull) return THAPI_E_UNSUPPORTED;  // levels below the kSelfAbs bit
+  SelfSlot *side = self_on ? alloc<SelfSlot>(total_events) : nullptr;
   if (sc_.failed) return THAPI_E_NOMEM;
   PkDesc *desc = alloc<PkDesc>(n);
   if (!desc) return THAPI_E_NOMEM;
@@ -639,6 +651,7 @@ int Loader::run() {
     ap.dense_count = reinterpret_cast<unsigned long long *>(misc_ + mDense);
     ap.slots_written = reinterpret_cast<unsigned long long *>(misc_ + mSlots);
     ap.cmd = cmd;
+    ap.side = side;
     ap.run_start = nullptr;
     if (n && warp_path) {
       ap.run_start = run_start;
@@ -720,6 +733,7 @@ int Loader::run() {
     fp.slots = slots;
     fp.sum_nvalid = sum_nvalid;
     fp.diag = reinterpret_cast<unsigned long long *>(misc_ + mDiag0);
+    fp.side = side;
     clk_.rec(PhaseClock::kFr0, s_);
     launch_frontier(fp, s_);
     clk_.rec(PhaseClock::kFr1, s_);
@@ -765,7 +779,7 @@ int Loader::run() {
     int tb = 1;
     while (tb < 64 && t1 > t0 && ((t1 - t0) >> tb)) ++tb;
     rc = percpu_pair(pcrec, m, m ? t0 : 0, tb, F, slots, sum_nvalid, reinterpret_cast<unsigned long long *>(misc_ + mDiag0),
-                     misc_ + mPcWord, sc_, s_, &pco);
+                     misc_ + mPcWord, self_on, sc_, s_, &pco);
     if (rc != THAPI_OK) return rc;
   }
 
@@ -876,6 +890,63 @@ int Loader::run() {
   }
   const uint64_t n_iv = n ? misc_h_[mIv] : 0;
   if (n_iv >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+
+  // ---- self time (when asked for): per-thread streams here, per-CPU threads from their pairing
+  if (self_on) {
+    clk_.rec(PhaseClock::kSe0, s_);
+    Cell *scells = alloc<Cell>(cells);
+    uint64_t *sflags = alloc<uint64_t>(cells);
+    thapi_tally_row *srows = alloc<thapi_tally_row>(cells);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    launch_tally_init(scells, cells, s_);
+    SelfIn si{};
+    si.slots = slots;
+    si.side = side;
+    si.evbase = evbase;
+    si.obase = obase;
+    si.nslot = sum_nslot;
+    si.A = A;
+    si.order = order;
+    si.pk_stream = pk_stream;
+    si.stream_group = d_group;
+    si.n_funcs = F;
+    si.n_streams = S;
+    si.n_order = n;
+    si.n_iv = n_iv;
+    si.num_sms = c_->num_sms;
+    if ((rc = self_time(si, scells, misc_ + mSelfWord, sc_, s_)) != THAPI_OK) return rc;
+    launch_tally_compact(scells, cells, d_gkeys, F, sflags, srows, misc_ + mSelfRows, sc_, s_);
+    thapi_tally_row *spcrows = nullptr;
+    if (pco.self_cells && pc_cells) {
+      uint64_t *pflags = alloc<uint64_t>(pc_cells);
+      spcrows = alloc<thapi_tally_row>(pc_cells);
+      if (sc_.failed) return THAPI_E_NOMEM;
+      launch_tally_compact(pco.self_cells, pc_cells, pco.keys, F, pflags, spcrows, misc_ + mSelfPcRows, sc_, s_);
+    }
+    if (sc_.failed) return THAPI_E_NOMEM;
+    CK(cudaGetLastError());
+    if ((rc = sync_misc()) != THAPI_OK) return rc;
+    uint64_t ns = cells ? misc_h_[mSelfRows] : 0;
+    if (spcrows && misc_h_[mSelfPcRows]) {  // per-CPU threads' rows merge into the per-thread rows
+      const uint64_t n_pc = misc_h_[mSelfPcRows];
+      thapi_tally_row *both = alloc<thapi_tally_row>(ns + n_pc);
+      thapi_tally_row *merged = alloc<thapi_tally_row>(ns + n_pc);
+      if (sc_.failed) return THAPI_E_NOMEM;
+      if (ns) CK(cudaMemcpyAsync(both, srows, ns * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice, s_));
+      CK(cudaMemcpyAsync(both + ns, spcrows, n_pc * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice, s_));
+      if (!tally_merge_device(both, ns + n_pc, merged, misc_ + mSelfMerged, sc_, s_))
+        return sc_.failed ? THAPI_E_NOMEM : THAPI_E_CUDA;
+      if ((rc = sync_misc()) != THAPI_OK) return rc;
+      ns = misc_h_[mSelfMerged];
+      srows = merged;
+    }
+    tr_->n_self_rows = ns;
+    tr_->self_rows_bytes = std::max<uint64_t>(ns, 1) * sizeof(thapi_tally_row);
+    tr_->self_rows = static_cast<thapi_tally_row *>(dev_alloc(c_, tr_->self_rows_bytes, s_));
+    if (!tr_->self_rows) return THAPI_E_NOMEM;
+    if (ns) CK(cudaMemcpyAsync(tr_->self_rows, srows, ns * sizeof(thapi_tally_row), cudaMemcpyDeviceToDevice, s_));
+    clk_.rec(PhaseClock::kSe1, s_);
+  }
   if (dev_on && misc_h_[mJoin0 + 5]) return THAPI_E_CUDA;  // a join table without room: not reached
   tr_->rows_bytes = std::max<uint64_t>(n_rows, 1) * sizeof(thapi_tally_row);
   tr_->rows = static_cast<thapi_tally_row *>(dev_alloc(c_, tr_->rows_bytes, s_));
@@ -940,6 +1011,7 @@ int Loader::run() {
                      (clk_.dense ? clk_.ms(PhaseClock::kDn0, PhaseClock::kDn1) : 0.f);
       t.frontier_ms = clk_.ms(PhaseClock::kFr0, PhaseClock::kFr1);
       t.join_ms = dev_on ? clk_.ms(PhaseClock::kJo0, PhaseClock::kJo1) : 0.f;
+      t.self_ms = self_on ? clk_.ms(PhaseClock::kSe0, PhaseClock::kSe1) : 0.f;
       t.tally_ms = clk_.ms(dev_on ? PhaseClock::kJo1 : PhaseClock::kFr1, PhaseClock::kTa1);
       t.compact_ms = clk_.ms(PhaseClock::kCo0, PhaseClock::kCo1);
       t.sort_ms = clk_.ms(PhaseClock::kCo1, PhaseClock::kSo1);
@@ -982,7 +1054,8 @@ int Loader::run() {
   inf.packet_bytes = P;
   inf.t_min = tmin == ~0ull ? 0 : tmin;
   inf.t_max = tmax;
-  inf.device_bytes = tr_->rows_bytes + tr_->tl_bytes + tr_->dev_rows_bytes;
+  inf.device_bytes = tr_->rows_bytes + tr_->tl_bytes + tr_->dev_rows_bytes + tr_->self_rows_bytes;
+  inf.self_time = self_on ? 1u : 0u;
   inf.device_rows = n_dev_rows;
   inf.device_intervals = dd.dev_intervals;
   tr_->strings.assign(L.strings.begin(), L.strings.end());
@@ -1191,6 +1264,7 @@ int thapi_ctx_destroy(thapi_ctx *ctx) {
     dev_free(ctx, t->rows, t->rows_bytes, t->stream);
     dev_free(ctx, t->tl, t->tl_bytes, t->stream);
     dev_free(ctx, t->dev_rows, t->dev_rows_bytes, t->stream);
+    dev_free(ctx, t->self_rows, t->self_rows_bytes, t->stream);
     cudaStreamSynchronize(t->stream);
     delete t;
   }
@@ -1223,6 +1297,7 @@ int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id) {
   dev_free(ctx, t->rows, t->rows_bytes, t->stream);
   dev_free(ctx, t->tl, t->tl_bytes, t->stream);
   dev_free(ctx, t->dev_rows, t->dev_rows_bytes, t->stream);
+  dev_free(ctx, t->self_rows, t->self_rows_bytes, t->stream);
   cudaStreamSynchronize(t->stream);
   ctx->used -= std::min(ctx->used, t->info.device_bytes);
   ctx->traces.erase(id);
@@ -1329,6 +1404,27 @@ int thapi_ctx_set_timing(thapi_ctx *ctx, int enable) {
   if (!ctx) return THAPI_E_INVALID;
   ctx->timing = enable ? 1 : 0;
   return THAPI_OK;
+}
+
+int thapi_ctx_set_self_time(thapi_ctx *ctx, int enable) {
+  if (!ctx) return THAPI_E_INVALID;
+  ctx->self_time = enable ? 1 : 0;
+  return THAPI_OK;
+}
+
+int thapi_self_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows) {
+  TraceRec *t = find(ctx, id);
+  if (!t || !n_rows || (cap && !rows) || !t->self_rows) return THAPI_E_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return THAPI_E_CUDA;
+  const uint64_t n = t->n_self_rows;
+  *n_rows = n;
+  if (cap == 0) return THAPI_OK;
+  if (cap < n) return THAPI_E_RANGE;
+  if (!n) return THAPI_OK;
+  if (cudaMemcpyAsync(rows, t->self_rows, n * sizeof(thapi_tally_row), cudaMemcpyDeviceToHost, t->stream) !=
+      cudaSuccess)
+    return THAPI_E_CUDA;
+  return cudaStreamSynchronize(t->stream) == cudaSuccess ? THAPI_OK : THAPI_E_CUDA;
 }
 
 int thapi_trace_timing(thapi_ctx *ctx, thapi_trace_id id, thapi_load_timing *out) {

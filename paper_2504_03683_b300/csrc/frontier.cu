@@ -97,12 +97,17 @@ __global__ void k_frontier_match(FrontierParams p) {
           atomicAdd(&cell.total, (unsigned long long)dur);
           atomicMin(&cell.mn, (unsigned long long)dur);
           atomicMax(&cell.mx, (unsigned long long)dur);
-          if (ex.aux) atomicAdd(&cell.err, 1ull);
+          if (ex.flags) atomicAdd(&cell.err, 1ull);
           if (p.slots && en.aux != 0xFFFFFFFFu) {
             thapi_interval &iv = p.slots[p.evbase[q] + en.aux];
             iv.end_ns = ex.ts;
-            iv.flags = (uint8_t)(kIvValid | (ex.aux ? kIvErr : 0u));
+            iv.flags = (uint8_t)(kIvValid | (ex.flags ? kIvErr : 0u));
             atomicAdd(&p.sum_nvalid[q], 1u);
+            if (p.side) {  // self time: the exit's position and the absolute level
+              SelfSlot &ss = p.side[p.evbase[q] + en.aux];
+              ss.exit_pos = p.evbase[i] + ex.aux;
+              ss.level = L | kSelfAbs;
+            }
           }
         } else {
           ++mism;

@@ -44,10 +44,22 @@ constexpr uint8_t kIvValid = 1u << 7;
 // that pops below the packet's starting depth.
 struct __align__(16) Frontier {
   uint64_t ts;
-  uint32_t aux;   // open: interval slot rank in its packet (or ~0u); pending exit: error flag
+  uint32_t aux;   // open: interval slot rank in its packet (or ~0u); pending exit: event index in its packet
   uint16_t func;
-  uint16_t flags;
+  uint16_t flags; // pending exit: error flag
 };
+
+// Self-time side record of an interval slot (written only when self time is
+// on): event positions (the packet's event base + the event's index in the
+// packet) of the entry and of the exit that closes it, and the entry's depth,
+// packet-relative clamped (the timeline compaction's level before the depth
+// carried into the packet is added) or, with kSelfAbs, absolute (pairs formed
+// across packets).
+struct SelfSlot {
+  uint64_t entry_pos, exit_pos;
+  uint32_t level, pad;
+};
+constexpr uint32_t kSelfAbs = 0x80000000u;
 
 // Tally cell of the global (group, function) table.
 struct __align__(8) Cell {
@@ -152,6 +164,7 @@ struct AnalyzeParams {
   uint32_t per_cta;              // work items per CTA
   const uint32_t *run_start;     // warp kernel: CTA c takes work items [run_start[c], run_start[c + 1])
   CmdOut cmd;                    // device-activity records (counts null: none)
+  SelfSlot *side;                // per interval slot (null: self time off)
 };
 
 struct FrontierParams {
@@ -171,6 +184,7 @@ struct FrontierParams {
   thapi_interval *slots;
   uint32_t *sum_nvalid;
   unsigned long long *diag;
+  SelfSlot *side;                // null: self time off
 };
 
 // ---------------------------------------------------------- launchers
@@ -300,13 +314,29 @@ cudaError_t launch_percpu_decode(const PcParams &p, uint32_t nw, uint32_t grid, 
 // *n_threads (host) = threads; cells / keys are allocated here (sc).
 struct PcPairOut {
   Cell *cells = nullptr;           // [threads * n_funcs]
+  Cell *self_cells = nullptr;      // [threads * n_funcs], self time (when asked for)
   uint32_t *keys = nullptr;        // [threads * 3] host, vpid, vtid
   uint64_t threads = 0;
 };
-// word: two device words (threads; largest level).
+// Self time of the calls of per-thread streams (self.cu), from the interval
+// slots and their SelfSlot records after pairing: cells [groups * n_funcs]
+// (initialised by the caller) receive count, total / min / max self time and
+// errors.  word: one device word.
+struct SelfIn {
+  const thapi_interval *slots;
+  const SelfSlot *side;
+  const uint64_t *evbase, *obase;
+  const uint32_t *nslot, *A, *order, *pk_stream, *stream_group;
+  uint32_t n_funcs, n_streams;
+  uint64_t n_order, n_iv;
+  int num_sms;
+};
+int self_time(const SelfIn &in, Cell *cells, uint64_t *word, Scratch &sc, cudaStream_t s);
+// word: two device words (threads; largest level).  self_cells (non-null: self
+// time on) receives the threads' self-time cells [threads * n_funcs].
 int percpu_pair(PcRec *rec, uint64_t m, uint64_t t_min, int ts_bits, uint32_t n_funcs, thapi_interval *slots,
-                uint32_t *sum_nvalid, unsigned long long *diag, uint64_t *word, Scratch &sc, cudaStream_t s,
-                PcPairOut *out);
+                uint32_t *sum_nvalid, unsigned long long *diag, uint64_t *word, bool self_on, Scratch &sc,
+                cudaStream_t s, PcPairOut *out);
 cudaError_t launch_decode_warp(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s);
 // Splits the stream-ordered packets into `grid` contiguous runs of about equal
 // cost (events + a per-packet constant): run_start[0..grid].

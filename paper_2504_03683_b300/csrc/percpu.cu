@@ -17,7 +17,11 @@
 //     that pops it (nothing at that level happens between them), so pairs
 //     are neighbours: equal functions make an interval (written into the
 //     entry's slot, tallied on the thread's cells), different ones a
-//     mismatched pair; an entry with no exit after it is unmatched.
+//     mismatched pair; an entry with no exit after it is unmatched;
+//  4. with self time on, the parent of a pair at level L > 0 is the last
+//     record of the (thread, L - 1) run before its entry (binary search); a
+//     parent that is a pair takes the child's duration, and each pair's self
+//     time (duration less its children's) is tallied per thread.
 #include <algorithm>
 
 #include "device_util.cuh"
@@ -231,11 +235,58 @@ __global__ void k_pc_pair(const PcRec *r, const uint64_t *key, const uint32_t *v
   }
 }
 
+// An entry at sorted position k that its neighbour closes with the same function.
+__device__ __forceinline__ bool is_pair(const PcRec *r, const uint64_t *key, const uint32_t *val, uint64_t m,
+                                        uint64_t k) {
+  if (k + 1 >= m || key[k + 1] != key[k]) return false;
+  const PcRec &en = r[val[k]], &ex = r[val[k + 1]];
+  return en.kind == kEntry && ex.kind == kExit && en.func == ex.func;
+}
+
+// Self time: the parent of the pair at k (level L > 0) is the entry open at
+// depth L - 1 when k's entry is pushed, the last record of the (thread, L - 1)
+// run before it in thread order; it takes the child's duration when it is a
+// pair itself.
+__global__ void k_pc_child(const PcRec *r, const uint64_t *key, const uint32_t *val, uint64_t m,
+                           uint64_t unmatched_key, int lb, unsigned long long *child) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const uint64_t kk = key[k];
+  if (kk == unmatched_key || (kk & ((1ull << lb) - 1)) == 0 || !is_pair(r, key, val, m, k)) return;
+  const uint64_t target = kk - 1;
+  const uint32_t pos = val[k];
+  uint64_t lo = 0, hi = k;
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    const uint64_t km = key[mid];
+    if (km < target || (km == target && val[mid] < pos))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo == 0 || key[lo - 1] != target || !is_pair(r, key, val, m, lo - 1)) return;
+  atomicAdd(&child[lo - 1], (unsigned long long)(r[val[k + 1]].ts - r[val[k]].ts));
+}
+
+__global__ void k_pc_self(const PcRec *r, const uint64_t *key, const uint32_t *val, uint64_t m,
+                          uint64_t unmatched_key, int lb, uint32_t F, const unsigned long long *child, Cell *cells) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m || key[k] == unmatched_key || !is_pair(r, key, val, m, k)) return;
+  const PcRec &en = r[val[k]], &ex = r[val[k + 1]];
+  const unsigned long long self = (ex.ts - en.ts) - child[k];
+  Cell &c = cells[(key[k] >> lb) * F + en.func];
+  atomicAdd(&c.count, 1ull);
+  atomicAdd(&c.total, self);
+  atomicMin(&c.mn, self);
+  atomicMax(&c.mx, self);
+  if (ex.err) atomicAdd(&c.err, 1ull);
+}
+
 }  // namespace
 
 int percpu_pair(PcRec *rec, uint64_t m, uint64_t t_min, int ts_bits, uint32_t F, thapi_interval *slots,
-                uint32_t *sum_nvalid, unsigned long long *diag, uint64_t *word, Scratch &sc, cudaStream_t s,
-                PcPairOut *out) {
+                uint32_t *sum_nvalid, unsigned long long *diag, uint64_t *word, bool self_on, Scratch &sc,
+                cudaStream_t s, PcPairOut *out) {
   *out = PcPairOut{};
   if (m == 0) return THAPI_OK;
   uint64_t *k1 = static_cast<uint64_t *>(sc.get(m * sizeof(uint64_t)));
@@ -292,9 +343,20 @@ int percpu_pair(PcRec *rec, uint64_t m, uint64_t t_min, int ts_bits, uint32_t F,
   bool alt = false;
   radix_sort_pairs(k1, v1, k2, v2, m, tb + lb, &alt, sc, s);
   if (sc.failed) return THAPI_E_NOMEM;
-  k_pc_pair<<<blocks(m), kT, 0, s>>>(r2, alt ? k2 : k1, alt ? v2 : v1, m, unmatched, lb, F, out->cells, slots,
-                                     sum_nvalid, diag);
+  const uint64_t *key = alt ? k2 : k1;
+  const uint32_t *val = alt ? v2 : v1;
+  k_pc_pair<<<blocks(m), kT, 0, s>>>(r2, key, val, m, unmatched, lb, F, out->cells, slots, sum_nvalid, diag);
   count_launches(15);
+  if (self_on) {  // 4. self time: children's durations to their parents, then the self tally
+    unsigned long long *child = static_cast<unsigned long long *>(sc.get(m * sizeof(uint64_t)));
+    out->self_cells = static_cast<Cell *>(sc.get(T * F * sizeof(Cell)));
+    if (sc.failed) return THAPI_E_NOMEM;
+    if (cudaMemsetAsync(child, 0, m * sizeof(uint64_t), s) != cudaSuccess) return THAPI_E_CUDA;
+    launch_tally_init(out->self_cells, T * F, s);
+    k_pc_child<<<blocks(m), kT, 0, s>>>(r2, key, val, m, unmatched, lb, child);
+    k_pc_self<<<blocks(m), kT, 0, s>>>(r2, key, val, m, unmatched, lb, F, child, out->self_cells);
+    count_launches(2);
+  }
   return cudaGetLastError() == cudaSuccess ? THAPI_OK : THAPI_E_CUDA;
 }
 

@@ -37,7 +37,8 @@ EXPORTED = (
     "thapi_trace_load_device", "thapi_trace_free", "thapi_tally", "thapi_timeline", "thapi_tally_device",
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
-    "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode",
+    "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode", "thapi_ctx_set_self_time",
+    "thapi_self_tally",
 )
 
 
@@ -59,7 +60,7 @@ class TraceInfo(ctypes.Structure):
     _fields_ = [("nbytes", ctypes.c_uint64), ("n_packets", ctypes.c_uint64), ("events", ctypes.c_uint64),
                 ("intervals", ctypes.c_uint64), ("tally_rows", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
                 ("n_streams", ctypes.c_uint32), ("n_classes", ctypes.c_uint32), ("n_funcs", ctypes.c_uint32),
-                ("n_hosts", ctypes.c_uint32), ("packet_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("n_hosts", ctypes.c_uint32), ("packet_bytes", ctypes.c_uint32), ("self_time", ctypes.c_uint32),
                 ("t_min", ctypes.c_uint64), ("t_max", ctypes.c_uint64),
                 ("device_rows", ctypes.c_uint64), ("device_intervals", ctypes.c_uint64)]
 
@@ -72,7 +73,7 @@ class LoadTiming(ctypes.Structure):
                                                "sort_ms", "gather_ms", "total_ms")] + \
                [(f, ctypes.c_uint64) for f in ("analyze_read_bytes", "analyze_write_bytes", "analyze_launches",
                                                 "launches")] + \
-               [(f, ctypes.c_float) for f in ("join_ms", "reserved_ms")]
+               [(f, ctypes.c_float) for f in ("join_ms", "self_ms")]
 
     def as_dict(self):
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
@@ -119,6 +120,8 @@ def library():
         "thapi_last_error_location": ([vp, P(i32), P(u64), P(u64)], i32),
         "thapi_strerror": ([i32], ctypes.c_char_p),
         "thapi_ctx_set_timing": ([vp, i32], i32),
+        "thapi_ctx_set_self_time": ([vp, i32], i32),
+        "thapi_self_tally": ([vp, u64, vp, u64, P(u64)], i32),
         "thapi_trace_timing": ([vp, u64, P(LoadTiming)], i32),
         "thapi_kernel_launches": ([], u64),
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
@@ -243,6 +246,18 @@ def thapi_device_tally(ctx: int, trace_id: int):
     return rows, d.as_dict()
 
 
+def thapi_self_tally(ctx: int, trace_id: int):
+    """Self-time rows (ROW_DTYPE: the tally's keys, counts and error counts;
+    total / min / max of self time) of a trace loaded with self time on."""
+    lib = library()
+    n = ctypes.c_uint64()
+    _check(lib.thapi_self_tally(ctx, trace_id, None, 0, ctypes.byref(n)), "thapi_self_tally")
+    rows = np.zeros(n.value, dtype=ROW_DTYPE)
+    if n.value:
+        _check(lib.thapi_self_tally(ctx, trace_id, rows.ctypes.data, n.value, ctypes.byref(n)), "thapi_self_tally")
+    return rows
+
+
 def thapi_tally_merge(ctx: int, rows, stream=None):
     """Merges tally rows (ROW_DTYPE, any order; e.g. several traces' or ranks' rows
     concatenated) into one row per key, in key order."""
@@ -316,6 +331,10 @@ def thapi_strerror(code: int) -> str:
 
 def thapi_ctx_set_timing(ctx: int, enable: bool = True) -> None:
     _check(library().thapi_ctx_set_timing(ctx, 1 if enable else 0), "thapi_ctx_set_timing")
+
+
+def thapi_ctx_set_self_time(ctx: int, enable: bool = True) -> None:
+    _check(library().thapi_ctx_set_self_time(ctx, 1 if enable else 0), "thapi_ctx_set_self_time")
 
 
 def thapi_trace_timing(ctx: int, trace_id: int) -> dict:
@@ -394,6 +413,12 @@ class Context:
 
     def tally_merge(self, rows, stream=None):
         return thapi_tally_merge(self.handle, rows, stream)
+
+    def set_self_time(self, enable: bool = True) -> None:
+        thapi_ctx_set_self_time(self.handle, enable)
+
+    def self_tally(self, trace_id: int):
+        return thapi_self_tally(self.handle, trace_id)
 
     def timeline(self, trace_id: int, t0: int = 0, t1: int = 2**64 - 1):
         return thapi_timeline(self.handle, trace_id, t0, t1)
