@@ -40,6 +40,10 @@ WORKLOADS = {
     "device": dict(preset="device", desc="512 host streams (8x8x8) of launch/memcpy calls (16 fns) carrying unique "
                                          "random 64-bit command ids; 64 device streams of begin/end events; 50M "
                                          "commands = 200M events; device pairing + merged timeline; 16 KB packets"),
+    "percpu": dict(preset="percpu", desc="the large workload's shape (8 hosts x 64 threads, 3 layers, depth<=6) "
+                                         "written as per-CPU buffers: 32 CPUs per host, threads rotated over CPUs "
+                                         "every 200 us (two threads interleaved per CPU); 50M calls = 100M events "
+                                         "with 16-byte headers; 16 KB packets"),
 }
 
 
@@ -56,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-once", action="store_true", help="one load only (for a profiler), no JSON")
+    ap.add_argument("--self-time", action="store_true", help="every load also computes self (exclusive) time")
     return ap.parse_args()
 
 
@@ -178,7 +183,7 @@ def sample_streams(workload, n_streams, cpu_streams):
     if workload == "device":  # the first host streams and the first device streams (ids 512..575)
         k = cpu_streams or 32
         return list(range(min(k, 512))) + list(range(512, min(n_streams, 514)))
-    k = cpu_streams or (200 if workload == "large" else 64)
+    k = cpu_streams or {"large": 200, "percpu": 24}.get(workload, 64)
     return list(range(max(1, min(n_streams, k))))
 
 
@@ -212,7 +217,8 @@ def run_reference(args, rank, world):
     plan = tg.Plan(cfg)
     n_streams = plan.n_streams
     plan.close()
-    streams = sample_streams(args.workload, n_streams, args.cpu_streams or {"large": 64, "device": 16}.get(args.workload, 0))
+    streams = sample_streams(args.workload, n_streams,
+                             args.cpu_streams or {"large": 64, "device": 16, "percpu": 8}.get(args.workload, 0))
     samples = []
     for i in range(args.warmup + args.steps):
         s = cpu_sample(host, n_streams, streams)
@@ -254,6 +260,8 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = thapi.Context(local)
     thapi.thapi_ctx_set_timing(ctx.handle, True)
+    if args.self_time:
+        thapi.thapi_ctx_set_self_time(ctx.handle, True)
 
     if args.profile_once:
         tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), stream)
@@ -265,6 +273,7 @@ def main():
     # first load sizes the output buffers
     tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), stream)
     info = ctx.info(tid)
+    n_self_rows = len(thapi.thapi_self_tally(ctx.handle, tid)) if args.self_time else 0
     ctx.free(tid)
     rows_d = torch.empty(max(1, info["tally_rows"]) * 56, dtype=torch.uint8, device="cuda")
     ivs_d = torch.empty(max(1, info["intervals"]) * 24, dtype=torch.uint8, device="cuda")
@@ -320,8 +329,8 @@ def main():
     achieved = an_bytes / (an_ms / 1e3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6400.0))
     phase = {k: round(statistics.mean(t[k] for t in timings), 4)
-             for k in ("index_ms", "analyze_ms", "frontier_ms", "join_ms", "tally_ms", "compact_ms", "sort_ms",
-                       "gather_ms", "total_ms")}
+             for k in ("index_ms", "analyze_ms", "frontier_ms", "join_ms", "percpu_ms", "tally_ms", "self_ms",
+                       "compact_ms", "sort_ms", "gather_ms", "total_ms")}
     traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze_warp.cu"), args.workload)
 
     # end to end through the public API: host bytes in, host results out
@@ -338,13 +347,15 @@ def main():
             tid = thapi.thapi_trace_load(ctx.handle, (host.data_ptr(), host.numel()), stream)
             rows, _d = thapi.thapi_tally(ctx.handle, tid)
             thapi.thapi_timeline(ctx.handle, tid, out=ivs_h)
+            if args.self_time:
+                thapi.thapi_self_tally(ctx.handle, tid)
             thapi.thapi_trace_free(ctx.handle, tid)
             dt = time.perf_counter() - t0
             if i > 0:
                 times.append(dt)
         e2e_s = statistics.median(times)
         h2d = meta["n_packets"] * int(cfg.packet_bytes)
-        d2h = info["tally_rows"] * 56 + n_iv * 24
+        d2h = (info["tally_rows"] + n_self_rows) * 56 + n_iv * 24
         e2e = {"value": events / e2e_s, "unit": "events/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_s * 1e3}
 
@@ -355,10 +366,12 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "events/s decode+pair+tally+timeline", "value": value, "unit": "events/s",
+            "metric": "events/s decode+pair+tally+timeline" + ("+self time" if args.self_time else ""),
+            "value": value, "unit": "events/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
+                       "self_time": bool(args.self_time),
                        "calls": int(cfg.total_calls), "events_per_rank": events, "trace_bytes": meta["nbytes"],
                        "packets": meta["n_packets"], "seed": int(cfg.seed), "parallelism": "replicas" if world > 1
                        else "single",

@@ -264,6 +264,10 @@ int thapi_trace_info_get(thapi_ctx *ctx, thapi_trace_id id, thapi_trace_info *in
 int thapi_trace_strings(thapi_ctx *ctx, thapi_trace_id id, int kind, uint32_t index, char *buf, uint64_t cap,
                         uint64_t *len);
 
+/* The layer of function func_id (the function row's u16 layer: which API of
+ * a layered stack, e.g. HIP over Level Zero, Sec. 4.3) to *layer. */
+int thapi_trace_func_layer(thapi_ctx *ctx, thapi_trace_id id, uint32_t func_id, uint32_t *layer);
+
 /* Where the last failed load of this context failed: level 0 = file header or
  * tables, 1 = packet header (packet = file index), 2 = packet content
  * (packet = file index, event = index of the event within the packet, or the
@@ -289,6 +293,8 @@ typedef struct thapi_load_timing {
   uint64_t launches;             /* all kernel launches of the load */
   float join_ms;                 /* device-activity pairing (includes one host wait) */
   float self_ms;                 /* self time (when on; includes host waits) */
+  float percpu_ms;               /* per-CPU buffers: event records, thread order, pairing (includes host waits) */
+  float reserved_ms;
 } thapi_load_timing;
 
 /* Enables (1) or disables (0) per-phase timing of subsequent loads. */

@@ -175,7 +175,7 @@ __device__ __forceinline__ TsM scan_ts(TsM x, uint32_t lane) {
 
 // DEV: device-activity records wanted (p.cmd.counts set); the kernel without
 // them carries none of that code.
-template <int BW, bool DEV>
+template <int BW, bool DEV, bool SIDE>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p, uint32_t NW, unsigned int *status) {
   extern __shared__ __align__(128) uint8_t sm[];
   constexpr uint32_t SEGW = 32u * (BW - 1) + 1;  // odd: lane k's segment starts in shared-memory bank k
@@ -541,7 +541,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           atomicMin(&cell.mn, (unsigned long long)dur);
           atomicMax(&cell.mx, (unsigned long long)dur);
           if (err) atomicAdd(&cell.err, 1ull);
-          if (p.side) {  // self time: the exit's position and the entry's exact packet-relative depth
+          if (SIDE) {  // self time: the exit's position and the entry's exact packet-relative depth
             SelfSlot &ss = p.side[d.evbase + ((em >> 16) & 0xFFFFu)];
             ss.exit_pos = d.evbase + e;
             ss.level = (uint32_t)(post - before.m);
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           put_interval(pslots + ((em >> 16) & 0xFFFFu), ets, t, (uint32_t)((em >> 40) & 0xFFFFu), efn,
                        (uint32_t)((em >> 32) & 0xFFu), flags);
       }
-      if (p.side && is_entry) p.side[d.evbase + rank].entry_pos = d.evbase + e;
+      if (SIDE && is_entry) p.side[d.evbase + rank].entry_pos = d.evbase + e;
       const uint32_t pbal = __ballot_sync(kFull, pend);
       if (pend && fbase != ~0ull) {
         Frontier fr;
@@ -666,7 +666,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
 
 template <int BW>
 cudaError_t launch_w(const AnalyzeParams &p, const WarpPlan &wp, uint32_t grid, cudaStream_t s, unsigned *status) {
-  auto fn = p.cmd.counts ? k_analyze_warp<BW, true> : k_analyze_warp<BW, false>;
+  auto fn = p.cmd.counts ? (p.side ? k_analyze_warp<BW, true, true> : k_analyze_warp<BW, true, false>)
+                         : (p.side ? k_analyze_warp<BW, false, true> : k_analyze_warp<BW, false, false>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wp.smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, wp.nw * 32, wp.smem, s>>>(p, wp.nw, status);
@@ -969,12 +970,11 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_percpu_decode(PcParams p,
       continue;
     }
     const uint32_t nrec_p = __reduce_add_sync(kFull, nrec);
-    unsigned long long rbase = 0;
-    if (lane == 0 && nrec_p) rbase = atomicAdd(p.count, (unsigned long long)nrec_p);
-    rbase = __shfl_sync(kFull, rbase, 0);
+    if (lane == 0 && nrec_p) atomicAdd(p.count, (unsigned long long)nrec_p);
+    const uint64_t rbase = p.pc_base[w];  // the packet's events at their positions
     const uint32_t host = p.stream_host[d.stream];
     uint64_t tcur = d.tsb;
-    uint32_t rank_e = 0, rank_r = 0;
+    uint32_t rank_e = 0;
     for (uint32_t e0 = 0; e0 < c_tot; e0 += 32) {
       const uint32_t e = e0 + lane;
       const bool act = e < c_tot;
@@ -989,11 +989,16 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_percpu_decode(PcParams p,
       const uint64_t r = act ? p.classes[c] : 0ull;
       const uint32_t kd = act ? cls_kind(r) : kSample;
       const bool is_e = kd == kEntry, is_x = kd == kExit;
-      const uint32_t eb = __ballot_sync(kFull, is_e), rb = __ballot_sync(kFull, is_e || is_x);
+      const uint32_t eb = __ballot_sync(kFull, is_e);
       if (act) {
         tmin = min(tmin, t);
         tmax = max(tmax, t);
         if (!is_e && !is_x) ++n_other;
+      }
+      if (act && !is_e && !is_x) {  // no call event: the position holds kPcNone
+        PcRec rec{};
+        rec.kind = kPcNone;
+        if (rbase + e < p.cap) p.rec[rbase + e] = rec;
       }
       if (is_e || is_x) {
         const uint32_t base = oo + HW + (ext ? 2u : 0u);
@@ -1002,15 +1007,12 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_percpu_decode(PcParams p,
         rec.ts = t;
         rec.thread = ((uint64_t)C[oo + 2] << 32) | C[oo + 3];
         rec.host = host;
-        rec.gpos = (uint32_t)(d.evbase + e);
         rec.slot = (uint32_t)(d.evbase + rank_e + __popc(eb & lt));
         rec.pos = (uint32_t)w;
         rec.func = (uint16_t)cls_func(r);
         rec.kind = (uint8_t)kd;
         rec.err = (is_x && rw >= 0 && C[min(base + rw, W)] != 0) ? 1 : 0;
-        rec.pad = 0;
-        const uint64_t at = rbase + rank_r + __popc(rb & lt);
-        if (at < p.cap) p.rec[at] = rec;
+        if (rbase + e < p.cap) p.rec[rbase + e] = rec;
         if (is_e && p.slots) {  // the entry's slot, invalid until paired
           unsigned long long *q = reinterpret_cast<unsigned long long *>(p.slots + rec.slot);
           q[0] = t;
@@ -1019,7 +1021,6 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_percpu_decode(PcParams p,
         }
       }
       rank_e += __popc(eb);
-      rank_r += __popc(rb);
     }
     if (lane == 0) {
       p.sum_nslot[w] = rank_e;

@@ -16,6 +16,13 @@
 
 #include "internal.cuh"
 
+// the ABI's struct layouts (include/thapi.h), as the binding reads them
+static_assert(sizeof(thapi_tally_row) == 56, "tally row");
+static_assert(sizeof(thapi_interval) == 24, "interval");
+static_assert(sizeof(thapi_event) == 40, "event");
+static_assert(sizeof(thapi_trace_info) == 104, "trace info");
+static_assert(sizeof(thapi_load_timing) == 80, "load timing");
+
 struct TraceRec {
   cudaStream_t stream = nullptr;
   thapi_trace_info info{};
@@ -31,6 +38,7 @@ struct TraceRec {
   uint64_t self_rows_bytes = 0, n_self_rows = 0;
   std::vector<char> strings;
   std::vector<uint32_t> host_name, func_name;
+  std::vector<uint16_t> func_layer;
   thapi_load_timing timing{};
 };
 
@@ -60,7 +68,7 @@ uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // CUDA events bracketing the phases of one load (only when timing is on).
 struct PhaseClock {
-  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kJo0, kJo1, kTa1, kSe0, kSe1, kCo0, kCo1, kSo1, kGa1, kN };
+  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kJo0, kJo1, kTa1, kSe0, kSe1, kPc0, kPc1, kCo0, kCo1, kSo1, kGa1, kN };
   cudaEvent_t ev[kN] = {};
   bool on = false, dense = false;
   void init(bool enable) {
@@ -173,6 +181,7 @@ struct HostLayout {
   std::vector<uint64_t> cls;
   std::vector<uint32_t> srow;  // 4 words per stream
   std::vector<uint32_t> host_name, func_name;
+  std::vector<uint16_t> func_layer;
   std::vector<uint8_t> strings;
 };
 
@@ -210,8 +219,10 @@ static int parse_layout(const Reader &r, HostLayout &L) {
     if (!name_ok(L.strings, L.host_name[i])) return THAPI_E_FORMAT;
   }
   L.func_name.resize(L.n_funcs);
+  L.func_layer.resize(L.n_funcs);
   for (uint32_t i = 0; i < L.n_funcs; ++i) {
     L.func_name[i] = rd<uint32_t>(fs.data() + 8ull * i);
+    L.func_layer[i] = rd<uint16_t>(fs.data() + 8ull * i + 4);
     if (!name_ok(L.strings, L.func_name[i])) return THAPI_E_FORMAT;
   }
   L.cls.resize(L.n_classes);
@@ -293,8 +304,7 @@ enum Misc {
   mDevRows = mJoin0 + 6,
   mPartMax,                   // records of the largest command-id partition
   mPcCount,                   // per-CPU records
-  mPcWord,                    // per-CPU pairing: threads
-  mPcLevel,                   // per-CPU pairing: largest call level (follows mPcWord)
+  mPcAll,                     // per-CPU buffers: events
   mPcRows,                    // per-CPU thread tally rows
   mMerged,                    // tally rows after merging the thread rows
   mSelfWord,                  // self time: largest level
@@ -742,8 +752,13 @@ int Loader::run() {
   // ---- per-CPU buffers: their events' records, then their threads paired
   PcPairOut pco;
   if (has_pc) {
+    clk_.rec(PhaseClock::kPc0, s_);
     uint32_t *d_shost = alloc<uint32_t>(S);
     PcRec *pcrec = alloc<PcRec>(total_events);
+    uint64_t *pc_base = alloc<uint64_t>(n);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    launch_pc_count(desc, n, pc_base, s_);
+    scan_exclusive_u64(pc_base, n, misc_ + mPcAll, sc_, s_);
     if (sc_.failed) return THAPI_E_NOMEM;
     CK(cudaMemcpyAsync(d_shost, stream_host.data(), 4ull * S, cudaMemcpyHostToDevice, s_));
     CK(cudaMemsetAsync(misc_ + mPcCount, 0, sizeof(uint64_t), s_));
@@ -756,6 +771,7 @@ int Loader::run() {
     pp.classes = d_cls;
     pp.stream_host = d_shost;
     pp.rec = pcrec;
+    pp.pc_base = pc_base;
     pp.cap = total_events;
     pp.count = reinterpret_cast<unsigned long long *>(misc_ + mPcCount);
     pp.slots = slots;
@@ -778,9 +794,10 @@ int Loader::run() {
     const uint64_t t0 = misc_h_[mTmin], t1 = misc_h_[mTmax];
     int tb = 1;
     while (tb < 64 && t1 > t0 && ((t1 - t0) >> tb)) ++tb;
-    rc = percpu_pair(pcrec, m, m ? t0 : 0, tb, F, slots, sum_nvalid, reinterpret_cast<unsigned long long *>(misc_ + mDiag0),
-                     misc_ + mPcWord, self_on, sc_, s_, &pco);
+    rc = percpu_pair(pcrec, misc_h_[mPcAll], m, m ? t0 : 0, tb, F, slots, sum_nvalid,
+                     reinterpret_cast<unsigned long long *>(misc_ + mDiag0), self_on, c_->num_sms, sc_, s_, &pco);
     if (rc != THAPI_OK) return rc;
+    clk_.rec(PhaseClock::kPc1, s_);
   }
 
   // ---- device-activity pairing: command table, then device intervals and tally
@@ -891,7 +908,8 @@ int Loader::run() {
   const uint64_t n_iv = n ? misc_h_[mIv] : 0;
   if (n_iv >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
 
-  // ---- self time (when asked for): per-thread streams here, per-CPU threads from their pairing
+  // ---- self time (when asked for): per-thread streams here (when the trace has any), per-CPU
+  //      threads from their pairing
   if (self_on) {
     clk_.rec(PhaseClock::kSe0, s_);
     Cell *scells = alloc<Cell>(cells);
@@ -914,7 +932,7 @@ int Loader::run() {
     si.n_order = n;
     si.n_iv = n_iv;
     si.num_sms = c_->num_sms;
-    if ((rc = self_time(si, scells, misc_ + mSelfWord, sc_, s_)) != THAPI_OK) return rc;
+    if (G && (rc = self_time(si, scells, misc_ + mSelfWord, sc_, s_)) != THAPI_OK) return rc;
     launch_tally_compact(scells, cells, d_gkeys, F, sflags, srows, misc_ + mSelfRows, sc_, s_);
     thapi_tally_row *spcrows = nullptr;
     if (pco.self_cells && pc_cells) {
@@ -1012,6 +1030,7 @@ int Loader::run() {
       t.frontier_ms = clk_.ms(PhaseClock::kFr0, PhaseClock::kFr1);
       t.join_ms = dev_on ? clk_.ms(PhaseClock::kJo0, PhaseClock::kJo1) : 0.f;
       t.self_ms = self_on ? clk_.ms(PhaseClock::kSe0, PhaseClock::kSe1) : 0.f;
+      t.percpu_ms = has_pc ? clk_.ms(PhaseClock::kPc0, PhaseClock::kPc1) : 0.f;
       t.tally_ms = clk_.ms(dev_on ? PhaseClock::kJo1 : PhaseClock::kFr1, PhaseClock::kTa1);
       t.compact_ms = clk_.ms(PhaseClock::kCo0, PhaseClock::kCo1);
       t.sort_ms = clk_.ms(PhaseClock::kCo1, PhaseClock::kSo1);
@@ -1061,6 +1080,7 @@ int Loader::run() {
   tr_->strings.assign(L.strings.begin(), L.strings.end());
   tr_->host_name = L.host_name;
   tr_->func_name = L.func_name;
+  tr_->func_layer = L.func_layer;
   return THAPI_OK;
 }
 
@@ -1397,6 +1417,13 @@ int thapi_trace_strings(thapi_ctx *ctx, thapi_trace_id id, int kind, uint32_t in
   *len = l;
   if (!buf || cap < l + 1) return THAPI_E_RANGE;
   std::memcpy(buf, s, l + 1);
+  return THAPI_OK;
+}
+
+int thapi_trace_func_layer(thapi_ctx *ctx, thapi_trace_id id, uint32_t func_id, uint32_t *layer) {
+  TraceRec *t = find(ctx, id);
+  if (!t || !layer || func_id >= t->func_layer.size()) return THAPI_E_INVALID;
+  *layer = t->func_layer[func_id];
   return THAPI_OK;
 }
 

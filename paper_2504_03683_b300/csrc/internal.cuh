@@ -66,6 +66,52 @@ struct __align__(8) Cell {
   unsigned long long count, total, mn, mx, err;
 };
 
+#ifdef __CUDACC__
+// Block b of nb takes chunk spread(b, nb): a bijection of [0, nb) under which
+// blocks that run at the same time (consecutive b) take chunks far apart, so
+// that their tally atomics spread over many cells instead of the few cells of
+// one stretch of the input (the chunks of a group of 1024 consecutive
+// blocks lie nb / 1024 apart).
+__device__ __forceinline__ uint64_t spread(uint64_t b, uint64_t nb) {
+  const uint64_t G = nb < 1024 ? nb : 1024;
+  const uint64_t g = b % G, k = b / G, q = nb / G, r = nb % G;
+  return g * q + (g < r ? g : r) + k;
+}
+
+// One call per active lane tallied into cells[idx], lanes of the warp with
+// the same cell combined first so that one lane per distinct cell issues the
+// atomics (neighbouring calls often share a cell, and atomics to one address
+// serialise).  Every lane of the warp calls it; scr: 32 entries of this warp.
+struct CellPart {
+  unsigned long long dur;
+  unsigned err, pad;
+};
+__device__ __forceinline__ void warp_tally(Cell *cells, uint64_t idx, bool act, unsigned long long dur, bool err,
+                                           CellPart *scr) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t peers = __match_any_sync(0xffffffffu, act ? (unsigned long long)idx : ~0ull);
+  scr[lane] = CellPart{dur, err ? 1u : 0u, 0u};
+  __syncwarp();
+  if (act && lane == (uint32_t)(__ffs(peers) - 1)) {
+    unsigned long long sum = 0, mn = ~0ull, mx = 0, e = 0;
+    for (uint32_t m = peers; m; m &= m - 1) {
+      const CellPart c = scr[__ffs(m) - 1];
+      sum += c.dur;
+      mn = c.dur < mn ? c.dur : mn;
+      mx = c.dur > mx ? c.dur : mx;
+      e += c.err;
+    }
+    Cell &c = cells[idx];
+    atomicAdd(&c.count, (unsigned long long)__popc(peers));
+    atomicAdd(&c.total, sum);
+    atomicMin(&c.mn, mn);
+    atomicMax(&c.mx, mx);
+    if (e) atomicAdd(&c.err, e);
+  }
+  __syncwarp();
+}
+#endif
+
 // Device error word: packet file index << 20 | event << 3 | code; ~0 = none.
 __host__ __device__ inline unsigned long long err_key(uint64_t packet, uint32_t event, uint32_t code) {
   return ((unsigned long long)packet << 20) | ((unsigned long long)(event & 0x1FFFFu) << 3) | (code & 7u);
@@ -279,17 +325,17 @@ uint32_t decode_warps(uint32_t P, uint32_t n_classes, int smem_optin);  // warps
 
 // Per-CPU buffers (percpu.cu): one record per ENTRY / EXIT of a per-CPU
 // buffer, written by k_percpu_decode (analyze_warp.cu).
+constexpr uint8_t kPcNone = 0xFF;  // PcRec.kind of a position that holds no ENTRY / EXIT
 struct __align__(8) PcRec {
   uint64_t ts;
   uint64_t thread;     // vpid << 32 | vtid
   uint32_t host;       // the buffer's host
-  uint32_t gpos;       // global event index (stream order): ties of equal timestamps
   uint32_t slot;       // ENTRY: its interval slot (global index)
   uint32_t pos;        // order position of its packet
   uint16_t func;
-  uint8_t kind, err;   // kEntry / kExit; EXIT result != 0
-  uint32_t pad;
+  uint8_t kind, err;   // kEntry / kExit / kPcNone; EXIT result != 0
 };
+static_assert(sizeof(PcRec) == 32, "per-CPU record");
 struct PcParams {
   const uint8_t *packets;
   uint32_t P, n_classes;
@@ -297,7 +343,8 @@ struct PcParams {
   const PkDesc *desc;
   const uint64_t *classes;
   const uint32_t *stream_host;   // host id per stream
-  PcRec *rec;
+  PcRec *rec;                    // at pc_base[order position] + event index in the packet
+  const uint64_t *pc_base;       // per order position: per-CPU events before its packet
   uint64_t cap;
   unsigned long long *count;     // records written (may pass cap: then nothing past it is written)
   thapi_interval *slots;
@@ -307,11 +354,17 @@ struct PcParams {
   unsigned long long *tminmax;
 };
 cudaError_t launch_percpu_decode(const PcParams &p, uint32_t nw, uint32_t grid, cudaStream_t s);
-// Pairs the threads of the per-CPU records: sorts them by (host, vpid, vtid,
-// ts, position), scans the depth monoid per thread, matches each entry with
-// its exit by (thread, level); tallies into per-thread cells, writes the
-// entries' interval slots and raises their packets' interval counts.
-// *n_threads (host) = threads; cells / keys are allocated here (sc).
+// Per order position: the packet's events if it is a per-CPU buffer, else 0
+// (their exclusive scan places the records).
+void launch_pc_count(const PkDesc *desc, uint64_t n, uint64_t *out, cudaStream_t s);
+// Pairs the threads of the per-CPU records (m_all positions in position
+// order, m of them ENTRY / EXIT records): thread numbers from a table of
+// (host, vpid, vtid) and one stable sort by (thread, ts), or stable sorts by
+// ts, thread and host when the table is full or two keys share a
+// fingerprint; then the depth monoid scanned per thread and each entry
+// matched with its exit by (thread, level).  Tallies into per-thread cells,
+// writes the entries' interval slots and raises their packets' interval
+// counts; cells / keys are allocated here (sc).
 struct PcPairOut {
   Cell *cells = nullptr;           // [threads * n_funcs]
   Cell *self_cells = nullptr;      // [threads * n_funcs], self time (when asked for)
@@ -332,11 +385,10 @@ struct SelfIn {
   int num_sms;
 };
 int self_time(const SelfIn &in, Cell *cells, uint64_t *word, Scratch &sc, cudaStream_t s);
-// word: two device words (threads; largest level).  self_cells (non-null: self
-// time on) receives the threads' self-time cells [threads * n_funcs].
-int percpu_pair(PcRec *rec, uint64_t m, uint64_t t_min, int ts_bits, uint32_t n_funcs, thapi_interval *slots,
-                uint32_t *sum_nvalid, unsigned long long *diag, uint64_t *word, bool self_on, Scratch &sc,
-                cudaStream_t s, PcPairOut *out);
+// self_on: also the threads' self-time cells (PcPairOut.self_cells).
+int percpu_pair(PcRec *rec, uint64_t m_all, uint64_t m, uint64_t t_min, int ts_bits, uint32_t n_funcs,
+                thapi_interval *slots, uint32_t *sum_nvalid, unsigned long long *diag, bool self_on, int num_sms,
+                Scratch &sc, cudaStream_t s, PcPairOut *out);
 cudaError_t launch_decode_warp(const DecodeParams &p, uint32_t nw, uint32_t grid, cudaStream_t s);
 // Splits the stream-ordered packets into `grid` contiguous runs of about equal
 // cost (events + a per-packet constant): run_start[0..grid].

@@ -108,8 +108,25 @@ __global__ void k_self_spos(const SelfRec *rec, const uint32_t *val, uint64_t n,
   if (i < n) spos[i] = rec[val[i]].entry_pos;
 }
 
+// First index in [lo, hi) whose (key, pos) is not below (tk, tp).
+template <class P>
+__device__ __forceinline__ uint64_t lower_kp(const uint64_t *key, const P *pos, uint64_t lo, uint64_t hi, uint64_t tk,
+                                             uint64_t tp) {
+  while (lo < hi) {
+    const uint64_t mid = (lo + hi) >> 1;
+    const uint64_t km = key[mid];
+    if (km < tk || (km == tk && (uint64_t)pos[mid] < tp))
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
 // Sorted order: the parent of the interval at k, if it is one, is the last
-// entry of the (stream, level - 1) run before it in entry order.
+// entry of the (stream, level - 1) run before it in entry order (a binary
+// search over the positions before k; neighbouring lanes share its first
+// steps in cache).
 __global__ void k_self_child(const uint64_t *key, const uint32_t *val, const uint64_t *spos, const SelfRec *rec,
                              uint64_t n, int lb, uint64_t sentinel, unsigned long long *child) {
   const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,34 +134,24 @@ __global__ void k_self_child(const uint64_t *key, const uint32_t *val, const uin
   const uint64_t kk = key[k];
   if (kk >= sentinel || (kk & ((1ull << lb) - 1)) == 0) return;
   const uint64_t target = kk - 1, pos = spos[k];
-  uint64_t lo = 0, hi = k;  // the (stream, level - 1) run lies before k
-  while (lo < hi) {
-    const uint64_t mid = (lo + hi) >> 1;
-    const uint64_t km = key[mid];
-    if (km < target || (km == target && spos[mid] < pos))
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
+  const uint64_t lo = lower_kp(key, spos, 0, k, target, pos);
   if (lo == 0) return;
-  const uint64_t j = lo - 1;
-  if (key[j] != target) return;
-  const uint32_t pj = val[j];
+  const uint64_t jp = lo - 1;
+  if (key[jp] != target) return;
+  const uint32_t pj = val[jp];
   if (rec[pj].exit_pos > pos) atomicAdd(&child[pj], (unsigned long long)rec[val[k]].dur);
 }
 
 __global__ void k_self_tally(const SelfRec *rec, const unsigned long long *child, uint64_t n, Cell *cells) {
-  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const SelfRec r = rec[i];
-  if (r.cell == ~0u) return;
-  const unsigned long long self = r.dur - child[i];
-  Cell &c = cells[r.cell];
-  atomicAdd(&c.count, 1ull);
-  atomicAdd(&c.total, self);
-  atomicMin(&c.mn, self);
-  atomicMax(&c.mx, self);
-  if (r.err) atomicAdd(&c.err, 1ull);
+  __shared__ CellPart scr[kT];
+  const uint64_t i = spread(blockIdx.x, gridDim.x) * blockDim.x + threadIdx.x;
+  SelfRec r{0, 0, 0, ~0u, 0};
+  unsigned long long self = 0;
+  if (i < n) {
+    r = rec[i];
+    self = r.dur - child[i];
+  }
+  warp_tally(cells, r.cell, r.cell != ~0u, self, r.err != 0, scr + (threadIdx.x & ~31u));
 }
 
 }  // namespace

@@ -124,3 +124,58 @@ def event_lines(events, func_names, host_names, stream_table, limit: int | None 
             int(r["ts"]), host_names[host], pid, tid, func_names[int(r["func_id"])], _KIND.get(kind, "event"),
             ", ".join(fields)))
     return out
+
+
+def func_layers(ctx, trace_id: int):
+    """Layer of every function of a loaded trace (thapi_trace_func_layer)."""
+    from .thapi import thapi_trace_func_layer, thapi_trace_info_get
+    h = ctx.handle if hasattr(ctx, "handle") else ctx
+    n = thapi_trace_info_get(h, trace_id)["n_funcs"]
+    return [thapi_trace_func_layer(h, trace_id, i) for i in range(n)]
+
+
+def _table(header, body, title):
+    widths = [max(len(header[i]), *(len(b[i]) for b in body)) if body else len(header[i]) for i in range(len(header))]
+    lines = [title] if title else []
+    lines.append(" | ".join(h.rjust(w) for h, w in zip(header, widths)) + " |")
+    lines.append("-|-".join("-" * w for w in widths) + "-|")
+    for b in body:
+        lines.append(" | ".join(c.rjust(w) for c, w in zip(b, widths)) + " |")
+    return "\n".join(lines) + "\n"
+
+
+def self_table(rows, self_rows, func_names, func_layers=None, title: str | None = None) -> str:
+    """Inclusive and self time side by side, per function, ordered by self time
+    descending (the layering view of Sec. 4.3: how much of hipDeviceSynchronize
+    is its own time and how much the zeEventHostSynchronize calls inside it
+    take).  Self(%) = self / inclusive time of the same function; Average is
+    the mean self time per call."""
+    incl = {d["key"]: d for d in summarize(rows, func_names)}
+    items = summarize(self_rows, func_names)
+    items.sort(key=lambda d: (-d["total"], d["name"]))
+    header = ["Name", "Layer", "Time", "Self", "Self(%)", "Calls", "Average"]
+    body = []
+    for d in items:
+        t = incl.get(d["key"], {}).get("total", 0)
+        layer = str(func_layers[d["key"][-1]]) if func_layers is not None else "-"
+        body.append([d["name"], layer, fmt_ns(t), fmt_ns(d["total"]),
+                     fmt_pct(100.0 * d["total"] / t) if t else "-", str(d["count"]),
+                     fmt_ns(d["total"] / d["count"]) if d["count"] else "-"])
+    return _table(header, body, title)
+
+
+def layer_summary(self_rows, func_layers, layer_names=None, title: str | None = None):
+    """Self time summed per layer (the time each API layer spends itself), as
+    (text, {layer: (self_ns, calls)}); Self(%) of the sum over all layers."""
+    acc = {}
+    for r in np.asarray(self_rows).tolist():
+        func, count, total = r[3], r[4], r[5]
+        a = acc.setdefault(func_layers[func], [0, 0])
+        a[0] = (a[0] + total) & ((1 << 64) - 1)
+        a[1] += count
+    grand = float(sum(v[0] for v in acc.values())) or 1.0
+    body = []
+    for layer in sorted(acc, key=lambda k: (-acc[k][0], k)):
+        name = layer_names[layer] if layer_names is not None else str(layer)
+        body.append([name, fmt_ns(acc[layer][0]), fmt_pct(100.0 * acc[layer][0] / grand), str(acc[layer][1])])
+    return _table(["Layer", "Self", "Self(%)", "Calls"], body, title), {k: tuple(v) for k, v in acc.items()}

@@ -38,7 +38,7 @@ EXPORTED = (
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
     "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode", "thapi_ctx_set_self_time",
-    "thapi_self_tally",
+    "thapi_self_tally", "thapi_trace_func_layer",
 )
 
 
@@ -73,7 +73,7 @@ class LoadTiming(ctypes.Structure):
                                                "sort_ms", "gather_ms", "total_ms")] + \
                [(f, ctypes.c_uint64) for f in ("analyze_read_bytes", "analyze_write_bytes", "analyze_launches",
                                                 "launches")] + \
-               [(f, ctypes.c_float) for f in ("join_ms", "self_ms")]
+               [(f, ctypes.c_float) for f in ("join_ms", "self_ms", "percpu_ms", "reserved_ms")]
 
     def as_dict(self):
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
@@ -122,6 +122,7 @@ def library():
         "thapi_ctx_set_timing": ([vp, i32], i32),
         "thapi_ctx_set_self_time": ([vp, i32], i32),
         "thapi_self_tally": ([vp, u64, vp, u64, P(u64)], i32),
+        "thapi_trace_func_layer": ([vp, u64, u32, P(u32)], i32),
         "thapi_trace_timing": ([vp, u64, P(LoadTiming)], i32),
         "thapi_kernel_launches": ([], u64),
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
@@ -331,6 +332,12 @@ def thapi_strerror(code: int) -> str:
 
 def thapi_ctx_set_timing(ctx: int, enable: bool = True) -> None:
     _check(library().thapi_ctx_set_timing(ctx, 1 if enable else 0), "thapi_ctx_set_timing")
+
+
+def thapi_trace_func_layer(ctx: int, trace_id: int, func_id: int) -> int:
+    v = ctypes.c_uint32()
+    _check(library().thapi_trace_func_layer(ctx, trace_id, func_id, ctypes.byref(v)), "thapi_trace_func_layer")
+    return int(v.value)
 
 
 def thapi_ctx_set_self_time(ctx: int, enable: bool = True) -> None:

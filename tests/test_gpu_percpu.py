@@ -120,3 +120,28 @@ def test_per_cpu_needs_packets_of_at_most_32k(ctx):
     with pytest.raises(thapi.ThapiError) as ei:
         ctx.load(tb.build())
     assert ei.value.code == thapi.E_UNSUPPORTED
+
+
+def test_per_cpu_many_threads_take_the_sort_path(ctx):
+    """40,000 threads (more than the thread table takes) in two per-CPU buffers:
+    the order comes from the fallback sorts; results as the oracle's."""
+    tb = TraceBuilder(packet_bytes=4096)
+    h = tb.add_host("h")
+    f, ef, xf = tb.add_call_func("f")
+    g, eg, xg = tb.add_call_func("g")
+    c0, c1 = tb.add_stream(h, 0, 0, 2), tb.add_stream(h, 0, 1, 2)
+    ev0, ev1 = [], []
+    t = 1000
+    for k in range(40_000):
+        th = (7 + k % 3, 100 + k)
+        (ev0 if k % 2 else ev1).append(Ev(ef, t, ctx=th))
+        (ev1 if k % 5 == 0 else (ev0 if k % 2 else ev1)).append(Ev(eg, t + 1, ctx=th))
+        (ev0 if k % 2 else ev1).append(Ev(xg, t + 2, result=0, ctx=th))
+        (ev0 if k % 2 else ev1).append(Ev(xf if k % 17 else xg, t + 4, result=k % 2, ctx=th))
+        t += 3
+    ev0.sort(key=lambda e: e.ts)
+    ev1.sort(key=lambda e: e.ts)
+    tb.place(tb.stream_events(c0, ev0, ts_begin=1000))
+    tb.place(tb.stream_events(c1, ev1, ts_begin=1000))
+    o = assert_parity(ctx, tb.build())
+    assert len(o.rows) > 40_000

@@ -688,3 +688,32 @@ def test_self_time_per_cpu_equals_per_thread():
                                       seed=21, p_drop=0.01))
     pc = to_per_cpu(b, n_cpus=3, seed=21)
     assert rows_equal(oracle.run(b).self_rows, oracle.run(pc).self_rows)
+
+
+@pytest.mark.parametrize("over", [
+    dict(total_calls=20_000, n_hosts=2, pids_per_host=2, tids_per_pid=3, n_cpus=4, slice_ns=30_000.0, seed=41,
+         p_drop=0.005),
+    dict(total_calls=15_000, n_hosts=1, pids_per_host=1, tids_per_pid=4, n_cpus=2, slice_ns=5_000.0, seed=42,
+         p_ext=0.02, packet_bytes=1024),
+])
+def test_generator_per_cpu_mode_writes_the_same_calls(over):
+    """The generator's per-CPU buffers (threads scheduled onto CPUs in time
+    slices) carry the same calls as its per-thread streams with the same seed:
+    the oracle gives the same tally, self time, diagnostics and intervals."""
+    per_cpu = tg.generate(tg.preset("large", **over))[0]
+    per_thread = tg.generate(tg.preset("large", **dict(over, n_cpus=0)))[0]
+    a, b = oracle.run(per_thread), oracle.run(per_cpu)
+    assert b.code == oracle.OK
+    st = stream_table(per_cpu)
+    assert np.all(st[:, 3] == 2) and len(st) == over["n_hosts"] * over["n_cpus"]
+    assert rows_equal(a.rows, b.rows) and rows_equal(a.self_rows, b.self_rows)
+    for k in ("events", "pairs", "unmatched_entries", "unmatched_exits", "mismatched_pairs", "other_events",
+              "discarded"):
+        assert a.diag[k] == b.diag[k], k
+    assert _iv_key(a.intervals) == _iv_key(b.intervals)
+    ev = oracle.decode(per_cpu)
+    # threads migrate: some thread has events in more than one buffer
+    sids = {}
+    for t, s in zip(ev["vtid"].tolist(), ev["stream_id"].tolist()):
+        sids.setdefault(t, set()).add(s)
+    assert max(len(v) for v in sids.values()) > 1

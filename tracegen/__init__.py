@@ -72,6 +72,9 @@ class TgConfig(ctypes.Structure):
         ("p_nest", ctypes.c_double),
         ("p_sample", ctypes.c_double),
         ("dev_dur_median_ns", ctypes.c_double),
+        ("n_cpus", ctypes.c_uint32),       # > 0: per-CPU buffers (n_cpus per host), threads scheduled onto CPUs
+        ("reserved", ctypes.c_uint32),
+        ("slice_ns", ctypes.c_double),     # per-CPU scheduling time slice
     ]
 
     def as_dict(self):
@@ -167,6 +170,12 @@ def preset(name: str, **overrides) -> TgConfig:
                     packet_bytes=16384, model=MODEL_DEVICE, max_depth=1, n_flat=16,
                     n_device_streams=64, dur_median_ns=5000.0, dur_sigma=1.0,
                     gap_mean_ns=1000.0, var_min=0, var_max=48, p_err=0.01, dev_dur_median_ns=400.0)
+    elif name == "percpu":  # the large workload's calls written as per-CPU buffers (32 CPUs per host)
+        base = dict(seed=1, total_calls=50_000_000, n_hosts=8, pids_per_host=8, tids_per_pid=8,
+                    packet_bytes=16384, model=MODEL_LAYERED, max_depth=6,
+                    n_portable=60, n_vendor=120, n_mpi=30,
+                    dur_median_ns=5000.0, dur_sigma=1.0, gap_mean_ns=1000.0,
+                    var_min=0, var_max=48, p_err=0.01, p_nest=0.25, n_cpus=32, slice_ns=200_000.0)
     else:
         raise KeyError(name)
     base.update(overrides)

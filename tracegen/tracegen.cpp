@@ -126,6 +126,9 @@ typedef struct tg_config {
   double p_nest;            // probability that a nestable call has children
   double p_sample;          // probability of an extra SAMPLE event after a call
   double dev_dur_median_ns; // device model: log-normal median of a command's device time (0 = dur_median_ns)
+  uint32_t n_cpus;          // > 0: per-CPU buffers, n_cpus per host (flat and layered models)
+  uint32_t reserved;
+  double slice_ns;          // per-CPU buffers: scheduling time slice
 } tg_config;
 
 // Ground-truth record of one generated call (entry and exit as written, before drops).
@@ -173,6 +176,7 @@ struct Ev {
   uint16_t var_len;
   bool dropped;
   bool force_ext;
+  uint32_t vpid, vtid;  // the thread, written into per-CPU buffer events
 };
 
 struct StreamDesc {
@@ -296,6 +300,8 @@ struct PacketSink {
   Xoshiro256ss *rng_bytes = nullptr;
   std::vector<uint64_t> ts_begins;  // pass 1 output
   std::vector<tg_event> *events = nullptr;
+  uint32_t hdr = 8;                 // event header bytes: 16 in a per-CPU buffer (+ u32 vpid, u32 vtid)
+  std::vector<Ev> *capture = nullptr;  // non-null: keep the events (a thread's, before CPU scheduling)
 
   uint32_t seq = 0;
   uint32_t used = 0, n = 0, discarded = 0;
@@ -337,6 +343,10 @@ struct PacketSink {
     open = false;
   }
   void put(const Ev &ev) {
+    if (capture) {
+      capture->push_back(ev);
+      return;
+    }
     if (ev.dropped) {
       ++discarded;
       return;
@@ -344,13 +354,13 @@ struct PacketSink {
     const ClassInfo &ci = (*classes)[ev.cls];
     uint64_t delta = ev.ts - prev_ts;
     bool ext = ev.force_ext || ev.ts < prev_ts || delta >= kDeltaLimit;
-    uint32_t size = 8u + (ext ? 8u : 0u) + ci.fixed + align4(ev.var_len);
+    uint32_t size = hdr + (ext ? 8u : 0u) + ci.fixed + align4(ev.var_len);
     if (used + size > P - 32u) {
       close_packet();
       open_packet(prev_ts);
       delta = ev.ts - prev_ts;
       ext = ev.force_ext || ev.ts < prev_ts || delta >= kDeltaLimit;
-      size = 8u + (ext ? 8u : 0u) + ci.fixed + align4(ev.var_len);
+      size = hdr + (ext ? 8u : 0u) + ci.fixed + align4(ev.var_len);
     }
     if (bytes) {
       uint8_t *p = cur + 32 + used;
@@ -358,10 +368,14 @@ struct PacketSink {
       std::memcpy(p, &tsw, 4);
       std::memcpy(p + 4, &ev.cls, 2);
       std::memcpy(p + 6, &ev.var_len, 2);
-      uint32_t o = 8;
+      uint32_t o = hdr;
+      if (hdr == 16) {
+        std::memcpy(p + 8, &ev.vpid, 4);
+        std::memcpy(p + 12, &ev.vtid, 4);
+      }
       if (ext) {
-        std::memcpy(p + 8, &ev.ts, 8);
-        o = 16;
+        std::memcpy(p + hdr, &ev.ts, 8);
+        o = hdr + 8;
       }
       // fixed part: filler handles, then the typed fields
       for (uint32_t k = 0; k < ci.fixed; k += 8) {
@@ -564,6 +578,17 @@ struct Plan {
     bool host_dropped;
   };
   std::vector<std::vector<DevWork>> dev_work;
+  // per-CPU buffers: every thread's events (host stream order), and per
+  // buffer (host * n_cpus + cpu) references to them in (ts, thread, index) order
+  struct EvRef {
+    uint64_t ts;
+    uint32_t thread, idx;
+  };
+  bool per_cpu = false;
+  std::vector<std::vector<Ev>> th_events;
+  std::vector<std::vector<EvRef>> cpu_refs;
+  std::vector<StreamDesc> out_streams;  // the file's stream table
+  std::vector<uint64_t> out_t0;
 };
 
 void for_streams(uint32_t n, uint32_t threads, const std::function<void(uint32_t)> &fn) {
@@ -676,6 +701,56 @@ void run_stream(Plan &pl, uint32_t s, PacketSink &sink, std::vector<tg_call> *tr
   }
 }
 
+// A per-CPU buffer: the events its CPU ran, each naming its thread.
+void run_cpu_stream(Plan &pl, uint32_t o, PacketSink &sink) {
+  sink.P = pl.c.packet_bytes;
+  sink.stream = o;
+  sink.classes = &pl.m.classes;
+  sink.hdr = 16;
+  sink.start(pl.out_t0[o]);
+  for (const Plan::EvRef &r : pl.cpu_refs[o]) {
+    Ev ev = pl.th_events[r.thread][r.idx];
+    ev.vpid = pl.m.streams[r.thread].pid;
+    ev.vtid = pl.m.streams[r.thread].tid;
+    sink.put(ev);
+  }
+  sink.finish();
+}
+
+// Per-CPU scheduling: time is cut into slices of slice_ns; in slice j the
+// k-th thread of a host runs on CPU (k + j) mod n_cpus, so threads migrate at
+// slice boundaries and a CPU interleaves the threads it runs in one slice.
+void schedule_cpus(Plan &pl) {
+  const tg_config &c = pl.c;
+  const uint32_t C = c.n_cpus, T = c.pids_per_host * c.tids_per_pid;
+  const uint64_t slice = std::max<uint64_t>(1, (uint64_t)std::llround(c.slice_ns));
+  pl.cpu_refs.assign((size_t)c.n_hosts * C, {});
+  pl.out_streams.clear();
+  for (uint32_t h = 0; h < c.n_hosts; ++h)
+    for (uint32_t q = 0; q < C; ++q) pl.out_streams.push_back({h, 0, q, 2});
+  for_streams(c.n_hosts, c.n_threads, [&](uint32_t h) {
+    for (uint32_t k = 0; k < T; ++k) {
+      const uint32_t th = h * T + k;
+      const std::vector<Ev> &ev = pl.th_events[th];
+      for (uint32_t i = 0; i < ev.size(); ++i) {
+        const uint32_t cpu = (uint32_t)((k + ev[i].ts / slice) % C);
+        pl.cpu_refs[(size_t)h * C + cpu].push_back({ev[i].ts, th, i});
+      }
+    }
+    for (uint32_t q = 0; q < C; ++q) {
+      auto &v = pl.cpu_refs[(size_t)h * C + q];
+      std::sort(v.begin(), v.end(), [](const Plan::EvRef &a, const Plan::EvRef &b) {
+        if (a.ts != b.ts) return a.ts < b.ts;
+        if (a.thread != b.thread) return a.thread < b.thread;
+        return a.idx < b.idx;
+      });
+    }
+  });
+  pl.out_t0.assign(pl.out_streams.size(), 0);
+  for (size_t o = 0; o < pl.out_streams.size(); ++o)
+    pl.out_t0[o] = pl.cpu_refs[o].empty() ? pl.t0[0] : pl.cpu_refs[o][0].ts;
+}
+
 void put32(std::vector<uint8_t> &b, uint64_t off, uint32_t v) { std::memcpy(&b[off], &v, 4); }
 
 }  // namespace
@@ -713,6 +788,8 @@ void tg_default_config(tg_config *c) {
   c->p_nest = 0.3;
   c->p_sample = 0.0;
   c->dev_dur_median_ns = 0.0;
+  c->n_cpus = 0;
+  c->slice_ns = 200000.0;
 }
 
 // Validates the config and runs the sizing pass.  Returns nullptr on a bad config.
@@ -727,8 +804,9 @@ tg_plan *tg_plan_create(const tg_config *cfg) {
   if ((c.model == MODEL_FLAT || c.model == MODEL_DEVICE) && c.n_flat == 0) return nullptr;
   if (c.model == MODEL_LAYERED && (c.n_portable == 0 || c.n_vendor == 0 || c.n_mpi == 0)) return nullptr;
   if (c.model == MODEL_DEVICE && c.n_device_streams == 0) return nullptr;
+  if (c.n_cpus && (c.model == MODEL_DEVICE || c.n_cpus > 4096 || !(c.slice_ns >= 1.0))) return nullptr;
   // largest event must fit a packet
-  uint32_t max_ev = 8 + 8 + 16 + align4(c.var_max);
+  uint32_t max_ev = (c.n_cpus ? 16 : 8) + 8 + 16 + align4(c.var_max);
   if (max_ev > P - 32) return nullptr;
 
   Plan *pl = new (std::nothrow) Plan();
@@ -750,11 +828,29 @@ tg_plan *tg_plan_create(const tg_config *cfg) {
   // sizing pass
   std::vector<std::vector<uint64_t>> ts_begins(S);
   std::vector<std::vector<IssuedCmd>> cmds(HS);
-  for_streams(HS, c.n_threads, [&](uint32_t s) {
-    PacketSink sink;
-    run_stream(*pl, s, sink, nullptr, c.model == MODEL_DEVICE ? &cmds[s] : nullptr);
-    ts_begins[s] = std::move(sink.ts_begins);
-  });
+  if (c.n_cpus) {  // per-CPU buffers: threads' events kept, scheduled onto CPUs, then sized per buffer
+    pl->per_cpu = true;
+    pl->th_events.assign(HS, {});
+    for_streams(HS, c.n_threads, [&](uint32_t s) {
+      PacketSink sink;
+      sink.capture = &pl->th_events[s];
+      run_stream(*pl, s, sink, nullptr, nullptr);
+    });
+    schedule_cpus(*pl);
+    S = (uint32_t)pl->out_streams.size();
+    ts_begins.assign(S, {});
+    for_streams(S, c.n_threads, [&](uint32_t o) {
+      PacketSink sink;
+      run_cpu_stream(*pl, o, sink);
+      ts_begins[o] = std::move(sink.ts_begins);
+    });
+  } else {
+    for_streams(HS, c.n_threads, [&](uint32_t s) {
+      PacketSink sink;
+      run_stream(*pl, s, sink, nullptr, c.model == MODEL_DEVICE ? &cmds[s] : nullptr);
+      ts_begins[s] = std::move(sink.ts_begins);
+    });
+  }
   if (c.model == MODEL_DEVICE) {
     plan_device_work(*pl, cmds);
     // a device stream's first packet starts no later than its first event, so
@@ -816,7 +912,10 @@ tg_plan *tg_plan_create(const tg_config *cfg) {
 
 uint64_t tg_plan_bytes(const tg_plan *p) { return reinterpret_cast<const Plan *>(p)->total_bytes; }
 uint64_t tg_plan_packets(const tg_plan *p) { return reinterpret_cast<const Plan *>(p)->n_packets; }
-uint32_t tg_plan_streams(const tg_plan *p) { return (uint32_t)reinterpret_cast<const Plan *>(p)->m.streams.size(); }
+uint32_t tg_plan_streams(const tg_plan *p) {
+  const Plan *pl = reinterpret_cast<const Plan *>(p);
+  return (uint32_t)(pl->per_cpu ? pl->out_streams.size() : pl->m.streams.size());
+}
 
 // Writes the trace into out[0 .. tg_plan_bytes).  Optional ground truth:
 // calls (one tg_call per generated call, stream-major, entry order) and
@@ -829,7 +928,8 @@ int tg_plan_write(tg_plan *p, void *out, tg_call *calls, uint64_t calls_cap, uin
   Plan &pl = *reinterpret_cast<Plan *>(p);
   const tg_config &c = pl.c;
   Model &m = pl.m;
-  uint32_t S = (uint32_t)m.streams.size();
+  const std::vector<StreamDesc> &file_streams = pl.per_cpu ? pl.out_streams : m.streams;
+  uint32_t S = (uint32_t)file_streams.size();
   std::vector<uint8_t> head(pl.packets_off, 0);
   put32(head, 0, kTraceMagic);
   uint16_t ver = 1, hb = 128;
@@ -850,10 +950,10 @@ int tg_plan_write(tg_plan *p, void *out, tg_call *calls, uint64_t calls_cap, uin
   std::memcpy(&head[88], &pl.packets_off, 8);
   for (uint32_t s = 0; s < S; ++s) {
     uint64_t o = pl.stream_table_off + 16ull * s;
-    put32(head, o, m.streams[s].host);
-    put32(head, o + 4, m.streams[s].pid);
-    put32(head, o + 8, m.streams[s].tid);
-    put32(head, o + 12, m.streams[s].flags);
+    put32(head, o, file_streams[s].host);
+    put32(head, o + 4, file_streams[s].pid);
+    put32(head, o + 8, file_streams[s].tid);
+    put32(head, o + 12, file_streams[s].flags);
   }
   for (uint32_t k = 0; k < m.classes.size(); ++k) {
     uint64_t o = pl.class_table_off + 16ull * k;
@@ -876,6 +976,7 @@ int tg_plan_write(tg_plan *p, void *out, tg_call *calls, uint64_t calls_cap, uin
   std::memcpy(bytes, head.data(), head.size());
 
   bool want_truth = calls != nullptr || events != nullptr || n_calls != nullptr || n_events != nullptr;
+  if (want_truth && pl.per_cpu) return 2;  // no ground truth for per-CPU buffers
   std::vector<std::vector<tg_call>> tcalls(want_truth ? S : 0);
   std::vector<std::vector<tg_event>> tevents(want_truth ? S : 0);
   auto body = [&](uint32_t s) {
@@ -887,6 +988,10 @@ int tg_plan_write(tg_plan *p, void *out, tg_call *calls, uint64_t calls_cap, uin
     rb.seed(stream_seed(c.seed, s, 1));
     sink.rng_bytes = &rb;
     sink.events = want_truth ? &tevents[s] : nullptr;
+    if (pl.per_cpu) {
+      run_cpu_stream(pl, s, sink);
+      return;
+    }
     std::vector<IssuedCmd> cmds;
     run_stream(pl, s, sink, want_truth ? &tcalls[s] : nullptr, c.model == MODEL_DEVICE ? &cmds : nullptr);
   };
