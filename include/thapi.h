@@ -294,7 +294,11 @@ typedef struct thapi_load_timing {
   float join_ms;                 /* device-activity pairing (includes one host wait) */
   float self_ms;                 /* self time (when on; includes host waits) */
   float percpu_ms;               /* per-CPU buffers: event records, thread order, pairing (includes host waits) */
-  float reserved_ms;
+  float percpu_decode_ms;        /* per-CPU buffers: the record-writing decode kernel alone */
+  uint64_t percpu_read_bytes;    /* sum over per-CPU packets of 32 + content_bytes (excluded from
+                                    analyze_read_bytes) */
+  uint64_t percpu_write_bytes;   /* written by that decode: 32 B per per-CPU event (its record or a
+                                    marked hole) and a 24 B interval slot per ENTRY */
 } thapi_load_timing;
 
 /* Enables (1) or disables (0) per-phase timing of subsequent loads. */

@@ -21,7 +21,7 @@ static_assert(sizeof(thapi_tally_row) == 56, "tally row");
 static_assert(sizeof(thapi_interval) == 24, "interval");
 static_assert(sizeof(thapi_event) == 40, "event");
 static_assert(sizeof(thapi_trace_info) == 104, "trace info");
-static_assert(sizeof(thapi_load_timing) == 80, "load timing");
+static_assert(sizeof(thapi_load_timing) == 96, "load timing");
 
 struct TraceRec {
   cudaStream_t stream = nullptr;
@@ -68,7 +68,7 @@ uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 // CUDA events bracketing the phases of one load (only when timing is on).
 struct PhaseClock {
-  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kJo0, kJo1, kTa1, kSe0, kSe1, kPc0, kPc1, kCo0, kCo1, kSo1, kGa1, kN };
+  enum { kIdx0 = 0, kIdx1, kAn0, kAn1, kDn0, kDn1, kFr0, kFr1, kJo0, kJo1, kTa1, kSe0, kSe1, kPc0, kPc1, kPd0, kPd1, kCo0, kCo1, kSo1, kGa1, kN };
   cudaEvent_t ev[kN] = {};
   bool on = false, dense = false;
   void init(bool enable) {
@@ -305,6 +305,8 @@ enum Misc {
   mPartMax,                   // records of the largest command-id partition
   mPcCount,                   // per-CPU records
   mPcAll,                     // per-CPU buffers: events
+  mPcRead,                    // per-CPU buffers: packet bytes (32 + content)
+  mPcEntries,                 // per-CPU buffers: ENTRY events (interval slots)
   mPcRows,                    // per-CPU thread tally rows
   mMerged,                    // tally rows after merging the thread rows
   mSelfWord,                  // self time: largest level
@@ -781,7 +783,10 @@ int Loader::run() {
     pp.tminmax = reinterpret_cast<unsigned long long *>(misc_ + mTmin);
     const uint32_t nw = decode_warps(P, L.n_classes, c_->smem_per_block);
     const uint64_t g = std::min<uint64_t>((n + nw - 1) / nw, (uint64_t)c_->num_sms * 4);
+    clk_.rec(PhaseClock::kPd0, s_);
     CK(launch_percpu_decode(pp, nw, (uint32_t)std::max<uint64_t>(g, 1), s_));
+    clk_.rec(PhaseClock::kPd1, s_);
+    launch_pc_bytes(desc, sum_nslot, n, reinterpret_cast<unsigned long long *>(misc_ + mPcRead), s_);
     if ((rc = sync_misc()) != THAPI_OK) return rc;
     if (misc_h_[mContentErr] != ~0ull) {
       const unsigned long long k = misc_h_[mContentErr];
@@ -1018,7 +1023,9 @@ int Loader::run() {
     thapi_load_timing &t = tr_->timing;
     t.launches = launches_total() - launches0;
     t.analyze_launches = analyze_launches;
-    t.analyze_read_bytes = misc_h_[mReadBytes];
+    t.analyze_read_bytes = misc_h_[mReadBytes] - misc_h_[mPcRead];
+    t.percpu_read_bytes = misc_h_[mPcRead];
+    t.percpu_write_bytes = 32ull * misc_h_[mPcAll] + sizeof(thapi_interval) * misc_h_[mPcEntries];
     t.analyze_write_bytes = misc_h_[mSlots] * sizeof(thapi_interval) +
                             (dev_on ? misc_h_[mCmdCount0] * sizeof(CmdBegin) + misc_h_[mCmdCount0 + 1] * sizeof(CmdEnd) +
                                           misc_h_[mCmdCount0 + 2] * sizeof(CmdHost)
@@ -1031,6 +1038,7 @@ int Loader::run() {
       t.join_ms = dev_on ? clk_.ms(PhaseClock::kJo0, PhaseClock::kJo1) : 0.f;
       t.self_ms = self_on ? clk_.ms(PhaseClock::kSe0, PhaseClock::kSe1) : 0.f;
       t.percpu_ms = has_pc ? clk_.ms(PhaseClock::kPc0, PhaseClock::kPc1) : 0.f;
+      t.percpu_decode_ms = has_pc ? clk_.ms(PhaseClock::kPd0, PhaseClock::kPd1) : 0.f;
       t.tally_ms = clk_.ms(dev_on ? PhaseClock::kJo1 : PhaseClock::kFr1, PhaseClock::kTa1);
       t.compact_ms = clk_.ms(PhaseClock::kCo0, PhaseClock::kCo1);
       t.sort_ms = clk_.ms(PhaseClock::kCo1, PhaseClock::kSo1);

@@ -357,6 +357,10 @@ cudaError_t launch_percpu_decode(const PcParams &p, uint32_t nw, uint32_t grid, 
 // Per order position: the packet's events if it is a per-CPU buffer, else 0
 // (their exclusive scan places the records).
 void launch_pc_count(const PkDesc *desc, uint64_t n, uint64_t *out, cudaStream_t s);
+// Over the per-CPU packets: out[0] += 32 + content bytes, out[1] += their
+// interval slots (ENTRY events, from sum_nslot after the decode).
+void launch_pc_bytes(const PkDesc *desc, const uint32_t *sum_nslot, uint64_t n, unsigned long long *out,
+                     cudaStream_t s);
 // Pairs the threads of the per-CPU records (m_all positions in position
 // order, m of them ENTRY / EXIT records): thread numbers from a table of
 // (host, vpid, vtid) and one stable sort by (thread, ts), or stable sorts by

@@ -446,6 +446,41 @@ static bool read_words(const uint64_t *d, uint64_t *h, int n, cudaStream_t s) {
          cudaStreamSynchronize(s) == cudaSuccess;
 }
 
+namespace {
+__global__ void k_pc_bytes(const PkDesc *desc, const uint32_t *sum_nslot, uint64_t n, unsigned long long *out) {
+  __shared__ unsigned long long part[kT / 32][2];
+  unsigned long long rd = 0, en = 0;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (uint64_t)gridDim.x * blockDim.x) {
+    const PkDesc d = dev::load_desc(desc + w);
+    if (d.group == kPerCpuGroup) {
+      rd += kPacketHeader + d.content;
+      en += sum_nslot[w];
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rd += __shfl_down_sync(0xffffffffu, rd, o);
+    en += __shfl_down_sync(0xffffffffu, en, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    part[threadIdx.x >> 5][0] = rd;
+    part[threadIdx.x >> 5][1] = en;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    unsigned long long v = 0;
+    for (int k = 0; k < kT / 32; ++k) v += part[k][threadIdx.x];
+    if (v) atomicAdd(&out[threadIdx.x], v);
+  }
+}
+}  // namespace
+
+void launch_pc_bytes(const PkDesc *desc, const uint32_t *sum_nslot, uint64_t n, unsigned long long *out,
+                     cudaStream_t s) {
+  if (!n) return;
+  k_pc_bytes<<<(unsigned)std::min<uint64_t>(blocks(n), 256), kT, 0, s>>>(desc, sum_nslot, n, out);
+  count_launches(1);
+}
+
 void launch_pc_count(const PkDesc *desc, uint64_t n, uint64_t *out, cudaStream_t s) {
   if (!n) return;
   k_pc_count<<<blocks(n), kT, 0, s>>>(desc, n, out);

@@ -73,7 +73,8 @@ class LoadTiming(ctypes.Structure):
                                                "sort_ms", "gather_ms", "total_ms")] + \
                [(f, ctypes.c_uint64) for f in ("analyze_read_bytes", "analyze_write_bytes", "analyze_launches",
                                                 "launches")] + \
-               [(f, ctypes.c_float) for f in ("join_ms", "self_ms", "percpu_ms", "reserved_ms")]
+               [(f, ctypes.c_float) for f in ("join_ms", "self_ms", "percpu_ms", "percpu_decode_ms")] + \
+               [(f, ctypes.c_uint64) for f in ("percpu_read_bytes", "percpu_write_bytes")]
 
     def as_dict(self):
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))

@@ -42,4 +42,4 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(thapi.Diag) == 64
     assert ctypes.sizeof(thapi.DeviceDiag) == 64
     assert ctypes.sizeof(thapi.TraceInfo) == 8 * 6 + 4 * 6 + 16 + 16
-    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4 + 4 * 4
+    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4 + 4 * 4 + 8 * 2
