@@ -213,6 +213,27 @@ int thapi_decode(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, thapi_event
                  void *cuda_stream);
 
 /* Releases a loaded trace's device results.  Errors: E_INVALID (unknown id). */
+/* Loads n traces as one trace (a batch: the per-rank traces of one run, say,
+ * analysed together, as the paper's tools read all ranks' traces at once,
+ * Sec. 3.4).  bytes[i] / nbytes[i]: trace i in HOST memory, or in device
+ * memory with on_device = 1 (16-byte aligned; read during the call only).
+ * The result is the trace whose streams are trace 0's, then trace 1's, ...
+ * (trace i's stream s becomes stream S_0 + ... + S_{i-1} + s) and whose hosts
+ * likewise follow one another (host ids offset the same way, host names from
+ * each trace's own string table); function and class ids are the traces'
+ * own, which must agree: every trace needs the same packet size, the same
+ * class table and the same function names and layers (E_UNSUPPORTED
+ * otherwise).  All packets of the batch are indexed, decoded, paired and
+ * tallied in one pass (one launch of each kernel over the batch's packet
+ * list); tally rows, timeline, device activity and self time are those of
+ * the combined trace, so trace i's rows are those whose host_id falls in its
+ * range and its intervals those whose stream_id does.  Errors: a trace that
+ * fails its file checks gives its code with thapi_last_error_location level
+ * 0 and packet = its index in the batch; packet and content errors give the
+ * packet's index in the batch (the traces' packets in order). */
+int thapi_trace_load_batch(thapi_ctx *ctx, const void *const *bytes, const uint64_t *nbytes, uint32_t n,
+                           int on_device, void *cuda_stream, thapi_trace_id *out);
+
 int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id);
 
 /* Copies the tally rows to HOST memory `rows` (capacity `cap` rows) and the

@@ -354,8 +354,22 @@ class Loader {
     tr_ = nullptr;
     return t;
   }
+  // a batch: n traces (host or device bytes) loaded as one trace
+  void set_batch(const void *const *bytes, const uint64_t *nbytes, uint32_t n, bool on_device) {
+    bptr_.assign(bytes, bytes + n);
+    bn_.assign(nbytes, nbytes + n);
+    bdev_ = on_device;
+    nbytes_ = 0;
+    for (uint32_t t = 0; t < n; ++t) nbytes_ += nbytes[t];
+  }
 
  private:
+  int parse_batch(HostLayout &L);
+  std::vector<const void *> bptr_;
+  std::vector<uint64_t> bn_;
+  std::vector<HostLayout> blay_;
+  bool bdev_ = false;
+
   template <class T>
   T *alloc(uint64_t count) {
     return static_cast<T *>(sc_.get((count ? count : 1) * sizeof(T)));
@@ -438,10 +452,72 @@ static int blocks_per_sm(thapi_ctx *c, uint32_t smem) {
   return b < 1 ? 1 : b;
 }
 
+// A batch's tables: every trace parsed and checked (same packet size, class
+// table, function names and layers), then one layout whose streams and hosts
+// are the traces' in order (host ids and stream ids offset by the earlier
+// traces' counts) and whose strings are the traces' string tables one after
+// the other.  A trace that fails its own checks reports level 0, packet =
+// its index in the batch.
+int Loader::parse_batch(HostLayout &L) {
+  const uint32_t nt = (uint32_t)bptr_.size();
+  blay_.assign(nt, HostLayout{});
+  for (uint32_t t = 0; t < nt; ++t) {
+    const uint8_t *p = static_cast<const uint8_t *>(bptr_[t]);
+    const Reader r{bdev_ ? nullptr : p, bdev_ ? p : nullptr, bn_[t], s_};
+    const int rc = parse_layout(r, blay_[t]);
+    if (rc != THAPI_OK) {
+      c_->err_level = 0;
+      c_->err_packet = t;
+      return rc;
+    }
+  }
+  const HostLayout &a = blay_[0];
+  auto fname = [](const HostLayout &x, uint32_t f) { return reinterpret_cast<const char *>(x.strings.data()) + x.func_name[f]; };
+  for (uint32_t t = 1; t < nt; ++t) {
+    const HostLayout &b = blay_[t];
+    if (b.P != a.P || b.cls != a.cls || b.n_funcs != a.n_funcs || b.func_layer != a.func_layer)
+      return THAPI_E_UNSUPPORTED;
+    for (uint32_t f = 0; f < a.n_funcs; ++f)
+      if (std::strcmp(fname(a, f), fname(b, f)) != 0) return THAPI_E_UNSUPPORTED;
+  }
+  L.P = a.P;
+  L.n_classes = a.n_classes;
+  L.n_funcs = a.n_funcs;
+  L.cls = a.cls;
+  L.func_name = a.func_name;
+  L.func_layer = a.func_layer;
+  L.strings = a.strings;
+  L.packets_off = 0;
+  uint64_t streams = 0, hosts = 0, packets = 0;
+  for (uint32_t t = 0; t < nt; ++t) {
+    const HostLayout &b = blay_[t];
+    const uint32_t soff = (uint32_t)L.strings.size();
+    if (t > 0) L.strings.insert(L.strings.end(), b.strings.begin(), b.strings.end());
+    for (uint32_t h = 0; h < b.n_hosts; ++h) L.host_name.push_back((t > 0 ? soff : 0u) + b.host_name[h]);
+    for (uint32_t s = 0; s < b.n_streams; ++s) {
+      L.srow.push_back(b.srow[4ull * s] + (uint32_t)hosts);
+      for (int j = 1; j < 4; ++j) L.srow.push_back(b.srow[4ull * s + j]);
+    }
+    streams += b.n_streams;
+    hosts += b.n_hosts;
+    packets += b.n_packets;
+  }
+  if (streams >= 0xFFFFFFFFull || hosts >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+  L.n_streams = (uint32_t)streams;
+  L.n_hosts = (uint32_t)hosts;
+  L.n_packets = packets;
+  return THAPI_OK;
+}
+
 int Loader::run() {
   HostLayout L;
-  const Reader r{host_, dev_, nbytes_, s_};
-  int rc = parse_layout(r, L);
+  int rc;
+  if (!bptr_.empty()) {
+    rc = parse_batch(L);
+  } else {
+    const Reader r{host_, dev_, nbytes_, s_};
+    rc = parse_layout(r, L);
+  }
   if (rc != THAPI_OK) return rc;
   const uint64_t n = L.n_packets;
   const uint32_t P = L.P, S = L.n_streams, F = L.n_funcs;
@@ -485,7 +561,7 @@ int Loader::run() {
   }
   // self time: a side record per slot, then per interval its record, sort keys and children's sum
   const bool self_on = c_->self_time != 0;
-  const uint64_t est = (host_ ? n * (uint64_t)P : 0) + n * 128 + cells * 80 + est_events * 24 +
+  const uint64_t est = (host_ || !bptr_.empty() ? n * (uint64_t)P : 0) + n * 128 + cells * 80 + est_events * 24 +
                        (dev_on ? est_events * 48 + cells * 80 : 0) + (self_on ? est_events * 96 + cells * 120 : 0);
   if (c_->cap && c_->used + est > c_->cap) return THAPI_E_NOMEM;
 
@@ -498,7 +574,38 @@ int Loader::run() {
 
   // ---- the packet area on the device
   const uint8_t *packets = nullptr;
-  if (host_) {
+  uint32_t *d_pk_trace = nullptr, *d_t_soff = nullptr, *d_t_ns = nullptr;
+  if (!bptr_.empty()) {  // a batch: every trace's packets in one area, in batch order
+    const uint32_t nt = (uint32_t)bptr_.size();
+    uint8_t *pk = alloc<uint8_t>(n * (uint64_t)P);
+    d_pk_trace = alloc<uint32_t>(n);
+    d_t_soff = alloc<uint32_t>(nt);
+    d_t_ns = alloc<uint32_t>(nt);
+    if (sc_.failed) return THAPI_E_NOMEM;
+    std::vector<uint32_t> pk_trace(n), t_soff(nt), t_ns(nt);
+    uint64_t at = 0;
+    uint32_t soff = 0;
+    for (uint32_t t = 0; t < nt; ++t) {
+      const HostLayout &b = blay_[t];
+      const uint8_t *src = static_cast<const uint8_t *>(bptr_[t]) + b.packets_off;
+      if (!bdev_ && b.n_packets)
+        CK(cudaMemcpyAsync(pk + at * P, src, b.n_packets * (uint64_t)P, cudaMemcpyHostToDevice, s_));
+      if (bdev_ && b.n_packets) {
+        if (reinterpret_cast<uintptr_t>(src) % 16 != 0) return THAPI_E_INVALID;
+        CK(cudaMemcpyAsync(pk + at * P, src, b.n_packets * (uint64_t)P, cudaMemcpyDeviceToDevice, s_));
+      }
+      for (uint64_t q = 0; q < b.n_packets; ++q) pk_trace[at + q] = t;
+      t_soff[t] = soff;
+      t_ns[t] = b.n_streams;
+      at += b.n_packets;
+      soff += b.n_streams;
+    }
+    if (n) CK(cudaMemcpyAsync(d_pk_trace, pk_trace.data(), 4ull * n, cudaMemcpyHostToDevice, s_));
+    CK(cudaMemcpyAsync(d_t_soff, t_soff.data(), 4ull * nt, cudaMemcpyHostToDevice, s_));
+    CK(cudaMemcpyAsync(d_t_ns, t_ns.data(), 4ull * nt, cudaMemcpyHostToDevice, s_));
+    CK(cudaStreamSynchronize(s_));  // the host tables above go out of scope
+    packets = pk;
+  } else if (host_) {
     uint8_t *pk = alloc<uint8_t>(n * (uint64_t)P);
     if (!pk) return THAPI_E_NOMEM;
     if (n) CK(cudaMemcpyAsync(pk, host_ + L.packets_off, n * (uint64_t)P, cudaMemcpyHostToDevice, s_));
@@ -534,7 +641,8 @@ int Loader::run() {
   unsigned long long *hdr_err = reinterpret_cast<unsigned long long *>(misc_ + mHdrErr);
   clk_.rec(PhaseClock::kIdx0, s_);
   launch_packet_headers(IndexParams{packets, reinterpret_cast<unsigned long long *>(misc_ + mReadBytes), P, n, S,
-                                    pk_stream, pk_nev, pk_content, pk_seq, pk_disc, pk_tsb, hdr_err},
+                                    pk_stream, pk_nev, pk_content, pk_seq, pk_disc, pk_tsb, hdr_err, d_pk_trace,
+                                    d_t_soff, d_t_ns},
                         s_);
   launch_stream_keys(pk_stream, n, keys, vals, s_);
   bool in_alt = false;
@@ -1114,6 +1222,30 @@ static int load_common(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, ui
   return THAPI_OK;
 }
 
+static int load_batch(thapi_ctx *c, const void *const *bytes, const uint64_t *nbytes, uint32_t n, int on_device,
+                      void *stream, thapi_trace_id *out) {
+  if (!c || !out || !bytes || !nbytes || n == 0) return THAPI_E_INVALID;
+  for (uint32_t t = 0; t < n; ++t)
+    if (!bytes[t]) return THAPI_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
+  c->err_level = 0;
+  c->err_packet = c->err_event = 0;
+  int rc;
+  TraceRec *tr = nullptr;
+  {
+    Loader ld(c, nullptr, nullptr, 0, static_cast<cudaStream_t>(stream));
+    ld.set_batch(bytes, nbytes, n, on_device != 0);
+    rc = ld.run();
+    if (rc == THAPI_OK) tr = ld.take();
+  }
+  if (rc != THAPI_OK) return rc;
+  const uint64_t id = c->next_id++;
+  c->traces[id] = tr;
+  c->used += tr->info.device_bytes;
+  *out = id;
+  return THAPI_OK;
+}
+
 static int decode_common(thapi_ctx *c, const uint8_t *host, uint64_t nbytes, thapi_event *out, uint64_t cap,
                          uint64_t *n_out, void *stream) {
   if (!c || !host || !n_out || (cap && !out)) return THAPI_E_INVALID;
@@ -1316,6 +1448,11 @@ int thapi_trace_load_device(thapi_ctx *ctx, const void *dev_bytes, uint64_t nbyt
 int thapi_decode(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, thapi_event *out, uint64_t cap, uint64_t *n_out,
                  void *cuda_stream) {
   return decode_common(ctx, static_cast<const uint8_t *>(bytes), nbytes, out, cap, n_out, cuda_stream);
+}
+
+int thapi_trace_load_batch(thapi_ctx *ctx, const void *const *bytes, const uint64_t *nbytes, uint32_t n,
+                           int on_device, void *cuda_stream, thapi_trace_id *out) {
+  return load_batch(ctx, bytes, nbytes, n, on_device, cuda_stream, out);
 }
 
 int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id) {

@@ -19,8 +19,15 @@ __global__ void k_packet_headers(IndexParams p) {
   uint4 b = __ldg(h + 1);
   uint32_t magic = a.x, stream = a.y, content = b.x, nev = b.y, seq = b.z, disc = b.w;
   uint64_t tsb = (uint64_t)a.z | ((uint64_t)a.w << 32);
-  bool bad = magic != kPacketMagic || stream >= p.n_streams || (content & 3u) != 0 ||
+  uint32_t ns = p.n_streams, soff = 0;
+  if (p.pk_trace) {  // a batch: the packet names a stream of its own trace
+    const uint32_t t = p.pk_trace[i];
+    ns = p.t_nstreams[t];
+    soff = p.t_soff[t];
+  }
+  bool bad = magic != kPacketMagic || stream >= ns || (content & 3u) != 0 ||
              content > p.P - kPacketHeader || nev > content / 8u;
+  stream += soff;
   if (bad) {
     atomicMin(p.hdr_err, (unsigned long long)i);
     stream = p.n_streams;  // sentinel group, sorted last

@@ -171,6 +171,9 @@ struct IndexParams {
   uint32_t *pk_stream, *pk_nev, *pk_content, *pk_seq, *pk_disc;
   uint64_t *pk_tsb;
   unsigned long long *hdr_err;  // min packet index with a header error
+  // a batch of traces (null: one trace): per packet its trace, per trace its
+  // first stream in the batch and its own stream count
+  const uint32_t *pk_trace, *t_soff, *t_nstreams;
 };
 
 // Stream group of a per-CPU buffer (stream flags bit 1): its events belong to

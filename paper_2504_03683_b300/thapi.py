@@ -38,7 +38,7 @@ EXPORTED = (
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
     "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode", "thapi_ctx_set_self_time",
-    "thapi_self_tally", "thapi_trace_func_layer",
+    "thapi_self_tally", "thapi_trace_func_layer", "thapi_trace_load_batch",
 )
 
 
@@ -124,6 +124,7 @@ def library():
         "thapi_ctx_set_self_time": ([vp, i32], i32),
         "thapi_self_tally": ([vp, u64, vp, u64, P(u64)], i32),
         "thapi_trace_func_layer": ([vp, u64, u32, P(u32)], i32),
+        "thapi_trace_load_batch": ([vp, vp, vp, u32, i32, vp, P(u64)], i32),
         "thapi_trace_timing": ([vp, u64, P(LoadTiming)], i32),
         "thapi_kernel_launches": ([], u64),
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
@@ -335,6 +336,28 @@ def thapi_ctx_set_timing(ctx: int, enable: bool = True) -> None:
     _check(library().thapi_ctx_set_timing(ctx, 1 if enable else 0), "thapi_ctx_set_timing")
 
 
+def thapi_trace_load_batch(ctx: int, traces, stream=None, on_device: bool = False) -> int:
+    """Loads several traces as one (see include/thapi.h).  traces: host buffers
+    (bytes / uint8 arrays), or with on_device (device pointer, nbytes) pairs."""
+    n = len(traces)
+    ptrs = (ctypes.c_void_p * max(n, 1))()
+    sizes = (ctypes.c_uint64 * max(n, 1))()
+    keep = []
+    for i, t in enumerate(traces):
+        if on_device:
+            ptrs[i], sizes[i] = int(t[0]), int(t[1])
+        else:
+            a = np.frombuffer(t, dtype=np.uint8) if isinstance(t, (bytes, bytearray)) else np.ascontiguousarray(t, dtype=np.uint8)
+            keep.append(a)
+            ptrs[i], sizes[i] = a.ctypes.data, a.nbytes
+    out = ctypes.c_uint64()
+    rc = library().thapi_trace_load_batch(ctx, ptrs, sizes, n, 1 if on_device else 0,
+                                          ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(out))
+    del keep
+    _check(rc, "thapi_trace_load_batch", ctx)
+    return int(out.value)
+
+
 def thapi_trace_func_layer(ctx: int, trace_id: int, func_id: int) -> int:
     v = ctypes.c_uint32()
     _check(library().thapi_trace_func_layer(ctx, trace_id, func_id, ctypes.byref(v)), "thapi_trace_func_layer")
@@ -406,6 +429,12 @@ class Context:
 
     def load(self, trace, stream=None) -> int:
         return thapi_trace_load(self.handle, trace, stream)
+
+    def load_batch(self, traces, stream=None) -> int:
+        return thapi_trace_load_batch(self.handle, traces, stream)
+
+    def load_batch_device(self, ptr_sizes, stream=None) -> int:
+        return thapi_trace_load_batch(self.handle, ptr_sizes, stream, on_device=True)
 
     def load_device(self, dev_ptr: int, nbytes: int, stream=None) -> int:
         return thapi_trace_load_device(self.handle, dev_ptr, nbytes, stream)
