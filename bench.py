@@ -40,6 +40,10 @@ WORKLOADS = {
     "device": dict(preset="device", desc="512 host streams (8x8x8) of launch/memcpy calls (16 fns) carrying unique "
                                          "random 64-bit command ids; 64 device streams of begin/end events; 50M "
                                          "commands = 200M events; device pairing + merged timeline; 16 KB packets"),
+    "batch": dict(preset="large", desc="4096 per-rank traces (1 host x 1 pid x 8 threads each, the large workload's "
+                                        "3-layer API mix, depth<=6), event counts log-uniform 10k-20M scaled to ~30 GB "
+                                        "in total and clamped to [10k, 20M]; 16 KB packets; one batched load vs 4096 "
+                                        "plain loads of the same device-resident traces"),
     "percpu": dict(preset="percpu", desc="the large workload's shape (8 hosts x 64 threads, 3 layers, depth<=6) "
                                          "written as per-CPU buffers: 32 CPUs per host, threads rotated over CPUs "
                                          "every 200 us (two threads interleaved per CPU); 50M calls = 100M events "
@@ -61,6 +65,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-once", action="store_true", help="one load only (for a profiler), no JSON")
     ap.add_argument("--self-time", action="store_true", help="every load also computes self (exclusive) time")
+    ap.add_argument("--batch-traces", type=int, default=4096, help="batch workload: traces")
+    ap.add_argument("--batch-gb", type=float, default=30.0, help="batch workload: total trace bytes (GB)")
     return ap.parse_args()
 
 
@@ -239,11 +245,171 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batch_sizes(n, total_events, seed):
+    """Event counts of the batch: log-uniform in [10k, 20M], scaled by one factor
+    so that they sum to about total_events, then clamped to [10k, 20M]."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    x = np.exp(rng.uniform(np.log(1e4), np.log(2e7), n))
+    x *= total_events / x.sum()
+    return np.clip(x, 1e4, 2e7).astype(np.int64)
+
+
+def batch_configs(args, rank):
+    import tracegen as tg
+    ev = batch_sizes(args.batch_traces, args.batch_gb * 1e9 / 40.2, 7 + rank)
+    cfgs = []
+    for i, e in enumerate(ev):
+        cfgs.append(tg.preset("large", total_calls=int(e) // 2, n_hosts=1, pids_per_host=1, tids_per_pid=8,
+                              seed=100000 * (rank + 1) + i))
+    return cfgs
+
+
+def run_batch(args, rank, world, local):
+    """Config 3: many per-rank traces in one batched load vs one plain load each."""
+    import numpy as np
+    import torch
+    import tracegen as tg
+    from paper_2504_03683_b300 import thapi
+    cfgs = batch_configs(args, rank)
+    plans = [tg.Plan(c) for c in cfgs]
+    offs, tot = [], 0
+    for pl in plans:
+        offs.append(tot)
+        tot += (pl.nbytes + 255) // 256 * 256
+    host = torch.empty(tot, dtype=torch.uint8, pin_memory=True)
+    for pl, o in zip(plans, offs):
+        pl.write(host.data_ptr() + o)
+    sizes = [pl.nbytes for pl in plans]
+    n_packets = sum(pl.n_packets for pl in plans)
+    for pl in plans:
+        pl.close()
+    dev = host.to("cuda")
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ctx = thapi.Context(local)
+    thapi.thapi_ctx_set_timing(ctx.handle, True)
+    dptr = [(dev.data_ptr() + o, n) for o, n in zip(offs, sizes)]
+    tid = ctx.load_batch_device(dptr, stream)
+    info = ctx.info(tid)
+    ctx.free(tid)
+    events = info["events"]
+    rows_d = torch.empty(max(1, info["tally_rows"]) * 56, dtype=torch.uint8, device="cuda")
+    ivs_d = torch.empty(max(1, info["intervals"]) * 24, dtype=torch.uint8, device="cuda")
+    timings = []
+
+    def batched(record=False):
+        t = thapi.thapi_trace_load_batch(ctx.handle, dptr, stream, on_device=True)
+        thapi.thapi_tally_device(ctx.handle, t, rows_d.data_ptr(), info["tally_rows"], stream)
+        thapi.thapi_timeline_device(ctx.handle, t, 0, 2**64 - 1, ivs_d.data_ptr(), info["intervals"], stream)
+        if record:
+            timings.append(thapi.thapi_trace_timing(ctx.handle, t))
+        thapi.thapi_trace_free(ctx.handle, t)
+
+    def plain():  # one load per trace, each trace's results copied out
+        for (p, n) in dptr:
+            t = thapi.thapi_trace_load_device(ctx.handle, p, n, stream)
+            i = ctx.info(t)
+            thapi.thapi_tally_device(ctx.handle, t, rows_d.data_ptr(), i["tally_rows"], stream)
+            thapi.thapi_timeline_device(ctx.handle, t, 0, 2**64 - 1, ivs_d.data_ptr(), i["intervals"], stream)
+            thapi.thapi_trace_free(ctx.handle, t)
+
+    for _ in range(args.warmup):
+        batched()
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = thapi.thapi_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batched(record=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = thapi.thapi_kernel_launches() - launches0
+    ms = e0.elapsed_time(e1) / args.steps
+    plain()  # warm
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pl_launch0 = thapi.thapi_kernel_launches()
+    p0.record(stream)
+    plain()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain_launches = thapi.thapi_kernel_launches() - pl_launch0
+    plain_ms = p0.elapsed_time(p1)
+    clocks = sampler.stop()
+    peaks, peak_src = measured_peaks()
+    an_ms = statistics.mean(t["analyze_ms"] for t in timings)
+    an_bytes = timings[0]["analyze_read_bytes"] + timings[0]["analyze_write_bytes"]
+    achieved = an_bytes / (an_ms / 1e3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    phase = {k: round(statistics.mean(t[k] for t in timings), 4)
+             for k in ("index_ms", "analyze_ms", "frontier_ms", "tally_ms", "compact_ms", "sort_ms", "gather_ms",
+                       "total_ms")}
+    # end to end: the batch from pinned host memory, results to the host
+    e2e = None
+    if not args.no_e2e:
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            t = ctx.load_batch([host[o:o + n].numpy() for o, n in zip(offs, sizes)], stream)
+            thapi.thapi_tally(ctx.handle, t)
+            thapi.thapi_timeline(ctx.handle, t)
+            thapi.thapi_trace_free(ctx.handle, t)
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        e2e_s = statistics.median(times)
+        e2e = {"value": events / e2e_s, "unit": "events/s", "h2d_bytes_per_step": n_packets * 16384,
+               "d2h_bytes_per_step": info["tally_rows"] * 56 + info["intervals"] * 24, "ms_per_step": e2e_s * 1e3}
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        k = sorted(range(len(sizes)), key=lambda i: sizes[i])[: max(1, len(sizes) // 8)]
+        t0 = time.perf_counter()
+        ev = 0
+        for i in k:
+            ev += oracle.run(host[offs[i]:offs[i] + sizes[i]].numpy()).diag["events"]
+        dt = time.perf_counter() - t0
+        cpu = {"value": ev / dt, "unit": "events/s", "cores": 1, "kind": "oracle",
+               "sample": "the %d smallest of the %d traces (%d events), decode+pair+tally+timeline, one thread"
+                         % (len(k), len(sizes), ev), "seconds": round(dt, 3)}
+    ev_sorted = np.sort([c.total_calls * 2 for c in cfgs])
+    line = {
+        "metric": "events/s decode+pair+tally+timeline, batched", "value": events / (ms / 1e3), "unit": "events/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batch", "desc": WORKLOADS["batch"]["desc"], "traces": len(cfgs), "events": events,
+                   "trace_bytes": int(sum(sizes)), "packets": int(n_packets),
+                   "events_per_trace": {"min": int(ev_sorted[0]), "p50": int(ev_sorted[len(ev_sorted) // 2]),
+                                        "max": int(ev_sorted[-1])},
+                   "l2": "inputs larger than L2; no flush"},
+        "plain": {"value": events / (plain_ms / 1e3), "unit": "events/s", "ms_per_pass": plain_ms,
+                  "gpu_launches": plain_launches, "desc": "one thapi_trace_load_device + tally + timeline per trace"},
+        "batched_over_plain": plain_ms / ms,
+        "phases_ms": phase,
+        "roofline": {"kernel": "k_analyze_warp (decode+validate+pair+tally, interval slots)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_src + " hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured"
+                     else "fallback", "bytes_per_launch": an_bytes, "launch_ms": an_ms, "traffic": None},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        import torch
+        torch.cuda.set_device(local)
+        return run_batch(args, rank, world, local)
 
     import numpy as np
     import torch

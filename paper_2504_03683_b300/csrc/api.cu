@@ -145,9 +145,15 @@ struct Reader {
   const uint8_t *dev;
   uint64_t n;
   cudaStream_t s;
+  const uint8_t *pre = nullptr;  // a host copy of the first pre_n bytes of a device trace
+  uint64_t pre_n = 0;
   bool get(uint64_t off, uint64_t len, std::vector<uint8_t> &out) const {
     out.resize(len);
     if (!len) return true;
+    if (pre && off + len <= pre_n) {
+      std::memcpy(out.data(), pre + off, len);
+      return true;
+    }
     if (host) {
       std::memcpy(out.data(), host + off, len);
       return true;
@@ -461,9 +467,46 @@ static int blocks_per_sm(thapi_ctx *c, uint32_t smem) {
 int Loader::parse_batch(HostLayout &L) {
   const uint32_t nt = (uint32_t)bptr_.size();
   blay_.assign(nt, HostLayout{});
+  // device traces: every trace's head (file header and tables, up to its
+  // packets) gathered by one kernel and read back at once, in two rounds
+  std::vector<uint8_t> heads;
+  std::vector<uint64_t> head_off(nt + 1, 0), head_len(nt, 0);
+  if (bdev_) {
+    const void **d_src = static_cast<const void **>(sc_.get(nt * sizeof(void *)));
+    uint64_t *d_len = static_cast<uint64_t *>(sc_.get(nt * sizeof(uint64_t)));
+    uint64_t *d_off = static_cast<uint64_t *>(sc_.get(nt * sizeof(uint64_t)));
+    if (sc_.failed) return THAPI_E_NOMEM;
+    CK(cudaMemcpyAsync(d_src, bptr_.data(), nt * sizeof(void *), cudaMemcpyHostToDevice, s_));
+    for (int round = 0; round < 2; ++round) {
+      std::vector<uint64_t> len(nt);
+      for (uint32_t t = 0; t < nt; ++t) {
+        len[t] = std::min<uint64_t>(bn_[t], kHeaderBytes);
+        if (round == 1 && head_len[t] >= 96)  // up to the packets (at most 16 MB), from the header read before
+          len[t] = std::max<uint64_t>(
+              len[t], std::min<uint64_t>(std::min<uint64_t>(bn_[t], rd<uint64_t>(heads.data() + head_off[t] + 88)),
+                                         16ull << 20));
+      }
+      for (uint32_t t = 0; t < nt; ++t) {
+        head_len[t] = len[t];
+        head_off[t + 1] = head_off[t] + len[t];
+      }
+      uint8_t *d_dst = static_cast<uint8_t *>(sc_.get(std::max<uint64_t>(head_off[nt], 1)));
+      if (sc_.failed) return THAPI_E_NOMEM;
+      CK(cudaMemcpyAsync(d_len, head_len.data(), nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
+      CK(cudaMemcpyAsync(d_off, head_off.data(), nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
+      launch_gather_bytes(reinterpret_cast<const uint8_t *const *>(d_src), d_len, d_off, nt, d_dst, s_);
+      heads.resize(head_off[nt]);
+      CK(cudaMemcpyAsync(heads.data(), d_dst, head_off[nt], cudaMemcpyDeviceToHost, s_));
+      CK(cudaStreamSynchronize(s_));
+    }
+  }
   for (uint32_t t = 0; t < nt; ++t) {
     const uint8_t *p = static_cast<const uint8_t *>(bptr_[t]);
-    const Reader r{bdev_ ? nullptr : p, bdev_ ? p : nullptr, bn_[t], s_};
+    Reader r{bdev_ ? nullptr : p, bdev_ ? p : nullptr, bn_[t], s_};
+    if (bdev_) {
+      r.pre = heads.data() + head_off[t];
+      r.pre_n = head_len[t];
+    }
     const int rc = parse_layout(r, blay_[t]);
     if (rc != THAPI_OK) {
       c_->err_level = 0;

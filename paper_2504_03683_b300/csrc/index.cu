@@ -46,6 +46,16 @@ __global__ void k_packet_headers(IndexParams p) {
   if ((threadIdx.x & 31) == 0 && rb) atomicAdd(p.read_bytes, rb);
 }
 
+__global__ void k_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
+                               uint8_t *dst) {
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const uint8_t *s = src[i];
+    uint8_t *d = dst + off[i];
+    const uint64_t l = len[i];
+    for (uint64_t k = threadIdx.x; k < l; k += blockDim.x) d[k] = s[k];
+  }
+}
+
 // Sort keys/values for grouping by stream.
 __global__ void k_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,6 +103,14 @@ void launch_packet_headers(const IndexParams &p, cudaStream_t s) {
     count_launches(1);
   }
 }
+void launch_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
+                         uint8_t *dst, cudaStream_t s) {
+  if (n) {
+    k_gather_bytes<<<n < 4096u ? n : 4096u, 256, 0, s>>>(src, len, off, n, dst);
+    count_launches(1);
+  }
+}
+
 void launch_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals, cudaStream_t s) {
   if (n) {
     k_stream_keys<<<grid_for(n, 256), 256, 0, s>>>(pk_stream, n, keys, vals);

@@ -298,6 +298,9 @@ void launch_build_desc(const uint32_t *order, const uint32_t *pk_stream, const u
                        const uint32_t *pk_content, const uint32_t *pk_disc, const uint64_t *pk_tsb,
                        const uint32_t *stream_group, const uint64_t *evbase, uint64_t n, PkDesc *desc, cudaStream_t s);
 void launch_packet_headers(const IndexParams &p, cudaStream_t s);
+// dst[off[i] .. off[i] + len[i]) = src[i][0 .. len[i]) for i < n (a block per source).
+void launch_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
+                         uint8_t *dst, cudaStream_t s);
 void launch_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals, cudaStream_t s);
 void launch_stream_bounds(const uint64_t *skey, const uint32_t *order, const uint32_t *pk_seq, const uint32_t *pk_nev,
                           uint64_t n, uint32_t n_streams, uint32_t *stream_first, uint32_t *stream_count,
