@@ -44,6 +44,10 @@ WORKLOADS = {
                                         "3-layer API mix, depth<=6), event counts log-uniform 10k-20M scaled to ~30 GB "
                                         "in total and clamped to [10k, 20M]; 16 KB packets; one batched load vs 4096 "
                                         "plain loads of the same device-resident traces"),
+    "serve": dict(preset="large", desc="serving loop: traces of the large workload's API mix (1 host x 1 pid x 8 "
+                                        "threads each) sized log-uniform 1 MB-4 GB, kept device-resident under a "
+                                        "120 GB admission cap; Poisson arrivals at 200 req/s, half tally and half "
+                                        "time-window timeline queries (window log-uniform 1e-4-1 of the span)"),
     "percpu": dict(preset="percpu", desc="the large workload's shape (8 hosts x 64 threads, 3 layers, depth<=6) "
                                          "written as per-CPU buffers: 32 CPUs per host, threads rotated over CPUs "
                                          "every 200 us (two threads interleaved per CPU); 50M calls = 100M events "
@@ -67,6 +71,9 @@ def parse():
     ap.add_argument("--self-time", action="store_true", help="every load also computes self (exclusive) time")
     ap.add_argument("--batch-traces", type=int, default=4096, help="batch workload: traces")
     ap.add_argument("--batch-gb", type=float, default=30.0, help="batch workload: total trace bytes (GB)")
+    ap.add_argument("--serve-gb", type=float, default=16.0, help="serve workload: resident trace bytes (GB)")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve workload: arrival window (s)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
     return ap.parse_args()
 
 
@@ -401,15 +408,86 @@ def run_batch(args, rank, world, local):
     ctx.close()
 
 
+def run_serve(args, rank, world, local):
+    """Config 5: queries against device-resident traces as they arrive; p50 / p99 latency."""
+    import numpy as np
+    import torch
+    import tracegen as tg
+    from paper_2504_03683_b300 import serve, thapi
+    rng = np.random.default_rng(11 + rank)
+    sizes, tot = [], 0.0
+    while tot < args.serve_gb * 1e9:
+        b = float(np.exp(rng.uniform(np.log(1e6), np.log(4e9))))
+        b = min(b, args.serve_gb * 1e9 - tot) if tot + b > args.serve_gb * 1e9 and sizes else b
+        sizes.append(b)
+        tot += b
+    srv = serve.Server(local, 120 * 10**9)
+    load_s, events, trace_bytes = 0.0, 0, 0
+    for i, b in enumerate(sizes):
+        cfg = tg.preset("large", total_calls=max(1000, int(b / 40.2) // 2), n_hosts=1, pids_per_host=1,
+                        tids_per_pid=8, seed=200000 + 1000 * rank + i)
+        host, meta = generate_pinned(cfg)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = srv.admit((host.data_ptr(), host.numel()))
+        torch.cuda.synchronize()
+        load_s += time.perf_counter() - t0
+        if k is not None:
+            events += srv.traces[k].events
+            trace_bytes += meta["nbytes"]
+        del host
+    spans = [(r.t_min, r.t_max) for r in srv.traces]
+    reqs = serve.poisson_requests(args.serve_rate, args.serve_seconds, spans, seed=13 + rank)
+    warm = serve.poisson_requests(args.serve_rate, 1.0, spans, seed=17 + rank)
+    srv.run(warm)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = thapi.thapi_kernel_launches()
+    t0 = time.perf_counter()
+    out = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    launches = thapi.thapi_kernel_launches() - launches0
+    clocks = sampler.stop()
+    lat = [o[0] * 1e3 for o in out]
+    lat_t = [o[0] * 1e3 for o, r in zip(out, sorted(reqs, key=lambda q: q.arrival)) if r.kind == "tally"]
+    lat_w = [o[0] * 1e3 for o, r in zip(out, sorted(reqs, key=lambda q: q.arrival)) if r.kind == "window"]
+    answered = sum(srv.traces[r.trace].events if r.kind == "tally" else 2 * n
+                   for (lt, n), r in zip(out, sorted(reqs, key=lambda q: q.arrival)))
+    line = {
+        "metric": "p99 latency of tally / window queries at %g req/s (arrival to result on the host)" % args.serve_rate,
+        "value": serve.percentile(lat, 99), "unit": "ms", "n_gpus": world, "steps": len(reqs), "warmup": len(warm),
+        "ms_per_step": float(np.mean(lat)), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serve", "desc": WORKLOADS["serve"]["desc"], "traces": len(srv.traces),
+                   "refused": srv.refused, "resident_trace_bytes": trace_bytes, "resident_events": events,
+                   "requests": len(reqs), "seconds": args.serve_seconds},
+        "latency_ms": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99), "max": max(lat),
+                       "tally_p50": serve.percentile(lat_t, 50) if lat_t else None,
+                       "tally_p99": serve.percentile(lat_t, 99) if lat_t else None,
+                       "window_p50": serve.percentile(lat_w, 50) if lat_w else None,
+                       "window_p99": serve.percentile(lat_w, 99) if lat_w else None},
+        "requests_per_s": len(reqs) / wall,
+        "answered_events_per_s": answered / wall,
+        "admission_load_events_per_s": events / load_s if load_s else None,
+        "e2e": {"value": serve.percentile(lat, 99), "unit": "ms", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": None, "note": "every latency is already arrival to result on the host"},
+        "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None, "roofline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload == "batch":
+    if args.workload in ("batch", "serve"):
         import torch
         torch.cuda.set_device(local)
-        return run_batch(args, rank, world, local)
+        return (run_batch if args.workload == "batch" else run_serve)(args, rank, world, local)
 
     import numpy as np
     import torch
