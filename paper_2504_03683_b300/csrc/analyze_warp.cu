@@ -694,7 +694,7 @@ int warp_bw(uint32_t P) {
 // index: the same boundary walk, stitch and checks as the analysis, then 32
 // events per batch with the timestamp monoid scanned across the batches.  No
 // pairing.  Plain coalesced loads stage the packet (one warp per packet).
-constexpr uint32_t kDecodeWarps = 8;
+constexpr uint32_t kDecodeWarps = 16;  // at most; shared memory sets the count (11 warps of 16 KB packets)
 
 __host__ __device__ inline uint32_t decode_warp_bytes(uint32_t P) {
   return rup(P + 48u, 128u) + rup(((P - kPacketHeader) / 8u + 1u) * 2u, 128u);
