@@ -322,6 +322,13 @@ typedef struct thapi_load_timing {
                                     marked hole) and a 24 B interval slot per ENTRY */
 } thapi_load_timing;
 
+/* The failure path of the library's bounded device waits, on purpose: one
+ * warp waits on an mbarrier that nothing completes for at most `limit` tries,
+ * gives up, and reports through a status word.  Returns THAPI_E_TIMEOUT (what
+ * a load returns when a packet copy never lands), E_INVALID for limit 0;
+ * nothing faults and the context stays usable. */
+int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream);
+
 /* Enables (1) or disables (0) per-phase timing of subsequent loads. */
 int thapi_ctx_set_timing(thapi_ctx *ctx, int enable);
 

@@ -1615,6 +1615,26 @@ int thapi_trace_func_layer(thapi_ctx *ctx, thapi_trace_id id, uint32_t func_id, 
   return THAPI_OK;
 }
 
+int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream) {
+  if (!ctx || limit == 0) return THAPI_E_INVALID;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return THAPI_E_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  Scratch sc;
+  sc.ctx = ctx;
+  sc.stream = s;
+  unsigned *d_status = static_cast<unsigned *>(sc.get(sizeof(unsigned)));
+  if (sc.failed) return THAPI_E_NOMEM;
+  unsigned status = THAPI_E_CUDA;
+  int rc = THAPI_OK;
+  if (cudaMemsetAsync(d_status, 0, sizeof(unsigned), s) != cudaSuccess || launch_wait_check(limit, d_status, s) != cudaSuccess ||
+      cudaMemcpyAsync(&status, d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    rc = THAPI_E_CUDA;
+  sc.release_all();
+  cudaStreamSynchronize(s);
+  return rc != THAPI_OK ? rc : (int)status;
+}
+
 int thapi_ctx_set_timing(thapi_ctx *ctx, int enable) {
   if (!ctx) return THAPI_E_INVALID;
   ctx->timing = enable ? 1 : 0;

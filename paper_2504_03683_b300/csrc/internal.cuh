@@ -298,6 +298,9 @@ void launch_build_desc(const uint32_t *order, const uint32_t *pk_stream, const u
                        const uint32_t *pk_content, const uint32_t *pk_disc, const uint64_t *pk_tsb,
                        const uint32_t *stream_group, const uint64_t *evbase, uint64_t n, PkDesc *desc, cudaStream_t s);
 void launch_packet_headers(const IndexParams &p, cudaStream_t s);
+// One warp waits on an mbarrier nothing completes, at most `limit` tries;
+// *status (device) = THAPI_E_TIMEOUT when the wait gives up.
+cudaError_t launch_wait_check(uint32_t limit, unsigned *status, cudaStream_t s);
 // dst[off[i] .. off[i] + len[i]) = src[i][0 .. len[i]) for i < n (a block per source).
 void launch_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
                          uint8_t *dst, cudaStream_t s);

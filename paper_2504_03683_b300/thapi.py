@@ -38,7 +38,7 @@ EXPORTED = (
     "thapi_timeline_device", "thapi_trace_info_get", "thapi_trace_strings", "thapi_last_error_location",
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
     "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode", "thapi_ctx_set_self_time",
-    "thapi_self_tally", "thapi_trace_func_layer", "thapi_trace_load_batch",
+    "thapi_self_tally", "thapi_trace_func_layer", "thapi_trace_load_batch", "thapi_check_device_wait",
 )
 
 
@@ -125,6 +125,7 @@ def library():
         "thapi_self_tally": ([vp, u64, vp, u64, P(u64)], i32),
         "thapi_trace_func_layer": ([vp, u64, u32, P(u32)], i32),
         "thapi_trace_load_batch": ([vp, vp, vp, u32, i32, vp, P(u64)], i32),
+        "thapi_check_device_wait": ([vp, u32, vp], i32),
         "thapi_trace_timing": ([vp, u64, P(LoadTiming)], i32),
         "thapi_kernel_launches": ([], u64),
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
@@ -356,6 +357,11 @@ def thapi_trace_load_batch(ctx: int, traces, stream=None, on_device: bool = Fals
     del keep
     _check(rc, "thapi_trace_load_batch", ctx)
     return int(out.value)
+
+
+def thapi_check_device_wait(ctx: int, limit: int = 1024, stream=None) -> int:
+    """Status code of a bounded device wait made to run out (THAPI_E_TIMEOUT expected)."""
+    return int(library().thapi_check_device_wait(ctx, limit, ctypes.c_void_p(_stream_ptr(stream))))
 
 
 def thapi_trace_func_layer(ctx: int, trace_id: int, func_id: int) -> int:

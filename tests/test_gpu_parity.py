@@ -458,3 +458,16 @@ def test_device_join_global_table_for_a_heavy_id(ctx):
     tb.place(tb.stream_events(sd, dev, ts_begin=10_000))
     o = assert_parity(ctx, tb.build())
     assert o.dev_diag["dev_unpaired"] == 2 * 8192 and o.dev_diag["host_unjoined"] == 6300
+
+
+def test_bounded_device_wait_runs_out_and_the_context_stays_usable(ctx):
+    """An mbarrier wait that nothing completes gives up after its limit and
+    reports THAPI_E_TIMEOUT through a status word; then a load on the same
+    context still matches the oracle."""
+    from paper_2504_03683_b300 import thapi
+    assert thapi.thapi_check_device_wait(ctx.handle, 256) == thapi.E_TIMEOUT
+    assert thapi.thapi_check_device_wait(ctx.handle, 0) == thapi.E_INVALID
+    tb, h, ids = _builder()
+    s = tb.add_stream(h, 1, 1)
+    tb.place(tb.stream_events(s, [Ev(ids[0][1], 10), Ev(ids[0][2], 20, result=0)], ts_begin=10))
+    assert_parity(ctx, tb.build())
