@@ -520,6 +520,7 @@ int Loader::parse_batch(HostLayout &L) {
     const HostLayout &b = blay_[t];
     if (b.P != a.P || b.cls != a.cls || b.n_funcs != a.n_funcs || b.func_layer != a.func_layer)
       return THAPI_E_UNSUPPORTED;
+    if (b.strings == a.strings && b.func_name == a.func_name) continue;  // same string table: same names
     for (uint32_t f = 0; f < a.n_funcs; ++f)
       if (std::strcmp(fname(a, f), fname(b, f)) != 0) return THAPI_E_UNSUPPORTED;
   }
@@ -626,6 +627,8 @@ int Loader::run() {
     d_t_ns = alloc<uint32_t>(nt);
     if (sc_.failed) return THAPI_E_NOMEM;
     std::vector<uint32_t> pk_trace(n), t_soff(nt), t_ns(nt);
+    std::vector<const uint8_t *> t_src(nt);
+    std::vector<uint64_t> t_first(nt);
     uint64_t at = 0;
     uint32_t soff = 0;
     for (uint32_t t = 0; t < nt; ++t) {
@@ -633,17 +636,25 @@ int Loader::run() {
       const uint8_t *src = static_cast<const uint8_t *>(bptr_[t]) + b.packets_off;
       if (!bdev_ && b.n_packets)
         CK(cudaMemcpyAsync(pk + at * P, src, b.n_packets * (uint64_t)P, cudaMemcpyHostToDevice, s_));
-      if (bdev_ && b.n_packets) {
-        if (reinterpret_cast<uintptr_t>(src) % 16 != 0) return THAPI_E_INVALID;
-        CK(cudaMemcpyAsync(pk + at * P, src, b.n_packets * (uint64_t)P, cudaMemcpyDeviceToDevice, s_));
-      }
+      if (bdev_ && b.n_packets && reinterpret_cast<uintptr_t>(src) % 16 != 0) return THAPI_E_INVALID;
       for (uint64_t q = 0; q < b.n_packets; ++q) pk_trace[at + q] = t;
+      t_src[t] = src;
+      t_first[t] = at;
       t_soff[t] = soff;
       t_ns[t] = b.n_streams;
       at += b.n_packets;
       soff += b.n_streams;
     }
     if (n) CK(cudaMemcpyAsync(d_pk_trace, pk_trace.data(), 4ull * n, cudaMemcpyHostToDevice, s_));
+    if (bdev_ && n) {  // device traces: one gather kernel instead of a copy per trace
+      const uint8_t **d_src = static_cast<const uint8_t **>(sc_.get(nt * sizeof(void *)));
+      uint64_t *d_first = static_cast<uint64_t *>(sc_.get(nt * sizeof(uint64_t)));
+      if (sc_.failed) return THAPI_E_NOMEM;
+      CK(cudaMemcpyAsync(d_src, t_src.data(), nt * sizeof(void *), cudaMemcpyHostToDevice, s_));
+      CK(cudaMemcpyAsync(d_first, t_first.data(), nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
+      launch_gather_packets(d_src, d_first, d_pk_trace, n, P, pk, c_->num_sms, s_);
+      CK(cudaGetLastError());
+    }
     CK(cudaMemcpyAsync(d_t_soff, t_soff.data(), 4ull * nt, cudaMemcpyHostToDevice, s_));
     CK(cudaMemcpyAsync(d_t_ns, t_ns.data(), 4ull * nt, cudaMemcpyHostToDevice, s_));
     CK(cudaStreamSynchronize(s_));  // the host tables above go out of scope

@@ -6,6 +6,8 @@
 // radix sort (file order is kept inside a stream), seq monotonicity is checked
 // between neighbours of one stream, and an exclusive scan of the event counts
 // in stream order gives every packet its first event slot.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace thapi {
@@ -56,6 +58,20 @@ __global__ void k_gather_bytes(const uint8_t *const *src, const uint64_t *len, c
   }
 }
 
+// A batch's packets into one area: a warp per packet, 16-byte copies.
+// src[t]: trace t's first packet; first[t]: its first packet in the batch.
+__global__ void k_gather_packets(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace,
+                                 uint64_t n, uint32_t P, uint8_t *dst) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t q = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += nw) {
+    const uint32_t t = pk_trace[q];
+    const uint4 *s = reinterpret_cast<const uint4 *>(src[t] + (q - first[t]) * P);
+    uint4 *d = reinterpret_cast<uint4 *>(dst + q * P);
+    for (uint32_t k = lane; k < P / 16u; k += 32) d[k] = s[k];
+  }
+}
+
 // Sort keys/values for grouping by stream.
 __global__ void k_stream_keys(const uint32_t *pk_stream, uint64_t n, uint64_t *keys, uint32_t *vals) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -103,6 +119,15 @@ void launch_packet_headers(const IndexParams &p, cudaStream_t s) {
     count_launches(1);
   }
 }
+void launch_gather_packets(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
+                           uint32_t P, uint8_t *dst, int num_sms, cudaStream_t s) {
+  if (n) {
+    const uint64_t blocks = std::min<uint64_t>((n + 7) / 8, (uint64_t)num_sms * 8);
+    k_gather_packets<<<(unsigned)blocks, 256, 0, s>>>(src, first, pk_trace, n, P, dst);
+    count_launches(1);
+  }
+}
+
 void launch_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
                          uint8_t *dst, cudaStream_t s) {
   if (n) {

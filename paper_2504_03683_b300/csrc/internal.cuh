@@ -301,6 +301,10 @@ void launch_packet_headers(const IndexParams &p, cudaStream_t s);
 // One warp waits on an mbarrier nothing completes, at most `limit` tries;
 // *status (device) = THAPI_E_TIMEOUT when the wait gives up.
 cudaError_t launch_wait_check(uint32_t limit, unsigned *status, cudaStream_t s);
+// dst + q * P = trace pk_trace[q]'s packet (q - first[t]) at src[t] (16-byte
+// aligned), a warp per packet.
+void launch_gather_packets(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
+                           uint32_t P, uint8_t *dst, int num_sms, cudaStream_t s);
 // dst[off[i] .. off[i] + len[i]) = src[i][0 .. len[i]) for i < n (a block per source).
 void launch_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
                          uint8_t *dst, cudaStream_t s);

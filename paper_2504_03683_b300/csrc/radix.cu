@@ -20,6 +20,18 @@ constexpr int kWarps = kT / 32;
 constexpr int kRounds = 16;                   // 32-item rounds per warp
 constexpr int kTile = kWarps * 32 * kRounds;  // 4096 items
 
+// Lanes of the warp whose digit equals this lane's (valid lanes only): one
+// ballot per digit bit, fewer issue slots than a match on the digit.
+__device__ __forceinline__ uint32_t same_digit(uint32_t d, bool valid) {
+  uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+  for (int bit = 0; bit < kBits; ++bit) {
+    const uint32_t m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+    peers &= ((d >> bit) & 1u) ? m : ~m;
+  }
+  return peers;
+}
+
 template <class K>
 __global__ void __launch_bounds__(kT) k_hist(const K *keys, uint64_t n, int shift, uint64_t *hist, uint64_t ntiles) {
   __shared__ uint32_t h[kBins];
@@ -30,8 +42,8 @@ __global__ void __launch_bounds__(kT) k_hist(const K *keys, uint64_t n, int shif
   for (int k = threadIdx.x; k < kTile; k += kT) {
     const uint64_t i = base + k;
     const bool in = i < n;
-    const uint32_t d = in ? (uint32_t)(keys[i] >> shift) & (kBins - 1) : kBins + lane;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t d = in ? (uint32_t)(keys[i] >> shift) & (kBins - 1) : 0u;
+    const uint32_t peers = same_digit(d, in);
     if (in && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&h[d], (uint32_t)__popc(peers));
   }
   __syncthreads();
@@ -66,8 +78,8 @@ __global__ void __launch_bounds__(kT) k_scatter(const K *kin, const uint32_t *vi
   for (int r = 0; r < kRounds; ++r) {
     const uint64_t i = wbase + (uint64_t)r * 32 + lane;
     const bool valid = i < n;
-    const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & (kBins - 1)) : kBins + lane;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & (kBins - 1)) : 0u;
+    const uint32_t peers = same_digit(d, valid);
     const uint32_t rank = __popc(peers & lt);
     const uint32_t before = valid ? wcount[warp][d] : 0u;
     __syncwarp();
