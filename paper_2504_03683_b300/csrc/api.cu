@@ -360,6 +360,8 @@ class Loader {
     tr_ = nullptr;
     return t;
   }
+  // the load's status with a scratch failure that was a timed-out wait reported as such
+  int status(int rc) const { return rc == THAPI_E_NOMEM && sc_.failed == 2 ? THAPI_E_TIMEOUT : rc; }
   // a batch: n traces (host or device bytes) loaded as one trace
   void set_batch(const void *const *bytes, const uint64_t *nbytes, uint32_t n, bool on_device) {
     bptr_.assign(bytes, bytes + n);
@@ -1265,7 +1267,7 @@ static int load_common(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, ui
   TraceRec *tr = nullptr;
   {
     Loader ld(c, host, dev, nbytes, s);
-    rc = ld.run();
+    rc = ld.status(ld.run());
     if (rc == THAPI_OK) tr = ld.take();
   }
   if (rc != THAPI_OK) return rc;
@@ -1289,7 +1291,7 @@ static int load_batch(thapi_ctx *c, const void *const *bytes, const uint64_t *nb
   {
     Loader ld(c, nullptr, nullptr, 0, static_cast<cudaStream_t>(stream));
     ld.set_batch(bytes, nbytes, n, on_device != 0);
-    rc = ld.run();
+    rc = ld.status(ld.run());
     if (rc == THAPI_OK) tr = ld.take();
   }
   if (rc != THAPI_OK) return rc;
@@ -1564,7 +1566,7 @@ int thapi_tally_merge(thapi_ctx *ctx, const thapi_tally_row *rows, uint64_t n, t
       break;
     }
     if (!tally_merge_device(d_in, n, d_out, d_m, sc, s)) {
-      rc = sc.failed ? THAPI_E_NOMEM : THAPI_E_CUDA;
+      rc = sc.failed == 2 ? THAPI_E_TIMEOUT : sc.failed ? THAPI_E_NOMEM : THAPI_E_CUDA;
       break;
     }
     if (cudaMemcpyAsync(&m, d_m, sizeof(m), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

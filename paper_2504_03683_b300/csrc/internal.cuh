@@ -282,7 +282,7 @@ struct Scratch {
   thapi_ctx *ctx = nullptr;
   cudaStream_t stream = nullptr;
   std::vector<std::pair<void *, uint64_t>> bufs;
-  int failed = 0;
+  int failed = 0;  // 1: an allocation failed; 2: a bounded device wait ran out (a sort's look-back)
   void *get(uint64_t bytes);
   void adopt(void *p, uint64_t bytes);
   void release_all();
