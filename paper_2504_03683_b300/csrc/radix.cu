@@ -258,21 +258,35 @@ __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vi
       atomicExch(mine, kIncl | run);
     } else {
       atomicExch(mine, kAggr | run);
+      // walk back kLook tiles per round (their loads in flight together), in
+      // order; an entry not yet published is polled again from there
+      constexpr int kLook = 8;
       int64_t j = (int64_t)tile - 1;
       uint32_t spins = 0;
-      while (j >= 0) {
-        const uint64_t v = *reinterpret_cast<volatile unsigned long long *>(status + (uint64_t)j * kBins + b);
-        const uint64_t f = v & ~kValMask;
-        if (f == 0) {
-          if (++spins > kSpinLimit) {
-            atomicExch(err, 1u);
-            break;
+      bool done = false;
+      while (!done && j >= 0) {
+        uint64_t v[kLook];
+#pragma unroll
+        for (int u = 0; u < kLook; ++u)
+          v[u] = j - u >= 0 ? *reinterpret_cast<volatile unsigned long long *>(status + (uint64_t)(j - u) * kBins + b)
+                            : kIncl;
+        int used = kLook;
+#pragma unroll
+        for (int u = 0; u < kLook; ++u) {
+          if (used < kLook || done) continue;
+          const uint64_t f = v[u] & ~kValMask;
+          if (f == 0) {  // not published yet: poll again from this entry
+            used = u;
+            continue;
           }
-          continue;
+          excl += v[u] & kValMask;
+          if (f == kIncl) done = true;
         }
-        excl += v & kValMask;
-        if (f == kIncl) break;
-        --j;
+        if (used < kLook && ++spins > kSpinLimit) {
+          atomicExch(err, 1u);
+          break;
+        }
+        j -= used;
       }
       atomicExch(mine, kIncl | (excl + run));
     }
