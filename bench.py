@@ -585,8 +585,9 @@ def main():
     phase = {k: round(statistics.mean(t[k] for t in timings), 4)
              for k in ("index_ms", "analyze_ms", "frontier_ms", "join_ms", "percpu_ms", "percpu_decode_ms", "tally_ms",
                        "self_ms", "compact_ms", "sort_ms", "gather_ms", "total_ms")}
+    # a capture is per kernel variant: loads with self time run the variant with side records
     traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze_warp.cu"), kname,
-                              args.workload)
+                              args.workload + ("_self" if args.self_time and kname == "k_analyze_warp" else ""))
 
     # end to end through the public API: host bytes in, host results out
     e2e = None
