@@ -43,9 +43,10 @@
  * like one stream's, in (ts, stream id, position) order; tally rows are keyed
  * by (host, vpid, vtid, function) and combine with per-thread rows of the same
  * key; an interval belongs to its entry's stream.  Per-CPU buffers take no
- * part in device-activity pairing, and need packets of at most 32 KB.
+ * part in device-activity pairing; a trace with them needs packets of at most
+ * 32 KB and fewer than 2^32 events (E_UNSUPPORTED otherwise).
  *
- * Semantics: one stream = one thread.  Per stream, events are paired with a
+ * Semantics: any other stream is one thread.  Per stream, events are paired with a
  * call stack: an EXIT pops the latest open ENTRY; equal functions make an
  * interval [entry ts, exit ts] (level = depth of the entry, 0 outermost,
  * saturated at 255; error flag = the exit's i32 result is nonzero).  An EXIT

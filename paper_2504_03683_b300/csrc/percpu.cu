@@ -5,14 +5,20 @@
 // (vpid / vtid context, Sec. 3.2), and a thread that migrates leaves its
 // events in several buffers.  A thread is (host, vpid, vtid); its events from
 // all buffers, ordered by (ts, stream, position), are paired with one call
-// stack.  Here, over the records k_percpu_decode wrote for every ENTRY and
-// EXIT of those buffers:
-//  1. stable LSD radix sorts by position, then ts, then (vpid, vtid), then
-//     host give the order (host, vpid, vtid, ts, position);
-//  2. thread boundaries, thread numbers (a scan of the boundaries) and a
-//     segmented scan of the depth monoid (sum, min-prefix) give every event
-//     its clamped depth before it, pre = S - min(0, min prefix S); an exit
-//     with pre = 0 is unmatched, an entry's level is pre, an exit's pre - 1;
+// stack.  Here, over the records k_percpu_decode wrote at the per-CPU event
+// positions (in (stream, position) order; positions of other events marked):
+//  1. thread numbers: a table of (host, vpid, vtid) fingerprints (one insert
+//     per distinct thread of a warp), then a scan of its used slots; every
+//     record looks its thread up and checks the full key.  One stable radix
+//     sort by (thread number, ts) of the position-ordered records gives the
+//     thread order (thread, ts, stream, position).  When the table would fill
+//     or two keys share a fingerprint, stable sorts by ts, (vpid, vtid) and
+//     host give it instead, and thread numbers come from a scan of the thread
+//     boundaries;
+//  2. a segmented scan of the depth monoid (sum, min-prefix) per thread gives
+//     every event its clamped depth before it, pre = S - min(0, min prefix
+//     S); an exit with pre = 0 is unmatched, an entry's level is pre, an
+//     exit's pre - 1;
 //  3. a stable sort by (thread, level) puts every entry right before the exit
 //     that pops it (nothing at that level happens between them), so pairs
 //     are neighbours: equal functions make an interval (written into the
