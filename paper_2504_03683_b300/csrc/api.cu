@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -502,20 +503,34 @@ int Loader::parse_batch(HostLayout &L) {
       CK(cudaStreamSynchronize(s_));
     }
   }
-  for (uint32_t t = 0; t < nt; ++t) {
-    const uint8_t *p = static_cast<const uint8_t *>(bptr_[t]);
-    Reader r{bdev_ ? nullptr : p, bdev_ ? p : nullptr, bn_[t], s_};
-    if (bdev_) {
-      r.pre = heads.data() + head_off[t];
-      r.pre_n = head_len[t];
+  // the traces' tables parsed on host threads (each trace on its own); the
+  // first failing trace in batch order is the one reported
+  std::vector<int> rcs(nt, THAPI_OK);
+  const uint32_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const uint32_t nthreads = nt < 64 ? 1u : std::min<uint32_t>(std::min(32u, hw), nt);
+  auto parse_some = [&](uint32_t first) {
+    for (uint32_t t = first; t < nt; t += nthreads) {
+      const uint8_t *p = static_cast<const uint8_t *>(bptr_[t]);
+      Reader r{bdev_ ? nullptr : p, bdev_ ? p : nullptr, bn_[t], s_};
+      if (bdev_) {
+        r.pre = heads.data() + head_off[t];
+        r.pre_n = head_len[t];
+      }
+      rcs[t] = parse_layout(r, blay_[t]);
     }
-    const int rc = parse_layout(r, blay_[t]);
-    if (rc != THAPI_OK) {
+  };
+  {
+    std::vector<std::thread> pool;
+    for (uint32_t k = 1; k < nthreads; ++k) pool.emplace_back(parse_some, k);
+    parse_some(0);
+    for (auto &th : pool) th.join();
+  }
+  for (uint32_t t = 0; t < nt; ++t)
+    if (rcs[t] != THAPI_OK) {
       c_->err_level = 0;
       c_->err_packet = t;
-      return rc;
+      return rcs[t];
     }
-  }
   const HostLayout &a = blay_[0];
   auto fname = [](const HostLayout &x, uint32_t f) { return reinterpret_cast<const char *>(x.strings.data()) + x.func_name[f]; };
   for (uint32_t t = 1; t < nt; ++t) {
