@@ -147,7 +147,9 @@ __global__ void k_pc_tkey(const PcRec *rec, uint64_t m, const unsigned long long
 }
 
 // Sorted records with the thread number in place of (host, vpid, vtid).
-__global__ void k_pc_gather_t(const PcRec *rec, const uint32_t *perm, const uint32_t *tid, uint64_t m, PcRec *out) {
+// Also tk[i] = thread number << 1 | (ENTRY): all the depth scan reads.
+__global__ void k_pc_gather_t(const PcRec *rec, const uint32_t *perm, const uint32_t *tid, uint64_t m, PcRec *out,
+                              uint32_t *tk) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const uint32_t j = perm[i];
@@ -155,6 +157,7 @@ __global__ void k_pc_gather_t(const PcRec *rec, const uint32_t *perm, const uint
   r.thread = tid[j];
   r.host = 0;
   out[i] = r;
+  tk[i] = tid[j] << 1 | (r.kind == kEntry ? 1u : 0u);
 }
 
 // Fallback order (table full or a fingerprint clash): stable sorts by ts,
@@ -200,11 +203,12 @@ __global__ void k_pc_keys(const PcRec *r, const uint64_t *excl, uint64_t m, uint
   }
 }
 
-__global__ void k_pc_renumber(PcRec *r, const uint32_t *tnum, uint64_t m) {
+__global__ void k_pc_renumber(PcRec *r, const uint32_t *tnum, uint64_t m, uint32_t *tk) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   r[i].thread = tnum[i];
   r[i].host = 0;
+  tk[i] = tnum[i] << 1 | (r[i].kind == kEntry ? 1u : 0u);
 }
 
 // Segmented monoid (head, DM): (ha, a) . (hb, b) = (ha | hb, hb ? b : a.b).
@@ -240,15 +244,17 @@ __device__ __forceinline__ SegDM block_scan(SegDM x, SegDM *wagg) {
   return x;
 }
 
-__device__ __forceinline__ SegDM element(const PcRec *r, uint64_t i, uint64_t m) {
+// tk: thread number << 1 | (ENTRY), in thread order
+__device__ __forceinline__ SegDM element(const uint32_t *tk, uint64_t i, uint64_t m) {
   if (i >= m) return SegDM{1u, DM{0, 0}};
-  const int e = r[i].kind == kEntry ? 1 : -1;
-  const bool h = i == 0 || !same_thread(r[i - 1], r[i]);
+  const uint32_t v = tk[i];
+  const int e = (v & 1u) ? 1 : -1;
+  const bool h = i == 0 || (tk[i - 1] >> 1) != (v >> 1);
   return SegDM{h ? 1u : 0u, DM{e, min(0, e)}};
 }
 
 // Per block: inclusive scan; the block's aggregate to agg[b].
-__global__ void __launch_bounds__(kSegThreads) k_seg_local(const PcRec *r, uint64_t m, SegDM *agg) {
+__global__ void __launch_bounds__(kSegThreads) k_seg_local(const uint32_t *r, uint64_t m, SegDM *agg) {
   __shared__ SegDM wagg[kSegThreads / 32];
   const uint64_t i = (uint64_t)blockIdx.x * kSegThreads + threadIdx.x;
   const SegDM x = block_scan(element(r, i, m), wagg);
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_blocks(SegDM *agg, uint64_t
 
 // pre = clamped depth before each event; key (thread << 32 | level), or ~0 for
 // an unmatched exit; the largest level to *lmax.
-__global__ void __launch_bounds__(kSegThreads) k_seg_apply(const PcRec *r, uint64_t m, const SegDM *carry,
+__global__ void __launch_bounds__(kSegThreads) k_seg_apply(const uint32_t *r, uint64_t m, const SegDM *carry,
                                                            uint64_t *key, uint32_t *val, unsigned long long *lmax,
                                                            unsigned long long *diag) {
   __shared__ SegDM wagg[kSegThreads / 32];
@@ -296,14 +302,14 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_apply(const PcRec *r, uint6
     ex = seg_op(carry[blockIdx.x], ex);
     const DM before = x.h ? DM{0, 0} : ex.d;
     const uint32_t pre = (uint32_t)(before.s - before.m);
-    const bool entry = r[i].kind == kEntry;
+    const bool entry = (r[i] & 1u) != 0;
     val[i] = (uint32_t)i;
     if (!entry && pre == 0) {
       key[i] = ~0ull;
       atomicAdd(&diag[dUnExit], 1ull);
     } else {
       lvl = entry ? pre : pre - 1;
-      key[i] = r[i].thread << 32 | lvl;  // the thread number
+      key[i] = (uint64_t)(r[i] >> 1) << 32 | lvl;  // the thread number
     }
   }
   lvl = __reduce_max_sync(0xffffffffu, lvl);
@@ -504,6 +510,7 @@ int percpu_pair(PcRec *rec, uint64_t m_all, uint64_t m, uint64_t t_min, int ts_b
   uint32_t *v2 = static_cast<uint32_t *>(sc.get(m_all * sizeof(uint32_t)));
   uint32_t *tid = static_cast<uint32_t *>(sc.get(m_all * sizeof(uint32_t)));
   PcRec *r2 = static_cast<PcRec *>(sc.get(m * sizeof(PcRec)));
+  uint32_t *tk = static_cast<uint32_t *>(sc.get(m * sizeof(uint32_t)));
   uint64_t *word = static_cast<uint64_t *>(sc.get(4 * sizeof(uint64_t)));  // threads, level, flags
   constexpr uint32_t kTabCap = 1u << 16, kTabMask = kTabCap - 1;
   unsigned long long *tfp = static_cast<unsigned long long *>(sc.get(kTabCap * sizeof(uint64_t)));
@@ -540,7 +547,7 @@ int percpu_pair(PcRec *rec, uint64_t m_all, uint64_t m, uint64_t t_min, int ts_b
     if (sc.failed) return THAPI_E_NOMEM;
     if (!read_words(word + 2, h + 2, 1, s)) return THAPI_E_CUDA;
     if (!(h[2] & 2)) {  // no fingerprint clash: the first m sorted positions are the records
-      k_pc_gather_t<<<blocks(m), kT, 0, s>>>(rec, alt ? v2 : v1, tid, m, r2);
+      k_pc_gather_t<<<blocks(m), kT, 0, s>>>(rec, alt ? v2 : v1, tid, m, r2, tk);
       count_launches(1);
       ordered = true;
     }
@@ -566,12 +573,13 @@ int percpu_pair(PcRec *rec, uint64_t m_all, uint64_t m, uint64_t t_min, int ts_b
     if (sc.failed) return THAPI_E_NOMEM;
     if (!read_words(word, h, 1, s)) return THAPI_E_CUDA;
     T = h[0];
+    if (T >= (1ull << 31)) return THAPI_E_UNSUPPORTED;  // thread numbers fit 31 bits of the scan words
     tb = 1;
     while ((1ull << tb) <= T) ++tb;
     out->keys = static_cast<uint32_t *>(sc.get(3 * T * sizeof(uint32_t)));
     if (sc.failed) return THAPI_E_NOMEM;
     k_pc_keys<<<blocks(m), kT, 0, s>>>(r2, head, m, out->keys, tid);
-    k_pc_renumber<<<blocks(m), kT, 0, s>>>(r2, tid, m);
+    k_pc_renumber<<<blocks(m), kT, 0, s>>>(r2, tid, m, tk);
     count_launches(2);
   }
   out->threads = T;
@@ -580,10 +588,10 @@ int percpu_pair(PcRec *rec, uint64_t m_all, uint64_t m, uint64_t t_min, int ts_b
   SegDM *agg = static_cast<SegDM *>(sc.get(nb * sizeof(SegDM)));
   if (sc.failed) return THAPI_E_NOMEM;
   launch_tally_init(out->cells, T * F, s);
-  k_seg_local<<<(unsigned)nb, kSegThreads, 0, s>>>(r2, m, agg);
+  k_seg_local<<<(unsigned)nb, kSegThreads, 0, s>>>(tk, m, agg);
   k_seg_blocks<<<1, kSegThreads, 0, s>>>(agg, nb);
   if (cudaMemsetAsync(word + 1, 0, sizeof(uint64_t), s) != cudaSuccess) return THAPI_E_CUDA;
-  k_seg_apply<<<(unsigned)nb, kSegThreads, 0, s>>>(r2, m, agg, k1, v1,
+  k_seg_apply<<<(unsigned)nb, kSegThreads, 0, s>>>(tk, m, agg, k1, v1,
                                                    reinterpret_cast<unsigned long long *>(word + 1), diag);
   uint64_t lmax = 0;
   if (cudaMemcpyAsync(&lmax, word + 1, sizeof(lmax), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
