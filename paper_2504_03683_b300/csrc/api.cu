@@ -1325,7 +1325,7 @@ static int decode_common(thapi_ctx *c, const uint8_t *host, uint64_t nbytes, tha
   c->err_packet = c->err_event = 0;
   Loader ld(c, host, nullptr, nbytes, static_cast<cudaStream_t>(stream));
   ld.set_decode(out, cap, n_out);
-  return ld.run();
+  return ld.status(ld.run());
 }
 
 static TraceRec *find(thapi_ctx *c, thapi_trace_id id) {
