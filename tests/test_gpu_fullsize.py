@@ -61,3 +61,132 @@ def test_large_workload_sampled_parity():
     mask = np.array([(r["host_id"], r["pid"], r["tid"]) in keys for r in rows])
     assert rows_equal(rows[mask], o.rows)
     assert intervals_equal(ivs[np.isin(ivs["stream_id"], sample)], o.intervals)
+
+
+def _resident(cfg):
+    """A workload written into pinned host memory and copied to the device (bench.py's resident trace)."""
+    import torch
+    plan = tg.Plan(cfg)
+    host = torch.empty(plan.nbytes, dtype=torch.uint8, pin_memory=True)
+    plan.write(host.data_ptr())
+    n_streams = plan.n_streams
+    plan.close()
+    return host, host.to("cuda"), n_streams
+
+
+def test_device_workload_full_size():
+    """Device workload (50M commands, 200M events): device-activity invariants on
+    everything, host rows and intervals of sampled host streams exactly."""
+    import torch
+    host, dev, n_streams = _resident(tg.preset("device"))
+    with thapi.Context(0) as ctx:
+        tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), torch.cuda.current_stream())
+        rows, diag = ctx.tally(tid)
+        drows, ddiag = ctx.device_tally(tid)
+        ivs = ctx.timeline(tid)
+        ctx.free(tid)
+    del dev
+    assert diag["events"] == 200_000_000
+    assert ddiag["dev_events"] == 2 * ddiag["dev_pairs"] + ddiag["dev_unpaired"]
+    assert ddiag["dev_pairs"] == ddiag["dev_intervals"] + ddiag["dev_unjoined"] + ddiag["dev_ambiguous"]
+    assert int(drows["count"].sum()) == ddiag["dev_intervals"]
+    dev_iv = ivs[(ivs["flags"] & thapi.IV_DEVICE) != 0]
+    assert len(dev_iv) == ddiag["dev_intervals"] and np.all(dev_iv["level"] == 0)
+    dur = (dev_iv["end_ns"] - dev_iv["start_ns"]).astype(np.uint64)
+    assert np.add.reduce(dur, dtype=np.uint64) == np.add.reduce(drows["total_ns"], dtype=np.uint64)
+    host_iv = ivs[(ivs["flags"] & thapi.IV_DEVICE) == 0]
+    assert len(host_iv) == diag["pairs"] == int(rows["count"].sum())
+    s = ivs["start_ns"]
+    assert np.all(s[1:] >= s[:-1])
+    sample = [0, 1, 255, 511]  # host streams (device streams follow them)
+    o = oracle.run(host.numpy(), streams=sample)
+    st = stream_table(host.numpy())
+    keys = {(int(st[k][0]), int(st[k][1]), int(st[k][2])) for k in sample}
+    mask = np.array([(r["host_id"], r["pid"], r["tid"]) in keys for r in rows])
+    assert rows_equal(rows[mask], o.rows)
+    assert intervals_equal(host_iv[np.isin(host_iv["stream_id"], sample)],
+                           o.intervals[(o.intervals["flags"] & oracle.IV_DEVICE) == 0])
+
+
+def test_percpu_workload_full_size_with_self_time():
+    """Per-CPU workload (100M events in 256 buffers): one host's 32 buffers hold all
+    of its threads' events, so the oracle on them gives that host's rows exactly."""
+    import torch
+    host, dev, n_streams = _resident(tg.preset("percpu"))
+    with thapi.Context(0) as ctx:
+        ctx.set_self_time(True)
+        tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), torch.cuda.current_stream())
+        rows, diag = ctx.tally(tid)
+        srows = ctx.self_tally(tid)
+        ivs = ctx.timeline(tid)
+        ctx.free(tid)
+    del dev
+    assert diag["events"] == 100_000_000 and diag["pairs"] == len(ivs) == int(rows["count"].sum())
+    s = ivs["start_ns"]
+    assert np.all(s[1:] >= s[:-1])
+    h = 3
+    sample = list(range(32 * h, 32 * (h + 1)))
+    o = oracle.run(host.numpy(), streams=sample)
+    assert o.code == oracle.OK
+    assert rows_equal(rows[rows["host_id"] == h], o.rows)
+    assert rows_equal(srows[srows["host_id"] == h], o.self_rows)
+    assert intervals_equal(ivs[np.isin(ivs["stream_id"], sample)], o.intervals)
+
+
+def test_large_workload_self_time_full_size():
+    import torch
+    host, dev, n_streams = _resident(tg.preset("large"))
+    with thapi.Context(0) as ctx:
+        ctx.set_self_time(True)
+        tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), torch.cuda.current_stream())
+        rows, _diag = ctx.tally(tid)
+        srows = ctx.self_tally(tid)
+        ctx.free(tid)
+    del dev
+    assert np.array_equal(srows["count"], rows["count"]) and np.all(srows["total_ns"] <= rows["total_ns"])
+    sample = [3, 100, 400, 511]
+    o = oracle.run(host.numpy(), streams=sample)
+    st = stream_table(host.numpy())
+    keys = {(int(st[k][0]), int(st[k][1]), int(st[k][2])) for k in sample}
+    mask = np.array([(r["host_id"], r["pid"], r["tid"]) in keys for r in srows])
+    assert rows_equal(srows[mask], o.self_rows)
+
+
+def test_batch_workload_full_size():
+    """The batch workload (4096 per-rank traces, ~30 GB) loaded as one from device
+    memory: sampled traces' rows (their host ids) equal the oracle on each trace alone."""
+    import sys
+    import torch
+    import bench
+    saved, sys.argv = sys.argv, [sys.argv[0]]
+    try:
+        args = bench.parse()  # the bench's default batch workload
+    finally:
+        sys.argv = saved
+    cfgs = bench.batch_configs(args, 0)
+    plans = [tg.Plan(c) for c in cfgs]
+    offs, tot = [], 0
+    for pl in plans:
+        offs.append(tot)
+        tot += (pl.nbytes + 255) // 256 * 256
+    host = torch.empty(tot, dtype=torch.uint8, pin_memory=True)
+    for pl, o in zip(plans, offs):
+        pl.write(host.data_ptr() + o)
+    sizes = [pl.nbytes for pl in plans]
+    for pl in plans:
+        pl.close()
+    dev = host.to("cuda")
+    with thapi.Context(0) as ctx:
+        tid = ctx.load_batch_device([(dev.data_ptr() + o, n) for o, n in zip(offs, sizes)],
+                                    torch.cuda.current_stream())
+        rows, diag = ctx.tally(tid)
+        info = ctx.info(tid)
+        ctx.free(tid)
+    del dev
+    assert info["n_hosts"] == len(cfgs) and info["n_streams"] == 8 * len(cfgs)
+    assert diag["pairs"] == int(rows["count"].sum())
+    for t in sorted({0, len(cfgs) - 1} | set(random.Random(7).sample(range(len(cfgs)), 6))):
+        o = oracle.run(host[offs[t]:offs[t] + sizes[t]].numpy())
+        mine = rows[rows["host_id"] == t].copy()
+        mine["host_id"] = 0
+        assert rows_equal(mine, o.rows), t
