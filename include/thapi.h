@@ -321,6 +321,8 @@ typedef struct thapi_load_timing {
                                     analyze_read_bytes) */
   uint64_t percpu_write_bytes;   /* written by that decode: 32 B per per-CPU event (its record or a
                                     marked hole) and a 24 B interval slot per ENTRY */
+  uint32_t grid_mult;            /* configuration used: analysis packet runs per resident CTA */
+  int32_t part_shift;            /* configuration used: device-join partition size 1536 << shift records */
 } thapi_load_timing;
 
 /* The failure path of the library's bounded device waits, on purpose: one
@@ -329,6 +331,16 @@ typedef struct thapi_load_timing {
  * a load returns when a packet copy never lands), E_INVALID for limit 0;
  * nothing faults and the context stays usable. */
 int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream);
+
+/* Enables (1) or disables (0) the autotuner for subsequent loads.  Its
+ * knobs: the analysis kernel's packet runs per resident CTA (1, 2, 4) and the
+ * device join's partition size (records aimed at per partition: 768, 1536,
+ * 3072).  The first load of a shape (packet size, device pairing on, batch or
+ * not, log2 of the packet count) loads the trace once per candidate — the
+ * results are identical — keeps the fastest (device time of the whole load)
+ * and remembers its configuration for later loads of that shape in this
+ * context.  thapi_trace_timing reports the configuration a load used. */
+int thapi_ctx_set_autotune(thapi_ctx *ctx, int enable);
 
 /* Enables (1) or disables (0) per-phase timing of subsequent loads. */
 int thapi_ctx_set_timing(thapi_ctx *ctx, int enable);

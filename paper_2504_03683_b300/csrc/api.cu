@@ -17,12 +17,22 @@
 
 #include "internal.cuh"
 
+namespace thapi {
+// Load configuration the autotuner chooses: analysis packet runs per resident
+// CTA (more runs: shorter runs, finer load balance) and the device join's
+// partition size (records aimed at per partition: 1536 << shift, 1536 >> -shift).
+struct Tuning {
+  uint32_t grid_mult = 1;
+  int32_t part_shift = 0;
+};
+}  // namespace thapi
+
 // the ABI's struct layouts (include/thapi.h), as the binding reads them
 static_assert(sizeof(thapi_tally_row) == 56, "tally row");
 static_assert(sizeof(thapi_interval) == 24, "interval");
 static_assert(sizeof(thapi_event) == 40, "event");
 static_assert(sizeof(thapi_trace_info) == 104, "trace info");
-static_assert(sizeof(thapi_load_timing) == 96, "load timing");
+static_assert(sizeof(thapi_load_timing) == 104, "load timing");
 
 struct TraceRec {
   cudaStream_t stream = nullptr;
@@ -59,6 +69,8 @@ struct thapi_ctx {
   uint64_t err_packet = 0, err_event = 0;
   int timing = 0;
   int self_time = 0;
+  int autotune = 0;
+  std::map<uint64_t, thapi::Tuning> tuned;  // per load shape (tune_key): the configuration kept
 };
 
 namespace thapi {
@@ -363,6 +375,12 @@ class Loader {
   }
   // the load's status with a scratch failure that was a timed-out wait reported as such
   int status(int rc) const { return rc == THAPI_E_NOMEM && sc_.failed == 2 ? THAPI_E_TIMEOUT : rc; }
+  void set_tuning(const Tuning &t) { tune_ = t; }
+  void set_input(const uint8_t *host, const uint8_t *dev, uint64_t nbytes) {
+    host_ = host;
+    dev_ = dev;
+    nbytes_ = nbytes;
+  }
   // a batch: n traces (host or device bytes) loaded as one trace
   void set_batch(const void *const *bytes, const uint64_t *nbytes, uint32_t n, bool on_device) {
     bptr_.assign(bytes, bytes + n);
@@ -374,6 +392,7 @@ class Loader {
 
  private:
   int parse_batch(HostLayout &L);
+  Tuning tune_;
   std::vector<const void *> bptr_;
   std::vector<uint64_t> bn_;
   std::vector<HostLayout> blay_;
@@ -764,7 +783,7 @@ int Loader::run() {
   uint64_t grid = 1, per = 1;
   if (n) {
     if (warp_path) {
-      grid = (uint64_t)c_->num_sms * wplan.ctas_per_sm;
+      grid = (uint64_t)c_->num_sms * wplan.ctas_per_sm * std::max<uint32_t>(1, tune_.grid_mult);
     } else {
       const uint32_t smem = analyze_smem_bytes(P, emax_main, stages, L.n_classes, F);
       grid = (uint64_t)c_->num_sms * blocks_per_sm(c_, smem);
@@ -784,7 +803,9 @@ int Loader::run() {
   uint64_t cap_b = dev_on ? total_events / 2 + 1024 : 0, cap_e = cap_b, cap_h = cap_b;
   // command-id partitions: about 1.5k records each at most (the records are at most the events)
   int part_bits = 1;
-  while (part_bits < 18 && (total_events >> part_bits) > 1536) ++part_bits;
+  const uint64_t part_target =
+      tune_.part_shift >= 0 ? 1536ull << tune_.part_shift : 1536ull >> (uint32_t)(-tune_.part_shift);
+  while (part_bits < 18 && (total_events >> part_bits) > part_target) ++part_bits;
   const uint64_t n_part = 1ull << part_bits;
   uint32_t *part_hist = dev_on ? alloc<uint32_t>(3 * n_part) : nullptr;
   if (dev_on && !part_hist) return THAPI_E_NOMEM;
@@ -1209,6 +1230,8 @@ int Loader::run() {
                             (dev_on ? misc_h_[mCmdCount0] * sizeof(CmdBegin) + misc_h_[mCmdCount0 + 1] * sizeof(CmdEnd) +
                                           misc_h_[mCmdCount0 + 2] * sizeof(CmdHost)
                                     : 0);
+    t.grid_mult = std::max<uint32_t>(1, tune_.grid_mult);
+    t.part_shift = tune_.part_shift;
     if (clk_.on && n) {
       t.index_ms = clk_.ms(PhaseClock::kIdx0, PhaseClock::kIdx1);
       t.analyze_ms = clk_.ms(PhaseClock::kAn0, PhaseClock::kAn1) +
@@ -1271,6 +1294,98 @@ int Loader::run() {
   return THAPI_OK;
 }
 
+// Releases the device results of a load that is not kept.
+static void drop_trace(thapi_ctx *c, TraceRec *t) {
+  dev_free(c, t->rows, t->rows_bytes, t->stream);
+  dev_free(c, t->tl, t->tl_bytes, t->stream);
+  dev_free(c, t->dev_rows, t->dev_rows_bytes, t->stream);
+  dev_free(c, t->self_rows, t->self_rows_bytes, t->stream);
+  cudaStreamSynchronize(t->stream);
+  delete t;
+}
+
+// A load's shape for the autotuner: packet size, device pairing on, batch,
+// and the size class (log2 of the packet count).
+static uint64_t tune_key(const HostLayout &L, bool batch, uint64_t bytes) {
+  bool dev_on = false;
+  for (uint64_t cl : L.cls) {
+    const uint32_t k = cls_kind(cl);
+    dev_on = dev_on || k == kDevBegin || k == kDevEnd || (k == kEntry && cls_cmdw(cl) >= 0);
+  }
+  int sz = 0;
+  while (((bytes / L.P) >> sz) > 1) ++sz;
+  return (uint64_t)L.P | ((uint64_t)dev_on << 32) | ((uint64_t)batch << 33) | ((uint64_t)sz << 40);
+}
+
+// One load (configure sets the loader's input), with the context's tuned
+// configuration for its shape; with autotuning on and the shape not tuned
+// yet, every candidate configuration is loaded (the results are the same),
+// the fastest (device time of the whole load) is kept and its configuration
+// remembered for the shape.
+template <class Configure>
+static int load_tuned(thapi_ctx *c, cudaStream_t s, const Reader &head, bool batch, uint64_t bytes,
+                      Configure configure, thapi_trace_id *out) {
+  auto once = [&](const Tuning &t, TraceRec **tr) {
+    Loader ld(c, nullptr, nullptr, 0, s);
+    configure(ld);
+    ld.set_tuning(t);
+    const int rc = ld.status(ld.run());
+    if (rc == THAPI_OK) *tr = ld.take();
+    return rc;
+  };
+  TraceRec *tr = nullptr;
+  int rc = THAPI_OK;
+  uint64_t key = 0;
+  bool tuned = false;
+  if (c->autotune) {
+    HostLayout L;
+    if (parse_layout(head, L) == THAPI_OK) {
+      key = tune_key(L, batch, bytes);
+      tuned = c->tuned.count(key) != 0;
+      if (!tuned) {  // try every candidate
+        std::vector<Tuning> cands;
+        const bool dev_on = (key >> 32) & 1;
+        for (uint32_t g : {1u, 2u, 4u})
+          for (int32_t ps : {-1, 0, 1})
+            if (dev_on || ps == 0) cands.push_back(Tuning{g, ps});
+        const int timing = c->timing;
+        c->timing = 1;
+        float best = 0.f;
+        for (const Tuning &t : cands) {
+          TraceRec *cand = nullptr;
+          rc = once(t, &cand);
+          if (rc != THAPI_OK) break;
+          const float ms = cand->timing.total_ms;
+          if (!tr || ms < best) {
+            if (tr) drop_trace(c, tr);
+            tr = cand;
+            best = ms;
+            c->tuned[key] = t;
+          } else {
+            drop_trace(c, cand);
+          }
+        }
+        c->timing = timing;
+        if (rc != THAPI_OK) {
+          if (tr) drop_trace(c, tr);
+          c->tuned.erase(key);
+          return rc;
+        }
+      }
+    }
+  }
+  if (!tr) {
+    const auto it = c->tuned.find(key);
+    rc = once(c->autotune && it != c->tuned.end() ? it->second : Tuning{}, &tr);
+    if (rc != THAPI_OK) return rc;
+  }
+  const uint64_t id = c->next_id++;
+  c->traces[id] = tr;
+  c->used += tr->info.device_bytes;
+  *out = id;
+  return THAPI_OK;
+}
+
 static int load_common(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, uint64_t nbytes, void *stream,
                        thapi_trace_id *out) {
   if (!c || !out || (!host && !dev)) return THAPI_E_INVALID;
@@ -1278,19 +1393,9 @@ static int load_common(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, ui
   c->err_level = 0;
   c->err_packet = c->err_event = 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int rc;
-  TraceRec *tr = nullptr;
-  {
-    Loader ld(c, host, dev, nbytes, s);
-    rc = ld.status(ld.run());
-    if (rc == THAPI_OK) tr = ld.take();
-  }
-  if (rc != THAPI_OK) return rc;
-  const uint64_t id = c->next_id++;
-  c->traces[id] = tr;
-  c->used += tr->info.device_bytes;
-  *out = id;
-  return THAPI_OK;
+  const Reader head{host, dev, nbytes, s};
+  return load_tuned(
+      c, s, head, false, nbytes, [&](Loader &ld) { ld.set_input(host, dev, nbytes); }, out);
 }
 
 static int load_batch(thapi_ctx *c, const void *const *bytes, const uint64_t *nbytes, uint32_t n, int on_device,
@@ -1301,20 +1406,13 @@ static int load_batch(thapi_ctx *c, const void *const *bytes, const uint64_t *nb
   if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
   c->err_level = 0;
   c->err_packet = c->err_event = 0;
-  int rc;
-  TraceRec *tr = nullptr;
-  {
-    Loader ld(c, nullptr, nullptr, 0, static_cast<cudaStream_t>(stream));
-    ld.set_batch(bytes, nbytes, n, on_device != 0);
-    rc = ld.status(ld.run());
-    if (rc == THAPI_OK) tr = ld.take();
-  }
-  if (rc != THAPI_OK) return rc;
-  const uint64_t id = c->next_id++;
-  c->traces[id] = tr;
-  c->used += tr->info.device_bytes;
-  *out = id;
-  return THAPI_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint8_t *b0 = static_cast<const uint8_t *>(bytes[0]);
+  const Reader head{on_device ? nullptr : b0, on_device ? b0 : nullptr, nbytes[0], s};  // the shape from trace 0
+  uint64_t total = 0;
+  for (uint32_t t = 0; t < n; ++t) total += nbytes[t];
+  return load_tuned(
+      c, s, head, true, total, [&](Loader &ld) { ld.set_batch(bytes, nbytes, n, on_device != 0); }, out);
 }
 
 static int decode_common(thapi_ctx *c, const uint8_t *host, uint64_t nbytes, thapi_event *out, uint64_t cap,
@@ -1661,6 +1759,12 @@ int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream) {
   sc.release_all();
   cudaStreamSynchronize(s);
   return rc != THAPI_OK ? rc : (int)status;
+}
+
+int thapi_ctx_set_autotune(thapi_ctx *ctx, int enable) {
+  if (!ctx) return THAPI_E_INVALID;
+  ctx->autotune = enable ? 1 : 0;
+  return THAPI_OK;
 }
 
 int thapi_ctx_set_timing(thapi_ctx *ctx, int enable) {

@@ -39,6 +39,7 @@ EXPORTED = (
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
     "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode", "thapi_ctx_set_self_time",
     "thapi_self_tally", "thapi_trace_func_layer", "thapi_trace_load_batch", "thapi_check_device_wait",
+    "thapi_ctx_set_autotune",
 )
 
 
@@ -74,7 +75,8 @@ class LoadTiming(ctypes.Structure):
                [(f, ctypes.c_uint64) for f in ("analyze_read_bytes", "analyze_write_bytes", "analyze_launches",
                                                 "launches")] + \
                [(f, ctypes.c_float) for f in ("join_ms", "self_ms", "percpu_ms", "percpu_decode_ms")] + \
-               [(f, ctypes.c_uint64) for f in ("percpu_read_bytes", "percpu_write_bytes")]
+               [(f, ctypes.c_uint64) for f in ("percpu_read_bytes", "percpu_write_bytes")] + \
+               [("grid_mult", ctypes.c_uint32), ("part_shift", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
@@ -126,6 +128,7 @@ def library():
         "thapi_trace_func_layer": ([vp, u64, u32, P(u32)], i32),
         "thapi_trace_load_batch": ([vp, vp, vp, u32, i32, vp, P(u64)], i32),
         "thapi_check_device_wait": ([vp, u32, vp], i32),
+        "thapi_ctx_set_autotune": ([vp, i32], i32),
         "thapi_trace_timing": ([vp, u64, P(LoadTiming)], i32),
         "thapi_kernel_launches": ([], u64),
         "thapi_tally_static": ([vp, u64, vp, u64, P(u64), P(Diag), vp], i32),
@@ -368,6 +371,10 @@ def thapi_trace_func_layer(ctx: int, trace_id: int, func_id: int) -> int:
     v = ctypes.c_uint32()
     _check(library().thapi_trace_func_layer(ctx, trace_id, func_id, ctypes.byref(v)), "thapi_trace_func_layer")
     return int(v.value)
+
+
+def thapi_ctx_set_autotune(ctx: int, enable: bool = True) -> None:
+    _check(library().thapi_ctx_set_autotune(ctx, 1 if enable else 0), "thapi_ctx_set_autotune")
 
 
 def thapi_ctx_set_self_time(ctx: int, enable: bool = True) -> None:

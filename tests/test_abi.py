@@ -1,7 +1,11 @@
 """The C ABI library loads and exports every entry point its header declares
 (no compute calls: runs without a GPU)."""
+import ctypes
 import os
 import re
+
+import numpy as np
+import pytest
 
 from paper_2504_03683_b300 import thapi
 
@@ -42,4 +46,39 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(thapi.Diag) == 64
     assert ctypes.sizeof(thapi.DeviceDiag) == 64
     assert ctypes.sizeof(thapi.TraceInfo) == 8 * 6 + 4 * 6 + 16 + 16
-    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4 + 4 * 4 + 8 * 2
+    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4 + 4 * 4 + 8 * 2 + 4 * 2
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ABI struct's size and field offsets, compiled from include/thapi.h
+    with the host C compiler, equal the binding's ctypes / numpy layouts."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    from paper_2504_03683_b300 import thapi
+    layouts = {
+        "thapi_tally_row": thapi.ROW_DTYPE, "thapi_interval": thapi.INTERVAL_DTYPE,
+        "thapi_event": thapi.EVENT_DTYPE, "thapi_diag": thapi.Diag, "thapi_device_diag": thapi.DeviceDiag,
+        "thapi_trace_info": thapi.TraceInfo, "thapi_load_timing": thapi.LoadTiming,
+    }
+    want = {}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "thapi.h"', "int main(void) {"]
+    for st, lay in layouts.items():
+        if isinstance(lay, np.dtype):
+            fields = [(f, lay.fields[f][1]) for f in lay.names]
+            size = lay.itemsize
+        else:
+            fields = [(f, getattr(lay, f).offset) for f, _t in lay._fields_]
+            size = ctypes.sizeof(lay)
+        want[st] = [size] + [o for _f, o in fields]
+        args = ", ".join(["sizeof(%s)" % st] + ["offsetof(%s, %s)" % (st, f) for f, _o in fields])
+        lines.append('  printf("' + st + " %zu" * (len(fields) + 1) + '\\n", ' + args + ");")
+    lines += ["  return 0;", "}"]
+    (tmp_path / "layout.c").write_text("\n".join(lines))
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I" + inc, str(tmp_path / "layout.c"), "-o", str(tmp_path / "layout")], check=True)
+    out = subprocess.run([str(tmp_path / "layout")], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in filter(None, out):
+        name, *vals = line.split()
+        assert [int(v) for v in vals] == want[name], name

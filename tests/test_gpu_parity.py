@@ -471,3 +471,31 @@ def test_bounded_device_wait_runs_out_and_the_context_stays_usable(ctx):
     s = tb.add_stream(h, 1, 1)
     tb.place(tb.stream_events(s, [Ev(ids[0][1], 10), Ev(ids[0][2], 20, result=0)], ts_begin=10))
     assert_parity(ctx, tb.build())
+
+
+def test_autotune_keeps_results_and_remembers_the_configuration():
+    """With the autotuner on, the first load of a shape tries every candidate
+    configuration and keeps the fastest; results equal the oracle's, and a
+    later load of the same shape uses the same configuration."""
+    from paper_2504_03683_b300 import thapi
+    b, _c, _e = tg.generate(tg.preset("device", total_calls=30_000, n_hosts=1, pids_per_host=2, tids_per_pid=2,
+                                      n_device_streams=3, seed=41))
+    o = oracle.run(b)
+    with thapi.Context(0) as c:
+        thapi.thapi_ctx_set_autotune(c.handle, True)
+        thapi.thapi_ctx_set_timing(c.handle, True)
+        seen = []
+        for _ in range(2):
+            tid = c.load(b)
+            try:
+                rows, diag = c.tally(tid)
+                drows, ddiag = c.device_tally(tid)
+                ivs = c.timeline(tid)
+                t = thapi.thapi_trace_timing(c.handle, tid)
+            finally:
+                c.free(tid)
+            assert rows_equal(rows, o.rows) and rows_equal(drows, o.dev_rows) and intervals_equal(ivs, o.intervals)
+            assert diag == o.diag and ddiag == o.dev_diag
+            assert t["grid_mult"] in (1, 2, 4) and t["part_shift"] in (-1, 0, 1)
+            seen.append((t["grid_mult"], t["part_shift"]))
+        assert seen[0] == seen[1]
