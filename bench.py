@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--profile-once", action="store_true", help="one load only (for a profiler), no JSON")
     ap.add_argument("--self-time", action="store_true", help="every load also computes self (exclusive) time")
+    ap.add_argument("--autotune", action="store_true", help="the context's autotuner picks the load configuration "
+                                                             "(during the warm-up steps)")
     ap.add_argument("--batch-traces", type=int, default=4096, help="batch workload: traces")
     ap.add_argument("--batch-gb", type=float, default=30.0, help="batch workload: total trace bytes (GB)")
     ap.add_argument("--serve-gb", type=float, default=16.0, help="serve workload: resident trace bytes (GB)")
@@ -296,6 +298,8 @@ def run_batch(args, rank, world, local):
     stream = torch.cuda.current_stream()
     ctx = thapi.Context(local)
     thapi.thapi_ctx_set_timing(ctx.handle, True)
+    if args.autotune:
+        thapi.thapi_ctx_set_autotune(ctx.handle, True)
     dptr = [(dev.data_ptr() + o, n) for o, n in zip(offs, sizes)]
     tid = ctx.load_batch_device(dptr, stream)
     info = ctx.info(tid)
@@ -392,6 +396,8 @@ def run_batch(args, rank, world, local):
                    "trace_bytes": int(sum(sizes)), "packets": int(n_packets),
                    "events_per_trace": {"min": int(ev_sorted[0]), "p50": int(ev_sorted[len(ev_sorted) // 2]),
                                         "max": int(ev_sorted[-1])},
+                   "load_config": {"grid_mult": timings[0]["grid_mult"], "part_shift": timings[0]["part_shift"],
+                                   "autotuned": bool(args.autotune)},
                    "l2": "inputs larger than L2; no flush"},
         "plain": {"value": events / (plain_ms / 1e3), "unit": "events/s", "ms_per_pass": plain_ms,
                   "gpu_launches": plain_launches, "desc": "one thapi_trace_load_device + tally + timeline per trace"},
@@ -506,6 +512,8 @@ def main():
     thapi.thapi_ctx_set_timing(ctx.handle, True)
     if args.self_time:
         thapi.thapi_ctx_set_self_time(ctx.handle, True)
+    if args.autotune:
+        thapi.thapi_ctx_set_autotune(ctx.handle, True)
 
     if args.profile_once:
         tid = thapi.thapi_trace_load_device(ctx.handle, dev.data_ptr(), dev.numel(), stream)
@@ -628,6 +636,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"],
                        "self_time": bool(args.self_time),
+                       "load_config": {"grid_mult": timings[0]["grid_mult"], "part_shift": timings[0]["part_shift"],
+                                       "autotuned": bool(args.autotune)},
                        "calls": int(cfg.total_calls), "events_per_rank": events, "trace_bytes": meta["nbytes"],
                        "packets": meta["n_packets"], "seed": int(cfg.seed), "parallelism": "replicas" if world > 1
                        else "single",

@@ -337,8 +337,8 @@ int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream);
  * device join's partition size (records aimed at per partition: 768, 1536,
  * 3072).  The first load of a shape (packet size, device pairing on, batch or
  * not, log2 of the packet count) loads the trace once per candidate — the
- * results are identical — keeps the fastest (device time of the whole load)
- * and remembers its configuration for later loads of that shape in this
+ * results are identical — keeps the fastest (device time of the analysis and
+ * the device join) and remembers its configuration for later loads of that shape in this
  * context.  thapi_trace_timing reports the configuration a load used. */
 int thapi_ctx_set_autotune(thapi_ctx *ctx, int enable);
 

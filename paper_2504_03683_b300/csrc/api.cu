@@ -1319,8 +1319,10 @@ static uint64_t tune_key(const HostLayout &L, bool batch, uint64_t bytes) {
 
 // One load (configure sets the loader's input), with the context's tuned
 // configuration for its shape; with autotuning on and the shape not tuned
-// yet, every candidate configuration is loaded (the results are the same),
-// the fastest (device time of the whole load) is kept and its configuration
+// yet, every candidate configuration is loaded once and dropped (the results
+// are the same), each knob takes the value whose best trial was fastest in
+// the phase it acts on (runs per CTA: the analysis; partition size: the device
+// join), and the trace is loaded with that configuration, which is
 // remembered for the shape.
 template <class Configure>
 static int load_tuned(thapi_ctx *c, cudaStream_t s, const Reader &head, bool batch, uint64_t bytes,
@@ -1342,35 +1344,32 @@ static int load_tuned(thapi_ctx *c, cudaStream_t s, const Reader &head, bool bat
     if (parse_layout(head, L) == THAPI_OK) {
       key = tune_key(L, batch, bytes);
       tuned = c->tuned.count(key) != 0;
-      if (!tuned) {  // try every candidate
-        std::vector<Tuning> cands;
+      if (!tuned) {  // try every candidate; each knob is chosen by the phase it acts on
         const bool dev_on = (key >> 32) & 1;
-        for (uint32_t g : {1u, 2u, 4u})
-          for (int32_t ps : {-1, 0, 1})
-            if (dev_on || ps == 0) cands.push_back(Tuning{g, ps});
+        const uint32_t grids[3] = {1u, 2u, 4u};
+        const int32_t parts[3] = {-1, 0, 1};
+        float an_best[3] = {1e30f, 1e30f, 1e30f}, jo_best[3] = {1e30f, 1e30f, 1e30f};
         const int timing = c->timing;
         c->timing = 1;
-        float best = 0.f;
-        for (const Tuning &t : cands) {
-          TraceRec *cand = nullptr;
-          rc = once(t, &cand);
-          if (rc != THAPI_OK) break;
-          const float ms = cand->timing.total_ms;
-          if (!tr || ms < best) {
-            if (tr) drop_trace(c, tr);
-            tr = cand;
-            best = ms;
-            c->tuned[key] = t;
-          } else {
+        for (int g = 0; g < 3 && rc == THAPI_OK; ++g)
+          for (int q = 0; q < 3 && rc == THAPI_OK; ++q) {
+            if (!dev_on && parts[q] != 0) continue;
+            TraceRec *cand = nullptr;
+            rc = once(Tuning{grids[g], parts[q]}, &cand);
+            if (rc != THAPI_OK) break;
+            an_best[g] = std::min(an_best[g], cand->timing.analyze_ms);   // the grid acts on the analysis
+            jo_best[q] = std::min(jo_best[q], cand->timing.join_ms);      // the partition size on the join
             drop_trace(c, cand);
           }
-        }
         c->timing = timing;
-        if (rc != THAPI_OK) {
-          if (tr) drop_trace(c, tr);
-          c->tuned.erase(key);
-          return rc;
-        }
+        if (rc != THAPI_OK) return rc;
+        // a knob leaves its default only for a clear gain (3 %): single trials are noisy
+        int bg = 0, bq = 1;
+        for (int g = 1; g < 3; ++g)
+          if (an_best[g] < 0.97f * an_best[0] && an_best[g] < an_best[bg]) bg = g;
+        for (int q = 0; q < 3 && dev_on; ++q)
+          if (q != 1 && jo_best[q] < 0.97f * jo_best[1] && jo_best[q] < jo_best[bq]) bq = q;
+        c->tuned[key] = Tuning{grids[bg], parts[bq]};  // the load below runs with it
       }
     }
   }
