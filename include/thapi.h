@@ -339,7 +339,8 @@ int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream);
  * not, log2 of the packet count) loads the trace once per candidate — the
  * results are identical — keeps the fastest (device time of the analysis and
  * the device join) and remembers its configuration for later loads of that shape in this
- * context.  thapi_trace_timing reports the configuration a load used. */
+ * context.  Without it a load uses 2 runs per CTA and 1536-record partitions.
+ * thapi_trace_timing reports the configuration a load used. */
 int thapi_ctx_set_autotune(thapi_ctx *ctx, int enable);
 
 /* Enables (1) or disables (0) per-phase timing of subsequent loads. */

@@ -22,7 +22,7 @@ namespace thapi {
 // CTA (more runs: shorter runs, finer load balance) and the device join's
 // partition size (records aimed at per partition: 1536 << shift, 1536 >> -shift).
 struct Tuning {
-  uint32_t grid_mult = 1;
+  uint32_t grid_mult = 2;  // two runs per resident CTA: a second wave balances uneven packets
   int32_t part_shift = 0;
 };
 }  // namespace thapi
@@ -1364,9 +1364,9 @@ static int load_tuned(thapi_ctx *c, cudaStream_t s, const Reader &head, bool bat
         c->timing = timing;
         if (rc != THAPI_OK) return rc;
         // a knob leaves its default only for a clear gain (3 %): single trials are noisy
-        int bg = 0, bq = 1;
-        for (int g = 1; g < 3; ++g)
-          if (an_best[g] < 0.97f * an_best[0] && an_best[g] < an_best[bg]) bg = g;
+        int bg = 1, bq = 1;  // the defaults: 2 runs per CTA, 1536-record partitions
+        for (int g = 0; g < 3; ++g)
+          if (g != 1 && an_best[g] < 0.97f * an_best[1] && an_best[g] < an_best[bg]) bg = g;
         for (int q = 0; q < 3 && dev_on; ++q)
           if (q != 1 && jo_best[q] < 0.97f * jo_best[1] && jo_best[q] < jo_best[bq]) bq = q;
         c->tuned[key] = Tuning{grids[bg], parts[bq]};  // the load below runs with it
