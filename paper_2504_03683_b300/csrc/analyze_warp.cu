@@ -43,7 +43,7 @@ namespace {
 using namespace dev;
 
 constexpr uint32_t kEvMax = 1024;       // events of one packet the warp path takes
-constexpr uint32_t kHeights = 64;       // per-height table rows (depth range of a packet)
+constexpr uint32_t kHeights = 32;       // per-height table rows (depth range of a packet)
 constexpr uint32_t kClsMax = 4096;      // class rows held in shared memory
 constexpr uint32_t kChunk = 2048;       // frontier items grabbed per global atomic
 constexpr uint32_t kMaxWarps = 16;      // warps per CTA
@@ -58,14 +58,16 @@ struct WLayout {
 
 __host__ __device__ inline WLayout wlayout(uint32_t P, uint32_t NW, uint32_t NC) {
   WLayout L;
-  uint32_t o = rup(P + 48u, 128u);  // packet (header + content) and a zeroed tail
+  // 16-byte granules (what the bulk copies and the mbarrier need): with 16 KB
+  // packets 12 warps and up to ~700 classes fit one SM's shared memory
+  uint32_t o = rup(P + 48u, 16u);  // packet (header + content) and a zeroed tail
   L.off_tab = o;
   o += kHeights * 16u;  // per-height table: entry timestamp, entry metadata
   L.off_off = o;
   o += kEvMax * 2u;
   L.off_bar = o;
   o += 16u;
-  L.warp_bytes = rup(o, 128u);
+  L.warp_bytes = rup(o, 16u);
   o = L.warp_bytes * NW;
   L.off_ctab = o;
   o += rup((NC + 1u) * 4u, 16u);

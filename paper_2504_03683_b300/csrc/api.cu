@@ -1199,8 +1199,9 @@ int Loader::run() {
   const bool bucket_on = bucket_plan(n_iv, bits, S, sc_, s_, &bcells);
   if (sc_.failed) return THAPI_E_NOMEM;
   clk_.rec(PhaseClock::kCo0, s_);
-  launch_timeline_compact(slots, evbase, sum_nslot, obase, A, order, pk_stream, n, n_iv ? tmin : 0, rec, k1,
-                          bits <= 32, nullptr, bucket_on ? &bcells : nullptr, c_->num_sms, s_);
+  launch_timeline_compact(slots, evbase, sum_nslot, obase, A, order, pk_stream, n, n_iv ? tmin : 0, rec,
+                          bucket_on ? nullptr : k1, bits <= 32, nullptr, bucket_on ? &bcells : nullptr, c_->num_sms,
+                          s_);
   clk_.rec(PhaseClock::kCo1, s_);
   tr_->tl_bytes = std::max<uint64_t>(n_iv, 1) * sizeof(thapi_interval);
   tr_->tl = static_cast<thapi_interval *>(dev_alloc(c_, tr_->tl_bytes, s_));
@@ -1211,6 +1212,7 @@ int Loader::run() {
     uint64_t *k2 = alloc<uint64_t>(n_iv);
     uint32_t *v1 = alloc<uint32_t>(n_iv), *v2 = alloc<uint32_t>(n_iv);
     if (sc_.failed) return THAPI_E_NOMEM;
+    if (bucket_on) launch_rec_keys(rec, n_iv, n_iv ? tmin : 0, k1, bits <= 32, s_);
     launch_iota_u32(v1, n_iv, s_);
     radix_sort_gather(k1, v1, k2, v2, n_iv, bits, rec, tr_->tl, sc_, s_);
   }

@@ -9,9 +9,15 @@
 //  1. reads its S cells, then the cells' runs of records into shared memory
 //     in (stream, position) order, a thread per record (its cell from a
 //     binary search of the cell starts), four loads in flight;
-//  2. sorts (low key bits, position) stably with an LSD radix in shared
-//     memory (9-bit digits, warp ranks from one ballot per digit bit), so
-//     that equal starts keep the (stream, position) order;
+//  2. sorts the items (low key bits, position) in shared memory: each item
+//     takes a rank in its bin of the key's top 9 bits from a shared-memory
+//     atomic and lands at its bin's start plus that rank; the ranks follow no
+//     order, so a thread per bin then insertion-sorts its bin by item value
+//     (about c / 512 items when the starts spread over the bucket).  Items
+//     are unique, so equal starts keep the (stream, position) order.  A
+//     bucket with a bin over kBinMax items (clustered starts) is sorted by
+//     stable LSD radix passes instead (9-bit digits, warp ranks from one
+//     ballot per digit bit);
 //  3. writes the records out in that order with coalesced stores, at the
 //     bucket's offset (an exclusive scan of the bucket sizes).
 // The result is the order (start, stream, entry position).  A cell's records
@@ -37,6 +43,7 @@ constexpr uint32_t kBins = 1u << kDigit;
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kRounds = kCap / kThreads;  // 32-record rounds per warp and radix pass
+constexpr uint32_t kBinMax = 32;               // items of one bin the insertion sort takes
 static_assert(kThreads == (int)kBins, "one thread per digit in the digit scan");
 static_assert(kMaxStreams == 4 * kThreads, "four cells per thread in the cell scan");
 
@@ -86,20 +93,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_bucket_sort(const uint32_t *cnt
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const uint64_t kmask = shift >= 64 ? ~0ull : ((1ull << shift) - 1);
-  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    const uint32_t c = (uint32_t)bsize[b];
-    if (c == 0) continue;
-    const uint64_t st = bstart[b];
-    // cells of this bucket: exclusive scan of the counts (thread t: entries 4t .. 4t+3)
-    {
-      uint32_t loc[4], sum = 0;
+  // the next bucket's cells (thread t: entries 4t .. 4t+3) are loaded while
+  // the current one is sorted
+  uint32_t ncnt[4], nfirst[4], nc = 0;
+  uint64_t nst = 0;
+  auto fetch = [&](uint32_t b) {
+    if (b >= nb) return;
+    nc = (uint32_t)bsize[b];
+    nst = bstart[b];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const uint32_t r = tid * 4 + q;
-        loc[q] = r < S ? cnt[(uint64_t)b * S + r] : 0u;
-        if (r < S) cfirst[r] = first[(uint64_t)b * S + r];
-        sum += loc[q];
-      }
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t r = tid * 4 + q;
+      ncnt[q] = r < S ? cnt[(uint64_t)b * S + r] : 0u;
+      nfirst[q] = r < S ? first[(uint64_t)b * S + r] : 0u;
+    }
+  };
+  fetch(blockIdx.x);
+  uint32_t pw = 1;  // largest power of two below S (at least 1)
+  while ((pw << 1) < S) pw <<= 1;
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const uint32_t c = nc;
+    const uint64_t st = nst;
+    uint32_t loc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      loc[q] = ncnt[q];
+      if (tid * 4 + q < S) cfirst[tid * 4 + q] = nfirst[q];
+    }
+    fetch(b + gridDim.x);
+    if (c == 0) continue;
+    // cells of this bucket: exclusive scan of the counts
+    {
+      uint32_t sum = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sum += loc[q];
       uint32_t inc = sum;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -122,7 +149,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_bucket_sort(const uint32_t *cnt
     // records of the bucket in (cell, position) order: thread per record, its
     // cell found by a binary search of the cell starts (the largest cell start
     // not above it belongs to a non-empty cell), so that neighbouring threads
-    // read neighbouring records of a cell; four records in flight per thread
+    // read neighbouring records of a cell; all of a thread's records in flight
     auto put = [&](uint32_t q, const thapi_interval &v) {
       srec[q] = v;
       const uint64_t key = v.start_ns - t_min;
@@ -130,38 +157,91 @@ __global__ void __launch_bounds__(kThreads, 1) k_bucket_sort(const uint32_t *cnt
       const uint64_t kl = (key - ((uint64_t)b << shift)) & kmask;
       ia[q] = ((IT)kl << QSH) | (IT)q;
     };
-    auto src_of = [&](uint32_t q) -> uint64_t {
-      uint32_t lo = 0, hi = S;
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (cpre[mid] <= q)
-          lo = mid;
-        else
-          hi = mid;
+    {
+      // branchless steps of decreasing powers of two, a thread's searches interleaved
+      uint32_t lo[kRounds];
+#pragma unroll
+      for (uint32_t u = 0; u < kRounds; ++u) lo[u] = 0;
+      for (uint32_t k = pw; k; k >>= 1) {
+#pragma unroll
+        for (uint32_t u = 0; u < kRounds; ++u) {
+          const uint32_t t = lo[u] + k;
+          if (t < S && cpre[t] <= tid + u * kThreads) lo[u] = t;
+        }
       }
-      return (uint64_t)cfirst[lo] + (q - cpre[lo]);
-    };
-    for (uint32_t q0 = tid; q0 < c; q0 += 4 * kThreads) {
-      uint64_t g[4];
-      thapi_interval v[4];
+      uint64_t g[kRounds];
+      thapi_interval v[kRounds];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t q = q0 + u * kThreads;
-        g[u] = q < c ? src_of(q) : 0;
+      for (uint32_t u = 0; u < kRounds; ++u) {
+        const uint32_t q = tid + u * kThreads;
+        g[u] = q < c ? (uint64_t)cfirst[lo[u]] + (q - cpre[lo[u]]) : 0;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (q0 + u * kThreads < c) v[u] = rec[g[u]];
+      for (uint32_t u = 0; u < kRounds; ++u)
+        if (tid + u * kThreads < c) v[u] = rec[g[u]];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (q0 + u * kThreads < c) put(q0 + u * kThreads, v[u]);
+      for (uint32_t u = 0; u < kRounds; ++u)
+        if (tid + u * kThreads < c) put(tid + u * kThreads, v[u]);
+    }
+    // bins of the key's top bits: counts and ranks from shared-memory atomics
+    const int dsh = shift > kDigit ? shift - kDigit : 0;
+    uint32_t *bcnt = wcount;  // [kBins]
+    bcnt[tid] = 0;
+    __syncthreads();
+    IT bv[kRounds];
+    uint32_t brk[kRounds];
+#pragma unroll
+    for (uint32_t r = 0; r < kRounds; ++r) {
+      const uint32_t q = tid + r * kThreads;
+      if (q < c) {
+        bv[r] = ia[q];
+        brk[r] = atomicAdd(&bcnt[(uint32_t)((bv[r] >> QSH) >> dsh)], 1u);
+      }
     }
     __syncthreads();
-    // stable LSD radix on the key bits above QSH
+    {
+      const uint32_t mine = bcnt[tid];
+      uint32_t inc = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= (uint32_t)o) inc += u;
+      }
+      if (lane == 31) wsum[warp] = inc;
+      __syncthreads();
+      uint32_t wbase = 0;
+      for (uint32_t w = 0; w < warp; ++w) wbase += wsum[w];
+      dstart[tid] = wbase + inc - mine;
+    }
+    IT *src = ia;
+    const bool crowded = __syncthreads_or(bcnt[tid] > kBinMax);
+    if (!crowded) {
+#pragma unroll
+      for (uint32_t r = 0; r < kRounds; ++r) {
+        const uint32_t q = tid + r * kThreads;
+        if (q < c) ib[dstart[(uint32_t)((bv[r] >> QSH) >> dsh)] + brk[r]] = bv[r];
+      }
+      __syncthreads();
+      // insertion sort of bin tid by item value (items are unique)
+      const uint32_t b0 = dstart[tid], nbin = bcnt[tid];
+      for (uint32_t i = 1; i < nbin; ++i) {
+        const IT x = ib[b0 + i];
+        uint32_t j = i;
+        for (; j > 0; --j) {
+          const IT y = ib[b0 + j - 1];
+          if (y < x) break;
+          ib[b0 + j] = y;
+        }
+        ib[b0 + j] = x;
+      }
+      __syncthreads();
+      src = ib;
+    }
+    // stable LSD radix on the key bits above QSH (buckets with a crowded bin)
     const uint32_t chunk = ((c + kThreads - 1) / kThreads) * 32;  // items per warp
     const uint32_t lo = warp * chunk, hi = min(lo + chunk, c);
-    IT *src = ia, *dst = ib;
-    for (int sh = QSH; sh < QSH + shift; sh += kDigit) {
+    IT *dst = ib;
+    for (int sh = QSH; crowded && sh < QSH + shift; sh += kDigit) {
       for (uint32_t d = lane; d < kBins; d += 32) wcount[warp * kBins + d] = 0;
       __syncwarp();
       IT v[kRounds];
@@ -216,7 +296,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_bucket_sort(const uint32_t *cnt
       src = dst;
       dst = t;
     }
-    for (uint32_t p = tid; p < c; p += kThreads) out[st + p] = srec[(uint32_t)(src[p] & QMASK)];
+    // out as 8-byte words, consecutive threads on consecutive words
+    const unsigned long long *sw = reinterpret_cast<const unsigned long long *>(srec);
+    unsigned long long *ow = reinterpret_cast<unsigned long long *>(out + st);
+    for (uint32_t w = tid; w < 3 * c; w += kThreads) {
+      const uint32_t p = w / 3;
+      ow[w] = sw[3 * (uint32_t)(src[p] & QMASK) + (w - 3 * p)];
+    }
     __syncthreads();
   }
 }

@@ -475,6 +475,7 @@ void launch_timeline_compact(const thapi_interval *slots, const uint64_t *evbase
 void launch_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uint64_t n, thapi_interval *out,
                             cudaStream_t s);
 void launch_iota_u32(uint32_t *v, uint64_t n, cudaStream_t s);
+void launch_rec_keys(const thapi_interval *rec, uint64_t n, uint64_t t_min, void *keys, bool key32, cudaStream_t s);
 void launch_window_count(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *hi_dev,
                          uint64_t *flags, uint64_t *n_dev, Scratch &sc, cudaStream_t s, uint64_t hi_host);
 void launch_window_write(const thapi_interval *tl, uint64_t hi, uint64_t t0, uint64_t t1, const uint64_t *pos,

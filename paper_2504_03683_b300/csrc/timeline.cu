@@ -48,10 +48,12 @@ __global__ void k_timeline_compact(const thapi_interval *slots, const uint64_t *
         iv.flags &= (uint8_t)(kIvErr | kIvDevice);
         rec[at] = iv;
         key = iv.start_ns - t_min;
-        if (key32)
+        if (!keys) {  // the bucket path takes its keys from the records
+        } else if (key32) {
           static_cast<uint32_t *>(keys)[at] = (uint32_t)key;
-        else
+        } else {
           static_cast<uint64_t *>(keys)[at] = key;
+        }
         if (vals) vals[at] = (uint32_t)at;
       }
       if (bc.cnt) {  // (bucket, stream) cells: records and first record, one atomic pair per run of a cell
@@ -73,6 +75,18 @@ __global__ void k_timeline_compact(const thapi_interval *slots, const uint64_t *
       ob += __popc(bal);
     }
   }
+}
+
+// keys[i] = start of rec[i] - t_min (the radix sort's keys when the
+// compaction left them out for the bucket path and that path gave up)
+__global__ void k_rec_keys(const thapi_interval *rec, uint64_t n, uint64_t t_min, void *keys, bool key32) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t key = rec[i].start_ns - t_min;
+  if (key32)
+    static_cast<uint32_t *>(keys)[i] = (uint32_t)key;
+  else
+    static_cast<uint64_t *>(keys)[i] = key;
 }
 
 __global__ void k_iota_u32(uint32_t *v, uint64_t n) {
@@ -157,6 +171,13 @@ void launch_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uin
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t blocks = std::min<uint64_t>((n + 1023) / 1024, (uint64_t)sms * 8);
     k_timeline_gather<<<(unsigned)std::max<uint64_t>(blocks, 1), 256, 0, s>>>(rec, vals, n, out);
+    count_launches(1);
+  }
+}
+
+void launch_rec_keys(const thapi_interval *rec, uint64_t n, uint64_t t_min, void *keys, bool key32, cudaStream_t s) {
+  if (n) {
+    k_rec_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec, n, t_min, keys, key32);
     count_launches(1);
   }
 }

@@ -286,6 +286,29 @@ def test_spread_starts_many_buckets(ctx):
     assert len(o.intervals) == 24 * 900
 
 
+def test_crowded_bin_inside_a_bucket(ctx):
+    # a burst of 700 calls at one instant among spread starts: the burst's
+    # bucket fits in shared memory but one bin of its starts' top bits is
+    # crowded, so that bucket is sorted by radix passes and the others by bin
+    # insertion; the order must still be (start, stream, position)
+    rng = random.Random(11)
+    tb, h, ids = _builder(P=1024)
+    streams = [tb.add_stream(h, 3, 20 + k) for k in range(12)]
+    for k, s in enumerate(streams):
+        t, evs = 1 << 22, []
+        for j in range(1500):
+            if k == 3 and j == 600:
+                evs += [Ev(ids[0][1], t), Ev(ids[0][2], t)] * 700
+            t += rng.choice([1, 13, 250, 4000])
+            f = rng.randrange(3)
+            d = rng.choice([0, 2, 90])
+            evs += [Ev(ids[f][1], t), Ev(ids[f][2], t + d)]
+            t += d
+        tb.place(tb.stream_events(s, evs, ts_begin=1 << 22))
+    o = assert_parity(ctx, tb.build())
+    assert len(o.intervals) == 12 * 1500 + 700
+
+
 def test_brute_force_sequences_in_one_trace(ctx):
     rng = random.Random(77)
     tb, h, ids = _builder(P=256, n_funcs=2)
