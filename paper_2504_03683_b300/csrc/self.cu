@@ -50,17 +50,34 @@ __global__ void k_self_compact(const thapi_interval *slots, const SelfSlot *side
   const uint64_t wg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   uint32_t mx = 0;
+  // one chunk of slots and the next packet's fields are loaded ahead
+  uint64_t n_sb = 0, n_ob = 0;
+  uint32_t n_n = 0, n_a = 0, n_stream = 0;
+  auto fields = [&](uint64_t i) {
+    if (i >= n_order) return;
+    n_sb = evbase[i];
+    n_n = nslot[i];
+    n_a = A[i];
+    n_stream = pk_stream[order[i]];
+    n_ob = out_base[i];
+  };
+  fields(wg);
   for (uint64_t i = wg; i < n_order; i += nw) {
-    const uint64_t sb = evbase[i];
-    const uint32_t n = nslot[i];
-    const uint32_t a = A[i];
-    const uint32_t stream = pk_stream[order[i]];
+    const uint64_t sb = n_sb;
+    const uint32_t n = n_n;
+    const uint32_t a = n_a;
+    const uint32_t stream = n_stream;
     const uint32_t group = stream_group[stream];
-    uint64_t ob = out_base[i];
+    uint64_t ob = n_ob;
+    fields(i + nw);
+    thapi_interval nxt{};
+    bool n_in = lane < n;
+    if (n_in) nxt = slots[sb + lane];
     for (uint32_t c = 0; c < n; c += 32) {
-      const bool in = c + lane < n;
-      thapi_interval iv{};
-      if (in) iv = slots[sb + c + lane];
+      const bool in = n_in;
+      thapi_interval iv = nxt;
+      n_in = c + 32 + lane < n;
+      if (n_in) nxt = slots[sb + c + 32 + lane];
       const bool valid = in && (iv.flags & kIvValid) != 0;
       const uint32_t bal = __ballot_sync(0xffffffffu, valid);
       if (valid) {

@@ -22,20 +22,35 @@ __global__ void k_timeline_compact(const thapi_interval *slots, const uint64_t *
   const int lane = threadIdx.x & 31;
   const uint64_t wg = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  // one chunk of slots and the next packet's fields are loaded ahead
+  uint64_t n_sb = 0, n_ob = 0;
+  uint32_t n_n = 0, n_a = 0, n_stream = 0;
+  auto fields = [&](uint64_t i) {
+    if (i >= n_order) return;
+    n_sb = evbase[i];
+    n_n = nslot[i];
+    n_a = A[i];
+    n_stream = pk_stream[order[i]];
+    n_ob = out_base[i];
+  };
+  fields(wg);
   for (uint64_t i = wg; i < n_order; i += nw) {
-    const uint64_t sb = evbase[i];
-    const uint32_t n = nslot[i];
-    const uint32_t a = A[i];
-    const uint32_t stream = pk_stream[order[i]];
-    uint64_t ob = out_base[i];
+    const uint64_t sb = n_sb;
+    const uint32_t n = n_n;
+    const uint32_t a = n_a;
+    const uint32_t stream = n_stream;
+    uint64_t ob = n_ob;
+    fields(i + nw);
+    thapi_interval nxt;
+    bool n_in = (uint32_t)lane < n;
+    if (n_in) nxt = slots[sb + lane];
     for (uint32_t c = 0; c < n; c += 32) {
-      bool in = c + lane < n;
-      thapi_interval iv;
+      const bool in = n_in;
+      thapi_interval iv = nxt;
+      n_in = c + 32 + lane < n;
+      if (n_in) nxt = slots[sb + c + 32 + lane];
       bool valid = false;
-      if (in) {
-        iv = slots[sb + c + lane];
-        valid = (iv.flags & kIvValid) != 0;
-      }
+      if (in) valid = (iv.flags & kIvValid) != 0;
       uint32_t bal = __ballot_sync(0xffffffffu, valid);
       const uint64_t at = ob + __popc(bal & ((1u << lane) - 1u));
       uint64_t key = 0;
