@@ -1047,7 +1047,7 @@ int Loader::run() {
       pp.ph = alloc<CmdHost>(nh);
       if (sc_.failed) return THAPI_E_NOMEM;
       launch_part_scatter(jp, pp, c_->num_sms, s_);
-      launch_part_join(jp, pp, s_);
+      launch_part_join(jp, pp, misc_h_[mPartMax], s_);
     } else {
       // one global table: room for twice the largest record kind, short probes;
       // if an insert runs out of probes, a table with room for twice every record

@@ -461,7 +461,7 @@ void launch_part_prep(const PartPlan &pp, cudaStream_t s);
 // Cursors from the scanned base, then every record to its partition.
 void launch_part_scatter(const JoinParams &jp, const PartPlan &pp, int num_sms, cudaStream_t s);
 // One CTA per partition: pairs, joins, emits (needs max_records <= kPartMaxRecords).
-void launch_part_join(const JoinParams &jp, const PartPlan &pp, cudaStream_t s);
+void launch_part_join(const JoinParams &jp, const PartPlan &pp, uint64_t max_records, cudaStream_t s);
 // merge.cu: rows (device, any order, n of them) -> out (device, >= n rows):
 // one row per distinct (host_id, pid, tid, func_id) in key order, *m_dev = rows.
 bool tally_merge_device(const thapi_tally_row *rows, uint64_t n, thapi_tally_row *out, uint64_t *m_dev, Scratch &sc,

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_cmd_emit(JoinParams p) {
 //   record's index, both within the partition, bit 63: a device pair.
 // The first index is only read when its count is one, so the order in which
 // the records arrive does not matter.
-constexpr uint32_t kTab = 4096;  // entries of the shared-memory table (+1 for the zero id)
+constexpr uint32_t kTab = 4096;  // most entries of the shared-memory table (+1 for the zero id)
 constexpr int kJoinThreads = 256;
 constexpr unsigned long long kPairBit = 1ull << 63;
 static_assert(kPartMaxRecords < kTab, "a partition's distinct ids always fit the table");
@@ -222,10 +222,10 @@ __global__ void __launch_bounds__(kThreads) k_part_scatter(JoinParams p, PartPla
 }
 
 // Entry of `key` in a partition table of `mask` + 1 entries (claimed if
-// absent; the zero id has entry kTab).  ~0u if the table had no room (never
-// with at most kPartMaxRecords records).
-__device__ __forceinline__ uint32_t sm_claim(unsigned long long *skey, uint32_t mask, uint64_t key) {
-  if (key == 0) return kTab;
+// absent; the zero id has entry T, past the largest table).  ~0u if the table
+// had no room (never with at most T / 2 records).
+__device__ __forceinline__ uint32_t sm_claim(unsigned long long *skey, uint32_t mask, uint32_t T, uint64_t key) {
+  if (key == 0) return T;
   uint32_t i = (uint32_t)cmd_hash(key) & mask;
   for (uint32_t n = 0; n <= mask; ++n) {
     const unsigned long long cur = atomicCAS(&skey[i], 0ull, (unsigned long long)key);
@@ -235,8 +235,8 @@ __device__ __forceinline__ uint32_t sm_claim(unsigned long long *skey, uint32_t 
   return ~0u;
 }
 
-__device__ __forceinline__ uint32_t sm_find(const unsigned long long *skey, uint32_t mask, uint64_t key) {
-  if (key == 0) return kTab;
+__device__ __forceinline__ uint32_t sm_find(const unsigned long long *skey, uint32_t mask, uint32_t T, uint64_t key) {
+  if (key == 0) return T;
   uint32_t i = (uint32_t)cmd_hash(key) & mask;
   for (uint32_t n = 0; n <= mask; ++n) {
     const unsigned long long cur = skey[i];
@@ -263,8 +263,12 @@ __device__ __forceinline__ void sm_count(unsigned long long *st, int kind, uint3
   }
 }
 
-__global__ void __launch_bounds__(kJoinThreads) k_part_join(JoinParams p, PartPlan pp, uint32_t P) {
-  __shared__ unsigned long long skey[kTab + 1], sst[kTab + 1];
+// T: table entries, a power of two at least twice the largest partition's
+// records (so that a CTA's shared memory, and with it the CTAs per SM,
+// follows the partition size).
+__global__ void __launch_bounds__(kJoinThreads) k_part_join(JoinParams p, PartPlan pp, uint32_t P, uint32_t T) {
+  extern __shared__ unsigned long long jsm[];
+  unsigned long long *skey = jsm, *sst = jsm + T + 1;
   __shared__ unsigned long long red[kJoinThreads / 32][5];
   const uint32_t tid = threadIdx.x;
   unsigned long long pairs = 0, joined = 0, unjoined = 0, ambiguous = 0, h_in_pairs = 0;
@@ -275,24 +279,24 @@ __global__ void __launch_bounds__(kJoinThreads) k_part_join(JoinParams p, PartPl
     const uint64_t h0 = pp.base[2ull * P + part] - p.nb - p.ne, h1 = pp.base[2ull * P + part + 1] - p.nb - p.ne;
     const uint32_t n_rec = (uint32_t)((b1 - b0) + (e1 - e0) + (h1 - h0));
     uint32_t tcap = 64;
-    while (tcap < 2 * n_rec && tcap < kTab) tcap <<= 1;
+    while (tcap < 2 * n_rec && tcap < T) tcap <<= 1;
     const uint32_t mask = tcap - 1;
     for (uint32_t k = tid; k < tcap; k += kJoinThreads) skey[k] = sst[k] = 0;
-    if (tid == 0) skey[kTab] = sst[kTab] = 0;
+    if (tid == 0) skey[T] = sst[T] = 0;
     __syncthreads();
     // count every record of the partition
     for (uint64_t i = e0 + tid; i < e1; i += kJoinThreads) {
-      const uint32_t at = sm_claim(skey, mask, pp.pe[i].cmd);
+      const uint32_t at = sm_claim(skey, mask, T, pp.pe[i].cmd);
       if (at == ~0u) { over = true; continue; }
       sm_count(&sst[at], 1, (uint32_t)(i - e0));
     }
     for (uint64_t i = h0 + tid; i < h1; i += kJoinThreads) {
-      const uint32_t at = sm_claim(skey, mask, pp.ph[i].cmd);
+      const uint32_t at = sm_claim(skey, mask, T, pp.ph[i].cmd);
       if (at == ~0u) { over = true; continue; }
       sm_count(&sst[at], 2, (uint32_t)(i - h0));
     }
     for (uint64_t i = b0 + tid; i < b1; i += kJoinThreads) {
-      const uint32_t at = sm_claim(skey, mask, pp.pb[i].cmd);
+      const uint32_t at = sm_claim(skey, mask, T, pp.pb[i].cmd);
       if (at == ~0u) { over = true; continue; }
       sm_count(&sst[at], 0, 0);
     }
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(kJoinThreads) k_part_join(JoinParams p, PartPl
     // every begin: pair? joined? then its interval, tally and packet count
     for (uint64_t i = b0 + tid; i < b1; i += kJoinThreads) {
       const CmdBegin r = pp.pb[i];
-      const uint32_t at = sm_find(skey, mask, r.cmd);
+      const uint32_t at = sm_find(skey, mask, T, r.cmd);
       if (at == ~0u) continue;  // not reached: counted above
       const unsigned long long st = sst[at];
       if ((st & 3u) != 1u || ((st >> 2) & 3u) != 1u) continue;
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(kJoinThreads) k_part_join(JoinParams p, PartPl
     __syncthreads();
     // host records whose id is a device pair
     for (uint64_t i = h0 + tid; i < h1; i += kJoinThreads) {
-      const uint32_t at = sm_find(skey, mask, pp.ph[i].cmd);
+      const uint32_t at = sm_find(skey, mask, T, pp.ph[i].cmd);
       if (at != ~0u && (sst[at] & kPairBit)) ++h_in_pairs;
     }
     __syncthreads();  // the table is cleared for the next partition
@@ -394,14 +398,18 @@ void launch_part_scatter(const JoinParams &jp, const PartPlan &pp, int num_sms, 
   count_launches(1);
 }
 
-void launch_part_join(const JoinParams &jp, const PartPlan &pp, cudaStream_t s) {
+void launch_part_join(const JoinParams &jp, const PartPlan &pp, uint64_t max_records, cudaStream_t s) {
   const uint32_t P = 1u << pp.part_bits;
+  uint32_t T = 64;
+  while (T < 2 * max_records && T < kTab) T <<= 1;
+  const size_t smem = 2ull * (T + 1) * sizeof(unsigned long long);
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_part_join, kJoinThreads, 0);
+  cudaFuncSetAttribute(k_part_join, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_part_join, kJoinThreads, smem);
   const uint64_t grid = std::min<uint64_t>(P, (uint64_t)std::max(1, sms) * std::max(1, per_sm));
-  k_part_join<<<(unsigned)grid, kJoinThreads, 0, s>>>(jp, pp, P);
+  k_part_join<<<(unsigned)grid, kJoinThreads, smem, s>>>(jp, pp, P, T);
   count_launches(1);
 }
 
