@@ -309,6 +309,31 @@ def test_crowded_bin_inside_a_bucket(ctx):
     assert len(o.intervals) == 12 * 1500 + 700
 
 
+def test_wide_span_buckets_take_64_bit_items(ctx):
+    # starts spread over about 2^38 ns: a bucket's key needs more than 20 bits,
+    # so the bucket sort's items are 64-bit.  One stream spreads its calls
+    # (bins of the top key bits hold a few items: insertion path), another
+    # bursts at the start (one crowded bin: radix passes over all key bits).
+    rng = random.Random(3)
+    tb, h, ids = _builder(P=1024)
+    s0, s1 = tb.add_stream(h, 4, 1), tb.add_stream(h, 4, 2)
+    evs, t = [], 1000
+    for _ in range(3000):
+        t += rng.randrange(1, 1 << 28)
+        d = rng.randrange(0, 100)
+        evs += [Ev(ids[0][1], t), Ev(ids[0][2], t + d)]
+        t += d
+    tb.place(tb.stream_events(s0, evs, ts_begin=1000))
+    evs, t = [], 5000
+    for _ in range(1500):
+        t += rng.choice([0, 1, 2])
+        evs += [Ev(ids[1][1], t), Ev(ids[1][2], t + 1)]
+        t += 1
+    tb.place(tb.stream_events(s1, evs, ts_begin=5000))
+    o = assert_parity(ctx, tb.build())
+    assert len(o.intervals) == 4500
+
+
 def test_brute_force_sequences_in_one_trace(ctx):
     rng = random.Random(77)
     tb, h, ids = _builder(P=256, n_funcs=2)
