@@ -60,6 +60,7 @@ struct thapi_ctx {
   thapi_alloc_fn alloc_fn = nullptr;
   thapi_free_fn free_fn = nullptr;
   void *user = nullptr;
+  cudaMemPool_t pool = nullptr;  // without allocator hooks: a stream-ordered pool that keeps freed memory
   int num_sms = 0;
   int smem_per_sm = 0;
   int smem_per_block = 0;
@@ -116,7 +117,8 @@ static void *dev_alloc(thapi_ctx *c, uint64_t bytes, cudaStream_t s) {
   bytes = (bytes + 255u) & ~255ull;
   if (c->alloc_fn) return c->alloc_fn(bytes, (void *)s, c->user);
   void *p = nullptr;
-  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+  const cudaError_t e = c->pool ? cudaMallocFromPoolAsync(&p, bytes, c->pool, s) : cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -1573,6 +1575,19 @@ int thapi_ctx_create(thapi_ctx **out, int device, uint64_t hbm_cap_bytes) {
     delete c;
     return THAPI_E_CUDA;
   }
+  // the context's own pool: memory freed by one load is reused by the next
+  // without going back to the driver at each synchronisation
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    cudaGetLastError();
+    c->pool = nullptr;  // the device's default pool then
+  }
   *out = c;
   return THAPI_OK;
 }
@@ -1599,6 +1614,10 @@ int thapi_ctx_destroy(thapi_ctx *ctx) {
     delete t;
   }
   ctx->traces.clear();
+  if (ctx->pool) {
+    cudaDeviceSynchronize();  // every stream-ordered free has completed
+    cudaMemPoolDestroy(ctx->pool);
+  }
   delete ctx;
   return THAPI_OK;
 }
