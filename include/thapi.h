@@ -68,7 +68,9 @@
  * with H = 0 (unjoined) or H > 1 (ambiguous), and device events outside a
  * pair, are counted in thapi_device_diag.
  *
- * Threading: a context may be used from one host thread at a time.
+ * Threading: a context may be used from one host thread at a time, except
+ * through a serving loop (thapi_server_*), which drives it from its own
+ * worker threads.
  * Errors: every call returns a THAPI_* status; nothing falls back to the CPU.
  */
 #ifndef THAPI_H
@@ -170,38 +172,50 @@ typedef struct thapi_trace_info {
 typedef void *(*thapi_alloc_fn)(uint64_t bytes, void *stream, void *user);
 typedef void (*thapi_free_fn)(void *ptr, uint64_t bytes, void *stream, void *user);
 
-/* Creates a context on CUDA device `device`.  hbm_cap_bytes caps the device
- * memory held by resident traces (results plus load temporaries); 0 = no cap.
- * *out receives the context.  Errors: E_INVALID (null out), E_CUDA. */
+/* Creates a context on CUDA device `device`: the holder of the decoded traces
+ * that stay resident for queries (the paper's analysis runs next to the
+ * traced job on its node, Sec. 3.7; it has no API for this, so the context
+ * is this library's own).  hbm_cap_bytes caps the device memory held by
+ * resident traces (results plus load temporaries); 0 = no cap.  *out receives
+ * the context.  Errors: E_INVALID (null out), E_CUDA. */
 int thapi_ctx_create(thapi_ctx **out, int device, uint64_t hbm_cap_bytes);
 
 /* Installs allocator hooks (both or neither; NULLs restore the default).
- * Must be called before the first load. */
+ * Must be called before the first load.  Plumbing with no counterpart in the
+ * paper.  Errors: E_INVALID (one hook without the other, or traces loaded). */
 int thapi_ctx_set_allocator(thapi_ctx *ctx, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user);
 
-/* Frees every trace of the context and the context. */
+/* Frees every trace of the context and the context (no paper counterpart).
+ * Errors: E_INVALID (null ctx). */
 int thapi_ctx_destroy(thapi_ctx *ctx);
 
 /* Loads a trace from HOST memory: copies `bytes` (caller-owned, may be freed on
  * return) to the device on `cuda_stream` (a cudaStream_t, NULL = legacy
- * default stream), validates it, decodes every packet, pairs entry/exit events,
- * builds the tally and the sorted timeline, and keeps those results resident
- * on the device.  The raw bytes are released before returning.  Blocks until
+ * default stream), validates it, decodes every packet (Sec. 3.1: the tracer's
+ * binary trace, with a full timestamp where a delta would not fit), pairs
+ * entry/exit events (Sec. 3.2: every call leaves an entry and an exit event,
+ * the exit with its result; Sec. 3.3: intervals from the two), builds the
+ * tally (Sec. 3.4: per hostname / process / thread and function) and the
+ * sorted timeline (Sec. 3.6), and keeps those results resident on the
+ * device.  The raw bytes are released before returning.  Blocks until
  * done.  *out receives the trace id.
  * Errors: E_INVALID, E_FORMAT / E_TRUNCATED (see thapi_last_error_location),
  * E_NOMEM (allocation failed or the HBM cap would be exceeded), E_UNSUPPORTED
  * (streams x functions above 2^28 tally cells), E_TIMEOUT, E_CUDA. */
 int thapi_trace_load(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, void *cuda_stream, thapi_trace_id *out);
 
-/* As thapi_trace_load, for a trace already in DEVICE memory (16-byte aligned,
- * caller-owned, read during the call only; not copied). */
+/* As thapi_trace_load (Sec. 3.2-3.6), for a trace already in DEVICE memory
+ * (16-byte aligned, caller-owned, read during the call only; not copied).
+ * Errors as thapi_trace_load; E_INVALID also for a misaligned pointer. */
 int thapi_trace_load_device(thapi_ctx *ctx, const void *dev_bytes, uint64_t nbytes, void *cuda_stream,
                             thapi_trace_id *out);
 
 /* Decodes every event of a trace in HOST memory (caller-owned, copied to the
  * device during the call) and writes one thapi_event per event to HOST
  * memory `out` (capacity `cap`), in stream order (streams by id, packets by
- * seq, events in packet order); *n_out = the trace's event count.  The
+ * seq, events in packet order); *n_out = the trace's event count.  This is
+ * the content of the paper's pretty-printed event lines (Sec. 3.2: timestamp,
+ * host, vpid, vtid, event name and fields).  The
  * records are the decode step of the analysis (event boundaries, timestamps
  * rebuilt from deltas and absolute values, class, result, command id) made
  * visible, for tools and text output.  cap = 0 is a size query (checks the
@@ -213,7 +227,6 @@ int thapi_trace_load_device(thapi_ctx *ctx, const void *dev_bytes, uint64_t nbyt
 int thapi_decode(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, thapi_event *out, uint64_t cap, uint64_t *n_out,
                  void *cuda_stream);
 
-/* Releases a loaded trace's device results.  Errors: E_INVALID (unknown id). */
 /* Loads n traces as one trace (a batch: the per-rank traces of one run, say,
  * analysed together, as the paper's tools read all ranks' traces at once,
  * Sec. 3.4).  bytes[i] / nbytes[i]: trace i in HOST memory, or in device
@@ -235,18 +248,27 @@ int thapi_decode(thapi_ctx *ctx, const void *bytes, uint64_t nbytes, thapi_event
 int thapi_trace_load_batch(thapi_ctx *ctx, const void *const *bytes, const uint64_t *nbytes, uint32_t n,
                            int on_device, void *cuda_stream, thapi_trace_id *out);
 
+/* Releases a loaded trace's device results (no paper counterpart).
+ * Errors: E_INVALID (unknown id). */
 int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id);
 
 /* Copies the tally rows to HOST memory `rows` (capacity `cap` rows) and the
- * diagnostics to `diag` (may be NULL).  *n_rows = number of rows.  cap = 0 is
- * a size query (returns OK); 0 < cap < rows returns E_RANGE with *n_rows set. */
+ * diagnostics to `diag` (may be NULL).  The tally is the paper's summary
+ * view: per (hostname, process, thread) and API function, the call count and
+ * total / min / max inclusive time (Sec. 3.4; the worked HIP-over-Level-Zero
+ * table of Sec. 4.3), plus the count of calls whose exit result was nonzero
+ * (Sec. 3.2: exits carry the result).  *n_rows = number of rows.  cap = 0 is
+ * a size query (returns OK); 0 < cap < rows returns E_RANGE with *n_rows set.
+ * Errors: E_INVALID (unknown id, null n_rows), E_RANGE, E_CUDA. */
 int thapi_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
                 thapi_diag *diag);
 
 /* Copies the device tally rows (device intervals per (host_id, pid, tid of
  * the device stream, function of the submitting host call), ordered by those
  * keys; err_count is 0) to HOST memory `rows` and the device diagnostics to
- * `diag` (may be NULL).  cap semantics as thapi_tally. */
+ * `diag` (may be NULL): the device-side timings the paper's GPU profiling
+ * records for the commands a call submits (Sec. 3.3, Sec. 3.5).  cap
+ * semantics and errors as thapi_tally. */
 int thapi_device_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
                        thapi_device_diag *diag);
 
@@ -266,23 +288,33 @@ int thapi_tally_merge(thapi_ctx *ctx, const thapi_tally_row *rows, uint64_t n, t
 
 /* Copies the timeline intervals with start_ns < t1 and end_ns >= t0 (t0 = 0,
  * t1 = UINT64_MAX: all), in timeline order, to HOST memory `out` (capacity
- * `cap`).  *n_out = number selected; cap semantics as thapi_tally. */
+ * `cap`): the paper's timeline view of host API calls and device activity
+ * (Sec. 3.6), in the time order its plugins see messages in (Sec. 3.4).
+ * *n_out = number selected; cap semantics as thapi_tally.  Errors: E_INVALID,
+ * E_RANGE, E_NOMEM (window scratch), E_CUDA. */
 int thapi_timeline(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
                    uint64_t cap, uint64_t *n_out);
 
-/* Device-output forms: `rows` / `out` are DEVICE pointers written in order on
- * `cuda_stream`; the call returns once the copy is enqueued and *n is known. */
+/* Device-output form of thapi_tally (Sec. 3.4): `rows` is a DEVICE pointer
+ * written in order on `cuda_stream`; the call returns once the copy is
+ * enqueued and *n_rows is known.  Errors as thapi_tally. */
 int thapi_tally_device(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
                        thapi_diag *diag, void *cuda_stream);
+/* Device-output form of thapi_timeline (Sec. 3.6): `out` is a DEVICE pointer
+ * written in order on `cuda_stream`; the call returns once the copy is
+ * enqueued and *n_out is known.  Errors as thapi_timeline. */
 int thapi_timeline_device(thapi_ctx *ctx, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
                           uint64_t cap, uint64_t *n_out, void *cuda_stream);
 
-/* Facts about a loaded trace. */
+/* Facts about a loaded trace (sizes, counts, time span; no paper counterpart).
+ * Errors: E_INVALID (unknown id). */
 int thapi_trace_info_get(thapi_ctx *ctx, thapi_trace_id id, thapi_trace_info *info);
 
 /* Copies a NUL-terminated name of a loaded trace into buf (capacity cap):
  * kind 0 = host name of host_id `index`, kind 1 = function name of func_id
- * `index`.  *len = name length without the NUL.  E_RANGE if it does not fit. */
+ * `index` (the names the tally and timeline show, Sec. 3.4, Sec. 4.3).
+ * *len = name length without the NUL.  Errors: E_INVALID (unknown id, kind or
+ * index), E_RANGE if it does not fit. */
 int thapi_trace_strings(thapi_ctx *ctx, thapi_trace_id id, int kind, uint32_t index, char *buf, uint64_t cap,
                         uint64_t *len);
 
@@ -290,7 +322,8 @@ int thapi_trace_strings(thapi_ctx *ctx, thapi_trace_id id, int kind, uint32_t in
  * a layered stack, e.g. HIP over Level Zero, Sec. 4.3) to *layer. */
 int thapi_trace_func_layer(thapi_ctx *ctx, thapi_trace_id id, uint32_t func_id, uint32_t *layer);
 
-/* Where the last failed load of this context failed: level 0 = file header or
+/* Where the last failed load of this context failed (no paper counterpart;
+ * the layout checks are this library's): level 0 = file header or
  * tables, 1 = packet header (packet = file index), 2 = packet content
  * (packet = file index, event = index of the event within the packet, or the
  * event count for a count mismatch). */
@@ -325,14 +358,21 @@ typedef struct thapi_load_timing {
   int32_t part_shift;            /* configuration used: device-join partition size 1536 << shift records */
 } thapi_load_timing;
 
-/* The failure path of the library's bounded device waits, on purpose: one
+/* Copies the per-phase timing of a loaded trace to *out (zeros if timing was
+ * off when it was loaded; measurement only, no paper counterpart).
+ * Errors: E_INVALID (unknown id, null out). */
+int thapi_trace_timing(thapi_ctx *ctx, thapi_trace_id id, thapi_load_timing *out);
+
+/* The failure path of the library's bounded device waits, on purpose (no
+ * paper counterpart; failure detection of this library): one
  * warp waits on an mbarrier that nothing completes for at most `limit` tries,
  * gives up, and reports through a status word.  Returns THAPI_E_TIMEOUT (what
  * a load returns when a packet copy never lands), E_INVALID for limit 0;
  * nothing faults and the context stays usable. */
 int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream);
 
-/* Enables (1) or disables (0) the autotuner for subsequent loads.  Its
+/* Enables (1) or disables (0) the autotuner for subsequent loads (no paper
+ * counterpart: the launch configuration is this library's).  Its
  * knobs: the analysis kernel's packet runs per resident CTA (1, 2, 4) and the
  * device join's partition size (records aimed at per partition: 768, 1536,
  * 3072).  The first load of a shape (packet size, device pairing on, batch or
@@ -343,7 +383,8 @@ int thapi_check_device_wait(thapi_ctx *ctx, uint32_t limit, void *cuda_stream);
  * thapi_trace_timing reports the configuration a load used. */
 int thapi_ctx_set_autotune(thapi_ctx *ctx, int enable);
 
-/* Enables (1) or disables (0) per-phase timing of subsequent loads. */
+/* Enables (1) or disables (0) per-phase timing of subsequent loads
+ * (measurement only, no paper counterpart).  Errors: E_INVALID. */
 int thapi_ctx_set_timing(thapi_ctx *ctx, int enable);
 
 /* Enables (1) or disables (0) self time for subsequent loads (off by default).
@@ -362,15 +403,14 @@ int thapi_ctx_set_timing(thapi_ctx *ctx, int enable);
 int thapi_ctx_set_self_time(thapi_ctx *ctx, int enable);
 
 /* Copies the self-time rows of a trace loaded with self time on to HOST
- * memory `rows`: the tally's keys, order, counts and error counts, with
+ * memory `rows` (the layering analysis of Sec. 4.3: what a call spends
+ * itself, apart from the calls it makes): the tally's keys, order, counts and error counts, with
  * total_ns / min_ns / max_ns over the calls' self times.  cap semantics as
  * thapi_tally; E_INVALID if the trace was loaded with self time off. */
 int thapi_self_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows);
 
-/* Timing of a loaded trace (zeros if timing was off when it was loaded). */
-int thapi_trace_timing(thapi_ctx *ctx, thapi_trace_id id, thapi_load_timing *out);
-
-/* Kernels this library has launched in this process (all contexts). */
+/* Kernels this library has launched in this process (all contexts); a
+ * measurement counter with no paper counterpart. */
 uint64_t thapi_kernel_launches(void);
 
 /* Tally of a small trace with no device allocation at all (the paper has no
@@ -397,7 +437,7 @@ uint64_t thapi_kernel_launches(void);
 int thapi_tally_static(const void *dev_bytes, uint64_t nbytes, thapi_tally_row *rows, uint64_t cap,
                        uint64_t *n_rows, thapi_diag *diag, void *cuda_stream);
 
-/* Static description of a status code. */
+/* Static description of a status code (no paper counterpart). */
 const char *thapi_strerror(int code);
 
 #ifdef __cplusplus

@@ -88,6 +88,7 @@
 #include <cstring>
 #include <map>
 #include <new>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -668,6 +669,112 @@ int orc_run(const void *bytes, uint64_t nbytes, const orc_opts *opts, orc_result
   r->code = rc;
   if (rc != ORC_OK) return rc;
   analyse(t, o, keep_p, *r, false);
+  return ORC_OK;
+}
+
+// The all-cores CPU baseline (a per-stream threaded run of the same
+// definition): the selected streams are dealt round robin to `threads`
+// std::threads, each of which validates and analyses its subset exactly as
+// orc_run does; the partial results are then merged.  Streams pair
+// independently only when no stream is a per-CPU buffer and no class carries
+// device activity (DEV_BEGIN / DEV_END or a command id), so any other trace,
+// or threads <= 1, runs as orc_run.  Merge: rows with one key combine
+// (count, total and errors add, min / max), the diagnostics add, and the
+// subsets' intervals, each already in (start, stream, entry position) order
+// over disjoint streams, merge by (start, stream).  Meant for valid traces:
+// an invalid subset returns its own code and location, which need not be the
+// whole trace's first failure.
+int orc_run_threads(const void *bytes, uint64_t nbytes, const orc_opts *opts, uint32_t threads, orc_result **out) {
+  const uint8_t *b = static_cast<const uint8_t *>(bytes);
+  Trace t{};
+  if (threads <= 1 || parse_file(b, nbytes, t) != ORC_OK) return orc_run(bytes, nbytes, opts, out);
+  bool independent = true;
+  for (const Stream &st : t.streams) independent = independent && !(st.flags & STREAM_PER_CPU);
+  for (const Class &c : t.classes)
+    independent = independent && c.kind != KIND_DEV_BEGIN && c.kind != KIND_DEV_END && c.cmd_off < 0;
+  if (!independent) return orc_run(bytes, nbytes, opts, out);
+  orc_opts o{};
+  if (opts) o = *opts;
+  if (!opts) {
+    o.want_intervals = 1;
+    o.t0 = 0;
+    o.t1 = UINT64_MAX;
+  }
+  std::vector<uint32_t> ids;
+  if (o.streams) {
+    std::vector<char> keep(t.n_streams, 0);
+    for (uint32_t i = 0; i < o.n_subset; ++i)
+      if (o.streams[i] < t.n_streams) keep[o.streams[i]] = 1;
+    for (uint32_t s = 0; s < t.n_streams; ++s)
+      if (keep[s]) ids.push_back(s);
+  } else {
+    for (uint32_t s = 0; s < t.n_streams; ++s) ids.push_back(s);
+  }
+  const uint32_t k = (uint32_t)std::min<uint64_t>(threads, std::max<uint64_t>(ids.size(), 1));
+  std::vector<std::vector<uint32_t>> subset(k);
+  for (size_t i = 0; i < ids.size(); ++i) subset[i % k].push_back(ids[i]);
+  std::vector<orc_result *> part(k, nullptr);
+  std::vector<int> code(k, ORC_OK);
+  std::vector<std::thread> pool;
+  for (uint32_t j = 0; j < k; ++j)
+    pool.emplace_back([&, j]() {
+      orc_opts so = o;
+      so.streams = subset[j].data();
+      so.n_subset = (uint32_t)subset[j].size();
+      code[j] = orc_run(bytes, nbytes, &so, &part[j]);
+    });
+  for (auto &th : pool) th.join();
+  Result *r = new (std::nothrow) Result();
+  if (!r) {
+    for (auto *q : part) delete reinterpret_cast<Result *>(q);
+    return ORC_E_INVALID;
+  }
+  *out = reinterpret_cast<orc_result *>(r);
+  for (uint32_t j = 0; j < k; ++j)
+    if (code[j] != ORC_OK || !part[j]) {
+      if (part[j]) *r = *reinterpret_cast<Result *>(part[j]);
+      r->code = part[j] ? code[j] : ORC_E_INVALID;
+      for (auto *q : part) delete reinterpret_cast<Result *>(q);
+      return r->code;
+    }
+  std::map<std::tuple<uint32_t, uint32_t, uint32_t, uint32_t>, orc_row> rows;
+  auto by_start = [](const orc_interval &x, const orc_interval &y) {
+    if (x.start_ns != y.start_ns) return x.start_ns < y.start_ns;
+    return x.stream_id < y.stream_id;
+  };
+  for (uint32_t j = 0; j < k; ++j) {
+    Result &q = *reinterpret_cast<Result *>(part[j]);
+    for (const orc_row &w : q.rows) {
+      auto key = std::make_tuple(w.host_id, w.pid, w.tid, w.func_id);
+      auto it = rows.find(key);
+      if (it == rows.end()) {
+        rows.emplace(key, w);
+        continue;
+      }
+      orc_row &m = it->second;
+      m.count += w.count;
+      m.total_ns += w.total_ns;
+      m.err_count += w.err_count;
+      m.min_ns = std::min(m.min_ns, w.min_ns);
+      m.max_ns = std::max(m.max_ns, w.max_ns);
+    }
+    r->diag.events += q.diag.events;
+    r->diag.pairs += q.diag.pairs;
+    r->diag.unmatched_entries += q.diag.unmatched_entries;
+    r->diag.unmatched_exits += q.diag.unmatched_exits;
+    r->diag.mismatched_pairs += q.diag.mismatched_pairs;
+    r->diag.other_events += q.diag.other_events;
+    r->diag.discarded += q.diag.discarded;
+    r->diag.packets += q.diag.packets;
+    std::vector<orc_interval> both;
+    both.reserve(r->intervals.size() + q.intervals.size());
+    std::merge(r->intervals.begin(), r->intervals.end(), q.intervals.begin(), q.intervals.end(),
+               std::back_inserter(both), by_start);
+    r->intervals.swap(both);
+    delete reinterpret_cast<Result *>(part[j]);
+    part[j] = nullptr;
+  }
+  for (auto &kv : rows) r->rows.push_back(kv.second);
   return ORC_OK;
 }
 

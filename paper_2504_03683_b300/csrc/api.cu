@@ -268,6 +268,27 @@ static int parse_layout(const Reader &r, HostLayout &L) {
   return THAPI_OK;
 }
 
+// A context whose every device allocation goes through the given hooks, for
+// callers that bring their own device memory (the static-scratch tally): the
+// device's attributes are read, and nothing is created on the device (no
+// memory pool, unlike thapi_ctx_create).
+thapi_ctx *hooked_ctx_create(int device, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user) {
+  thapi_ctx *c = new (std::nothrow) thapi_ctx();
+  if (!c) return nullptr;
+  c->device = device;
+  c->alloc_fn = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->smem_per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return nullptr;
+  }
+  return c;
+}
+
 // Header, tables and (host, pid, tid) group numbering of a trace in device
 // memory, for callers outside the loader (the static-scratch tally).
 int describe_device_trace(const uint8_t *dev, uint64_t nbytes, cudaStream_t s, TraceDescription &td) {

@@ -275,6 +275,8 @@ struct TraceDescription {
   std::vector<uint32_t> stream_group, group_keys;
 };
 int describe_device_trace(const uint8_t *dev, uint64_t nbytes, cudaStream_t s, TraceDescription &td);
+// A context that allocates only through the given hooks (creates nothing on the device).
+thapi_ctx *hooked_ctx_create(int device, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user);
 
 // Scratch allocator used inside one library call: every buffer it hands out
 // is released (in stream order) by release_all.

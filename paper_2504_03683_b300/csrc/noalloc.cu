@@ -88,8 +88,10 @@ int tally_static(const uint8_t *dev, uint64_t nbytes, thapi_tally_row *rows, uin
         cudaDeviceGetAttribute(&ds.smem_per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
             cudaSuccess)
       return THAPI_E_CUDA;
-    const int rc = thapi_ctx_create(&ds.ctx, device, 0);
-    if (rc != THAPI_OK) return rc;
+    // a bare context whose allocations all come from the array (no pool, no
+    // driver allocation): it only carries the allocator hooks set per call
+    ds.ctx = hooked_ctx_create(device, arena_alloc, arena_free, nullptr);
+    if (!ds.ctx) return THAPI_E_CUDA;
     ds.scratch = static_cast<uint8_t *>(ptr);
     ds.done = true;
   }

@@ -22,6 +22,16 @@ from tests._util import intervals_equal, rows_equal, stream_table
 pytestmark = pytest.mark.gpu
 
 
+def _check_tie_order(ivs):
+    """Timeline order is (start, stream id, entry position): among intervals
+    with equal starts the stream ids never decrease (the position order within
+    a stream is checked exactly on the sampled streams)."""
+    s, sid = ivs["start_ns"], ivs["stream_id"]
+    tie = s[1:] == s[:-1]
+    assert tie.any()  # the property is exercised: the workload has equal starts
+    assert np.all(sid[1:][tie] >= sid[:-1][tie])
+
+
 def test_large_workload_sampled_parity():
     import torch
 
@@ -48,6 +58,7 @@ def test_large_workload_sampled_parity():
     assert diag["unmatched_entries"] == diag["unmatched_exits"] == diag["mismatched_pairs"] == 0
     s = ivs["start_ns"]
     assert np.all(s[1:] >= s[:-1])
+    _check_tie_order(ivs)
     dur = (ivs["end_ns"] - ivs["start_ns"]).astype(np.uint64)
     assert np.add.reduce(dur, dtype=np.uint64) == np.add.reduce(rows["total_ns"], dtype=np.uint64)
     assert int(((ivs["flags"] & 1) > 0).sum()) == int(rows["err_count"].sum())
@@ -98,6 +109,7 @@ def test_device_workload_full_size():
     assert len(host_iv) == diag["pairs"] == int(rows["count"].sum())
     s = ivs["start_ns"]
     assert np.all(s[1:] >= s[:-1])
+    _check_tie_order(ivs)
     sample = [0, 1, 255, 511]  # host streams (device streams follow them)
     o = oracle.run(host.numpy(), streams=sample)
     st = stream_table(host.numpy())
