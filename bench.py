@@ -45,9 +45,11 @@ WORKLOADS = {
                                         "in total and clamped to [10k, 20M]; 16 KB packets; one batched load vs 4096 "
                                         "plain loads of the same device-resident traces"),
     "serve": dict(preset="large", desc="serving loop: traces of the large workload's API mix (1 host x 1 pid x 8 "
-                                        "threads each) sized log-uniform 1 MB-4 GB, kept device-resident under a "
-                                        "120 GB admission cap; Poisson arrivals at 200 req/s, half tally and half "
-                                        "time-window timeline queries (window log-uniform 1e-4-1 of the span)"),
+                                        "threads each) sized log-uniform 1 MB-4 GB, decoded results kept "
+                                        "device-resident under a 120 GB admission cap (90 GB resident at the "
+                                        "start); Poisson arrivals at 200 req/s: 5% trace loads from pinned host "
+                                        "memory, 5% frees of the oldest trace, the rest half tally and half "
+                                        "time-window queries (width log-uniform 1e-4-1 of the span)"),
     "percpu": dict(preset="percpu", desc="the large workload's shape (8 hosts x 64 threads, 3 layers, depth<=6) "
                                          "written as per-CPU buffers: 32 CPUs per host, threads rotated over CPUs "
                                          "every 200 us (two threads interleaved per CPU); 50M calls = 100M events "
@@ -73,9 +75,15 @@ def parse():
                                                              "(during the warm-up steps)")
     ap.add_argument("--batch-traces", type=int, default=4096, help="batch workload: traces")
     ap.add_argument("--batch-gb", type=float, default=30.0, help="batch workload: total trace bytes (GB)")
-    ap.add_argument("--serve-gb", type=float, default=16.0, help="serve workload: resident trace bytes (GB)")
+    ap.add_argument("--serve-sources", type=int, default=40, help="serve workload: distinct traces in the pool")
+    ap.add_argument("--serve-cap-gb", type=float, default=120.0, help="serve workload: admission cap (GB)")
+    ap.add_argument("--serve-resident-gb", type=float, default=90.0,
+                    help="serve workload: device bytes of the results resident at the start (GB)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve workload: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
+    ap.add_argument("--serve-p-load", type=float, default=0.05, help="serve workload: share of loads (and of frees)")
+    ap.add_argument("--serve-load-slots", type=int, default=2)
+    ap.add_argument("--serve-query-slots", type=int, default=6)
     return ap.parse_args()
 
 
@@ -439,75 +447,171 @@ def run_batch(args, rank, world, local):
     ctx.close()
 
 
-def run_serve(args, rank, world, local):
-    """Config 5: queries against device-resident traces as they arrive; p50 / p99 latency."""
+def serve_pool(args, rank):
+    """Trace sources of the serve workload: sizes log-uniform in 1 MB - 4 GB (the
+    large workload's API mix, 1 host x 1 pid x 8 threads each), written into
+    one pinned host buffer; returns (host tensor, [(offset, nbytes)])."""
     import numpy as np
     import torch
     import tracegen as tg
-    from paper_2504_03683_b300 import serve, thapi
     rng = np.random.default_rng(11 + rank)
-    sizes, tot = [], 0.0
-    while tot < args.serve_gb * 1e9:
-        b = float(np.exp(rng.uniform(np.log(1e6), np.log(4e9))))
-        b = min(b, args.serve_gb * 1e9 - tot) if tot + b > args.serve_gb * 1e9 and sizes else b
-        sizes.append(b)
-        tot += b
-    srv = serve.Server(local, 120 * 10**9)
-    load_s, events, trace_bytes = 0.0, 0, 0
-    for i, b in enumerate(sizes):
-        cfg = tg.preset("large", total_calls=max(1000, int(b / 40.2) // 2), n_hosts=1, pids_per_host=1,
-                        tids_per_pid=8, seed=200000 + 1000 * rank + i)
-        host, meta = generate_pinned(cfg)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        k = srv.admit((host.data_ptr(), host.numel()))
-        torch.cuda.synchronize()
-        load_s += time.perf_counter() - t0
-        if k is not None:
-            events += srv.traces[k].events
-            trace_bytes += meta["nbytes"]
-        del host
-    spans = [(r.t_min, r.t_max) for r in srv.traces]
-    reqs = serve.poisson_requests(args.serve_rate, args.serve_seconds, spans, seed=13 + rank)
-    warm = serve.poisson_requests(args.serve_rate, 1.0, spans, seed=17 + rank)
-    srv.run(warm)
+    sizes = [float(np.exp(rng.uniform(np.log(1e6), np.log(4e9)))) for _ in range(args.serve_sources)]
+    plans = [tg.Plan(tg.preset("large", total_calls=max(1000, int(b / 40.2) // 2), n_hosts=1, pids_per_host=1,
+                               tids_per_pid=8, seed=200000 + 1000 * rank + i)) for i, b in enumerate(sizes)]
+    offs, tot = [], 0
+    for pl in plans:
+        offs.append((tot, pl.nbytes))
+        tot += (pl.nbytes + 255) // 256 * 256
+    host = torch.empty(tot, dtype=torch.uint8, pin_memory=True)
+    for pl, (o, _n) in zip(plans, offs):
+        pl.write(host.data_ptr() + o)
+        pl.close()
+    return host, offs
+
+
+def run_serve(args, rank, world, local):
+    """Config 5: a Poisson stream of trace loads, tally / window queries and trace
+    frees over traces kept resident near the 120 GB admission cap, served by the
+    serving loop (continuous batching, thapi_server_*) and, on the same
+    schedule from the same resident set, one request at a time with plain
+    launches on one stream."""
+    import numpy as np
+    import torch
+    from paper_2504_03683_b300 import serve, thapi
+    host, offs = serve_pool(args, rank)
+    dev = host.to("cuda")
+    torch.cuda.synchronize()
+    host_src = [(host.data_ptr() + o, n, False) for o, n in offs]
+    dev_src = [(dev.data_ptr() + o, n, True) for o, n in offs]
+    cap = int(args.serve_cap_gb * 1e9)
+    ctx = thapi.Context(local, cap, use_torch_allocator=False)
+    stream = torch.cuda.current_stream()
+    k_src = len(offs)
+
+    def preload():
+        """Loads sources round robin from device memory until the resident
+        results reach the target; returns (trace ids, their sources)."""
+        ids, srcs, k = [], [], 0
+        target = int(args.serve_resident_gb * 1e9)
+        used = 0
+        while used < target:
+            s = k % k_src
+            tid = thapi.thapi_trace_load_device(ctx.handle, dev_src[s][0], dev_src[s][1], stream)
+            ids.append(tid)
+            srcs.append(s)
+            used += thapi.thapi_trace_info_get(ctx.handle, tid)["device_bytes"]
+            k += 1
+        return ids, srcs, used
+
+    def unload_all(ids_alive):
+        for tid in ids_alive:
+            thapi.thapi_trace_free(ctx.handle, tid)
+
+    t_pre = time.perf_counter()
+    ids, srcs, resident_bytes = preload()
+    pre_s = time.perf_counter() - t_pre
+    info = {}
+    for tid, s in zip(ids, srcs):
+        if s not in info:
+            info[s] = thapi.thapi_trace_info_get(ctx.handle, tid)
+    spans = [(info[s]["t_min"], info[s]["t_max"]) for s in range(k_src)]
+    src_events = [info[s]["events"] for s in range(k_src)]
+    max_iv = max(info[s]["intervals"] for s in range(k_src))
+    steps = serve.make_schedule(args.serve_rate, args.serve_seconds, srcs, spans, seed=13 + rank,
+                                p_load=args.serve_p_load, p_free=args.serve_p_load)
+    warm = serve.make_schedule(args.serve_rate, 0.5, srcs, spans, seed=17 + rank, p_load=0.0, p_free=0.0)
+
+    def answered(kind, n, events):
+        return events if kind == "tally" else (2 * n if kind == "window" else (events if kind == "load" else 0))
+
+    # ---- one request at a time with plain launches
+    rows_out = np.zeros(1 << 16, dtype=thapi.ROW_DTYPE)
+    ivs_pin = torch.empty(max(1, max_iv) * 24, dtype=torch.uint8, pin_memory=True)
+    ivs_out = ivs_pin.numpy().view(thapi.INTERVAL_DTYPE)
+    serve.serve_serial(ctx, warm, ids, host_src, rows_out, ivs_out, stream)
+    t0 = time.perf_counter()
+    serial = serve.serve_serial(ctx, steps, ids, host_src, rows_out, ivs_out, stream)
+    serial_wall = time.perf_counter() - t0
+    # the resident set as it was before the schedule: every trace now resident leaves, the preload is redone
+    alive = {}
+    for i, tid in enumerate(ids):
+        alive[i] = tid
+    for st, o in zip(steps, serial):
+        if o is None or o.status != thapi.OK:
+            continue
+        if st.kind == "load":
+            alive[st.handle] = o.trace
+        elif st.kind == "free":
+            alive.pop(st.handle, None)
+    unload_all(alive.values())
+    ids, srcs2, resident_bytes = preload()
+    assert srcs2 == srcs
+
+    # ---- the serving loop
+    srv = serve.Server(ctx, args.serve_load_slots, args.serve_query_slots)
+    srv.replay(warm, ids, host_src)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
     launches0 = thapi.thapi_kernel_launches()
     t0 = time.perf_counter()
-    out = srv.run(reqs)
+    res = srv.replay(steps, ids, host_src)
     wall = time.perf_counter() - t0
     launches = thapi.thapi_kernel_launches() - launches0
     clocks = sampler.stop()
-    lat = [o[0] * 1e3 for o in out]
-    lat_t = [o[0] * 1e3 for o, r in zip(out, sorted(reqs, key=lambda q: q.arrival)) if r.kind == "tally"]
-    lat_w = [o[0] * 1e3 for o, r in zip(out, sorted(reqs, key=lambda q: q.arrival)) if r.kind == "window"]
-    answered = sum(srv.traces[r.trace].events if r.kind == "tally" else 2 * n
-                   for (lt, n), r in zip(out, sorted(reqs, key=lambda q: q.arrival)))
+    stats = srv.stats()
+    srv.close()
+
+    def totals(outs, wall_s):
+        ev = {"load": 0, "tally": 0, "window": 0}
+        h2d = d2h = 0
+        for st, o in zip(steps, outs):
+            if o is None or o.status != thapi.OK or st.kind == "free":
+                continue
+            ev[st.kind] += answered(st.kind, o.n, o.events)
+            if st.kind == "load":
+                h2d += offs[st.source][1]
+            else:
+                d2h += o.n * (56 if st.kind == "tally" else 24)
+        end = max((o.t_done for o in outs if o is not None), default=0.0) - min(s.arrival for s in steps)
+        return {"answered_events_per_s": (ev["tally"] + ev["window"]) / wall_s,
+                "loaded_events_per_s": ev["load"] / wall_s, "wall_s": wall_s, "h2d_bytes": h2d, "d2h_bytes": d2h,
+                "last_result_s": end}
+
+    srv_sum, ser_sum = serve.summary(res), serve.summary(serial)
+    srv_tot, ser_tot = totals(res, wall), totals(serial, serial_wall)
+    q99 = srv_sum["queries"]["p99"]
     line = {
-        "metric": "p99 latency of tally / window queries at %g req/s (arrival to result on the host)" % args.serve_rate,
-        "value": serve.percentile(lat, 99), "unit": "ms", "n_gpus": world, "steps": len(reqs), "warmup": len(warm),
-        "ms_per_step": float(np.mean(lat)), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic",
-        "config": {"workload": "serve", "desc": WORKLOADS["serve"]["desc"], "traces": len(srv.traces),
-                   "refused": srv.refused, "resident_trace_bytes": trace_bytes, "resident_events": events,
-                   "requests": len(reqs), "seconds": args.serve_seconds},
-        "latency_ms": {"p50": serve.percentile(lat, 50), "p99": serve.percentile(lat, 99), "max": max(lat),
-                       "tally_p50": serve.percentile(lat_t, 50) if lat_t else None,
-                       "tally_p99": serve.percentile(lat_t, 99) if lat_t else None,
-                       "window_p50": serve.percentile(lat_w, 50) if lat_w else None,
-                       "window_p99": serve.percentile(lat_w, 99) if lat_w else None},
-        "requests_per_s": len(reqs) / wall,
-        "answered_events_per_s": answered / wall,
-        "admission_load_events_per_s": events / load_s if load_s else None,
-        "e2e": {"value": serve.percentile(lat, 99), "unit": "ms", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": None, "note": "every latency is already arrival to result on the host"},
+        "metric": "p99 latency of tally / window queries at %g req/s with loads and frees, arrival to result "
+                  "on the host" % args.serve_rate,
+        "value": q99, "unit": "ms", "n_gpus": world, "steps": len(steps), "warmup": len(warm),
+        "ms_per_step": float(np.mean([(o.t_done - o.t_arrival) * 1e3 for o in res if o.status == thapi.OK])),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serve", "desc": WORKLOADS["serve"]["desc"], "sources": k_src,
+                   "source_bytes": {"min": int(min(n for _o, n in offs)), "max": int(max(n for _o, n in offs)),
+                                    "total": int(sum(n for _o, n in offs))},
+                   "cap_bytes": cap, "resident_at_start": {"traces": len(ids), "device_bytes": resident_bytes},
+                   "preload_s": round(pre_s, 2), "requests": len(steps),
+                   "mix": {k: sum(1 for s in steps if s.kind == k) for k in serve.KINDS},
+                   "seconds": args.serve_seconds, "slots": {"load": args.serve_load_slots,
+                                                            "query": args.serve_query_slots},
+                   "loads_from": "pinned host memory"},
+        "latency_ms": srv_sum,
+        "serial": {"latency_ms": ser_sum, **ser_tot,
+                   "desc": "the same schedule one request at a time in arrival order with the plain entry points "
+                           "(thapi_trace_load, thapi_tally, thapi_timeline, thapi_trace_free) on one stream"},
+        "served_over_serial_p99": ser_sum["queries"]["p99"] / q99 if q99 else None,
+        **srv_tot,
+        "server_stats": stats,
+        "e2e": {"value": q99, "unit": "ms", "h2d_bytes_per_step": srv_tot["h2d_bytes"] / len(steps),
+                "d2h_bytes_per_step": srv_tot["d2h_bytes"] / len(steps),
+                "note": "every latency is already arrival to result in host memory; loads read pinned host memory"},
         "gpu_launches": launches, "clocks": clocks, "cpu_baseline": None, "roofline": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
-    srv.close()
+    ctx.close()
+    del dev, host
 
 
 def main():

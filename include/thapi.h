@@ -91,6 +91,7 @@ extern "C" {
 #define THAPI_E_CUDA 6        /* a CUDA runtime call failed */
 #define THAPI_E_RANGE 7       /* output capacity too small; the needed count is returned */
 #define THAPI_E_UNSUPPORTED 8 /* valid trace outside this build's limits (see thapi_trace_load) */
+/* 9: THAPI_PENDING, a serving-loop request not completed yet (thapi_server_poll) */
 
 typedef struct thapi_ctx thapi_ctx;
 typedef uint64_t thapi_trace_id;
@@ -436,6 +437,118 @@ uint64_t thapi_kernel_launches(void);
  * E_TIMEOUT, E_RANGE, E_CUDA. */
 int thapi_tally_static(const void *dev_bytes, uint64_t nbytes, thapi_tally_row *rows, uint64_t cap,
                        uint64_t *n_rows, thapi_diag *diag, void *cuda_stream);
+
+/* ------------------------------------------------------------------ serving
+ * A serving loop over the traces a context keeps resident, with continuous
+ * batching.  The paper's analysis runs on the traced job's node and keeps up
+ * with it (Sec. 3.7, on-node processing), answering with the tally and
+ * timeline views (Sec. 3.4, Sec. 3.6); served, that is a stream of requests:
+ * a trace arrives (LOAD: decoded, paired, tallied and ordered as by
+ * thapi_trace_load), its tally is asked for (TALLY), the intervals of a time
+ * range of its timeline (WINDOW, as thapi_timeline), and it leaves (FREE).
+ *
+ * Requests that arrive while others are on the GPU do not queue behind them:
+ * each starts as soon as a slot of its class is free (load slots and query
+ * slots, each a host thread with its own CUDA stream; query streams have the
+ * highest priority, load streams the lowest) and, for a load, as soon as the
+ * context's HBM cap (thapi_ctx_create) has room for the load's coarse peak
+ * next to what is resident and what running loads were charged (admission by
+ * HBM footprint; loads are admitted in arrival order; queries and frees pass
+ * waiting loads).  A load whose charge exceeds the whole cap is refused
+ * (E_NOMEM).  The work of different requests overlaps on the device; every
+ * result equals that of the plain entry points.  Per trace, a FREE waits for
+ * the queries submitted before it, and queries submitted after it fail with
+ * E_INVALID.  While a server runs, its context may be used by other host
+ * threads only through thread-safe calls (tally, timeline, info, loads
+ * without autotuning). */
+#define THAPI_PENDING 9 /* thapi_server_poll: the request has not completed within the wait */
+
+#define THAPI_REQ_LOAD 0u   /* a trace arrives: load it (bytes, nbytes, on_device) */
+#define THAPI_REQ_TALLY 1u  /* the tally rows of a trace */
+#define THAPI_REQ_WINDOW 2u /* the timeline intervals of a trace with start < t1 and end >= t0 */
+#define THAPI_REQ_FREE 3u   /* the trace leaves: its results are released */
+
+typedef struct thapi_server thapi_server;
+
+/* One request (72 B). */
+typedef struct thapi_request {
+  uint32_t kind;         /* THAPI_REQ_* */
+  uint32_t on_device;    /* LOAD: `bytes` is DEVICE memory (16-byte aligned), else HOST memory */
+  const void *bytes;     /* LOAD: the trace, caller-owned and unchanged until the request completes */
+  uint64_t nbytes;       /* LOAD */
+  thapi_trace_id trace;  /* TALLY / WINDOW / FREE: a resident trace (when after = 0) */
+  uint64_t after;        /* TALLY / WINDOW / FREE: the ticket of the LOAD that brings the trace in (0: none);
+                            the request starts once that load has completed, and fails with its status */
+  uint64_t t0, t1;       /* WINDOW: the window [t0, t1) */
+  void *out;             /* TALLY / WINDOW: result memory (HOST or DEVICE; pinned host memory is written by
+                            the device directly), or NULL: pinned memory the server owns */
+  uint64_t cap;          /* capacity of `out` in rows / intervals (E_RANGE with n set when too small) */
+} thapi_request;
+
+/* What a request did (64 B).  Times are seconds on the server's clock
+ * (thapi_server_now). */
+typedef struct thapi_result {
+  int32_t status;        /* THAPI_OK or the request's error */
+  uint32_t kind;
+  thapi_trace_id trace;  /* the trace (LOAD: the new id) */
+  uint64_t n;            /* rows / intervals of the result (the count needed on E_RANGE) */
+  uint64_t events;       /* events of the trace */
+  const void *data;      /* the result: `out`, or server-owned pinned memory valid until thapi_server_release */
+  double t_arrival;      /* submission (or, through thapi_server_replay, the scheduled arrival) */
+  double t_admit;        /* the request started on its slot */
+  double t_done;         /* the result is in place */
+} thapi_result;
+
+typedef struct thapi_server_stats {
+  uint64_t submitted, completed;
+  uint64_t load_waits;      /* loads whose admission waited for device memory */
+  uint64_t peak_running;    /* most requests in flight at once */
+  uint64_t peak_committed;  /* most device memory resident plus charged to running loads (bytes) */
+} thapi_server_stats;
+
+/* Starts a serving loop on `ctx` with load_slots loads and query_slots
+ * queries / frees in flight at most (1..63 together).  The context's cap is
+ * the admission cap.  Errors: E_INVALID, E_NOMEM, E_CUDA. */
+int thapi_server_create(thapi_ctx *ctx, uint32_t load_slots, uint32_t query_slots, thapi_server **out);
+
+/* Submits a request; *ticket names it.  The request's own failures (refused
+ * load, unknown or departed trace, failed load it waits for, format errors)
+ * come back through its result.  Errors: E_INVALID (malformed request, or
+ * `after` naming no earlier LOAD), E_NOMEM. */
+int thapi_server_submit(thapi_server *s, const thapi_request *req, uint64_t *ticket);
+
+/* Waits up to wait_ms (UINT32_MAX: without limit) for the request to complete
+ * and copies its result to *res.  Returns THAPI_PENDING if it has not
+ * completed; E_INVALID for an unknown or released ticket. */
+int thapi_server_poll(thapi_server *s, uint64_t ticket, uint32_t wait_ms, thapi_result *res);
+
+/* Forgets a completed request and returns its server-owned result memory.
+ * Errors: E_INVALID (unknown, released or not completed). */
+int thapi_server_release(thapi_server *s, uint64_t ticket);
+
+/* Seconds since the server was created (steady clock). */
+double thapi_server_now(thapi_server *s);
+
+/* Replays a schedule: request i is submitted at arrival_s[i] seconds after
+ * the call starts (nondecreasing), its `after`, if nonzero, being 1 + the
+ * index of an earlier LOAD of the schedule; then every request is waited for
+ * and its result copied to results[i] (t_arrival = the scheduled time, so
+ * latencies include any delay of the submission).  keep = 0 returns each
+ * result's server-owned memory as soon as the request completes
+ * (results[i].data is then NULL); keep = 1 keeps it, valid until
+ * thapi_server_destroy.  Errors: E_INVALID (a malformed schedule; nothing is
+ * submitted). */
+int thapi_server_replay(thapi_server *s, const thapi_request *reqs, const double *arrival_s, uint64_t n, int keep,
+                        thapi_result *results);
+
+/* Counters of the serving loop so far.  Errors: E_INVALID. */
+int thapi_server_stats_get(thapi_server *s, thapi_server_stats *st);
+
+/* Waits for every submitted request, stops the loop and frees it; loads
+ * that could never be admitted (nothing running, nothing left to free) end
+ * with E_NOMEM.  The traces it loaded stay resident in the context.
+ * Errors: E_INVALID. */
+int thapi_server_destroy(thapi_server *s);
 
 /* Static description of a status code (no paper counterpart). */
 const char *thapi_strerror(int code);

@@ -10,6 +10,7 @@
 #include <atomic>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <thread>
 #include <tuple>
@@ -51,6 +52,10 @@ struct TraceRec {
   std::vector<uint32_t> host_name, func_name;
   std::vector<uint16_t> func_layer;
   thapi_load_timing timing{};
+  // window index (prefix maxima of interval ends per block), built by the first window query
+  std::mutex win_mu;
+  uint64_t *win_bmax = nullptr;
+  uint64_t win_bytes = 0;
 };
 
 struct thapi_ctx {
@@ -72,6 +77,9 @@ struct thapi_ctx {
   int self_time = 0;
   int autotune = 0;
   std::map<uint64_t, thapi::Tuning> tuned;  // per load shape (tune_key): the configuration kept
+  // guards traces, next_id, used, tuned and the error location, so that loads
+  // and queries of the serving loop may run from several host threads
+  std::mutex mu;
 };
 
 namespace thapi {
@@ -111,6 +119,14 @@ struct PhaseClock {
       if (e) cudaEventDestroy(e);
   }
 };
+
+// Where a load failed (thapi_last_error_location).
+static void set_err(thapi_ctx *c, int level, uint64_t packet, uint64_t event) {
+  std::lock_guard<std::mutex> g(c->mu);
+  c->err_level = level;
+  c->err_packet = packet;
+  c->err_event = event;
+}
 
 static void *dev_alloc(thapi_ctx *c, uint64_t bytes, cudaStream_t s) {
   if (bytes == 0) bytes = 256;
@@ -358,6 +374,32 @@ enum Misc {
   mCount
 };
 
+// Coarse peak device memory of one load (packets when copied, index, tally
+// cells, interval slots, the timeline's sort; device-activity records and
+// self-time records when the trace has them): what admission against the
+// context's cap charges up front.  G = (host, pid, tid) groups.
+static uint64_t load_estimate(const HostLayout &L, uint64_t G, bool copies_packets, bool self_on) {
+  const uint64_t n = L.n_packets, P = L.P, cells = G * (uint64_t)L.n_funcs;
+  const uint64_t est_events = n * (uint64_t)((P - kPacketHeader) / 8);
+  bool dev_on = false;
+  for (uint64_t c : L.cls) {
+    const uint32_t k = cls_kind(c);
+    dev_on = dev_on || k == kDevBegin || k == kDevEnd || (k == kEntry && cls_cmdw(c) >= 0);
+  }
+  return (copies_packets ? n * P : 0) + n * 128 + cells * 80 + est_events * 24 +
+         (dev_on ? est_events * 48 + cells * 80 : 0) + (self_on ? est_events * 96 + cells * 120 : 0);
+}
+
+// Number of (host, pid, tid) groups of the per-thread streams.
+static uint64_t group_count(const HostLayout &L) {
+  std::vector<std::tuple<uint32_t, uint32_t, uint32_t>> k;
+  for (uint32_t i = 0; i < L.n_streams; ++i)
+    if (!(L.srow[4ull * i + 3] & kStreamPerCpu))
+      k.push_back(std::make_tuple(L.srow[4ull * i], L.srow[4ull * i + 1], L.srow[4ull * i + 2]));
+  std::sort(k.begin(), k.end());
+  return (uint64_t)(std::unique(k.begin(), k.end()) - k.begin());
+}
+
 #define CK(x)                                   \
   do {                                          \
     if ((x) != cudaSuccess) {                   \
@@ -399,6 +441,8 @@ class Loader {
   // the load's status with a scratch failure that was a timed-out wait reported as such
   int status(int rc) const { return rc == THAPI_E_NOMEM && sc_.failed == 2 ? THAPI_E_TIMEOUT : rc; }
   void set_tuning(const Tuning &t) { tune_ = t; }
+  // the serving loop charged this load against the cap already
+  void set_admitted() { admitted_ = true; }
   void set_input(const uint8_t *host, const uint8_t *dev, uint64_t nbytes) {
     host_ = host;
     dev_ = dev;
@@ -416,6 +460,7 @@ class Loader {
  private:
   int parse_batch(HostLayout &L);
   Tuning tune_;
+  bool admitted_ = false;
   std::vector<const void *> bptr_;
   std::vector<uint64_t> bn_;
   std::vector<HostLayout> blay_;
@@ -481,9 +526,7 @@ int Loader::decode(const HostLayout &L, uint64_t n, uint64_t total_events, const
   if ((rc = sync_misc()) != THAPI_OK) return rc;
   if (misc_h_[mContentErr] != ~0ull) {
     const unsigned long long k = misc_h_[mContentErr];
-    c_->err_level = 2;
-    c_->err_packet = k >> 20;
-    c_->err_event = (k >> 3) & 0x1FFFFu;
+    set_err(c_, 2, k >> 20, (k >> 3) & 0x1FFFFu);
     return (int)(k & 7u);
   }
   CK(cudaMemcpyAsync(dec_out_, d_ev, total_events * sizeof(thapi_event), cudaMemcpyDeviceToHost, s_));
@@ -569,8 +612,7 @@ int Loader::parse_batch(HostLayout &L) {
   }
   for (uint32_t t = 0; t < nt; ++t)
     if (rcs[t] != THAPI_OK) {
-      c_->err_level = 0;
-      c_->err_packet = t;
+      set_err(c_, 0, t, 0);
       return rcs[t];
     }
   const HostLayout &a = blay_[0];
@@ -654,8 +696,6 @@ int Loader::run() {
   const uint64_t cells = (uint64_t)G * F;
   if (cells > (1ull << 28) || n >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
 
-  // admission: coarse peak of this load (packets, index, table, slots, sort)
-  const uint64_t est_events = n * (uint64_t)((P - kPacketHeader) / 8);
   // device-activity pairing: records of events carrying a command id, their table, a device tally
   bool dev_on = false;
   for (uint64_t c : L.cls) {
@@ -664,9 +704,12 @@ int Loader::run() {
   }
   // self time: a side record per slot, then per interval its record, sort keys and children's sum
   const bool self_on = c_->self_time != 0;
-  const uint64_t est = (host_ || !bptr_.empty() ? n * (uint64_t)P : 0) + n * 128 + cells * 80 + est_events * 24 +
-                       (dev_on ? est_events * 48 + cells * 80 : 0) + (self_on ? est_events * 96 + cells * 120 : 0);
-  if (c_->cap && c_->used + est > c_->cap) return THAPI_E_NOMEM;
+  // admission: coarse peak of this load (unless the serving loop admitted it already)
+  if (!admitted_) {
+    const uint64_t est = load_estimate(L, G, host_ || !bptr_.empty(), self_on);
+    std::lock_guard<std::mutex> g(c_->mu);
+    if (c_->cap && c_->used + est > c_->cap) return THAPI_E_NOMEM;
+  }
 
   tr_ = new (std::nothrow) TraceRec();
   if (!tr_) return THAPI_E_NOMEM;
@@ -772,8 +815,7 @@ int Loader::run() {
   CK(cudaGetLastError());
   if ((rc = sync_misc()) != THAPI_OK) return rc;
   if (misc_h_[mHdrErr] != ~0ull) {
-    c_->err_level = 1;
-    c_->err_packet = misc_h_[mHdrErr];
+    set_err(c_, 1, misc_h_[mHdrErr], 0);
     return THAPI_E_FORMAT;
   }
   const uint64_t total_events = n ? misc_h_[mEvents] : 0;
@@ -928,9 +970,7 @@ int Loader::run() {
     if (misc_h_[mStatus] == THAPI_E_TIMEOUT) return THAPI_E_TIMEOUT;
     if (misc_h_[mContentErr] != ~0ull) {
       const unsigned long long k = misc_h_[mContentErr];
-      c_->err_level = 2;
-      c_->err_packet = k >> 20;
-      c_->err_event = (k >> 3) & 0x1FFFFu;
+      set_err(c_, 2, k >> 20, (k >> 3) & 0x1FFFFu);
       return (int)(k & 7u);
     }
     const uint64_t nb = misc_h_[mCmdCount0], ne = misc_h_[mCmdCount0 + 1], nh = misc_h_[mCmdCount0 + 2];
@@ -1013,9 +1053,7 @@ int Loader::run() {
     if ((rc = sync_misc()) != THAPI_OK) return rc;
     if (misc_h_[mContentErr] != ~0ull) {
       const unsigned long long k = misc_h_[mContentErr];
-      c_->err_level = 2;
-      c_->err_packet = k >> 20;
-      c_->err_event = (k >> 3) & 0x1FFFFu;
+      set_err(c_, 2, k >> 20, (k >> 3) & 0x1FFFFu);
       return (int)(k & 7u);
     }
     const uint64_t m = misc_h_[mPcCount];
@@ -1321,6 +1359,7 @@ int Loader::run() {
 
 // Releases the device results of a load that is not kept.
 static void drop_trace(thapi_ctx *c, TraceRec *t) {
+  dev_free(c, t->win_bmax, t->win_bytes, t->stream);
   dev_free(c, t->rows, t->rows_bytes, t->stream);
   dev_free(c, t->tl, t->tl_bytes, t->stream);
   dev_free(c, t->dev_rows, t->dev_rows_bytes, t->stream);
@@ -1351,11 +1390,12 @@ static uint64_t tune_key(const HostLayout &L, bool batch, uint64_t bytes) {
 // remembered for the shape.
 template <class Configure>
 static int load_tuned(thapi_ctx *c, cudaStream_t s, const Reader &head, bool batch, uint64_t bytes,
-                      Configure configure, thapi_trace_id *out) {
+                      Configure configure, thapi_trace_id *out, bool admitted = false) {
   auto once = [&](const Tuning &t, TraceRec **tr) {
     Loader ld(c, nullptr, nullptr, 0, s);
     configure(ld);
     ld.set_tuning(t);
+    if (admitted) ld.set_admitted();
     const int rc = ld.status(ld.run());
     if (rc == THAPI_OK) *tr = ld.take();
     return rc;
@@ -1368,7 +1408,10 @@ static int load_tuned(thapi_ctx *c, cudaStream_t s, const Reader &head, bool bat
     HostLayout L;
     if (parse_layout(head, L) == THAPI_OK) {
       key = tune_key(L, batch, bytes);
-      tuned = c->tuned.count(key) != 0;
+      {
+        std::lock_guard<std::mutex> g(c->mu);
+        tuned = c->tuned.count(key) != 0;
+      }
       if (!tuned) {  // try every candidate; each knob is chosen by the phase it acts on
         const bool dev_on = (key >> 32) & 1;
         const uint32_t grids[3] = {1u, 2u, 4u};
@@ -1394,15 +1437,22 @@ static int load_tuned(thapi_ctx *c, cudaStream_t s, const Reader &head, bool bat
           if (g != 1 && an_best[g] < 0.97f * an_best[1] && an_best[g] < an_best[bg]) bg = g;
         for (int q = 0; q < 3 && dev_on; ++q)
           if (q != 1 && jo_best[q] < 0.97f * jo_best[1] && jo_best[q] < jo_best[bq]) bq = q;
+        std::lock_guard<std::mutex> g(c->mu);
         c->tuned[key] = Tuning{grids[bg], parts[bq]};  // the load below runs with it
       }
     }
   }
   if (!tr) {
-    const auto it = c->tuned.find(key);
-    rc = once(c->autotune && it != c->tuned.end() ? it->second : Tuning{}, &tr);
+    Tuning t{};
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      const auto it = c->tuned.find(key);
+      if (c->autotune && it != c->tuned.end()) t = it->second;
+    }
+    rc = once(t, &tr);
     if (rc != THAPI_OK) return rc;
   }
+  std::lock_guard<std::mutex> g(c->mu);
   const uint64_t id = c->next_id++;
   c->traces[id] = tr;
   c->used += tr->info.device_bytes;
@@ -1414,8 +1464,7 @@ static int load_common(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, ui
                        thapi_trace_id *out) {
   if (!c || !out || (!host && !dev)) return THAPI_E_INVALID;
   if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
-  c->err_level = 0;
-  c->err_packet = c->err_event = 0;
+  set_err(c, 0, 0, 0);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Reader head{host, dev, nbytes, s};
   return load_tuned(
@@ -1428,8 +1477,7 @@ static int load_batch(thapi_ctx *c, const void *const *bytes, const uint64_t *nb
   for (uint32_t t = 0; t < n; ++t)
     if (!bytes[t]) return THAPI_E_INVALID;
   if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
-  c->err_level = 0;
-  c->err_packet = c->err_event = 0;
+  set_err(c, 0, 0, 0);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint8_t *b0 = static_cast<const uint8_t *>(bytes[0]);
   const Reader head{on_device ? nullptr : b0, on_device ? b0 : nullptr, nbytes[0], s};  // the shape from trace 0
@@ -1443,8 +1491,7 @@ static int decode_common(thapi_ctx *c, const uint8_t *host, uint64_t nbytes, tha
                          uint64_t *n_out, void *stream) {
   if (!c || !host || !n_out || (cap && !out)) return THAPI_E_INVALID;
   if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
-  c->err_level = 0;
-  c->err_packet = c->err_event = 0;
+  set_err(c, 0, 0, 0);
   Loader ld(c, host, nullptr, nbytes, static_cast<cudaStream_t>(stream));
   ld.set_decode(out, cap, n_out);
   return ld.status(ld.run());
@@ -1452,50 +1499,81 @@ static int decode_common(thapi_ctx *c, const uint8_t *host, uint64_t nbytes, tha
 
 static TraceRec *find(thapi_ctx *c, thapi_trace_id id) {
   if (!c) return nullptr;
+  std::lock_guard<std::mutex> g(c->mu);
   auto it = c->traces.find(id);
   return it == c->traces.end() ? nullptr : it->second;
 }
 
-// Selects the window [t0, t1) of a resident timeline into dst (device memory),
-// or only counts it when dst is null.  Returns the count through *n.
-static int select_window(thapi_ctx *c, TraceRec *tr, uint64_t t0, uint64_t t1, thapi_interval *dst, uint64_t cap,
-                         uint64_t *n, cudaStream_t s, bool *is_full) {
-  const uint64_t total = tr->info.intervals;
-  *is_full = t0 == 0 && t1 == ~0ull;
-  if (*is_full || total == 0) {
-    *n = *is_full ? total : 0;
-    return THAPI_OK;
+// Releases a trace's device results in stream order on `s` and forgets it.
+int free_trace_on(thapi_ctx *c, thapi_trace_id id, cudaStream_t s) {
+  TraceRec *t = nullptr;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    auto it = c->traces.find(id);
+    if (it == c->traces.end()) return THAPI_E_INVALID;
+    t = it->second;
+    c->traces.erase(it);
+    c->used -= std::min(c->used, t->info.device_bytes + t->win_bytes);
   }
-  Scratch sc;
-  sc.ctx = c;
-  sc.stream = s;
-  uint64_t *words = static_cast<uint64_t *>(sc.get(2 * sizeof(uint64_t)));
-  if (!words) return THAPI_E_NOMEM;
-  launch_lower_bound_start(tr->tl, total, t1, words, s);
-  uint64_t hi = 0;
-  if (cudaMemcpyAsync(&hi, words, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    sc.release_all();
+  cudaSetDevice(c->device);
+  dev_free(c, t->rows, t->rows_bytes, s);
+  dev_free(c, t->tl, t->tl_bytes, s);
+  dev_free(c, t->dev_rows, t->dev_rows_bytes, s);
+  dev_free(c, t->self_rows, t->self_rows_bytes, s);
+  dev_free(c, t->win_bmax, t->win_bytes, s);
+  const bool ok = cudaStreamSynchronize(s) == cudaSuccess;
+  delete t;
+  return ok ? THAPI_OK : THAPI_E_CUDA;
+}
+
+// Device-visible address of a destination buffer: device or managed memory
+// as it is, pinned host memory through its device mapping; null for pageable
+// host memory (whose copies are staged).
+void *device_view(void *p) {
+  cudaPointerAttributes a{};
+  if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  return nullptr;
+}
+
+// Builds a trace's window index (per block of interval slots in timeline
+// order, the running maximum of their ends) the first time a window of it is
+// asked for; queries on any stream find it complete afterwards.
+static int ensure_win_index(thapi_ctx *c, TraceRec *tr, cudaStream_t s) {
+  std::lock_guard<std::mutex> g(tr->win_mu);
+  if (tr->win_bmax || tr->info.intervals == 0) return THAPI_OK;
+  const uint64_t nb = (tr->info.intervals + kWinBlock - 1) / kWinBlock;
+  const uint64_t bytes = nb * sizeof(uint64_t);
+  uint64_t *b = static_cast<uint64_t *>(dev_alloc(c, bytes, s));
+  if (!b) return THAPI_E_NOMEM;
+  launch_win_index(tr->tl, tr->info.intervals, b, s);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    dev_free(c, b, bytes, s);
     return THAPI_E_CUDA;
   }
-  uint64_t *flags = static_cast<uint64_t *>(sc.get((hi ? hi : 1) * sizeof(uint64_t)));
-  if (!flags) {
-    sc.release_all();
-    return THAPI_E_NOMEM;
-  }
-  launch_window_count(tr->tl, total, t0, t1, words, flags, words + 1, sc, s, hi);
-  uint64_t cnt = 0;
-  if (cudaMemcpyAsync(&cnt, words + 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    sc.release_all();
-    return THAPI_E_CUDA;
-  }
-  *n = cnt;
-  if (dst && cnt <= cap) launch_window_write(tr->tl, hi, t0, t1, flags, dst, s);
-  int rc = cudaGetLastError() == cudaSuccess ? THAPI_OK : THAPI_E_CUDA;
-  sc.release_all();
-  cudaStreamSynchronize(s);
-  return rc;
+  std::lock_guard<std::mutex> gc(c->mu);
+  tr->win_bytes = bytes;
+  tr->win_bmax = b;
+  c->used += bytes;
+  return THAPI_OK;
+}
+
+// The window [t0, t1) of a resident timeline: its intervals in timeline order
+// to dst (device-visible; null: count only) when they fit cap, and their
+// number to *total (device-visible).  Enqueued on s; w: a WinWork in device
+// memory, used by one query at a time.
+int window_enqueue(thapi_ctx *c, TraceRec *tr, uint64_t t0, uint64_t t1, thapi_interval *dst, uint64_t cap,
+                   WinWork *w, unsigned long long *total, cudaStream_t s) {
+  const int rc = ensure_win_index(c, tr, s);
+  if (rc != THAPI_OK) return rc;
+  launch_win_query(tr->tl, tr->info.intervals, tr->win_bmax, t0, t1, w, 2u * (uint32_t)c->num_sms, dst, cap, total,
+                   s);
+  return cudaGetLastError() == cudaSuccess ? THAPI_OK : THAPI_E_CUDA;
 }
 
 static int timeline_impl(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
@@ -1503,36 +1581,119 @@ static int timeline_impl(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t 
   TraceRec *tr = find(c, id);
   if (!tr || !n_out || (cap && !out)) return THAPI_E_INVALID;
   if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
-  bool full = false;
-  uint64_t cnt = 0;
-  int rc = select_window(c, tr, t0, t1, nullptr, 0, &cnt, s, &full);
-  if (rc != THAPI_OK) return rc;
-  *n_out = cnt;
-  if (cap == 0) return THAPI_OK;
-  if (cap < cnt) return THAPI_E_RANGE;
-  if (cnt == 0) return THAPI_OK;
-  if (full) {
+  const uint64_t total = tr->info.intervals;
+  const bool full = t0 == 0 && t1 == ~0ull;
+  if (full || total == 0) {  // the whole timeline (or nothing): one copy
+    const uint64_t cnt = full ? total : 0;
+    *n_out = cnt;
+    if (cap == 0) return THAPI_OK;
+    if (cap < cnt) return THAPI_E_RANGE;
+    if (cnt == 0) return THAPI_OK;
     cudaError_t e = cudaMemcpyAsync(out, tr->tl, cnt * sizeof(thapi_interval),
                                     device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return THAPI_E_CUDA;
     if (!device_out && cudaStreamSynchronize(s) != cudaSuccess) return THAPI_E_CUDA;
     return THAPI_OK;
   }
-  if (device_out) return select_window(c, tr, t0, t1, out, cap, &cnt, s, &full);
   Scratch sc;
   sc.ctx = c;
   sc.stream = s;
-  thapi_interval *tmp = static_cast<thapi_interval *>(sc.get(cnt * sizeof(thapi_interval)));
-  if (!tmp) return THAPI_E_NOMEM;
-  rc = select_window(c, tr, t0, t1, tmp, cnt, &cnt, s, &full);
+  WinWork *w = static_cast<WinWork *>(sc.get(sizeof(WinWork)));
+  unsigned long long *tot = static_cast<unsigned long long *>(sc.get(sizeof(unsigned long long)));
+  if (!w || !tot) {
+    sc.release_all();
+    return THAPI_E_NOMEM;
+  }
+  // destinations the device can write take the matches directly; pageable
+  // host memory gets a count first, then a staged copy
+  thapi_interval *dst = cap ? (device_out ? out : static_cast<thapi_interval *>(device_view(out))) : nullptr;
+  int rc = window_enqueue(c, tr, t0, t1, dst, dst ? cap : 0, w, tot, s);
+  unsigned long long cnt = 0;
+  if (rc == THAPI_OK && (cudaMemcpyAsync(&cnt, tot, sizeof(cnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                         cudaStreamSynchronize(s) != cudaSuccess))
+    rc = THAPI_E_CUDA;
   if (rc == THAPI_OK) {
-    if (cudaMemcpyAsync(out, tmp, cnt * sizeof(thapi_interval), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      rc = THAPI_E_CUDA;
+    *n_out = cnt;
+    if (cap && cap < cnt) {
+      rc = THAPI_E_RANGE;
+    } else if (cap && cnt && !dst) {
+      thapi_interval *tmp = static_cast<thapi_interval *>(sc.get(cnt * sizeof(thapi_interval)));
+      if (!tmp)
+        rc = THAPI_E_NOMEM;
+      else if ((rc = window_enqueue(c, tr, t0, t1, tmp, cnt, w, tot, s)) == THAPI_OK &&
+               (cudaMemcpyAsync(out, tmp, cnt * sizeof(thapi_interval), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess))
+        rc = THAPI_E_CUDA;
+    }
   }
   sc.release_all();
   cudaStreamSynchronize(s);
   return rc;
+}
+
+// ---------------------------------------------------------------- serving-loop hooks (server.cu)
+int ctx_device(const thapi_ctx *c) { return c->device; }
+int ctx_num_sms(const thapi_ctx *c) { return c->num_sms; }
+void ctx_memory(thapi_ctx *c, uint64_t *cap, uint64_t *used) {
+  std::lock_guard<std::mutex> g(c->mu);
+  *cap = c->cap;
+  *used = c->used;
+}
+void *ctx_alloc(thapi_ctx *c, uint64_t bytes, cudaStream_t s) { return dev_alloc(c, bytes, s); }
+void ctx_free(thapi_ctx *c, void *p, uint64_t bytes, cudaStream_t s) { dev_free(c, p, bytes, s); }
+
+// What admission charges for loading this trace (the load's coarse peak).
+int load_charge(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, uint64_t nbytes, cudaStream_t s,
+                uint64_t *est) {
+  HostLayout L;
+  const Reader r{host, dev, nbytes, s};
+  const int rc = parse_layout(r, L);
+  if (rc != THAPI_OK) return rc;
+  *est = load_estimate(L, group_count(L), host != nullptr, c->self_time != 0);
+  return THAPI_OK;
+}
+
+// A load the serving loop admitted (no cap check here).  The trace is left
+// bound to no stream: later frees outside the loop use the default stream.
+int load_admitted(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, uint64_t nbytes, cudaStream_t s,
+                  thapi_trace_id *out) {
+  if (!c || !out || (!host && !dev)) return THAPI_E_INVALID;
+  if (cudaSetDevice(c->device) != cudaSuccess) return THAPI_E_CUDA;
+  const Reader head{host, dev, nbytes, s};
+  const int rc = load_tuned(
+      c, s, head, false, nbytes, [&](Loader &ld) { ld.set_input(host, dev, nbytes); }, out, true);
+  if (rc == THAPI_OK) {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->traces[*out]->stream = nullptr;
+  }
+  return rc;
+}
+
+int trace_sizes(thapi_ctx *c, thapi_trace_id id, uint64_t *rows, uint64_t *intervals, uint64_t *events) {
+  TraceRec *t = find(c, id);
+  if (!t) return THAPI_E_INVALID;
+  *rows = t->info.tally_rows;
+  *intervals = t->info.intervals;
+  *events = t->info.events;
+  return THAPI_OK;
+}
+
+// Tally rows to dst (host or device memory; the copy is enqueued on s).
+int tally_enqueue(thapi_ctx *c, thapi_trace_id id, thapi_tally_row *dst, uint64_t cap, uint64_t *n, cudaStream_t s) {
+  TraceRec *t = find(c, id);
+  if (!t) return THAPI_E_INVALID;
+  *n = t->info.tally_rows;
+  if (cap < *n) return THAPI_E_RANGE;
+  if (*n && cudaMemcpyAsync(dst, t->rows, *n * sizeof(thapi_tally_row), cudaMemcpyDefault, s) != cudaSuccess)
+    return THAPI_E_CUDA;
+  return THAPI_OK;
+}
+
+int window_enqueue_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *dst, uint64_t cap,
+                      WinWork *w, unsigned long long *total, cudaStream_t s) {
+  TraceRec *t = find(c, id);
+  if (!t) return THAPI_E_INVALID;
+  return window_enqueue(c, t, t0, t1, dst, cap, w, total, s);
 }
 
 static int tally_impl(thapi_ctx *c, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
@@ -1631,6 +1792,7 @@ int thapi_ctx_destroy(thapi_ctx *ctx) {
     dev_free(ctx, t->tl, t->tl_bytes, t->stream);
     dev_free(ctx, t->dev_rows, t->dev_rows_bytes, t->stream);
     dev_free(ctx, t->self_rows, t->self_rows_bytes, t->stream);
+    dev_free(ctx, t->win_bmax, t->win_bytes, t->stream);
     cudaStreamSynchronize(t->stream);
     delete t;
   }
@@ -1668,16 +1830,7 @@ int thapi_trace_load_batch(thapi_ctx *ctx, const void *const *bytes, const uint6
 int thapi_trace_free(thapi_ctx *ctx, thapi_trace_id id) {
   TraceRec *t = find(ctx, id);
   if (!t) return THAPI_E_INVALID;
-  cudaSetDevice(ctx->device);
-  dev_free(ctx, t->rows, t->rows_bytes, t->stream);
-  dev_free(ctx, t->tl, t->tl_bytes, t->stream);
-  dev_free(ctx, t->dev_rows, t->dev_rows_bytes, t->stream);
-  dev_free(ctx, t->self_rows, t->self_rows_bytes, t->stream);
-  cudaStreamSynchronize(t->stream);
-  ctx->used -= std::min(ctx->used, t->info.device_bytes);
-  ctx->traces.erase(id);
-  delete t;
-  return THAPI_OK;
+  return free_trace_on(ctx, id, t->stream);
 }
 
 int thapi_tally(thapi_ctx *ctx, thapi_trace_id id, thapi_tally_row *rows, uint64_t cap, uint64_t *n_rows,
@@ -1863,6 +2016,7 @@ const char *thapi_strerror(int code) {
     case THAPI_E_CUDA: return "CUDA runtime error";
     case THAPI_E_RANGE: return "output capacity too small";
     case THAPI_E_UNSUPPORTED: return "trace outside this build's limits";
+    case THAPI_PENDING: return "request not completed yet";
     default: return "unknown status";
   }
 }

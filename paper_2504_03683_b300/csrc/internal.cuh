@@ -275,6 +275,23 @@ struct TraceDescription {
   std::vector<uint32_t> stream_group, group_keys;
 };
 int describe_device_trace(const uint8_t *dev, uint64_t nbytes, cudaStream_t s, TraceDescription &td);
+// api.cu hooks of the serving loop (server.cu); contexts are thread-safe for these.
+int ctx_device(const thapi_ctx *c);
+int ctx_num_sms(const thapi_ctx *c);
+void ctx_memory(thapi_ctx *c, uint64_t *cap, uint64_t *used);
+void *ctx_alloc(thapi_ctx *c, uint64_t bytes, cudaStream_t s);
+void ctx_free(thapi_ctx *c, void *p, uint64_t bytes, cudaStream_t s);
+int load_charge(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, uint64_t nbytes, cudaStream_t s,
+                uint64_t *est);
+int load_admitted(thapi_ctx *c, const uint8_t *host, const uint8_t *dev, uint64_t nbytes, cudaStream_t s,
+                  thapi_trace_id *out);
+int trace_sizes(thapi_ctx *c, thapi_trace_id id, uint64_t *rows, uint64_t *intervals, uint64_t *events);
+int tally_enqueue(thapi_ctx *c, thapi_trace_id id, thapi_tally_row *dst, uint64_t cap, uint64_t *n, cudaStream_t s);
+struct WinWork;
+int window_enqueue_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *dst, uint64_t cap,
+                      WinWork *w, unsigned long long *total, cudaStream_t s);
+int free_trace_on(thapi_ctx *c, thapi_trace_id id, cudaStream_t s);
+void *device_view(void *p);
 // A context that allocates only through the given hooks (creates nothing on the device).
 thapi_ctx *hooked_ctx_create(int device, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user);
 
@@ -478,10 +495,20 @@ void launch_timeline_gather(const thapi_interval *rec, const uint32_t *vals, uin
                             cudaStream_t s);
 void launch_iota_u32(uint32_t *v, uint64_t n, cudaStream_t s);
 void launch_rec_keys(const thapi_interval *rec, uint64_t n, uint64_t t_min, void *keys, bool key32, cudaStream_t s);
-void launch_window_count(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *hi_dev,
-                         uint64_t *flags, uint64_t *n_dev, Scratch &sc, cudaStream_t s, uint64_t hi_host);
-void launch_window_write(const thapi_interval *tl, uint64_t hi, uint64_t t0, uint64_t t1, const uint64_t *pos,
-                         thapi_interval *out, cudaStream_t s);
-void launch_lower_bound_start(const thapi_interval *tl, uint64_t n, uint64_t t1, uint64_t *out, cudaStream_t s);
+
+// window.cu: time-window queries.  A trace's window index holds, per block of
+// kWinBlock intervals in timeline order, the running maximum of their ends;
+// a query finds its range with it and writes the matches in order.
+constexpr uint32_t kWinBlock = 2048;
+constexpr uint32_t kWinCtas = 512;  // most CTAs of one query
+struct WinWork {                    // device working record of one query in flight
+  unsigned long long lo, hi;        // the range searched: [lo, hi)
+  unsigned long long cnt[kWinCtas]; // matches per CTA chunk
+};
+void launch_win_index(const thapi_interval *tl, uint64_t n, uint64_t *bmax, cudaStream_t s);
+// matches to out (device-visible; null: count only) only when *total_out <= cap
+void launch_win_query(const thapi_interval *tl, uint64_t n, const uint64_t *bmax, uint64_t t0, uint64_t t1,
+                      WinWork *w, uint32_t grid, thapi_interval *out, uint64_t cap, unsigned long long *total_out,
+                      cudaStream_t s);
 
 }  // namespace thapi

@@ -7,8 +7,8 @@
 // ordering them by start time (relative to the trace's first timestamp) is
 // done by bucket.cu, or by a stable LSD radix sort over only as many bits as
 // the span needs when the buckets do not fit shared memory.  Either way the
-// timeline order is (start, stream, entry position).  Window queries [t0, t1) select intervals
-// with start < t1 and end >= t0 from the sorted array.
+// timeline order is (start, stream, entry position).  Window queries [t0, t1)
+// over the ordered timeline are in window.cu.
 #include <algorithm>
 
 #include "internal.cuh"
@@ -130,35 +130,6 @@ __global__ void k_timeline_gather(const thapi_interval *__restrict__ rec, const 
   }
 }
 
-// Window selection: flags[i] = (start < t1 && end >= t0) over the sorted timeline.
-__global__ void k_window_flags(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *flags) {
-  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const thapi_interval &v = tl[i];
-  flags[i] = (v.start_ns < t1 && v.end_ns >= t0) ? 1u : 0u;
-}
-
-__global__ void k_window_write(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, const uint64_t *pos,
-                               thapi_interval *out) {
-  uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const thapi_interval v = tl[i];
-  if (v.start_ns < t1 && v.end_ns >= t0) out[pos[i]] = v;
-}
-
-// First index with start >= t1 (sorted by start), single thread.
-__global__ void k_lower_bound_start(const thapi_interval *tl, uint64_t n, uint64_t t1, uint64_t *out) {
-  uint64_t lo = 0, hi = n;
-  while (lo < hi) {
-    uint64_t mid = lo + (hi - lo) / 2;
-    if (tl[mid].start_ns < t1)
-      lo = mid + 1;
-    else
-      hi = mid;
-  }
-  *out = lo;
-}
-
 }  // namespace thapi
 
 namespace thapi {
@@ -202,33 +173,6 @@ void launch_iota_u32(uint32_t *v, uint64_t n, cudaStream_t s) {
     k_iota_u32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n);
     count_launches(1);
   }
-}
-
-// Selects the window of the sorted timeline into `out` (capacity checked by
-// the caller through *n_dev, computed first when out == nullptr).
-void launch_window_count(const thapi_interval *tl, uint64_t n, uint64_t t0, uint64_t t1, uint64_t *hi_dev,
-                         uint64_t *flags, uint64_t *n_dev, Scratch &sc, cudaStream_t s, uint64_t hi_host) {
-  (void)hi_dev;
-  if (!hi_host) {
-    cudaMemsetAsync(n_dev, 0, sizeof(uint64_t), s);
-    return;
-  }
-  k_window_flags<<<(unsigned)((hi_host + 255) / 256), 256, 0, s>>>(tl, hi_host, t0, t1, flags);
-  count_launches(1);
-  scan_exclusive_u64(flags, hi_host, n_dev, sc, s);
-}
-
-void launch_window_write(const thapi_interval *tl, uint64_t hi, uint64_t t0, uint64_t t1, const uint64_t *pos,
-                         thapi_interval *out, cudaStream_t s) {
-  if (hi) {
-    k_window_write<<<(unsigned)((hi + 255) / 256), 256, 0, s>>>(tl, hi, t0, t1, pos, out);
-    count_launches(1);
-  }
-}
-
-void launch_lower_bound_start(const thapi_interval *tl, uint64_t n, uint64_t t1, uint64_t *out, cudaStream_t s) {
-  k_lower_bound_start<<<1, 1, 0, s>>>(tl, n, t1, out);
-  count_launches(1);
 }
 
 }  // namespace thapi

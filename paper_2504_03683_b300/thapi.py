@@ -16,7 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libthapi.so")
 
-OK, E_INVALID, E_FORMAT, E_TRUNCATED, E_NOMEM, E_TIMEOUT, E_CUDA, E_RANGE, E_UNSUPPORTED = range(9)
+OK, E_INVALID, E_FORMAT, E_TRUNCATED, E_NOMEM, E_TIMEOUT, E_CUDA, E_RANGE, E_UNSUPPORTED, PENDING = range(10)
+REQ_LOAD, REQ_TALLY, REQ_WINDOW, REQ_FREE = range(4)  # serving-loop request kinds
 
 ROW_DTYPE = np.dtype([("host_id", "<u4"), ("pid", "<u4"), ("tid", "<u4"), ("func_id", "<u4"),
                       ("count", "<u8"), ("total_ns", "<u8"), ("min_ns", "<u8"), ("max_ns", "<u8"),
@@ -39,7 +40,9 @@ EXPORTED = (
     "thapi_strerror", "thapi_ctx_set_timing", "thapi_trace_timing", "thapi_kernel_launches",
     "thapi_tally_static", "thapi_device_tally", "thapi_tally_merge", "thapi_decode", "thapi_ctx_set_self_time",
     "thapi_self_tally", "thapi_trace_func_layer", "thapi_trace_load_batch", "thapi_check_device_wait",
-    "thapi_ctx_set_autotune",
+    "thapi_ctx_set_autotune", "thapi_server_create", "thapi_server_submit", "thapi_server_poll",
+    "thapi_server_release", "thapi_server_now", "thapi_server_replay", "thapi_server_stats_get",
+    "thapi_server_destroy",
 )
 
 
@@ -81,6 +84,31 @@ class LoadTiming(ctypes.Structure):
     def as_dict(self):
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
                 for f, t in self._fields_}
+
+
+class Request(ctypes.Structure):
+    """thapi_request (72 B)."""
+    _fields_ = [("kind", ctypes.c_uint32), ("on_device", ctypes.c_uint32), ("bytes", ctypes.c_void_p),
+                ("nbytes", ctypes.c_uint64), ("trace", ctypes.c_uint64), ("after", ctypes.c_uint64),
+                ("t0", ctypes.c_uint64), ("t1", ctypes.c_uint64), ("out", ctypes.c_void_p), ("cap", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    """thapi_result (72 B)."""
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_uint32), ("trace", ctypes.c_uint64),
+                ("n", ctypes.c_uint64), ("events", ctypes.c_uint64), ("data", ctypes.c_void_p),
+                ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "load_waits", "peak_running",
+                                                "peak_committed")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p)
@@ -135,6 +163,14 @@ def library():
         "thapi_device_tally": ([vp, u64, vp, u64, P(u64), P(DeviceDiag)], i32),
         "thapi_tally_merge": ([vp, vp, u64, vp, u64, P(u64), vp], i32),
         "thapi_decode": ([vp, vp, u64, vp, u64, P(u64), vp], i32),
+        "thapi_server_create": ([vp, u32, u32, P(vp)], i32),
+        "thapi_server_submit": ([vp, P(Request), P(u64)], i32),
+        "thapi_server_poll": ([vp, u64, u32, P(Result)], i32),
+        "thapi_server_release": ([vp, u64], i32),
+        "thapi_server_now": ([vp], ctypes.c_double),
+        "thapi_server_replay": ([vp, P(Request), P(ctypes.c_double), u64, i32, P(Result)], i32),
+        "thapi_server_stats_get": ([vp, P(ServerStats)], i32),
+        "thapi_server_destroy": ([vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -401,6 +437,74 @@ def thapi_tally_static(dev_ptr: int, nbytes: int, rows_dev_ptr: int, cap: int, s
                                         ctypes.byref(n), ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream))),
            "thapi_tally_static")
     return n.value, d.as_dict()
+
+
+# ------------------------------------------------- serving loop
+def thapi_server_create(ctx: int, load_slots: int = 2, query_slots: int = 4) -> int:
+    h = ctypes.c_void_p()
+    _check(library().thapi_server_create(ctx, load_slots, query_slots, ctypes.byref(h)), "thapi_server_create")
+    return h.value
+
+
+def thapi_server_submit(srv: int, req: Request) -> int:
+    t = ctypes.c_uint64()
+    _check(library().thapi_server_submit(srv, ctypes.byref(req), ctypes.byref(t)), "thapi_server_submit")
+    return int(t.value)
+
+
+def thapi_server_poll(srv: int, ticket: int, wait_ms: int = 0xFFFFFFFF):
+    """The request's Result, or None if it has not completed within wait_ms."""
+    r = Result()
+    rc = library().thapi_server_poll(srv, ticket, wait_ms, ctypes.byref(r))
+    if rc == PENDING:
+        return None
+    _check(rc, "thapi_server_poll")
+    return r
+
+
+def thapi_server_release(srv: int, ticket: int) -> None:
+    _check(library().thapi_server_release(srv, ticket), "thapi_server_release")
+
+
+def thapi_server_now(srv: int) -> float:
+    return float(library().thapi_server_now(srv))
+
+
+def thapi_server_replay(srv: int, reqs, arrivals, keep: bool = False):
+    """Submits reqs[i] (Request) at arrivals[i] seconds from the call, waits for
+    all; returns the list of Result."""
+    n = len(reqs)
+    arr_t = (Request * max(n, 1))(*reqs)
+    at = (ctypes.c_double * max(n, 1))(*[float(a) for a in arrivals])
+    res = (Result * max(n, 1))()
+    _check(library().thapi_server_replay(srv, arr_t, at, n, 1 if keep else 0, res), "thapi_server_replay")
+    return [res[i] for i in range(n)]
+
+
+def thapi_server_stats_get(srv: int) -> dict:
+    st = ServerStats()
+    _check(library().thapi_server_stats_get(srv, ctypes.byref(st)), "thapi_server_stats_get")
+    return st.as_dict()
+
+
+def thapi_server_destroy(srv: int) -> None:
+    _check(library().thapi_server_destroy(srv), "thapi_server_destroy")
+
+
+def result_rows(res: Result) -> np.ndarray:
+    """A TALLY result's rows (a copy of the result memory)."""
+    if res.status != OK or not res.n:
+        return np.zeros(0, dtype=ROW_DTYPE)
+    return np.ctypeslib.as_array(ctypes.cast(res.data, ctypes.POINTER(ctypes.c_uint8)),
+                                 (res.n * ROW_DTYPE.itemsize,)).view(ROW_DTYPE).copy()
+
+
+def result_intervals(res: Result) -> np.ndarray:
+    """A WINDOW result's intervals (a copy of the result memory)."""
+    if res.status != OK or not res.n:
+        return np.zeros(0, dtype=INTERVAL_DTYPE)
+    return np.ctypeslib.as_array(ctypes.cast(res.data, ctypes.POINTER(ctypes.c_uint8)),
+                                 (res.n * INTERVAL_DTYPE.itemsize,)).view(INTERVAL_DTYPE).copy()
 
 
 # ------------------------------------------------- torch device memory

@@ -34,8 +34,8 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_strerror_is_static_and_total():
-    for code in range(9):
-        assert thapi.thapi_strerror(code)
+    for code in range(10):
+        assert thapi.thapi_strerror(code) != "unknown status"
     assert thapi.thapi_strerror(99) == "unknown status"
 
 
@@ -61,6 +61,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         "thapi_tally_row": thapi.ROW_DTYPE, "thapi_interval": thapi.INTERVAL_DTYPE,
         "thapi_event": thapi.EVENT_DTYPE, "thapi_diag": thapi.Diag, "thapi_device_diag": thapi.DeviceDiag,
         "thapi_trace_info": thapi.TraceInfo, "thapi_load_timing": thapi.LoadTiming,
+        "thapi_request": thapi.Request, "thapi_result": thapi.Result, "thapi_server_stats": thapi.ServerStats,
     }
     want = {}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "thapi.h"', "int main(void) {"]
