@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve workload: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
     ap.add_argument("--serve-p-load", type=float, default=0.05, help="serve workload: share of loads (and of frees)")
+    ap.add_argument("--serve-result-gb", type=float, default=8.0,
+                    help="serve workload: pinned host memory the serving loop sets aside for results (GB)")
     ap.add_argument("--serve-load-slots", type=int, default=2)
     ap.add_argument("--serve-query-slots", type=int, default=6)
     return ap.parse_args()
@@ -548,7 +550,7 @@ def run_serve(args, rank, world, local):
     assert srcs2 == srcs
 
     # ---- the serving loop
-    srv = serve.Server(ctx, args.serve_load_slots, args.serve_query_slots)
+    srv = serve.Server(ctx, args.serve_load_slots, args.serve_query_slots, int(args.serve_result_gb * 1e9))
     srv.replay(warm, ids, host_src)
     sampler = ClockSampler(local)
     sampler.start()

@@ -504,12 +504,18 @@ typedef struct thapi_server_stats {
   uint64_t load_waits;      /* loads whose admission waited for device memory */
   uint64_t peak_running;    /* most requests in flight at once */
   uint64_t peak_committed;  /* most device memory resident plus charged to running loads (bytes) */
+  uint64_t result_allocs;   /* server-owned results that found no room in the pinned result memory */
 } thapi_server_stats;
 
 /* Starts a serving loop on `ctx` with load_slots loads and query_slots
  * queries / frees in flight at most (1..63 together).  The context's cap is
- * the admission cap.  Errors: E_INVALID, E_NOMEM, E_CUDA. */
-int thapi_server_create(thapi_ctx *ctx, uint32_t load_slots, uint32_t query_slots, thapi_server **out);
+ * the admission cap.  result_bytes (0: 1 GiB) of pinned, device-mapped host
+ * memory are set aside once for results the server owns (requests with
+ * out = NULL), so that serving pins and unpins nothing; a result that finds
+ * no room there gets its own pinned allocation.  Errors: E_INVALID, E_NOMEM,
+ * E_CUDA. */
+int thapi_server_create(thapi_ctx *ctx, uint32_t load_slots, uint32_t query_slots, uint64_t result_bytes,
+                        thapi_server **out);
 
 /* Submits a request; *ticket names it.  The request's own failures (refused
  * load, unknown or departed trace, failed load it waits for, format errors)

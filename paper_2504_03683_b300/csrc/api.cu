@@ -1504,7 +1504,8 @@ static TraceRec *find(thapi_ctx *c, thapi_trace_id id) {
   return it == c->traces.end() ? nullptr : it->second;
 }
 
-// Releases a trace's device results in stream order on `s` and forgets it.
+// Releases a trace's device results in stream order on `s` and forgets it;
+// the memory counts as used until the frees have completed.
 int free_trace_on(thapi_ctx *c, thapi_trace_id id, cudaStream_t s) {
   TraceRec *t = nullptr;
   {
@@ -1513,7 +1514,6 @@ int free_trace_on(thapi_ctx *c, thapi_trace_id id, cudaStream_t s) {
     if (it == c->traces.end()) return THAPI_E_INVALID;
     t = it->second;
     c->traces.erase(it);
-    c->used -= std::min(c->used, t->info.device_bytes + t->win_bytes);
   }
   cudaSetDevice(c->device);
   dev_free(c, t->rows, t->rows_bytes, s);
@@ -1522,6 +1522,10 @@ int free_trace_on(thapi_ctx *c, thapi_trace_id id, cudaStream_t s) {
   dev_free(c, t->self_rows, t->self_rows_bytes, s);
   dev_free(c, t->win_bmax, t->win_bytes, s);
   const bool ok = cudaStreamSynchronize(s) == cudaSuccess;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    c->used -= std::min(c->used, t->info.device_bytes + t->win_bytes);
+  }
   delete t;
   return ok ? THAPI_OK : THAPI_E_CUDA;
 }
@@ -1576,6 +1580,42 @@ int window_enqueue(thapi_ctx *c, TraceRec *tr, uint64_t t0, uint64_t t1, thapi_i
   return cudaGetLastError() == cudaSuccess ? THAPI_OK : THAPI_E_CUDA;
 }
 
+// The window's matches into HOST memory `out` once their number n is known:
+// small results through the memory's device mapping when it is pinned, the
+// others staged in device memory (`stage`, room for n intervals; null: taken
+// from the context here) and copied by the copy engine, which moves large
+// blocks over the host link faster than stores from the SMs.  Synchronises s.
+constexpr uint64_t kMappedMax = 1ull << 20;
+static int window_to_host(thapi_ctx *c, TraceRec *tr, uint64_t t0, uint64_t t1, void *out, uint64_t n,
+                          thapi_interval *stage, WinWork *w, unsigned long long *total, cudaStream_t s) {
+  if (!n) return THAPI_OK;
+  const uint64_t bytes = n * sizeof(thapi_interval);
+  thapi_interval *mapped = bytes <= kMappedMax ? static_cast<thapi_interval *>(device_view(out)) : nullptr;
+  if (mapped) {
+    int rc = window_enqueue(c, tr, t0, t1, mapped, n, w, total, s);
+    if (rc == THAPI_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = THAPI_E_CUDA;
+    return rc;
+  }
+  Scratch sc;
+  sc.ctx = c;
+  sc.stream = s;
+  if (!stage) stage = static_cast<thapi_interval *>(sc.get(bytes));
+  int rc = stage ? window_enqueue(c, tr, t0, t1, stage, n, w, total, s) : THAPI_E_NOMEM;
+  if (rc == THAPI_OK && (cudaMemcpyAsync(out, stage, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                         cudaStreamSynchronize(s) != cudaSuccess))
+    rc = THAPI_E_CUDA;
+  sc.release_all();
+  cudaStreamSynchronize(s);
+  return rc;
+}
+
+int window_to_host_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, void *out, uint64_t n,
+                      thapi_interval *stage, WinWork *w, unsigned long long *total, cudaStream_t s) {
+  TraceRec *tr = find(c, id);
+  if (!tr) return THAPI_E_INVALID;
+  return window_to_host(c, tr, t0, t1, out, n, stage, w, total, s);
+}
+
 static int timeline_impl(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *out,
                          uint64_t cap, uint64_t *n_out, bool device_out, cudaStream_t s) {
   TraceRec *tr = find(c, id);
@@ -1604,9 +1644,9 @@ static int timeline_impl(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t 
     sc.release_all();
     return THAPI_E_NOMEM;
   }
-  // destinations the device can write take the matches directly; pageable
-  // host memory gets a count first, then a staged copy
-  thapi_interval *dst = cap ? (device_out ? out : static_cast<thapi_interval *>(device_view(out))) : nullptr;
+  // device destinations take the matches in the counting pass; host ones
+  // are written once the count is known
+  thapi_interval *dst = cap && device_out ? out : nullptr;
   int rc = window_enqueue(c, tr, t0, t1, dst, dst ? cap : 0, w, tot, s);
   unsigned long long cnt = 0;
   if (rc == THAPI_OK && (cudaMemcpyAsync(&cnt, tot, sizeof(cnt), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -1614,17 +1654,10 @@ static int timeline_impl(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t 
     rc = THAPI_E_CUDA;
   if (rc == THAPI_OK) {
     *n_out = cnt;
-    if (cap && cap < cnt) {
+    if (cap && cap < cnt)
       rc = THAPI_E_RANGE;
-    } else if (cap && cnt && !dst) {
-      thapi_interval *tmp = static_cast<thapi_interval *>(sc.get(cnt * sizeof(thapi_interval)));
-      if (!tmp)
-        rc = THAPI_E_NOMEM;
-      else if ((rc = window_enqueue(c, tr, t0, t1, tmp, cnt, w, tot, s)) == THAPI_OK &&
-               (cudaMemcpyAsync(out, tmp, cnt * sizeof(thapi_interval), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess))
-        rc = THAPI_E_CUDA;
-    }
+    else if (cap && !device_out)
+      rc = window_to_host(c, tr, t0, t1, out, cnt, nullptr, w, tot, s);
   }
   sc.release_all();
   cudaStreamSynchronize(s);
@@ -1766,6 +1799,10 @@ int thapi_ctx_create(thapi_ctx **out, int device, uint64_t hbm_cap_bytes) {
   if (cudaMemPoolCreate(&c->pool, &props) == cudaSuccess) {
     uint64_t keep = ~0ull;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // memory freed on one stream is reused by another only once the free has
+    // completed: no waits between the streams of concurrent loads and queries
+    int no = 0;
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   } else {
     cudaGetLastError();
     c->pool = nullptr;  // the device's default pool then

@@ -291,6 +291,8 @@ struct WinWork;
 int window_enqueue_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, thapi_interval *dst, uint64_t cap,
                       WinWork *w, unsigned long long *total, cudaStream_t s);
 int free_trace_on(thapi_ctx *c, thapi_trace_id id, cudaStream_t s);
+int window_to_host_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, void *out, uint64_t n,
+                      thapi_interval *stage, WinWork *w, unsigned long long *total, cudaStream_t s);
 void *device_view(void *p);
 // A context that allocates only through the given hooks (creates nothing on the device).
 thapi_ctx *hooked_ctx_create(int device, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user);

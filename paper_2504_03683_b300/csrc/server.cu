@@ -23,7 +23,9 @@
 // released.  Every result equals that of the plain entry points
 // (thapi_trace_load, thapi_tally, thapi_timeline): the same kernels run, only
 // on other streams and at other times.
+#include <algorithm>
 #include <chrono>
+#include <iterator>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -38,61 +40,88 @@
 // the ABI's struct layouts (include/thapi.h), as the binding reads them
 static_assert(sizeof(thapi_request) == 72, "request");
 static_assert(sizeof(thapi_result) == 64, "result");
-static_assert(sizeof(thapi_server_stats) == 40, "server stats");
+static_assert(sizeof(thapi_server_stats) == 48, "server stats");
 
 namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr uint64_t kIdKey = 1ull << 63;      // trace key of a trace the server did not load: id | kIdKey
-constexpr uint64_t kMinClass = 64ull << 10;  // smallest pinned result buffer
-constexpr uint64_t kSlotBufMax = 256ull << 20;
+constexpr uint64_t kArenaAlign = 256;
+// results above this many intervals go through the slot's device staging buffer
+// (smaller ones are written through the pinned memory's mapping)
+constexpr uint64_t kStageMinIntervals = (1ull << 20) / sizeof(thapi_interval);
 
-// Pinned, device-mapped host buffers for results the server owns, kept by
-// power-of-two size class and reused (pinning is slow); at most `limit`
-// bytes are kept idle.
-struct PinnedPool {
+// Pinned, device-mapped host memory for results the server owns: one block
+// pinned when the server starts (pinning pages is slow, and freeing pinned
+// memory waits for the whole device), handed out first-fit and coalesced on
+// return.  A result that finds no room gets its own pinned allocation (the
+// slow path, released with cudaFreeHost).
+struct HostArena {
   std::mutex mu;
-  std::map<uint64_t, std::vector<void *>> idle;
-  uint64_t idle_bytes = 0, limit = 8ull << 30;
-  static uint64_t cls_of(uint64_t bytes) {
-    uint64_t c = kMinClass;
-    while (c < bytes) c <<= 1;
-    return c;
+  uint8_t *base = nullptr;
+  uint64_t size = 0;
+  std::map<uint64_t, uint64_t> idle;  // offset -> bytes, disjoint and coalesced
+  uint64_t own_allocs = 0;            // results that took the slow path
+  bool init(uint64_t bytes) {
+    bytes = (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign;
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    base = static_cast<uint8_t *>(p);
+    size = bytes;
+    idle[0] = bytes;
+    return true;
   }
-  void *get(uint64_t bytes, uint64_t *cls) {
-    *cls = cls_of(bytes);
+  // *own: the memory is a separate allocation (not from the block)
+  void *get(uint64_t bytes, bool *own) {
+    bytes = std::max<uint64_t>(kArenaAlign, (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign);
     {
       std::lock_guard<std::mutex> g(mu);
-      auto it = idle.find(*cls);
-      if (it != idle.end() && !it->second.empty()) {
-        void *p = it->second.back();
-        it->second.pop_back();
-        idle_bytes -= *cls;
-        return p;
+      for (auto it = idle.begin(); it != idle.end(); ++it) {
+        if (it->second < bytes) continue;
+        const uint64_t off = it->first, left = it->second - bytes;
+        idle.erase(it);
+        if (left) idle[off + bytes] = left;
+        *own = false;
+        return base + off;
       }
+      own_allocs += 1;
     }
     void *p = nullptr;
-    if (cudaHostAlloc(&p, *cls, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    if (cudaHostAlloc(&p, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
+    *own = true;
     return p;
   }
-  void put(void *p, uint64_t cls) {
+  void put(void *p, uint64_t bytes, bool own) {
     if (!p) return;
-    {
-      std::lock_guard<std::mutex> g(mu);
-      if (idle_bytes + cls <= limit) {
-        idle[cls].push_back(p);
-        idle_bytes += cls;
+    if (own) {
+      cudaFreeHost(p);
+      return;
+    }
+    bytes = std::max<uint64_t>(kArenaAlign, (bytes + kArenaAlign - 1) / kArenaAlign * kArenaAlign);
+    std::lock_guard<std::mutex> g(mu);
+    uint64_t off = static_cast<uint8_t *>(p) - base;
+    auto nx = idle.lower_bound(off);
+    if (nx != idle.end() && off + bytes == nx->first) {  // merge with the next free range
+      bytes += nx->second;
+      nx = idle.erase(nx);
+    }
+    if (nx != idle.begin()) {  // and with the previous one
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        pv->second += bytes;
         return;
       }
     }
-    cudaFreeHost(p);
+    idle[off] = bytes;
   }
-  ~PinnedPool() {
-    for (auto &kv : idle)
-      for (void *p : kv.second) cudaFreeHost(p);
+  ~HostArena() {
+    if (base) cudaFreeHost(base);
   }
 };
 
@@ -108,7 +137,8 @@ struct Req {
   thapi_trace_id trace = 0;  // resolved trace
   thapi_result res{};
   void *buf = nullptr;       // server-owned result
-  uint64_t buf_cls = 0;
+  uint64_t buf_bytes = 0;
+  bool buf_own = false;      // a separate pinned allocation, not arena memory
 };
 
 struct Slot {
@@ -118,8 +148,6 @@ struct Slot {
   thapi::WinWork *w = nullptr;               // device
   unsigned long long *total_h = nullptr;     // pinned, device-mapped count word
   unsigned long long *total_d = nullptr;     // its device view
-  void *buf = nullptr;                       // pinned result buffer the next window fills first
-  uint64_t buf_cls = 0;
   thapi_interval *stage = nullptr;           // device staging for pageable destinations
   uint64_t stage_bytes = 0;
 };
@@ -145,7 +173,7 @@ struct thapi_server {
   std::vector<Slot *> slots;
   cudaStream_t head_stream = nullptr;  // reads the file heads of device traces at submission
   std::mutex head_mu;
-  PinnedPool pool;
+  HostArena arena;
   thapi_server_stats st{};
 };
 
@@ -183,7 +211,7 @@ void complete(thapi_server *S, Req *q, int status) {
     q->counted = false;
   }
   if (q->auto_release && q->buf) {
-    S->pool.put(q->buf, q->buf_cls);
+    S->arena.put(q->buf, q->buf_bytes, q->buf_own);
     q->buf = nullptr;
     q->res.data = nullptr;
   }
@@ -294,7 +322,8 @@ int execute(thapi_server *S, Slot *sl, Req *q) {
     void *dst = r.out;
     uint64_t cap = r.cap;
     if (!dst) {
-      q->buf = S->pool.get(rows * sizeof(thapi_tally_row), &q->buf_cls);
+      q->buf_bytes = rows * sizeof(thapi_tally_row);
+      q->buf = S->arena.get(q->buf_bytes, &q->buf_own);
       if (!q->buf) return THAPI_E_NOMEM;
       dst = q->buf;
       cap = rows;
@@ -304,65 +333,34 @@ int execute(thapi_server *S, Slot *sl, Req *q) {
     if (rc == THAPI_OK) res.data = dst;
     return rc;
   }
-  // WINDOW
-  if (r.out) {
-    thapi_interval *dv = static_cast<thapi_interval *>(thapi::device_view(r.out));
-    if (dv) {
-      rc = window_once(S, sl, q->trace, r, dv, r.cap, &res.n);
-      if (rc == THAPI_OK && res.n > r.cap) rc = THAPI_E_RANGE;
-      if (rc == THAPI_OK) res.data = r.out;
-      return rc;
-    }
-    // pageable host memory: count, stage on the device, copy
-    if ((rc = window_once(S, sl, q->trace, r, nullptr, 0, &res.n)) != THAPI_OK) return rc;
+  // WINDOW: a device destination takes the matches in the counting pass; host
+  // destinations (the caller's, or the server's pinned result memory) are
+  // written once the count is known
+  cudaPointerAttributes pa{};
+  const bool to_device = r.out && cudaPointerGetAttributes(&pa, r.out) == cudaSuccess &&
+                         (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  if ((rc = window_once(S, sl, q->trace, r, to_device ? static_cast<thapi_interval *>(r.out) : nullptr,
+                        to_device ? r.cap : 0, &res.n)) != THAPI_OK)
+    return rc;
+  if (to_device) {
     if (res.n > r.cap) return THAPI_E_RANGE;
-    if (!res.n) {
-      res.data = r.out;
-      return THAPI_OK;
-    }
-    if ((rc = grow_stage(S, sl, res.n * sizeof(thapi_interval))) != THAPI_OK) return rc;
-    uint64_t n2 = 0;
-    if ((rc = window_once(S, sl, q->trace, r, sl->stage, res.n, &n2)) != THAPI_OK) return rc;
-    if (cudaMemcpyAsync(r.out, sl->stage, res.n * sizeof(thapi_interval), cudaMemcpyDeviceToHost, sl->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(sl->stream) != cudaSuccess) {
-      cudaGetLastError();
-      return THAPI_E_CUDA;
-    }
     res.data = r.out;
     return THAPI_OK;
   }
-  // server-owned result: the slot's pinned buffer first (one pass when it fits;
-  // the ticket then keeps it and the slot takes another of that size)
-  if (!sl->buf) {
-    sl->buf = S->pool.get(kMinClass, &sl->buf_cls);
-    if (!sl->buf) return THAPI_E_NOMEM;
-  }
-  const uint64_t slot_cap = sl->buf_cls / sizeof(thapi_interval);
-  void *dview = thapi::device_view(sl->buf);
-  if (!dview) return THAPI_E_CUDA;
-  if ((rc = window_once(S, sl, q->trace, r, static_cast<thapi_interval *>(dview), slot_cap, &res.n)) != THAPI_OK)
-    return rc;
-  if (res.n <= slot_cap) {
-    q->buf = sl->buf;
-    q->buf_cls = sl->buf_cls;
-    sl->buf = S->pool.get(sl->buf_cls, &sl->buf_cls);  // (null is retried at the next window)
-  } else {
-    q->buf = S->pool.get(res.n * sizeof(thapi_interval), &q->buf_cls);
+  void *dst = r.out;
+  if (dst && res.n > r.cap) return THAPI_E_RANGE;
+  if (!dst && res.n) {
+    q->buf_bytes = res.n * sizeof(thapi_interval);
+    q->buf = S->arena.get(q->buf_bytes, &q->buf_own);
     if (!q->buf) return THAPI_E_NOMEM;
-    void *qv = thapi::device_view(q->buf);
-    uint64_t n2 = 0;
-    if (!qv) return THAPI_E_CUDA;
-    if ((rc = window_once(S, sl, q->trace, r, static_cast<thapi_interval *>(qv), res.n, &n2)) != THAPI_OK) return rc;
-    // the slot's buffers grow toward the results it sees, up to a bound
-    const uint64_t want = PinnedPool::cls_of(res.n * sizeof(thapi_interval));
-    if (want <= kSlotBufMax && want > sl->buf_cls) {
-      S->pool.put(sl->buf, sl->buf_cls);
-      sl->buf = S->pool.get(want, &sl->buf_cls);
-    }
+    dst = q->buf;
   }
-  res.data = q->buf;
-  return THAPI_OK;
+  if (res.n > kStageMinIntervals && (rc = grow_stage(S, sl, res.n * sizeof(thapi_interval))) != THAPI_OK) return rc;
+  rc = thapi::window_to_host_id(S->ctx, q->trace, r.t0, r.t1, dst, res.n,
+                                res.n > kStageMinIntervals ? sl->stage : nullptr, sl->w, sl->total_d, sl->stream);
+  if (rc == THAPI_OK) res.data = dst;
+  return rc;
 }
 
 void run_slot(thapi_server *S, Slot *sl) {
@@ -393,7 +391,6 @@ void destroy_slot(thapi_server *S, Slot *sl) {
   if (sl->w) thapi::ctx_free(S->ctx, sl->w, sizeof(thapi::WinWork), sl->stream);
   if (sl->stage) thapi::ctx_free(S->ctx, sl->stage, sl->stage_bytes, sl->stream);
   if (sl->stream) cudaStreamSynchronize(sl->stream);
-  if (sl->buf) S->pool.put(sl->buf, sl->buf_cls);
   if (sl->total_h) cudaFreeHost(sl->total_h);
   if (sl->stream) cudaStreamDestroy(sl->stream);
   delete sl;
@@ -477,7 +474,7 @@ int release(thapi_server *S, uint64_t ticket) {
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end() || it->second->state != 2) return THAPI_E_INVALID;
   Req *q = it->second;
-  if (q->buf) S->pool.put(q->buf, q->buf_cls);
+  if (q->buf) S->arena.put(q->buf, q->buf_bytes, q->buf_own);
   S->reqs.erase(it);
   delete q;
   return THAPI_OK;
@@ -487,7 +484,8 @@ int release(thapi_server *S, uint64_t ticket) {
 
 extern "C" {
 
-int thapi_server_create(thapi_ctx *ctx, uint32_t load_slots, uint32_t query_slots, thapi_server **out) {
+int thapi_server_create(thapi_ctx *ctx, uint32_t load_slots, uint32_t query_slots, uint64_t result_bytes,
+                        thapi_server **out) {
   if (!ctx || !out || load_slots == 0 || query_slots == 0 || load_slots + query_slots > 64) return THAPI_E_INVALID;
   *out = nullptr;
   thapi_server *S = new (std::nothrow) thapi_server();
@@ -502,7 +500,8 @@ int thapi_server_create(thapi_ctx *ctx, uint32_t load_slots, uint32_t query_slot
   int least = 0, greatest = 0;
   cudaDeviceGetStreamPriorityRange(&least, &greatest);
   int rc = THAPI_OK;
-  if (cudaStreamCreateWithFlags(&S->head_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (!S->arena.init(result_bytes ? result_bytes : (1ull << 30)) ||
+      cudaStreamCreateWithFlags(&S->head_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     delete S;
     return THAPI_E_CUDA;
@@ -593,6 +592,8 @@ int thapi_server_stats_get(thapi_server *s, thapi_server_stats *st) {
   if (!s || !st) return THAPI_E_INVALID;
   std::lock_guard<std::mutex> g(s->mu);
   *st = s->st;
+  std::lock_guard<std::mutex> ga(s->arena.mu);
+  st->result_allocs = s->arena.own_allocs;
   return THAPI_OK;
 }
 
@@ -623,7 +624,7 @@ int thapi_server_destroy(thapi_server *s) {
   for (Slot *sl : s->slots) destroy_slot(s, sl);
   cudaStreamDestroy(s->head_stream);
   for (auto &kv : s->reqs) {
-    if (kv.second->buf) s->pool.put(kv.second->buf, kv.second->buf_cls);
+    if (kv.second->buf) s->arena.put(kv.second->buf, kv.second->buf_bytes, kv.second->buf_own);
     delete kv.second;
   }
   delete s;

@@ -128,9 +128,9 @@ class Server:
     Results of queries land in pinned host memory the loop owns (replay
     returns them as soon as each request completes unless `keep`)."""
 
-    def __init__(self, ctx: thapi.Context, load_slots: int = 2, query_slots: int = 6):
+    def __init__(self, ctx: thapi.Context, load_slots: int = 2, query_slots: int = 6, result_bytes: int = 0):
         self.ctx = ctx
-        self.handle = thapi.thapi_server_create(ctx.handle, load_slots, query_slots)
+        self.handle = thapi.thapi_server_create(ctx.handle, load_slots, query_slots, result_bytes)
 
     def replay(self, steps, ids, sources, keep: bool = False):
         """Serves the schedule; returns one thapi.Result per step (times on the
@@ -279,17 +279,23 @@ class _PlainBackend:
 
 
 def summary(outcomes, kinds=KINDS):
-    """Latency percentiles (ms) per kind and overall, from Results or Outcomes."""
+    """Latency percentiles (ms) per kind and overall, from Results or Outcomes:
+    arrival to result, and its two parts, the wait before the request started
+    and its service time."""
     lat = {k: [] for k in kinds}
     failed = 0
     for o in outcomes:
         if o is None or o.status != thapi.OK:
             failed += 1
             continue
-        lat[KINDS[o.kind]].append((o.t_done - o.t_arrival) * 1e3)
+        lat[KINDS[o.kind]].append(((o.t_done - o.t_arrival) * 1e3, (o.t_admit - o.t_arrival) * 1e3,
+                                   (o.t_done - o.t_admit) * 1e3))
     allq = [x for k in ("tally", "window") for x in lat.get(k, [])]
     out = {"failed": failed}
     for k, xs in list(lat.items()) + [("queries", allq)]:
         if xs:
-            out[k] = {"n": len(xs), "p50": percentile(xs, 50), "p99": percentile(xs, 99), "max": max(xs)}
+            tot, wait, svc = ([x[j] for x in xs] for j in range(3))
+            out[k] = {"n": len(xs), "p50": percentile(tot, 50), "p99": percentile(tot, 99), "max": max(tot),
+                      "wait_p50": percentile(wait, 50), "wait_p99": percentile(wait, 99),
+                      "service_p50": percentile(svc, 50), "service_p99": percentile(svc, 99)}
     return out

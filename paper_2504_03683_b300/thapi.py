@@ -105,7 +105,7 @@ class Result(ctypes.Structure):
 
 class ServerStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_uint64) for f in ("submitted", "completed", "load_waits", "peak_running",
-                                                "peak_committed")]
+                                                "peak_committed", "result_allocs")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -163,7 +163,7 @@ def library():
         "thapi_device_tally": ([vp, u64, vp, u64, P(u64), P(DeviceDiag)], i32),
         "thapi_tally_merge": ([vp, vp, u64, vp, u64, P(u64), vp], i32),
         "thapi_decode": ([vp, vp, u64, vp, u64, P(u64), vp], i32),
-        "thapi_server_create": ([vp, u32, u32, P(vp)], i32),
+        "thapi_server_create": ([vp, u32, u32, u64, P(vp)], i32),
         "thapi_server_submit": ([vp, P(Request), P(u64)], i32),
         "thapi_server_poll": ([vp, u64, u32, P(Result)], i32),
         "thapi_server_release": ([vp, u64], i32),
@@ -440,9 +440,10 @@ def thapi_tally_static(dev_ptr: int, nbytes: int, rows_dev_ptr: int, cap: int, s
 
 
 # ------------------------------------------------- serving loop
-def thapi_server_create(ctx: int, load_slots: int = 2, query_slots: int = 4) -> int:
+def thapi_server_create(ctx: int, load_slots: int = 2, query_slots: int = 4, result_bytes: int = 0) -> int:
     h = ctypes.c_void_p()
-    _check(library().thapi_server_create(ctx, load_slots, query_slots, ctypes.byref(h)), "thapi_server_create")
+    _check(library().thapi_server_create(ctx, load_slots, query_slots, result_bytes, ctypes.byref(h)),
+           "thapi_server_create")
     return h.value
 
 
