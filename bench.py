@@ -46,7 +46,7 @@ WORKLOADS = {
                                         "plain loads of the same device-resident traces"),
     "serve": dict(preset="large", desc="serving loop: traces of the large workload's API mix (1 host x 1 pid x 8 "
                                         "threads each) sized log-uniform 1 MB-4 GB, decoded results kept "
-                                        "device-resident under a 120 GB admission cap (90 GB resident at the "
+                                        "device-resident under a 120 GB admission cap (100 GB resident at the "
                                         "start); Poisson arrivals at 200 req/s: 5% trace loads from pinned host "
                                         "memory, 5% frees of the oldest trace, the rest half tally and half "
                                         "time-window queries (width log-uniform 1e-4-1 of the span)"),
@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--batch-gb", type=float, default=30.0, help="batch workload: total trace bytes (GB)")
     ap.add_argument("--serve-sources", type=int, default=40, help="serve workload: distinct traces in the pool")
     ap.add_argument("--serve-cap-gb", type=float, default=120.0, help="serve workload: admission cap (GB)")
-    ap.add_argument("--serve-resident-gb", type=float, default=90.0,
+    ap.add_argument("--serve-resident-gb", type=float, default=100.0,
                     help="serve workload: device bytes of the results resident at the start (GB)")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serve workload: arrival window (s)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
@@ -575,7 +575,9 @@ def run_serve(args, rank, world, local):
                 h2d += offs[st.source][1]
             else:
                 d2h += o.n * (56 if st.kind == "tally" else 24)
-        end = max((o.t_done for o in outs if o is not None), default=0.0) - min(s.arrival for s in steps)
+        # the last result, on the schedule's clock (each result's latency after its arrival)
+        end = max((st.arrival + o.t_done - o.t_arrival for st, o in zip(steps, outs) if o is not None),
+                  default=0.0)
         return {"answered_events_per_s": (ev["tally"] + ev["window"]) / wall_s,
                 "loaded_events_per_s": ev["load"] / wall_s, "wall_s": wall_s, "h2d_bytes": h2d, "d2h_bytes": d2h,
                 "last_result_s": end}
