@@ -47,6 +47,11 @@ constexpr uint32_t kHeights = 32;       // per-height table rows (depth range of
 constexpr uint32_t kClsMax = 4096;      // class rows held in shared memory
 constexpr uint32_t kChunk = 2048;       // frontier items grabbed per global atomic
 constexpr uint32_t kMaxWarps = 16;      // warps per CTA
+// Per-lane pairing (the fast path): each lane's pending exits and open
+// entries, 8 bytes each, in the warp's table and offset area (2,560 bytes =
+// 32 lanes x kLaneSlots, lane-interleaved so that lanes at any slot hit
+// distinct banks)
+constexpr uint32_t kLaneSlots = (kHeights * 16u + kEvMax * 2u) / (32u * 8u);
 constexpr uint32_t kFull = 0xffffffffu;
 
 __host__ __device__ inline uint32_t rup(uint32_t v, uint32_t a) { return (v + a - 1u) / a * a; }
@@ -241,8 +246,210 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   bool issued = false;  // a copy is in flight into buf
   bool timed_out = false;
 
+  // room for a packet's frontier items, from lane 0's chunk (~0: none, the host retries)
+  auto grab_frontier = [&](uint32_t need) -> uint64_t {
+    uint64_t fb = 0;
+    if (lane == 0 && need) {
+      if (need > fr_left) {
+        const uint32_t grab = need > kChunk ? need : kChunk;
+        fr_base = atomicAdd(p.frontier_top, (unsigned long long)grab);
+        fr_left = grab;
+        if (fr_base + grab > p.frontier_cap) fr_left = 0;  // overflow: the host retries with more room
+      }
+      if (need <= fr_left) {
+        fb = fr_base;
+        fr_base += need;
+        fr_left -= need;
+      } else {
+        fb = ~0ull;
+      }
+    }
+    return __shfl_sync(kFull, fb, 0);
+  };
+
   uint64_t w = w_begin + warp;
   PkDesc dcur{}, dnext{};
+
+  // Per-lane pairing of one packet whose events are valid, carry no absolute
+  // timestamp, have deltas summing below 2^32 and need at most kLaneSlots
+  // slots per lane.  Each lane walks its own events in order with a call
+  // stack of its own: an exit pops the lane's latest open entry or, on an
+  // empty stack, is a pending exit of the lane.  A lane's slots hold its
+  // pending exits (at most one per new minimum depth, so they come first),
+  // then its stack.  Timestamps are relative to the packet's ts_begin.
+  // Afterwards, the k-th pending exit of a lane that starts at depth D closes
+  // height D - 1 - k: it pairs with the open entry at that height of the
+  // latest earlier lane that has one (per-height lane masks from ballots),
+  // and with none it pops below the packet's start (a frontier item).  The
+  // latest lane's open entry at each height from the packet's minimum depth
+  // to its final depth is an open entry of the packet.  The running minimum
+  // depth when an exit closes an entry equals the one when the entry was
+  // made (the depth stays above the entry's height in between), which gives
+  // the interval's packet-relative level and depth below the packet start.
+  auto pair_lanes = [&](const PkDesc &d, uint64_t pos, bool has_next, DM dc, DM ex, DM ld, const Bits<BW> &bits,
+                        uint32_t a, uint32_t e0, uint32_t c_tot, uint32_t ecnt, uint64_t dsum) {
+    const int dmin = dc.m;
+    const uint32_t P_p = (uint32_t)(-dmin), O_p = (uint32_t)(dc.s - dmin);
+    const uint64_t fbase = grab_frontier(P_p + O_p);
+    thapi_interval *const pslots = p.slots ? p.slots + d.evbase : nullptr;
+    Cell *const gcells = p.tally + (uint64_t)d.group * F;
+    uint2 *const stk = reinterpret_cast<uint2 *>(wb + L.off_tab);  // [slot][lane]
+    // lane prefixes: the slot rank of the lane's first entry and the time
+    // before its first event (entries in bits 40.., deltas below)
+    const uint64_t own = ((uint64_t)ecnt << 40) | dsum;
+    uint64_t inc = own;
+#pragma unroll
+    for (int q = 1; q < 32; q <<= 1) {
+      const uint64_t u = __shfl_up_sync(kFull, inc, q);
+      if (lane >= (uint32_t)q) inc += u;
+    }
+    const uint64_t exs = inc - own;
+    const uint32_t n_ent = (uint32_t)(__shfl_sync(kFull, inc, 31) >> 40);
+    uint32_t rank = (uint32_t)(exs >> 40);
+    uint32_t trel = (uint32_t)exs;  // the deltas of the whole packet sum below 2^32
+    const int D = ex.s, Mex = ex.m;  // depth at the lane's start, running minimum before it
+    uint32_t valid = 0, mism = 0, other = 0;
+    // one pair: entry (time, slot rank, function) closed by an exit; post =
+    // depth after the exit, bm = running minimum depth before it
+    auto pair = [&](uint32_t ets, uint32_t erank, uint32_t efn, uint32_t xts, uint32_t xfn, uint32_t err, int post,
+                    int bm) {
+      uint32_t flags = 0;
+      if (efn == xfn) {
+        ++valid;
+        flags = kIvValid | err;
+        const unsigned long long dur = (unsigned long long)(xts - ets);
+        Cell &cell = gcells[xfn];
+        atomicAdd(&cell.count, 1ull);
+        atomicAdd(&cell.total, dur);
+        atomicMin(&cell.mn, dur);
+        atomicMax(&cell.mx, dur);
+        if (err) atomicAdd(&cell.err, 1ull);
+      } else {
+        ++mism;  // mismatched pair: no interval
+      }
+      if (pslots)
+        put_interval(pslots + erank, d.tsb + ets, d.tsb + xts, (uint32_t)(-bm), efn, (uint32_t)min(post - bm, 255),
+                     flags);
+    };
+    int sd = 0, md = 0;     // the lane's depth and running minimum, relative to its start
+    uint32_t sp = 0, np = 0;  // open entries on the lane's stack; pending exits below them
+    uint32_t e = e0;          // event index in the packet
+    uint32_t tfirst = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < BW; ++k) {
+      uint32_t mb = bits.w[k];
+      while (mb) {
+        const uint32_t oo = a + k * 32 + (__ffs(mb) - 1);
+        mb &= mb - 1;
+        const uint32_t w0 = C[oo], w1 = C[oo + 1];
+        const uint32_t c = w1 & 0xFFFFu;
+        const uint32_t r = ctab[c];
+        const uint32_t kd = row_kind(r);
+        const uint32_t fn = cfn[c];
+        trel += w0 & kDeltaMask;
+        tfirst = min(tfirst, trel);
+        if (kd == kEntry) {
+          stk[(np + sp) * 32 + lane] = make_uint2(trel, fn | (rank << 16));
+          ++sp;
+          ++rank;
+          ++sd;
+        } else if (kd == kExit) {
+          const int32_t rw = row_resw(r);
+          const uint32_t err = (rw >= 0 && C[oo + 2 + (uint32_t)rw] != 0) ? 1u : 0u;
+          --sd;
+          if (sp) {
+            --sp;
+            const uint2 q = stk[(np + sp) * 32 + lane];
+            pair(q.x, q.y >> 16, q.y & 0xFFFFu, trel, fn, err, D + sd, min(Mex, D + md));
+          } else {
+            stk[np * 32 + lane] = make_uint2(trel, fn | (e << 16) | (err << 31));
+            ++np;
+            md = sd;
+          }
+        } else {
+          ++other;
+        }
+        ++e;
+      }
+    }
+    const uint32_t tlast = trel;
+    __syncwarp();  // every lane's slots are written; the packet bytes are no longer needed
+    if (lane == 0 && has_next && dcur.group != kPerCpuGroup) issue(dcur);
+    issued = has_next && dcur.group != kPerCpuGroup;
+    // heights indexed from the packet's minimum depth; the lane's open entries are [lo, hi)
+    const int lo = D + ld.m - dmin, hi = D + ld.s - dmin;
+    const int hn = __reduce_max_sync(kFull, hi);
+    uint32_t hmask = 0;  // lane u: the lanes with an open entry at height index u
+    for (int u = 0; u < hn; ++u) {
+      const uint32_t bal = __ballot_sync(kFull, lo <= u && u < hi);
+      if (lane == (uint32_t)u) hmask = bal;
+    }
+    const uint32_t maxp = __reduce_max_sync(kFull, np);
+    for (uint32_t k = 0; k < maxp; ++k) {
+      const bool act = k < np;
+      const int h = D - 1 - (int)k;  // the height this pending exit closes
+      const int u = act ? h - dmin : 0;
+      const uint32_t lu = __shfl_sync(kFull, hmask, u);
+      const uint32_t cand = act ? (lu & lt) : 0u;
+      const int j = cand ? 31 - __clz(cand) : (int)lane;
+      const int lo_j = __shfl_sync(kFull, lo, j);
+      const uint32_t np_j = __shfl_sync(kFull, np, j);
+      if (act) {
+        const uint2 x = stk[k * 32 + lane];
+        const uint32_t xfn = x.y & 0xFFFFu, xe = (x.y >> 16) & 0x7FFFu, xerr = x.y >> 31;
+        if (cand) {
+          const uint2 q = stk[(np_j + (uint32_t)(u - lo_j)) * 32 + (uint32_t)j];
+          pair(q.x, q.y >> 16, q.y & 0xFFFFu, x.x, xfn, xerr, h, min(Mex, D - (int)k));
+        } else if (fbase != ~0ull) {  // it pops below the packet's start
+          Frontier fr;
+          fr.ts = d.tsb + x.x;
+          fr.aux = xe;
+          fr.func = (uint16_t)xfn;
+          fr.flags = (uint16_t)xerr;
+          p.frontier[fbase + (uint64_t)(-h - 1)] = fr;
+        }
+      }
+    }
+    {  // the packet's open entries, one height per lane
+      const uint32_t ow = lane < O_p ? hmask : 0u;
+      const int j = ow ? 31 - __clz(ow) : (int)lane;
+      const int lo_j = __shfl_sync(kFull, lo, j);
+      const uint32_t np_j = __shfl_sync(kFull, np, j);
+      if (ow) {
+        const uint2 q = stk[(np_j + (lane - (uint32_t)lo_j)) * 32 + (uint32_t)j];
+        const uint32_t orank = q.y >> 16, ofn = q.y & 0xFFFFu;
+        if (fbase != ~0ull) {
+          Frontier fr;
+          fr.ts = d.tsb + q.x;
+          fr.aux = pslots ? orank : 0xFFFFFFFFu;
+          fr.func = (uint16_t)ofn;
+          fr.flags = 0;
+          p.frontier[fbase + P_p + lane] = fr;
+        }
+        if (pslots) put_interval(pslots + orank, d.tsb + q.x, 0, (uint32_t)(-dmin), ofn, min(lane, 255u), kIvOpen);
+      }
+    }
+    __syncwarp();  // the slots are read before the next packet's offsets reuse the area
+    n_mismatch += mism;
+    n_pairs += valid;
+    n_other += other;
+    if (tfirst != 0xFFFFFFFFu) {
+      tmin = min(tmin, d.tsb + tfirst);
+      tmax = max(tmax, d.tsb + tlast);
+    }
+    const uint32_t vsum = __reduce_add_sync(kFull, valid);
+    if (lane == 0) {
+      p.sum_pend[pos] = P_p;
+      p.sum_open[pos] = O_p;
+      p.sum_fbase[pos] = fbase;
+      p.sum_nslot[pos] = n_ent;
+      p.sum_nvalid[pos] = vsum;
+      n_events += c_tot;
+      if (p.slots) n_slots += n_ent;
+      n_disc += d.disc;
+      n_pk += 1;
+    }
+  };
   if (w < w_end) {
     dcur = load_desc(p.desc + pos_of(w));
     dnext = dcur;
@@ -324,12 +531,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     DM ld{0, 0};
     int lmax = 0;
     uint32_t nrec = 0;  // device-activity records of the lane's events: begin | end << 10 | host << 20
+    // for per-lane pairing: the lane's entries, the sum of its timestamp deltas, an EXT event seen
+    uint32_t ecnt = 0;
+    uint64_t dsum = 0;
+    bool lext = false;
     if (!fallback) {
       uint32_t e = cinc - cnt;
       // one event: its error code (0 if none) and depth step
       // (rec: its device-activity record, counted in nrec's fields)
-      auto check = [&](uint32_t oo, uint32_t &code, int &dv, uint32_t &rec) {
+      auto check = [&](uint32_t oo, uint32_t &code, int &dv, uint32_t &rec, uint32_t &dl) {
         const uint32_t w0 = C[oo], w1 = C[oo + 1];
+        dl = w0;
         const uint32_t c = w1 & 0xFFFFu;
         const bool ext = (w0 & kExtBit) != 0;
         const uint32_t r = ctab[c < NC ? c : NC];
@@ -343,8 +555,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
                   ? (kd == kDevBegin ? 1u : kd == kDevEnd ? (1u << 10) : kd == kEntry ? (1u << 20) : 0u)
                   : 0u;
       };
-      auto fold = [&](uint32_t code, int dv, uint32_t rec) {
+      auto fold = [&](uint32_t code, int dv, uint32_t rec, uint32_t dl) {
         nrec += rec;
+        ecnt += dv > 0 ? 1u : 0u;
+        dsum += dl & kDeltaMask;
+        lext = lext || (dl & kExtBit) != 0;
         if (code) ekey = min(ekey, (e << 3) | code);
         ld.s += dv;
         ld.m = min(ld.m, ld.s);
@@ -362,23 +577,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
           m &= m - 1;  // (no-op when m is 0)
           s_off[e] = (uint16_t)oo0;
           if (two) s_off[e + 1] = (uint16_t)oo1;
-          uint32_t c0, c1, r0, r1;
+          uint32_t c0, c1, r0, r1, l0, l1;
           int d0, d1;
-          check(oo0, c0, d0, r0);
-          check(oo1, c1, d1, r1);
-          fold(c0, d0, r0);
-          if (two) fold(c1, d1, r1);
+          check(oo0, c0, d0, r0, l0);
+          check(oo1, c1, d1, r1, l1);
+          fold(c0, d0, r0, l0);
+          if (two) fold(c1, d1, r1, l1);
         }
       }
     }
     __syncwarp();
     const uint32_t nb = fallback ? 0u : (c_tot + 31) >> 5;  // batches of 32 events
     // the packet's depth range: exclusive scan of the lanes' depth monoids
-    DM dc;
+    DM dc, ex;
     int dmax;
     {
       DM inc = scan_dm(ld, lane);
-      DM ex{__shfl_up_sync(kFull, inc.s, 1), __shfl_up_sync(kFull, inc.m, 1)};
+      ex = DM{__shfl_up_sync(kFull, inc.s, 1), __shfl_up_sync(kFull, inc.m, 1)};
       if (lane == 0) ex = DM{0, 0};
       dc = DM{__shfl_sync(kFull, inc.s, 31), __shfl_sync(kFull, inc.m, 31)};
       dmax = __reduce_max_sync(kFull, ex.s + lmax);
@@ -400,6 +615,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
       continue;
     }
 
+    // ---- 3a. per-lane pairing, for packets without absolute timestamps, with
+    // a span below 2^32 ns and nesting shallow enough for the lanes' slots
+    if constexpr (!DEV && !SIDE) {
+      uint64_t dtot = dsum;
+#pragma unroll
+      for (int q = 16; q; q >>= 1) dtot += __shfl_xor_sync(kFull, dtot, q);
+      const bool fast = !__any_sync(kFull, lext) && dtot < (1ull << 32) &&
+                        !__any_sync(kFull, lmax - 2 * ld.m > (int)kLaneSlots);
+      if (fast) {
+        pair_lanes(d, pos, has_next, dc, ex, ld, bits, a, cinc - cnt, c_tot, ecnt, dsum);
+        continue;
+      }
+    }
+
     // ---- 3. pairing, 32 events at a time
     const int dmin = dc.m;  // minimum depth (packet-relative, <= 0); heights are indexed from it
     const uint32_t P_p = (uint32_t)(-dmin);
@@ -416,26 +645,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         if (nh_p) rbase_h = atomicAdd(&p.cmd.counts[2], (unsigned long long)nh_p);
       }
     }
-    uint64_t fbase = 0;
-    if (lane == 0) {
-      const uint32_t need = P_p + O_p;
-      if (need) {
-        if (need > fr_left) {
-          const uint32_t grab = need > kChunk ? need : kChunk;
-          fr_base = atomicAdd(p.frontier_top, (unsigned long long)grab);
-          fr_left = grab;
-          if (fr_base + grab > p.frontier_cap) fr_left = 0;  // overflow: the host retries with more room
-        }
-        if (need <= fr_left) {
-          fbase = fr_base;
-          fr_base += need;
-          fr_left -= need;
-        } else {
-          fbase = ~0ull;
-        }
-      }
-    }
-    fbase = __shfl_sync(kFull, fbase, 0);
+    const uint64_t fbase = grab_frontier(P_p + O_p);
     if (dev_on) {
       rbase_b = __shfl_sync(kFull, rbase_b, 0);
       rbase_e = __shfl_sync(kFull, rbase_e, 0);
