@@ -146,14 +146,73 @@ __device__ __forceinline__ uint32_t resolve_seg(const uint32_t *C, uint32_t y, u
   return m;
 }
 
-// Interval slot, written as three 8-byte words.
+// The set marks of a lane's bitmap in increasing order, one per next():
+// the words sit in a shift register (static indexes keep them in registers)
+// so that one loop body serves every word.
+template <int BW>
+struct MarkIter {
+  uint32_t w[BW];
+  uint32_t base;
+  __device__ __forceinline__ MarkIter(const Bits<BW> &b, uint32_t a) : base(a) {
+#pragma unroll
+    for (int k = 0; k < BW; ++k) w[k] = b.w[k];
+  }
+  // the next marked offset (only while marks are left)
+  __device__ __forceinline__ uint32_t next() {
+    while (w[0] == 0) {
+#pragma unroll
+      for (int k = 0; k + 1 < BW; ++k) w[k] = w[k + 1];
+      w[BW - 1] = 0;
+      base += 32;
+    }
+    const uint32_t o = base + (uint32_t)(__ffs(w[0]) - 1);
+    w[0] &= w[0] - 1;
+    return o;
+  }
+};
+
+// Marks set in increasing offset order: the word being filled is kept
+// apart and pushed into a shift register when the offsets pass it (after BW
+// pushes the words are in order), instead of a select over every word per
+// mark.
+template <int BW>
+struct MarkFill {
+  uint32_t w[BW];
+  uint32_t cur = 0, lim = 32, pushed = 0;
+  __device__ __forceinline__ MarkFill() {
+#pragma unroll
+    for (int k = 0; k < BW; ++k) w[k] = 0;
+  }
+  __device__ __forceinline__ void push() {
+#pragma unroll
+    for (int k = 0; k + 1 < BW; ++k) w[k] = w[k + 1];
+    w[BW - 1] = cur;
+    cur = 0;
+    lim += 32;
+    ++pushed;
+  }
+  __device__ __forceinline__ void set(uint32_t rel) {  // rel: nondecreasing, < 32 * BW
+    while (rel >= lim) push();
+    cur |= 1u << (rel & 31u);
+  }
+  __device__ __forceinline__ void finish(Bits<BW> &out) {
+    while (pushed < (uint32_t)BW) push();
+#pragma unroll
+    for (int k = 0; k < BW; ++k) out.w[k] = w[k];
+  }
+};
+
+// Interval slot (24 bytes at a multiple of 24 from a 16-byte aligned base):
+// one 16-byte and one 8-byte store, the 16-byte one on whichever half is
+// aligned.
 __device__ __forceinline__ void put_interval(thapi_interval *dst, uint64_t start, uint64_t end, uint32_t np,
                                              uint32_t fn, uint32_t lvl, uint32_t flags) {
   unsigned long long *q = reinterpret_cast<unsigned long long *>(dst);
-  q[0] = start;
-  q[1] = end;
-  q[2] = (unsigned long long)np | ((unsigned long long)fn << 32) | ((unsigned long long)lvl << 48) |
-         ((unsigned long long)flags << 56);
+  const unsigned long long w2 = (unsigned long long)np | ((unsigned long long)fn << 32) |
+                                ((unsigned long long)lvl << 48) | ((unsigned long long)flags << 56);
+  const bool lo16 = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
+  *reinterpret_cast<ulonglong2 *>(lo16 ? q : q + 1) = lo16 ? make_ulonglong2(start, end) : make_ulonglong2(end, w2);
+  q[lo16 ? 2 : 0] = lo16 ? w2 : start;
 }
 
 // Entry metadata: func | rank << 16 | level << 32 | depth below the packet start << 40.
@@ -287,7 +346,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
   // made (the depth stays above the entry's height in between), which gives
   // the interval's packet-relative level and depth below the packet start.
   auto pair_lanes = [&](const PkDesc &d, uint64_t pos, bool has_next, DM dc, DM ex, DM ld, const Bits<BW> &bits,
-                        uint32_t a, uint32_t e0, uint32_t c_tot, uint32_t ecnt, uint64_t dsum) {
+                        uint32_t a, uint32_t e0, uint32_t cnt, uint32_t c_tot, uint32_t ecnt, uint64_t dsum) {
     const int dmin = dc.m;
     const uint32_t P_p = (uint32_t)(-dmin), O_p = (uint32_t)(dc.s - dmin);
     const uint64_t fbase = grab_frontier(P_p + O_p);
@@ -334,43 +393,34 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     int sd = 0, md = 0;     // the lane's depth and running minimum, relative to its start
     uint32_t sp = 0, np = 0;  // open entries on the lane's stack; pending exits below them
     uint32_t e = e0;          // event index in the packet
-    uint32_t tfirst = 0xFFFFFFFFu;
-#pragma unroll
-    for (int k = 0; k < BW; ++k) {
-      uint32_t mb = bits.w[k];
-      while (mb) {
-        const uint32_t oo = a + k * 32 + (__ffs(mb) - 1);
-        mb &= mb - 1;
-        const uint32_t w0 = C[oo], w1 = C[oo + 1];
-        const uint32_t c = w1 & 0xFFFFu;
-        const uint32_t r = ctab[c];
-        const uint32_t kd = row_kind(r);
-        const uint32_t fn = cfn[c];
-        trel += w0 & kDeltaMask;
-        tfirst = min(tfirst, trel);
-        if (kd == kEntry) {
-          stk[(np + sp) * 32 + lane] = make_uint2(trel, fn | (rank << 16));
-          ++sp;
-          ++rank;
-          ++sd;
-        } else if (kd == kExit) {
-          const int32_t rw = row_resw(r);
-          const uint32_t err = (rw >= 0 && C[oo + 2 + (uint32_t)rw] != 0) ? 1u : 0u;
-          --sd;
-          if (sp) {
-            --sp;
-            const uint2 q = stk[(np + sp) * 32 + lane];
-            pair(q.x, q.y >> 16, q.y & 0xFFFFu, trel, fn, err, D + sd, min(Mex, D + md));
-          } else {
-            stk[np * 32 + lane] = make_uint2(trel, fn | (e << 16) | (err << 31));
-            ++np;
-            md = sd;
-          }
-        } else {
-          ++other;
-        }
-        ++e;
-      }
+    const uint32_t first_delta = C[0] & kDeltaMask;  // the packet's first event starts at word 0
+    MarkIter<BW> it(bits, a);
+    for (uint32_t left = cnt; left; --left) {
+      const uint32_t oo = it.next();
+      const uint32_t w0 = C[oo], w1 = C[oo + 1];
+      const uint32_t c = w1 & 0xFFFFu;
+      const uint32_t r = ctab[c];
+      const uint32_t kd = row_kind(r);
+      const uint32_t fn = cfn[c];
+      trel += w0 & kDeltaMask;
+      const bool is_e = kd == kEntry, is_x = kd == kExit;
+      const bool pop = is_x && sp != 0, pend = is_x && sp == 0;
+      const int32_t rw = row_resw(r);
+      const uint32_t err = (is_x && rw >= 0 && C[oo + 2 + (uint32_t)max(rw, 0)] != 0) ? 1u : 0u;
+      // an entry pushes at np + sp, a pop reads np + sp - 1, a pending exit writes np (sp = 0)
+      const uint32_t slot = (np + sp - (pop ? 1u : 0u)) * 32 + lane;
+      uint2 q = make_uint2(0u, 0u);
+      if (pop) q = stk[slot];
+      if (is_e || pend) stk[slot] = make_uint2(trel, fn | ((is_e ? rank : (e | (err << 15))) << 16));
+      sd += is_e ? 1 : (is_x ? -1 : 0);
+      if (pop) pair(q.x, q.y >> 16, q.y & 0xFFFFu, trel, fn, err, D + sd, min(Mex, D + md));
+      sp += is_e ? 1u : 0u;
+      sp -= pop ? 1u : 0u;
+      np += pend ? 1u : 0u;
+      rank += is_e ? 1u : 0u;
+      md = pend ? sd : md;
+      other += (!is_e && !is_x) ? 1u : 0u;
+      ++e;
     }
     const uint32_t tlast = trel;
     __syncwarp();  // every lane's slots are written; the packet bytes are no longer needed
@@ -433,8 +483,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     n_mismatch += mism;
     n_pairs += valid;
     n_other += other;
-    if (tfirst != 0xFFFFFFFFu) {
-      tmin = min(tmin, d.tsb + tfirst);
+    if (c_tot) {  // timestamps never decrease here: the packet's first and last event bound them
+      tmin = min(tmin, d.tsb + first_delta);
       tmax = max(tmax, d.tsb + tlast);
     }
     const uint32_t vsum = __reduce_add_sync(kFull, valid);
@@ -493,11 +543,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     const uint32_t a = lane * SEGW;
     const uint32_t b = min(a + SEGW, W);
     Bits<BW> spec, bits;
-    spec.clear();
     uint32_t o = a;
-    while (o < b) {
-      spec.set(o - a);
-      o = step(C, o, ctab, NC);
+    {
+      MarkFill<BW> mf;
+      while (o < b) {
+        mf.set(o - a);
+        o = step(C, o, ctab, NC);
+      }
+      mf.finish(spec);
     }
     const uint32_t spec_x = a < b ? o : a;
     const bool succ_live = a + SEGW < W;
@@ -535,6 +588,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     uint32_t ecnt = 0;
     uint64_t dsum = 0;
     bool lext = false;
+    int lneed = 0;  // most slots the lane's pending exits and stack take at once: max(depth - 2 min)
     if (!fallback) {
       uint32_t e = cinc - cnt;
       // one event: its error code (0 if none) and depth step
@@ -564,26 +618,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
         ld.s += dv;
         ld.m = min(ld.m, ld.s);
         lmax = max(lmax, ld.s);
+        lneed = max(lneed, ld.s - 2 * ld.m);
         ++e;
       };
-#pragma unroll
-      for (int k = 0; k < BW; ++k) {
-        uint32_t m = bits.w[k];
-        while (m) {  // two events per iteration: their loads overlap
-          const uint32_t oo0 = a + k * 32 + (__ffs(m) - 1);
-          m &= m - 1;
-          const bool two = m != 0;
-          const uint32_t oo1 = two ? a + k * 32 + (__ffs(m) - 1) : oo0;
-          m &= m - 1;  // (no-op when m is 0)
-          s_off[e] = (uint16_t)oo0;
-          if (two) s_off[e + 1] = (uint16_t)oo1;
-          uint32_t c0, c1, r0, r1, l0, l1;
-          int d0, d1;
-          check(oo0, c0, d0, r0, l0);
-          check(oo1, c1, d1, r1, l1);
-          fold(c0, d0, r0, l0);
-          if (two) fold(c1, d1, r1, l1);
-        }
+      MarkIter<BW> it(bits, a);
+      for (uint32_t left = cnt; left;) {  // two events per iteration: their loads overlap
+        const uint32_t oo0 = it.next();
+        const bool two = left > 1;
+        const uint32_t oo1 = two ? it.next() : oo0;
+        left -= two ? 2u : 1u;
+        s_off[e] = (uint16_t)oo0;
+        if (two) s_off[e + 1] = (uint16_t)oo1;
+        uint32_t c0, c1, r0, r1, l0, l1;
+        int d0, d1;
+        check(oo0, c0, d0, r0, l0);
+        check(oo1, c1, d1, r1, l1);
+        fold(c0, d0, r0, l0);
+        if (two) fold(c1, d1, r1, l1);
       }
     }
     __syncwarp();
@@ -622,9 +673,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
 #pragma unroll
       for (int q = 16; q; q >>= 1) dtot += __shfl_xor_sync(kFull, dtot, q);
       const bool fast = !__any_sync(kFull, lext) && dtot < (1ull << 32) &&
-                        !__any_sync(kFull, lmax - 2 * ld.m > (int)kLaneSlots);
+                        !__any_sync(kFull, lneed > (int)kLaneSlots);
       if (fast) {
-        pair_lanes(d, pos, has_next, dc, ex, ld, bits, a, cinc - cnt, c_tot, ecnt, dsum);
+        pair_lanes(d, pos, has_next, dc, ex, ld, bits, a, cinc - cnt, cnt, c_tot, ecnt, dsum);
         continue;
       }
     }
