@@ -41,9 +41,9 @@ WORKLOADS = {
                                          "random 64-bit command ids; 64 device streams of begin/end events; 50M "
                                          "commands = 200M events; device pairing + merged timeline; 16 KB packets"),
     "batch": dict(preset="large", desc="4096 per-rank traces (1 host x 1 pid x 8 threads each, the large workload's "
-                                        "3-layer API mix, depth<=6), event counts log-uniform 10k-20M scaled to ~30 GB "
-                                        "in total and clamped to [10k, 20M]; 16 KB packets; one batched load vs 4096 "
-                                        "plain loads of the same device-resident traces"),
+                                        "3-layer API mix, depth<=6), event counts log-uniform 10k-20M scaled to ~60 GB "
+                                        "in total and clamped to [10k, 20M]; 16 KB packets; one batched load reading "
+                                        "the device-resident traces in place vs 4096 plain loads of the same traces"),
     "serve": dict(preset="large", desc="serving loop: traces of the large workload's API mix (1 host x 1 pid x 8 "
                                         "threads each) sized log-uniform 1 MB-4 GB, decoded results kept "
                                         "device-resident under a 120 GB admission cap (100 GB resident at the "
@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--autotune", action="store_true", help="the context's autotuner picks the load configuration "
                                                              "(during the warm-up steps)")
     ap.add_argument("--batch-traces", type=int, default=4096, help="batch workload: traces")
-    ap.add_argument("--batch-gb", type=float, default=30.0, help="batch workload: total trace bytes (GB)")
+    ap.add_argument("--batch-gb", type=float, default=60.0, help="batch workload: total trace bytes (GB)")
     ap.add_argument("--serve-sources", type=int, default=40, help="serve workload: distinct traces in the pool")
     ap.add_argument("--serve-cap-gb", type=float, default=120.0, help="serve workload: admission cap (GB)")
     ap.add_argument("--serve-resident-gb", type=float, default=100.0,
@@ -393,7 +393,7 @@ def run_batch(args, rank, world, local):
     peak = float(peaks.get("hbm_gbs", 6400.0))
     phase = {k: round(statistics.mean(t[k] for t in timings), 4)
              for k in ("index_ms", "analyze_ms", "frontier_ms", "tally_ms", "compact_ms", "sort_ms", "gather_ms",
-                       "total_ms")}
+                       "total_ms", "parse_ms", "call_ms")}
     # end to end: the batch from pinned host memory, results to the host
     e2e = None
     if not args.no_e2e:
@@ -725,7 +725,7 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6400.0))
     phase = {k: round(statistics.mean(t[k] for t in timings), 4)
              for k in ("index_ms", "analyze_ms", "frontier_ms", "join_ms", "percpu_ms", "percpu_decode_ms", "tally_ms",
-                       "self_ms", "compact_ms", "sort_ms", "gather_ms", "total_ms")}
+                       "self_ms", "compact_ms", "sort_ms", "gather_ms", "total_ms", "parse_ms", "call_ms")}
     # a capture is per kernel variant: loads with self time run the variant with side records
     traffic = profile_traffic(os.path.join(ROOT, "paper_2504_03683_b300", "csrc", "analyze_warp.cu"), kname,
                               args.workload + ("_self" if args.self_time and kname == "k_analyze_warp" else ""))

@@ -357,6 +357,10 @@ typedef struct thapi_load_timing {
                                     marked hole) and a 24 B interval slot per ENTRY */
   uint32_t grid_mult;            /* configuration used: analysis packet runs per resident CTA */
   int32_t part_shift;            /* configuration used: device-join partition size 1536 << shift records */
+  float parse_ms;                /* host: the call's start to the first kernel (file heads and tables read,
+                                    checked and combined) */
+  float call_ms;                 /* host: wall time of the load call up to its results (scratch release
+                                    not included) */
 } thapi_load_timing;
 
 /* Copies the per-phase timing of a loaded trace to *out (zeros if timing was

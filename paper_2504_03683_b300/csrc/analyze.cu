@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kT) k_analyze(AnalyzeParams p, unsigned int *s
     uint8_t *dst = sm + L.off_buf + s * L.buf_bytes;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&bar[s], bytes);
-    bulk_copy_g2s(dst, p.packets + (uint64_t)d.pk * p.P, bytes, &bar[s]);
+    bulk_copy_g2s(dst, packet_at(p.packets, p.pk_addr, d.pk, p.P), bytes, &bar[s]);
   };
   PkDesc dnext;  // thread 0: descriptor of the packet after the one in flight
   uint64_t fr_base = 0;

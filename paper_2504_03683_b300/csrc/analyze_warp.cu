@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_analyze_warp(AnalyzeParams p
     const uint32_t bytes = align16(kPacketHeader + d.content);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, bytes);
-    bulk_copy_g2s(buf, p.packets + (uint64_t)d.pk * p.P, bytes, bar);
+    bulk_copy_g2s(buf, packet_at(p.packets, p.pk_addr, d.pk, p.P), bytes, bar);
   };
 
   uint64_t fr_base = 0;
@@ -972,7 +972,7 @@ __device__ __forceinline__ void decode_packet(const DecodeParams &p, const PkDes
   uint32_t *C = reinterpret_cast<uint32_t *>(buf + kPacketHeader);
   const uint32_t W = d.content >> 2;
   {  // stage header + content
-    const uint4 *src = reinterpret_cast<const uint4 *>(p.packets + (uint64_t)d.pk * p.P);
+    const uint4 *src = reinterpret_cast<const uint4 *>(packet_at(p.packets, p.pk_addr, d.pk, p.P));
     uint4 *dst = reinterpret_cast<uint4 *>(buf);
     const uint32_t n16 = align16(kPacketHeader + d.content) / 16u;
     for (uint32_t k = lane; k < n16; k += 32) dst[k] = src[k];
@@ -1157,7 +1157,7 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_percpu_decode(PcParams p,
     if (d.group != kPerCpuGroup) continue;  // uniform over the warp
     const uint32_t W = d.content >> 2;
     {
-      const uint4 *src = reinterpret_cast<const uint4 *>(p.packets + (uint64_t)d.pk * p.P);
+      const uint4 *src = reinterpret_cast<const uint4 *>(packet_at(p.packets, p.pk_addr, d.pk, p.P));
       uint4 *dst = reinterpret_cast<uint4 *>(buf);
       const uint32_t n16 = align16(kPacketHeader + d.content) / 16u;
       for (uint32_t k = lane; k < n16; k += 32) dst[k] = src[k];

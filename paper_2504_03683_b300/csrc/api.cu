@@ -8,6 +8,7 @@
 // No step of the analysis runs on the CPU.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -33,7 +34,7 @@ static_assert(sizeof(thapi_tally_row) == 56, "tally row");
 static_assert(sizeof(thapi_interval) == 24, "interval");
 static_assert(sizeof(thapi_event) == 40, "event");
 static_assert(sizeof(thapi_trace_info) == 104, "trace info");
-static_assert(sizeof(thapi_load_timing) == 104, "load timing");
+static_assert(sizeof(thapi_load_timing) == 112, "load timing");
 
 struct TraceRec {
   cudaStream_t stream = nullptr;
@@ -574,9 +575,9 @@ int Loader::parse_batch(HostLayout &L) {
               len[t], std::min<uint64_t>(std::min<uint64_t>(bn_[t], rd<uint64_t>(heads.data() + head_off[t] + 88)),
                                          16ull << 20));
       }
-      for (uint32_t t = 0; t < nt; ++t) {
+      for (uint32_t t = 0; t < nt; ++t) {  // each head at a 16-byte boundary (16-byte copies)
         head_len[t] = len[t];
-        head_off[t + 1] = head_off[t] + len[t];
+        head_off[t + 1] = head_off[t] + (len[t] + 15) / 16 * 16;
       }
       uint8_t *d_dst = static_cast<uint8_t *>(sc_.get(std::max<uint64_t>(head_off[nt], 1)));
       if (sc_.failed) return THAPI_E_NOMEM;
@@ -655,6 +656,7 @@ int Loader::parse_batch(HostLayout &L) {
 }
 
 int Loader::run() {
+  const auto host_t0 = std::chrono::steady_clock::now();
   HostLayout L;
   int rc;
   if (!bptr_.empty()) {
@@ -706,7 +708,7 @@ int Loader::run() {
   const bool self_on = c_->self_time != 0;
   // admission: coarse peak of this load (unless the serving loop admitted it already)
   if (!admitted_) {
-    const uint64_t est = load_estimate(L, G, host_ || !bptr_.empty(), self_on);
+    const uint64_t est = load_estimate(L, G, host_ || (!bptr_.empty() && !bdev_), self_on);
     std::lock_guard<std::mutex> g(c_->mu);
     if (c_->cap && c_->used + est > c_->cap) return THAPI_E_NOMEM;
   }
@@ -715,15 +717,20 @@ int Loader::run() {
   if (!tr_) return THAPI_E_NOMEM;
   tr_->stream = s_;
   clk_.init(c_->timing != 0);
+  tr_->timing.parse_ms =
+      std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - host_t0).count();
   const uint64_t launches0 = launches_total();
   uint64_t analyze_launches = 0;
 
   // ---- the packet area on the device
   const uint8_t *packets = nullptr;
+  uint64_t *pk_addr = nullptr;  // a batch of device traces: every packet read where it is
   uint32_t *d_pk_trace = nullptr, *d_t_soff = nullptr, *d_t_ns = nullptr;
-  if (!bptr_.empty()) {  // a batch: every trace's packets in one area, in batch order
+  if (!bptr_.empty()) {  // a batch: host traces' packets copied into one area in batch order;
+                         // device traces' packets read in place through an address per packet
     const uint32_t nt = (uint32_t)bptr_.size();
-    uint8_t *pk = alloc<uint8_t>(n * (uint64_t)P);
+    uint8_t *pk = bdev_ ? nullptr : alloc<uint8_t>(n * (uint64_t)P);
+    if (bdev_) pk_addr = alloc<uint64_t>(n);
     d_pk_trace = alloc<uint32_t>(n);
     d_t_soff = alloc<uint32_t>(nt);
     d_t_ns = alloc<uint32_t>(nt);
@@ -748,13 +755,13 @@ int Loader::run() {
       soff += b.n_streams;
     }
     if (n) CK(cudaMemcpyAsync(d_pk_trace, pk_trace.data(), 4ull * n, cudaMemcpyHostToDevice, s_));
-    if (bdev_ && n) {  // device traces: one gather kernel instead of a copy per trace
+    if (bdev_ && n) {  // device traces: the address of every packet, no copy
       const uint8_t **d_src = static_cast<const uint8_t **>(sc_.get(nt * sizeof(void *)));
       uint64_t *d_first = static_cast<uint64_t *>(sc_.get(nt * sizeof(uint64_t)));
       if (sc_.failed) return THAPI_E_NOMEM;
       CK(cudaMemcpyAsync(d_src, t_src.data(), nt * sizeof(void *), cudaMemcpyHostToDevice, s_));
       CK(cudaMemcpyAsync(d_first, t_first.data(), nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
-      launch_gather_packets(d_src, d_first, d_pk_trace, n, P, pk, c_->num_sms, s_);
+      launch_packet_addrs(d_src, d_first, d_pk_trace, n, P, pk_addr, s_);
       CK(cudaGetLastError());
     }
     CK(cudaMemcpyAsync(d_t_soff, t_soff.data(), 4ull * nt, cudaMemcpyHostToDevice, s_));
@@ -796,8 +803,8 @@ int Loader::run() {
   CK(cudaMemsetAsync(stream_count, 0, 4ull * (S ? S : 1), s_));
   unsigned long long *hdr_err = reinterpret_cast<unsigned long long *>(misc_ + mHdrErr);
   clk_.rec(PhaseClock::kIdx0, s_);
-  launch_packet_headers(IndexParams{packets, reinterpret_cast<unsigned long long *>(misc_ + mReadBytes), P, n, S,
-                                    pk_stream, pk_nev, pk_content, pk_seq, pk_disc, pk_tsb, hdr_err, d_pk_trace,
+  launch_packet_headers(IndexParams{packets, pk_addr, reinterpret_cast<unsigned long long *>(misc_ + mReadBytes), P,
+                                    n, S, pk_stream, pk_nev, pk_content, pk_seq, pk_disc, pk_tsb, hdr_err, d_pk_trace,
                                     d_t_soff, d_t_ns},
                         s_);
   launch_stream_keys(pk_stream, n, keys, vals, s_);
@@ -903,6 +910,7 @@ int Loader::run() {
     CK(cudaMemcpyAsync(misc_ + mSlots, misc_h_ + mSlots, sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
     AnalyzeParams ap{};
     ap.packets = packets;
+    ap.pk_addr = pk_addr;
     ap.P = P;
     ap.emax = emax_main;
     ap.n_order = n;
@@ -1029,6 +1037,7 @@ int Loader::run() {
     CK(cudaMemsetAsync(misc_ + mPcCount, 0, sizeof(uint64_t), s_));
     PcParams pp{};
     pp.packets = packets;
+    pp.pk_addr = pk_addr;
     pp.P = P;
     pp.n_classes = L.n_classes;
     pp.n_order = n;
@@ -1294,6 +1303,7 @@ int Loader::run() {
                                           misc_h_[mCmdCount0 + 2] * sizeof(CmdHost)
                                     : 0);
     t.grid_mult = std::max<uint32_t>(1, tune_.grid_mult);
+    t.call_ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - host_t0).count();
     t.part_shift = tune_.part_shift;
     if (clk_.on && n) {
       t.index_ms = clk_.ms(PhaseClock::kIdx0, PhaseClock::kIdx1);

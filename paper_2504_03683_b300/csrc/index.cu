@@ -16,7 +16,7 @@ __global__ void k_packet_headers(IndexParams p) {
   uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long rb = 0;
   if (i < p.n_packets) {
-  const uint4 *h = reinterpret_cast<const uint4 *>(p.packets + i * (uint64_t)p.P);
+  const uint4 *h = reinterpret_cast<const uint4 *>(packet_at(p.packets, p.pk_addr, i, p.P));
   uint4 a = __ldg(h);
   uint4 b = __ldg(h + 1);
   uint32_t magic = a.x, stream = a.y, content = b.x, nev = b.y, seq = b.z, disc = b.w;
@@ -48,28 +48,30 @@ __global__ void k_packet_headers(IndexParams p) {
   if ((threadIdx.x & 31) == 0 && rb) atomicAdd(p.read_bytes, rb);
 }
 
+// Byte ranges gathered into one buffer, a block per source: 16-byte copies
+// while source and destination are both 16-byte aligned, bytes for the rest.
 __global__ void k_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
                                uint8_t *dst) {
   for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
     const uint8_t *s = src[i];
     uint8_t *d = dst + off[i];
     const uint64_t l = len[i];
-    for (uint64_t k = threadIdx.x; k < l; k += blockDim.x) d[k] = s[k];
+    const bool vec = ((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+    const uint64_t l16 = vec ? l / 16 : 0;
+    for (uint64_t k = threadIdx.x; k < l16; k += blockDim.x)
+      reinterpret_cast<uint4 *>(d)[k] = reinterpret_cast<const uint4 *>(s)[k];
+    for (uint64_t k = l16 * 16 + threadIdx.x; k < l; k += blockDim.x) d[k] = s[k];
   }
 }
 
-// A batch's packets into one area: a warp per packet, 16-byte copies.
-// src[t]: trace t's first packet; first[t]: its first packet in the batch.
-__global__ void k_gather_packets(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace,
-                                 uint64_t n, uint32_t P, uint8_t *dst) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t q = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < n; q += nw) {
-    const uint32_t t = pk_trace[q];
-    const uint4 *s = reinterpret_cast<const uint4 *>(src[t] + (q - first[t]) * P);
-    uint4 *d = reinterpret_cast<uint4 *>(dst + q * P);
-    for (uint32_t k = lane; k < P / 16u; k += 32) d[k] = s[k];
-  }
+// The address of each packet of a batch read in place: src[t] is trace t's
+// first packet, first[t] its first packet in the batch.
+__global__ void k_packet_addrs(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
+                               uint32_t P, uint64_t *addr) {
+  const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const uint32_t t = pk_trace[q];
+  addr[q] = reinterpret_cast<uint64_t>(src[t] + (q - first[t]) * P);
 }
 
 // Sort keys/values for grouping by stream.
@@ -119,11 +121,10 @@ void launch_packet_headers(const IndexParams &p, cudaStream_t s) {
     count_launches(1);
   }
 }
-void launch_gather_packets(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
-                           uint32_t P, uint8_t *dst, int num_sms, cudaStream_t s) {
+void launch_packet_addrs(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
+                         uint32_t P, uint64_t *addr, cudaStream_t s) {
   if (n) {
-    const uint64_t blocks = std::min<uint64_t>((n + 7) / 8, (uint64_t)num_sms * 8);
-    k_gather_packets<<<(unsigned)blocks, 256, 0, s>>>(src, first, pk_trace, n, P, dst);
+    k_packet_addrs<<<grid_for(n, 256), 256, 0, s>>>(src, first, pk_trace, n, P, addr);
     count_launches(1);
   }
 }

@@ -162,8 +162,19 @@ __host__ __device__ __forceinline__ uint32_t cmd_part(uint64_t id, int part_bits
 }
 
 // ------------------------------------------------------ kernel params
+// Where packet pk (its index in the trace, or in a batch's packet list) is:
+// a table of addresses when a batch reads its traces' packets in place,
+// else consecutive packets from `packets`.
+#ifdef __CUDACC__
+__device__ __forceinline__ const uint8_t *packet_at(const uint8_t *packets, const uint64_t *addr, uint64_t pk,
+                                                    uint32_t P) {
+  return addr ? reinterpret_cast<const uint8_t *>(__ldg(addr + pk)) : packets + pk * (uint64_t)P;
+}
+#endif
+
 struct IndexParams {
   const uint8_t *packets;  // first packet
+  const uint64_t *pk_addr; // per packet its address (a batch read in place), or null
   unsigned long long *read_bytes;  // sum of 32 + content_bytes over valid packets
   uint32_t P;
   uint64_t n_packets;
@@ -190,6 +201,7 @@ struct __align__(16) PkDesc {
 
 struct AnalyzeParams {
   const uint8_t *packets;
+  const uint64_t *pk_addr;       // per packet its address, or null (see packet_at)
   uint32_t P;
   uint32_t emax;                 // shared-memory event table capacity of this launch
   uint64_t n_order;              // work items of this launch
@@ -324,8 +336,10 @@ void launch_packet_headers(const IndexParams &p, cudaStream_t s);
 cudaError_t launch_wait_check(uint32_t limit, unsigned *status, cudaStream_t s);
 // dst + q * P = trace pk_trace[q]'s packet (q - first[t]) at src[t] (16-byte
 // aligned), a warp per packet.
-void launch_gather_packets(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
-                           uint32_t P, uint8_t *dst, int num_sms, cudaStream_t s);
+// addr[i] = src[t] + (i - first[t]) * P with t = pk_trace[i]: the address of
+// each packet of a batch whose traces stay where they are in device memory.
+void launch_packet_addrs(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
+                         uint32_t P, uint64_t *addr, cudaStream_t s);
 // dst[off[i] .. off[i] + len[i]) = src[i][0 .. len[i]) for i < n (a block per source).
 void launch_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
                          uint8_t *dst, cudaStream_t s);
@@ -347,6 +361,7 @@ uint64_t analyze_warp_frontier_slack(uint64_t warps);
 // Decode of every event (thapi_decode): one warp per packet, packets up to 32 KB.
 struct DecodeParams {
   const uint8_t *packets;
+  const uint64_t *pk_addr;       // per packet its address, or null (see packet_at)
   uint32_t P, n_classes;
   uint64_t n_order;
   const PkDesc *desc;            // per order position
@@ -372,6 +387,7 @@ struct __align__(8) PcRec {
 static_assert(sizeof(PcRec) == 32, "per-CPU record");
 struct PcParams {
   const uint8_t *packets;
+  const uint64_t *pk_addr;       // per packet its address, or null (see packet_at)
   uint32_t P, n_classes;
   uint64_t n_order;
   const PkDesc *desc;

@@ -154,7 +154,7 @@ int tally_static(const uint8_t *dev, uint64_t nbytes, thapi_tally_row *rows, uin
 
   // ---- index: headers, group by stream, seq check, event offsets
   unsigned long long *hdr_err = reinterpret_cast<unsigned long long *>(words + wHdrErr);
-  launch_packet_headers(IndexParams{packets, reinterpret_cast<unsigned long long *>(words + wReadBytes), P, n, S,
+  launch_packet_headers(IndexParams{packets, nullptr, reinterpret_cast<unsigned long long *>(words + wReadBytes), P, n, S,
                                     pk_stream, pk_nev, pk_content, pk_seq, pk_disc, pk_tsb, hdr_err},
                         s);
   launch_stream_keys(pk_stream, n, keys, vals, s);

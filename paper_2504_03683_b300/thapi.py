@@ -79,7 +79,8 @@ class LoadTiming(ctypes.Structure):
                                                 "launches")] + \
                [(f, ctypes.c_float) for f in ("join_ms", "self_ms", "percpu_ms", "percpu_decode_ms")] + \
                [(f, ctypes.c_uint64) for f in ("percpu_read_bytes", "percpu_write_bytes")] + \
-               [("grid_mult", ctypes.c_uint32), ("part_shift", ctypes.c_int32)]
+               [("grid_mult", ctypes.c_uint32), ("part_shift", ctypes.c_int32)] + \
+               [(f, ctypes.c_float) for f in ("parse_ms", "call_ms")]
 
     def as_dict(self):
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))

@@ -46,7 +46,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(thapi.Diag) == 64
     assert ctypes.sizeof(thapi.DeviceDiag) == 64
     assert ctypes.sizeof(thapi.TraceInfo) == 8 * 6 + 4 * 6 + 16 + 16
-    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4 + 4 * 4 + 8 * 2 + 4 * 2
+    assert ctypes.sizeof(thapi.LoadTiming) == 4 * 8 + 8 * 4 + 4 * 4 + 8 * 2 + 4 * 2 + 4 * 2
 
 
 def test_struct_layouts_match_the_header(tmp_path):

@@ -165,7 +165,7 @@ def test_large_workload_self_time_full_size():
 
 
 def test_batch_workload_full_size():
-    """The batch workload (4096 per-rank traces, ~30 GB) loaded as one from device
+    """The batch workload (4096 per-rank traces, ~60 GB) loaded as one from device
     memory: sampled traces' rows (their host ids) equal the oracle on each trace alone."""
     import sys
     import torch
