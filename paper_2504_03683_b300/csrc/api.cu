@@ -81,6 +81,11 @@ struct thapi_ctx {
   // guards traces, next_id, used, tuned and the error location, so that loads
   // and queries of the serving loop may run from several host threads
   std::mutex mu;
+  // pinned host memory the file heads of a batch's device traces are read
+  // into (kept between batches: pinning is slow, pageable copies slower)
+  std::mutex heads_mu;
+  uint8_t *heads = nullptr;
+  uint64_t heads_cap = 0;
 };
 
 namespace thapi {
@@ -558,9 +563,11 @@ int Loader::parse_batch(HostLayout &L) {
   blay_.assign(nt, HostLayout{});
   // device traces: every trace's head (file header and tables, up to its
   // packets) gathered by one kernel and read back at once, in two rounds
-  std::vector<uint8_t> heads;
+  std::unique_lock<std::mutex> heads_lock(c_->heads_mu, std::defer_lock);
+  uint8_t *heads = nullptr;
   std::vector<uint64_t> head_off(nt + 1, 0), head_len(nt, 0);
   if (bdev_) {
+    heads_lock.lock();
     const void **d_src = static_cast<const void **>(sc_.get(nt * sizeof(void *)));
     uint64_t *d_len = static_cast<uint64_t *>(sc_.get(nt * sizeof(uint64_t)));
     uint64_t *d_off = static_cast<uint64_t *>(sc_.get(nt * sizeof(uint64_t)));
@@ -572,7 +579,7 @@ int Loader::parse_batch(HostLayout &L) {
         len[t] = std::min<uint64_t>(bn_[t], kHeaderBytes);
         if (round == 1 && head_len[t] >= 96)  // up to the packets (at most 16 MB), from the header read before
           len[t] = std::max<uint64_t>(
-              len[t], std::min<uint64_t>(std::min<uint64_t>(bn_[t], rd<uint64_t>(heads.data() + head_off[t] + 88)),
+              len[t], std::min<uint64_t>(std::min<uint64_t>(bn_[t], rd<uint64_t>(heads + head_off[t] + 88)),
                                          16ull << 20));
       }
       for (uint32_t t = 0; t < nt; ++t) {  // each head at a 16-byte boundary (16-byte copies)
@@ -584,71 +591,121 @@ int Loader::parse_batch(HostLayout &L) {
       CK(cudaMemcpyAsync(d_len, head_len.data(), nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
       CK(cudaMemcpyAsync(d_off, head_off.data(), nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
       launch_gather_bytes(reinterpret_cast<const uint8_t *const *>(d_src), d_len, d_off, nt, d_dst, s_);
-      heads.resize(head_off[nt]);
-      CK(cudaMemcpyAsync(heads.data(), d_dst, head_off[nt], cudaMemcpyDeviceToHost, s_));
+      if (c_->heads_cap < head_off[nt]) {
+        if (c_->heads) cudaFreeHost(c_->heads);
+        c_->heads = nullptr;
+        c_->heads_cap = 0;
+        const uint64_t want = std::max<uint64_t>(head_off[nt], 1) * 5 / 4;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&c_->heads), want, cudaHostAllocDefault) != cudaSuccess) {
+          cudaGetLastError();
+          c_->heads = nullptr;
+          return THAPI_E_NOMEM;
+        }
+        c_->heads_cap = want;
+      }
+      heads = c_->heads;
+      CK(cudaMemcpyAsync(heads, d_dst, head_off[nt], cudaMemcpyDeviceToHost, s_));
       CK(cudaStreamSynchronize(s_));
     }
   }
-  // the traces' tables parsed on host threads (each trace on its own); the
-  // first failing trace in batch order is the one reported
+  // the traces' tables parsed on host threads (each trace on its own), trace 0
+  // first: every other trace is checked against it as it is parsed.  The
+  // first failing trace in batch order is the one reported, file errors
+  // before disagreements.
   std::vector<int> rcs(nt, THAPI_OK);
+  std::vector<char> agree(nt, 1);
+  auto reader = [&](uint32_t t) {
+    const uint8_t *p = static_cast<const uint8_t *>(bptr_[t]);
+    Reader r{bdev_ ? nullptr : p, bdev_ ? p : nullptr, bn_[t], s_};
+    if (bdev_) {
+      r.pre = heads + head_off[t];
+      r.pre_n = head_len[t];
+    }
+    return r;
+  };
+  rcs[0] = parse_layout(reader(0), blay_[0]);
+  if (rcs[0] != THAPI_OK) {
+    set_err(c_, 0, 0, 0);
+    return rcs[0];
+  }
+  const HostLayout &a = blay_[0];
+  auto fname = [](const HostLayout &x, uint32_t f) { return reinterpret_cast<const char *>(x.strings.data()) + x.func_name[f]; };
+  // the bytes of trace 0's function names (from the lowest name offset to the
+  // end of the highest name): traces whose names sit at the same offsets and
+  // whose bytes there are equal have the same names (one comparison instead
+  // of one per name; the traces' host names usually differ, so whole string
+  // tables rarely match)
+  uint64_t nlo = ~0ull, nhi = 0;
+  for (uint32_t f = 0; f < a.n_funcs; ++f) {
+    nlo = std::min<uint64_t>(nlo, a.func_name[f]);
+    nhi = std::max<uint64_t>(nhi, a.func_name[f] + std::strlen(fname(a, f)) + 1);
+  }
+  auto same_as_first = [&](const HostLayout &x) {
+    if (x.P != a.P || x.cls != a.cls || x.n_funcs != a.n_funcs || x.func_layer != a.func_layer) return false;
+    if (x.func_name == a.func_name &&
+        (x.strings == a.strings ||
+         (a.n_funcs && x.strings.size() >= nhi && std::memcmp(a.strings.data() + nlo, x.strings.data() + nlo, nhi - nlo) == 0)))
+      return true;
+    for (uint32_t f = 0; f < a.n_funcs; ++f)
+      if (std::strcmp(fname(a, f), fname(x, f)) != 0) return false;
+    return true;
+  };
   const uint32_t hw = std::max(1u, std::thread::hardware_concurrency());
   const uint32_t nthreads = nt < 64 ? 1u : std::min<uint32_t>(std::min(32u, hw), nt);
-  auto parse_some = [&](uint32_t first) {
-    for (uint32_t t = first; t < nt; t += nthreads) {
-      const uint8_t *p = static_cast<const uint8_t *>(bptr_[t]);
-      Reader r{bdev_ ? nullptr : p, bdev_ ? p : nullptr, bn_[t], s_};
-      if (bdev_) {
-        r.pre = heads.data() + head_off[t];
-        r.pre_n = head_len[t];
-      }
-      rcs[t] = parse_layout(r, blay_[t]);
-    }
-  };
-  {
+  auto run_pool = [&](auto body) {
     std::vector<std::thread> pool;
-    for (uint32_t k = 1; k < nthreads; ++k) pool.emplace_back(parse_some, k);
-    parse_some(0);
+    for (uint32_t k = 1; k < nthreads; ++k) pool.emplace_back(body, k);
+    body(0u);
     for (auto &th : pool) th.join();
-  }
+  };
+  run_pool([&](uint32_t first) {
+    for (uint32_t t = 1 + first; t < nt; t += nthreads) {
+      rcs[t] = parse_layout(reader(t), blay_[t]);
+      if (rcs[t] == THAPI_OK) agree[t] = same_as_first(blay_[t]) ? 1 : 0;
+    }
+  });
   for (uint32_t t = 0; t < nt; ++t)
     if (rcs[t] != THAPI_OK) {
       set_err(c_, 0, t, 0);
       return rcs[t];
     }
-  const HostLayout &a = blay_[0];
-  auto fname = [](const HostLayout &x, uint32_t f) { return reinterpret_cast<const char *>(x.strings.data()) + x.func_name[f]; };
-  for (uint32_t t = 1; t < nt; ++t) {
-    const HostLayout &b = blay_[t];
-    if (b.P != a.P || b.cls != a.cls || b.n_funcs != a.n_funcs || b.func_layer != a.func_layer)
-      return THAPI_E_UNSUPPORTED;
-    if (b.strings == a.strings && b.func_name == a.func_name) continue;  // same string table: same names
-    for (uint32_t f = 0; f < a.n_funcs; ++f)
-      if (std::strcmp(fname(a, f), fname(b, f)) != 0) return THAPI_E_UNSUPPORTED;
-  }
+  for (uint32_t t = 0; t < nt; ++t)
+    if (!agree[t]) return THAPI_E_UNSUPPORTED;
   L.P = a.P;
   L.n_classes = a.n_classes;
   L.n_funcs = a.n_funcs;
   L.cls = a.cls;
   L.func_name = a.func_name;
   L.func_layer = a.func_layer;
-  L.strings = a.strings;
   L.packets_off = 0;
-  uint64_t streams = 0, hosts = 0, packets = 0;
+  // the combined tables: each trace's strings, host names and stream rows at
+  // offsets from prefix sums, filled by the same threads
+  std::vector<uint64_t> str_at(nt + 1, 0), host_at(nt + 1, 0), stream_at(nt + 1, 0);
+  uint64_t packets = 0;
   for (uint32_t t = 0; t < nt; ++t) {
     const HostLayout &b = blay_[t];
-    const uint32_t soff = (uint32_t)L.strings.size();
-    if (t > 0) L.strings.insert(L.strings.end(), b.strings.begin(), b.strings.end());
-    for (uint32_t h = 0; h < b.n_hosts; ++h) L.host_name.push_back((t > 0 ? soff : 0u) + b.host_name[h]);
-    for (uint32_t s = 0; s < b.n_streams; ++s) {
-      L.srow.push_back(b.srow[4ull * s] + (uint32_t)hosts);
-      for (int j = 1; j < 4; ++j) L.srow.push_back(b.srow[4ull * s + j]);
-    }
-    streams += b.n_streams;
-    hosts += b.n_hosts;
+    str_at[t + 1] = str_at[t] + b.strings.size();
+    host_at[t + 1] = host_at[t] + b.n_hosts;
+    stream_at[t + 1] = stream_at[t] + b.n_streams;
     packets += b.n_packets;
   }
+  const uint64_t streams = stream_at[nt], hosts = host_at[nt];
   if (streams >= 0xFFFFFFFFull || hosts >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+  L.strings.resize(str_at[nt]);
+  L.host_name.resize(hosts);
+  L.srow.resize(4 * streams);
+  run_pool([&](uint32_t first) {
+    for (uint32_t t = first; t < nt; t += nthreads) {
+      const HostLayout &b = blay_[t];
+      if (!b.strings.empty()) std::memcpy(L.strings.data() + str_at[t], b.strings.data(), b.strings.size());
+      for (uint32_t h = 0; h < b.n_hosts; ++h) L.host_name[host_at[t] + h] = (uint32_t)str_at[t] + b.host_name[h];
+      for (uint32_t s = 0; s < b.n_streams; ++s) {
+        uint32_t *row = L.srow.data() + 4 * (stream_at[t] + s);
+        row[0] = b.srow[4ull * s] + (uint32_t)host_at[t];
+        for (int j = 1; j < 4; ++j) row[j] = b.srow[4ull * s + j];
+      }
+    }
+  });
   L.n_streams = (uint32_t)streams;
   L.n_hosts = (uint32_t)hosts;
   L.n_packets = packets;
@@ -735,7 +792,7 @@ int Loader::run() {
     d_t_soff = alloc<uint32_t>(nt);
     d_t_ns = alloc<uint32_t>(nt);
     if (sc_.failed) return THAPI_E_NOMEM;
-    std::vector<uint32_t> pk_trace(n), t_soff(nt), t_ns(nt);
+    std::vector<uint32_t> t_soff(nt), t_ns(nt);
     std::vector<const uint8_t *> t_src(nt);
     std::vector<uint64_t> t_first(nt);
     uint64_t at = 0;
@@ -746,7 +803,6 @@ int Loader::run() {
       if (!bdev_ && b.n_packets)
         CK(cudaMemcpyAsync(pk + at * P, src, b.n_packets * (uint64_t)P, cudaMemcpyHostToDevice, s_));
       if (bdev_ && b.n_packets && reinterpret_cast<uintptr_t>(src) % 16 != 0) return THAPI_E_INVALID;
-      for (uint64_t q = 0; q < b.n_packets; ++q) pk_trace[at + q] = t;
       t_src[t] = src;
       t_first[t] = at;
       t_soff[t] = soff;
@@ -754,14 +810,17 @@ int Loader::run() {
       at += b.n_packets;
       soff += b.n_streams;
     }
-    if (n) CK(cudaMemcpyAsync(d_pk_trace, pk_trace.data(), 4ull * n, cudaMemcpyHostToDevice, s_));
-    if (bdev_ && n) {  // device traces: the address of every packet, no copy
-      const uint8_t **d_src = static_cast<const uint8_t **>(sc_.get(nt * sizeof(void *)));
+    {  // per packet its trace (from the traces' first packets), and with device
+       // traces the address of every packet, no copy
       uint64_t *d_first = static_cast<uint64_t *>(sc_.get(nt * sizeof(uint64_t)));
+      const uint8_t **d_src = bdev_ ? static_cast<const uint8_t **>(sc_.get(nt * sizeof(void *))) : nullptr;
       if (sc_.failed) return THAPI_E_NOMEM;
-      CK(cudaMemcpyAsync(d_src, t_src.data(), nt * sizeof(void *), cudaMemcpyHostToDevice, s_));
       CK(cudaMemcpyAsync(d_first, t_first.data(), nt * sizeof(uint64_t), cudaMemcpyHostToDevice, s_));
-      launch_packet_addrs(d_src, d_first, d_pk_trace, n, P, pk_addr, s_);
+      launch_packet_traces(d_first, nt, n, d_pk_trace, s_);
+      if (bdev_ && n) {
+        CK(cudaMemcpyAsync(d_src, t_src.data(), nt * sizeof(void *), cudaMemcpyHostToDevice, s_));
+        launch_packet_addrs(d_src, d_first, d_pk_trace, n, P, pk_addr, s_);
+      }
       CK(cudaGetLastError());
     }
     CK(cudaMemcpyAsync(d_t_soff, t_soff.data(), 4ull * nt, cudaMemcpyHostToDevice, s_));
@@ -1844,6 +1903,7 @@ int thapi_ctx_destroy(thapi_ctx *ctx) {
     delete t;
   }
   ctx->traces.clear();
+  if (ctx->heads) cudaFreeHost(ctx->heads);
   if (ctx->pool) {
     cudaDeviceSynchronize();  // every stream-ordered free has completed
     cudaMemPoolDestroy(ctx->pool);

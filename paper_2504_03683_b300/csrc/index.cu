@@ -64,6 +64,22 @@ __global__ void k_gather_bytes(const uint8_t *const *src, const uint64_t *len, c
   }
 }
 
+// The trace of each packet of a batch: the last trace whose first packet is
+// at or before it (binary search of the traces' first packets).
+__global__ void k_packet_traces(const uint64_t *first, uint32_t nt, uint64_t n, uint32_t *pk_trace) {
+  const uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  uint32_t lo = 0, hi = nt;  // first[lo] <= q < first[hi] (first[nt] taken as n)
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (first[mid] <= q)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  pk_trace[q] = lo;
+}
+
 // The address of each packet of a batch read in place: src[t] is trace t's
 // first packet, first[t] its first packet in the batch.
 __global__ void k_packet_addrs(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
@@ -118,6 +134,12 @@ static unsigned grid_for(uint64_t n, unsigned t) { return (unsigned)((n + t - 1)
 void launch_packet_headers(const IndexParams &p, cudaStream_t s) {
   if (p.n_packets) {
     k_packet_headers<<<grid_for(p.n_packets, 256), 256, 0, s>>>(p);
+    count_launches(1);
+  }
+}
+void launch_packet_traces(const uint64_t *first, uint32_t nt, uint64_t n, uint32_t *pk_trace, cudaStream_t s) {
+  if (n && nt) {
+    k_packet_traces<<<grid_for(n, 256), 256, 0, s>>>(first, nt, n, pk_trace);
     count_launches(1);
   }
 }

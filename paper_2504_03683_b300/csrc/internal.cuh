@@ -340,6 +340,9 @@ cudaError_t launch_wait_check(uint32_t limit, unsigned *status, cudaStream_t s);
 // each packet of a batch whose traces stay where they are in device memory.
 void launch_packet_addrs(const uint8_t *const *src, const uint64_t *first, const uint32_t *pk_trace, uint64_t n,
                          uint32_t P, uint64_t *addr, cudaStream_t s);
+// pk_trace[q] = the trace t whose packets [first[t], first[t + 1]) hold q
+// (first: nt nondecreasing first-packet indexes, first[0] = 0).
+void launch_packet_traces(const uint64_t *first, uint32_t nt, uint64_t n, uint32_t *pk_trace, cudaStream_t s);
 // dst[off[i] .. off[i] + len[i]) = src[i][0 .. len[i]) for i < n (a block per source).
 void launch_gather_bytes(const uint8_t *const *src, const uint64_t *len, const uint64_t *off, uint32_t n,
                          uint8_t *dst, cudaStream_t s);
