@@ -975,7 +975,7 @@ __device__ __forceinline__ void decode_packet(const DecodeParams &p, const PkDes
     const uint4 *src = reinterpret_cast<const uint4 *>(packet_at(p.packets, p.pk_addr, d.pk, p.P));
     uint4 *dst = reinterpret_cast<uint4 *>(buf);
     const uint32_t n16 = align16(kPacketHeader + d.content) / 16u;
-    for (uint32_t k = lane; k < n16; k += 32) dst[k] = src[k];
+    for (uint32_t k = lane; k < n16; k += 32) dst[k] = __ldg(src + k);  // packets are read-only here
   }
   __syncwarp();
   if (lane < 8) C[W + lane] = 0;
@@ -1160,7 +1160,7 @@ __global__ void __launch_bounds__(kDecodeWarps * 32) k_percpu_decode(PcParams p,
       const uint4 *src = reinterpret_cast<const uint4 *>(packet_at(p.packets, p.pk_addr, d.pk, p.P));
       uint4 *dst = reinterpret_cast<uint4 *>(buf);
       const uint32_t n16 = align16(kPacketHeader + d.content) / 16u;
-      for (uint32_t k = lane; k < n16; k += 32) dst[k] = src[k];
+      for (uint32_t k = lane; k < n16; k += 32) dst[k] = __ldg(src + k);  // packets are read-only here
     }
     __syncwarp();
     if (lane < 8) C[W + lane] = 0;
