@@ -1342,7 +1342,6 @@ int Loader::run() {
     uint32_t *v1 = alloc<uint32_t>(n_iv), *v2 = alloc<uint32_t>(n_iv);
     if (sc_.failed) return THAPI_E_NOMEM;
     if (bucket_on) launch_rec_keys(rec, n_iv, n_iv ? tmin : 0, k1, bits <= 32, s_);
-    launch_iota_u32(v1, n_iv, s_);
     radix_sort_gather(k1, v1, k2, v2, n_iv, bits, rec, tr_->tl, sc_, s_);
   }
   if (sc_.failed) return THAPI_E_NOMEM;

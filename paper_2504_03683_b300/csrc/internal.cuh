@@ -274,7 +274,8 @@ struct BucketCells {
 bool bucket_plan(uint64_t n, int bits, uint32_t S, Scratch &sc, cudaStream_t s, BucketCells *bc);
 bool bucket_run(const BucketCells &bc, uint64_t t_min, uint64_t n, const thapi_interval *rec, thapi_interval *out,
                 Scratch &sc, cudaStream_t s, int num_sms);
-// keys hold u32 values when bits <= 32 (u64 otherwise); rec_out[i] = rec[value of the i-th smallest key]
+// keys hold u32 values when bits <= 32 (u64 otherwise); rec_out[i] = rec[index
+// of the i-th smallest key] (stable); vals and vals_alt are work space
 void radix_sort_gather(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
                        const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc, cudaStream_t s);
 

@@ -200,6 +200,13 @@ __global__ void __launch_bounds__(kBins) k_os_scan(const uint32_t *ghist, int pa
   }
 }
 
+// Items of a tile are addressed by 32-bit offsets from the tile's first item;
+// vin null: the values are the items' indexes (the first pass of a sort whose
+// values start as 0, 1, 2, ...).  The write-out handles kOut items per thread
+// at a time, their loads (and, gathering, their records) in flight together.
+constexpr int kOut = 8;
+static_assert(kTile % (kT * kOut) == 0, "whole write-out rounds");
+
 template <class K>
 __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vin, K *kout, uint32_t *vout, uint64_t n,
                                                  int shift, const uint64_t *gbase, unsigned long long *status,
@@ -211,27 +218,29 @@ __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vi
   uint32_t *s_val = reinterpret_cast<uint32_t *>(smem + sizeof(K) * kTile);
   __shared__ uint32_t wcount[kWarps][kBins];
   __shared__ uint32_t dstart[kBins];
-  __shared__ uint64_t dglob[kBins];
+  __shared__ unsigned long long doff[kBins];  // output position of tile slot j of digit d: doff[d] + j
   __shared__ uint32_t s_tile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
   for (int b = lane; b < kBins; b += 32) wcount[warp][b] = 0;
   __syncthreads();
   const uint64_t tile = s_tile;
-  const uint64_t wbase = tile * kTile + (uint64_t)warp * 32 * kRounds;
+  const uint64_t tbase = tile * kTile;
+  const uint32_t tile_n = (uint32_t)(n - tbase < (uint64_t)kTile ? n - tbase : (uint64_t)kTile);
+  const K *tk = kin + tbase;
+  const uint32_t wfirst = (uint32_t)warp * 32 * kRounds + (uint32_t)lane;
   const uint32_t lt = (1u << lane) - 1u;
   K key[kRounds];
   uint32_t val[kRounds], local[kRounds];
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
-    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
-    key[r] = i < n ? kin[i] : (K)0;
-    val[r] = i < n ? vin[i] : 0u;
+    const uint32_t i = wfirst + (uint32_t)r * 32;
+    key[r] = i < tile_n ? tk[i] : (K)0;
+    val[r] = i < tile_n ? (vin ? vin[tbase + i] : (uint32_t)(tbase + i)) : 0u;
   }
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
-    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
-    const bool valid = i < n;
+    const bool valid = wfirst + (uint32_t)r * 32 < tile_n;
     const uint32_t d = valid ? ((uint32_t)(key[r] >> shift) & (kBins - 1)) : 0u;
     const uint32_t peers = same_digit(d, valid);
     const uint32_t rank = __popc(peers & lt);
@@ -242,6 +251,7 @@ __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vi
     local[r] = before + rank;
   }
   __syncthreads();
+  uint64_t dglob;  // this thread's digit: first output position of the tile's items of that digit
   {  // digit b = threadIdx.x: prefix over warps, publish, look back
     const int b = threadIdx.x;
     uint32_t run = 0;
@@ -290,7 +300,7 @@ __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vi
       }
       atomicExch(mine, kIncl | (excl + run));
     }
-    dglob[b] = gbase[b] + excl;
+    dglob = gbase[b] + excl;
   }
   __syncthreads();
   if (warp == 0) {  // exclusive scan of the tile's digit counts
@@ -308,10 +318,10 @@ __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vi
     }
   }
   __syncthreads();
+  doff[threadIdx.x] = dglob - dstart[threadIdx.x];
 #pragma unroll
   for (int r = 0; r < kRounds; ++r) {
-    const uint64_t i = wbase + (uint64_t)r * 32 + lane;
-    if (i < n) {
+    if (wfirst + (uint32_t)r * 32 < tile_n) {
       const uint32_t d = (uint32_t)(key[r] >> shift) & (kBins - 1);
       const uint32_t at = dstart[d] + wcount[warp][d] + local[r];
       s_key[at] = key[r];
@@ -319,17 +329,35 @@ __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vi
     }
   }
   __syncthreads();
-  const uint64_t rest = n - tile * kTile;
-  const uint64_t tile_n = rest < (uint64_t)kTile ? rest : (uint64_t)kTile;
-  for (uint32_t j = threadIdx.x; j < tile_n; j += kT) {
-    const K k = s_key[j];
-    const uint32_t d = (uint32_t)(k >> shift) & (kBins - 1);
-    const uint64_t pos = dglob[d] + (j - dstart[d]);
+  // runs of equal digits to consecutive output positions
+  for (uint32_t j0 = threadIdx.x; j0 < tile_n; j0 += kT * kOut) {
+    uint64_t pos[kOut];
+    uint32_t v[kOut];
+    K k[kOut];
+#pragma unroll
+    for (int u = 0; u < kOut; ++u) {
+      const uint32_t j = j0 + (uint32_t)u * kT;
+      if (j < tile_n) {
+        k[u] = s_key[j];
+        v[u] = s_val[j];
+        pos[u] = doff[(uint32_t)(k[u] >> shift) & (kBins - 1)] + j;
+      }
+    }
     if (rec_out) {
-      rec_out[pos] = rec[s_val[j]];
+      thapi_interval g[kOut];
+#pragma unroll
+      for (int u = 0; u < kOut; ++u)
+        if (j0 + (uint32_t)u * kT < tile_n) g[u] = rec[v[u]];
+#pragma unroll
+      for (int u = 0; u < kOut; ++u)
+        if (j0 + (uint32_t)u * kT < tile_n) rec_out[pos[u]] = g[u];
     } else {
-      kout[pos] = k;
-      vout[pos] = s_val[j];
+#pragma unroll
+      for (int u = 0; u < kOut; ++u)
+        if (j0 + (uint32_t)u * kT < tile_n) {
+          kout[pos[u]] = k[u];
+          vout[pos[u]] = v[u];
+        }
     }
   }
 }
@@ -337,7 +365,7 @@ __global__ void __launch_bounds__(kT) k_os_pass(const K *kin, const uint32_t *vi
 // Returns false when a look-back wait ran out (then sc.failed = 2).
 template <class K>
 bool sort_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
-                   bool *result_in_alt, const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc,
+                   bool *result_in_alt, const thapi_interval *rec, thapi_interval *rec_out, bool iota, Scratch &sc,
                    cudaStream_t s) {
   const int passes = (bits + kBits - 1) / kBits;
   const uint64_t ntiles = (n + kTile - 1) / kTile;
@@ -362,8 +390,9 @@ bool sort_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uin
   for (int p = 0; p < passes; ++p) {
     const bool last = p == passes - 1;
     cudaMemsetAsync(status, 0, ntiles * kBins * sizeof(uint64_t), s);
-    k_os_pass<K><<<(unsigned)ntiles, kT, smem, s>>>(ki, vi, ko, vo, n, p * kBits, gbase + p * kBins, status, ctr + p,
-                                                     err, rec, last && gather ? rec_out : nullptr);
+    k_os_pass<K><<<(unsigned)ntiles, kT, smem, s>>>(ki, p == 0 && iota ? nullptr : vi, ko, vo, n, p * kBits,
+                                                     gbase + p * kBins, status, ctr + p, err, rec,
+                                                     last && gather ? rec_out : nullptr);
     count_launches(1);
     if (last && gather) break;
     K *tk = ki;
@@ -384,22 +413,28 @@ bool sort_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uin
   return true;
 }
 
+// iota: the values are the items' indexes 0, 1, 2, ... (vals is not read
+// before the first pass writes it).
 template <class K>
 void sort_impl(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_t n, int bits, bool *result_in_alt,
-               const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc, cudaStream_t s) {
+               const thapi_interval *rec, thapi_interval *rec_out, bool iota, Scratch &sc, cudaStream_t s) {
   *result_in_alt = false;
   const bool gather = rec_out != nullptr;
   if (n == 0) return;
   if (bits <= 0) {
     if (gather) {
-      launch_timeline_gather(rec, vals, n, rec_out, s);
+      if (iota)
+        cudaMemcpyAsync(rec_out, rec, n * sizeof(thapi_interval), cudaMemcpyDeviceToDevice, s);
+      else
+        launch_timeline_gather(rec, vals, n, rec_out, s);
     }
     return;
   }
   if (n >= kOneSweepMin) {
-    sort_onesweep<K>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, rec, rec_out, sc, s);
+    sort_onesweep<K>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, rec, rec_out, iota, sc, s);
     return;
   }
+  if (iota) launch_iota_u32(vals, n, s);
   const uint64_t ntiles = (n + kTile - 1) / kTile;
   uint64_t *hist = static_cast<uint64_t *>(sc.get(ntiles * kBins * sizeof(uint64_t)));
   if (!hist) return;
@@ -431,23 +466,24 @@ void sort_impl(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt, uint64_
 
 void radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
                       bool *result_in_alt, Scratch &sc, cudaStream_t s) {
-  sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, nullptr, nullptr, sc, s);
+  sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, nullptr, nullptr, false, sc, s);
 }
 
 void radix_sort_pairs32(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
                         bool *result_in_alt, Scratch &sc, cudaStream_t s) {
-  sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, nullptr, nullptr, sc, s);
+  sort_impl<uint32_t>(keys, vals, keys_alt, vals_alt, n, bits, result_in_alt, nullptr, nullptr, false, sc, s);
 }
 
-// Sorts (key, value) pairs and writes rec_out[i] = rec[value of the i-th smallest key] (stable).
+// Sorts the keys stably and writes rec_out[i] = rec[index of the i-th smallest
+// key]; vals and vals_alt are work space.
 void radix_sort_gather(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt, uint64_t n, int bits,
                        const thapi_interval *rec, thapi_interval *rec_out, Scratch &sc, cudaStream_t s) {
   bool alt = false;
   if (bits <= 32) {
     sort_impl<uint32_t>(reinterpret_cast<uint32_t *>(keys), vals, reinterpret_cast<uint32_t *>(keys_alt), vals_alt, n,
-                        bits, &alt, rec, rec_out, sc, s);
+                        bits, &alt, rec, rec_out, true, sc, s);
   } else {
-    sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, &alt, rec, rec_out, sc, s);
+    sort_impl<uint64_t>(keys, vals, keys_alt, vals_alt, n, bits, &alt, rec, rec_out, true, sc, s);
   }
 }
 
