@@ -228,12 +228,15 @@ struct HostLayout {
   std::vector<uint8_t> strings;
 };
 
-// File header and tables, in the documented check order.
-static int parse_layout(const Reader &r, HostLayout &L) {
-  if (r.n < kHeaderBytes) return THAPI_E_TRUNCATED;
-  std::vector<uint8_t> h;
-  if (!r.get(0, kHeaderBytes, h)) return THAPI_E_CUDA;
-  const uint8_t *b = h.data();
+// Table offsets of a file header: streams, classes, functions, hosts,
+// strings (and the string block's size).
+struct TableAt {
+  uint64_t st = 0, cl = 0, fn = 0, ho = 0, so = 0, sb = 0;
+};
+
+// The 128-byte file header b of a trace of n bytes, in the documented check
+// order (the table rows are checked by the callers).
+static int parse_head(const uint8_t *b, uint64_t n, HostLayout &L, TableAt &o) {
   if (rd<uint32_t>(b) != kTraceMagic || rd<uint16_t>(b + 4) != 1 || rd<uint16_t>(b + 6) != kHeaderBytes)
     return THAPI_E_FORMAT;
   L.P = rd<uint32_t>(b + 8);
@@ -242,16 +245,42 @@ static int parse_layout(const Reader &r, HostLayout &L) {
   L.n_funcs = rd<uint32_t>(b + 20);
   L.n_hosts = rd<uint32_t>(b + 24);
   L.n_packets = rd<uint64_t>(b + 32);
-  const uint64_t st = rd<uint64_t>(b + 40), cl = rd<uint64_t>(b + 48), fn = rd<uint64_t>(b + 56),
-                 ho = rd<uint64_t>(b + 64), so = rd<uint64_t>(b + 72), sb = rd<uint64_t>(b + 80);
+  o.st = rd<uint64_t>(b + 40);
+  o.cl = rd<uint64_t>(b + 48);
+  o.fn = rd<uint64_t>(b + 56);
+  o.ho = rd<uint64_t>(b + 64);
+  o.so = rd<uint64_t>(b + 72);
+  o.sb = rd<uint64_t>(b + 80);
   L.packets_off = rd<uint64_t>(b + 88);
   if (L.P < 256 || L.P > kMaxPacket || (L.P & (L.P - 1))) return THAPI_E_FORMAT;
   if (L.n_classes > 65536 || L.n_funcs > 65536) return THAPI_E_FORMAT;
-  if (!in_file(st, L.n_streams, 16, r.n) || !in_file(cl, L.n_classes, 16, r.n) || !in_file(fn, L.n_funcs, 8, r.n) ||
-      !in_file(ho, L.n_hosts, 8, r.n) || !in_file(so, sb, 1, r.n))
+  if (!in_file(o.st, L.n_streams, 16, n) || !in_file(o.cl, L.n_classes, 16, n) || !in_file(o.fn, L.n_funcs, 8, n) ||
+      !in_file(o.ho, L.n_hosts, 8, n) || !in_file(o.so, o.sb, 1, n))
     return THAPI_E_TRUNCATED;
   if (L.packets_off % 256 != 0) return THAPI_E_FORMAT;
-  if (!in_file(L.packets_off, L.n_packets, L.P, r.n)) return THAPI_E_TRUNCATED;
+  if (!in_file(L.packets_off, L.n_packets, L.P, n)) return THAPI_E_TRUNCATED;
+  return THAPI_OK;
+}
+
+// Stream rows: 4 words each, the host inside the trace.
+static bool parse_streams(const uint8_t *ss, HostLayout &L) {
+  L.srow.resize(4ull * L.n_streams);
+  for (uint32_t s = 0; s < L.n_streams; ++s) {
+    for (int j = 0; j < 4; ++j) L.srow[4ull * s + j] = rd<uint32_t>(ss + 16ull * s + 4 * j);
+    if (L.srow[4ull * s] >= L.n_hosts) return false;
+  }
+  return true;
+}
+
+// File header and tables, in the documented check order.
+static int parse_layout(const Reader &r, HostLayout &L) {
+  if (r.n < kHeaderBytes) return THAPI_E_TRUNCATED;
+  std::vector<uint8_t> h;
+  if (!r.get(0, kHeaderBytes, h)) return THAPI_E_CUDA;
+  TableAt o;
+  const int rc = parse_head(h.data(), r.n, L, o);
+  if (rc != THAPI_OK) return rc;
+  const uint64_t st = o.st, cl = o.cl, fn = o.fn, ho = o.ho, so = o.so, sb = o.sb;
   std::vector<uint8_t> hs, fs, cs, ss;
   if (!r.get(so, sb, L.strings) || !r.get(ho, 8ull * L.n_hosts, hs) || !r.get(fn, 8ull * L.n_funcs, fs) ||
       !r.get(cl, 16ull * L.n_classes, cs) || !r.get(st, 16ull * L.n_streams, ss))
@@ -282,12 +311,44 @@ static int parse_layout(const Reader &r, HostLayout &L) {
                ((uint64_t)(roff >= 0 ? (roff >> 2) + 1 : 0) << 33) |
                ((uint64_t)(coff >= 0 ? (coff >> 2) + 1 : 0) << 48);
   }
-  L.srow.resize(4ull * L.n_streams);
-  for (uint32_t s = 0; s < L.n_streams; ++s) {
-    for (int j = 0; j < 4; ++j) L.srow[4ull * s + j] = rd<uint32_t>(ss.data() + 16ull * s + 4 * j);
-    if (L.srow[4ull * s] >= L.n_hosts) return THAPI_E_FORMAT;
+  return parse_streams(ss.data(), L) ? THAPI_OK : THAPI_E_FORMAT;
+}
+
+// A trace of a batch whose class table, function table and function-name
+// bytes [nlo, nhi) of its string block equal those of the batch's first trace
+// (which parse_layout checked): raw holds its first raw_n bytes in host
+// memory, first / o0 the first trace's.  Returns the check result of the
+// header, host names and stream rows, in parse_layout's order (the equal
+// tables pass as the first trace's did), and sets *same; with *same false
+// (a table differs or lies past raw_n) nothing but the header is read and the
+// caller parses the trace in full (so too with first null).  Host names are
+// offsets into the trace's own string block, which stays in raw (nothing is
+// copied).
+static int parse_like_first(const uint8_t *raw, uint64_t raw_n, uint64_t n, const uint8_t *first, const TableAt &o0,
+                            const HostLayout &a, uint64_t nlo, uint64_t nhi, HostLayout &L, bool *same) {
+  *same = false;
+  if (n < kHeaderBytes) return THAPI_E_TRUNCATED;
+  if (!first || raw_n < kHeaderBytes) return THAPI_OK;
+  TableAt o;
+  const int rc = parse_head(raw, n, L, o);
+  if (rc != THAPI_OK) return rc;
+  auto within = [&](uint64_t off, uint64_t len) { return off <= raw_n && len <= raw_n - off; };
+  const uint64_t ncl = 16ull * L.n_classes, nfn = 8ull * L.n_funcs;
+  if (L.P != a.P || L.n_classes != a.n_classes || L.n_funcs != a.n_funcs || !within(o.cl, ncl) ||
+      !within(o.fn, nfn) || !within(o.so, o.sb) || !within(o.ho, 8ull * L.n_hosts) ||
+      !within(o.st, 16ull * L.n_streams) || std::memcmp(raw + o.cl, first + o0.cl, ncl) != 0 ||
+      std::memcmp(raw + o.fn, first + o0.fn, nfn) != 0 ||
+      (a.n_funcs && (o.sb < nhi || std::memcmp(raw + o.so + nlo, first + o0.so + nlo, nhi - nlo) != 0)))
+    return THAPI_OK;
+  *same = true;
+  const uint8_t *strs = raw + o.so;
+  L.host_name.resize(L.n_hosts);
+  for (uint32_t i = 0; i < L.n_hosts; ++i) {
+    const uint32_t off = rd<uint32_t>(raw + o.ho + 8ull * i);
+    if (off >= o.sb || !std::memchr(strs + off, 0, o.sb - off)) return THAPI_E_FORMAT;
+    L.host_name[i] = off;
   }
-  return THAPI_OK;
+  return parse_streams(raw + o.st, L) ? THAPI_OK : THAPI_E_FORMAT;
 }
 
 // A context whose every device allocation goes through the given hooks, for
@@ -650,6 +711,26 @@ int Loader::parse_batch(HostLayout &L) {
       if (std::strcmp(fname(a, f), fname(x, f)) != 0) return false;
     return true;
   };
+  // a trace's bytes in host memory: its gathered head, or the trace itself
+  auto raw_of = [&](uint32_t t, uint64_t *raw_n) -> const uint8_t * {
+    *raw_n = bdev_ ? head_len[t] : bn_[t];
+    return bdev_ ? heads + head_off[t] : static_cast<const uint8_t *>(bptr_[t]);
+  };
+  uint64_t first_n = 0;
+  const uint8_t *first = raw_of(0, &first_n);
+  TableAt o0;
+  {
+    HostLayout tmp;
+    if (parse_head(first, bn_[0], tmp, o0) != THAPI_OK) return THAPI_E_FORMAT;  // not reached: checked above
+    auto within = [&](uint64_t off, uint64_t len) { return off <= first_n && len <= first_n - off; };
+    if (!within(o0.cl, 16ull * a.n_classes) || !within(o0.fn, 8ull * a.n_funcs) || !within(o0.so, o0.sb))
+      first = nullptr;  // trace 0's tables are not all in host memory: every trace is parsed in full
+  }
+  // per trace its string block (host names are offsets into it)
+  std::vector<const uint8_t *> t_str(nt, nullptr);
+  std::vector<uint64_t> t_strn(nt, 0);
+  t_str[0] = a.strings.data();
+  t_strn[0] = a.strings.size();
   const uint32_t hw = std::max(1u, std::thread::hardware_concurrency());
   const uint32_t nthreads = nt < 64 ? 1u : std::min<uint32_t>(std::min(32u, hw), nt);
   auto run_pool = [&](auto body) {
@@ -658,10 +739,28 @@ int Loader::parse_batch(HostLayout &L) {
     body(0u);
     for (auto &th : pool) th.join();
   };
-  run_pool([&](uint32_t first) {
-    for (uint32_t t = 1 + first; t < nt; t += nthreads) {
+  // a trace whose tables equal trace 0's only has its header, host names and
+  // stream rows read; any other is parsed in full and compared
+  run_pool([&](uint32_t first_t) {
+    for (uint32_t t = 1 + first_t; t < nt; t += nthreads) {
+      uint64_t raw_n = 0;
+      const uint8_t *raw = raw_of(t, &raw_n);
+      bool same = false;
+      rcs[t] = parse_like_first(raw, raw_n, bn_[t], first, o0, a, nlo, nhi, blay_[t], &same);
+      if (rcs[t] != THAPI_OK) continue;
+      if (same) {
+        const uint64_t so = rd<uint64_t>(raw + 72), sb = rd<uint64_t>(raw + 80);
+        t_str[t] = raw + so;
+        t_strn[t] = sb;
+        continue;
+      }
+      blay_[t] = HostLayout{};
       rcs[t] = parse_layout(reader(t), blay_[t]);
-      if (rcs[t] == THAPI_OK) agree[t] = same_as_first(blay_[t]) ? 1 : 0;
+      if (rcs[t] == THAPI_OK) {
+        agree[t] = same_as_first(blay_[t]) ? 1 : 0;
+        t_str[t] = blay_[t].strings.data();
+        t_strn[t] = blay_[t].strings.size();
+      }
     }
   });
   for (uint32_t t = 0; t < nt; ++t)
@@ -678,34 +777,41 @@ int Loader::parse_batch(HostLayout &L) {
   L.func_name = a.func_name;
   L.func_layer = a.func_layer;
   L.packets_off = 0;
-  // the combined tables: each trace's strings, host names and stream rows at
-  // offsets from prefix sums, filled by the same threads
-  std::vector<uint64_t> str_at(nt + 1, 0), host_at(nt + 1, 0), stream_at(nt + 1, 0);
+  // the combined tables: trace 0's string block (its function and host
+  // names), then the host names of the other traces; stream rows with their
+  // hosts renumbered from prefix sums
+  std::vector<uint64_t> host_at(nt + 1, 0), stream_at(nt + 1, 0);
   uint64_t packets = 0;
   for (uint32_t t = 0; t < nt; ++t) {
     const HostLayout &b = blay_[t];
-    str_at[t + 1] = str_at[t] + b.strings.size();
     host_at[t + 1] = host_at[t] + b.n_hosts;
     stream_at[t + 1] = stream_at[t] + b.n_streams;
     packets += b.n_packets;
   }
   const uint64_t streams = stream_at[nt], hosts = host_at[nt];
   if (streams >= 0xFFFFFFFFull || hosts >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
-  L.strings.resize(str_at[nt]);
+  L.strings = a.strings;
   L.host_name.resize(hosts);
-  L.srow.resize(4 * streams);
-  run_pool([&](uint32_t first) {
-    for (uint32_t t = first; t < nt; t += nthreads) {
-      const HostLayout &b = blay_[t];
-      if (!b.strings.empty()) std::memcpy(L.strings.data() + str_at[t], b.strings.data(), b.strings.size());
-      for (uint32_t h = 0; h < b.n_hosts; ++h) L.host_name[host_at[t] + h] = (uint32_t)str_at[t] + b.host_name[h];
-      for (uint32_t s = 0; s < b.n_streams; ++s) {
-        uint32_t *row = L.srow.data() + 4 * (stream_at[t] + s);
-        row[0] = b.srow[4ull * s] + (uint32_t)host_at[t];
-        for (int j = 1; j < 4; ++j) row[j] = b.srow[4ull * s + j];
-      }
+  for (uint32_t h = 0; h < a.n_hosts; ++h) L.host_name[h] = a.host_name[h];
+  for (uint32_t t = 1; t < nt; ++t) {
+    const HostLayout &b = blay_[t];
+    for (uint32_t h = 0; h < b.n_hosts; ++h) {
+      const char *nm = reinterpret_cast<const char *>(t_str[t] + b.host_name[h]);
+      const size_t len = std::strlen(nm) + 1;  // NUL-terminated inside the block (checked)
+      if (L.strings.size() + len >= 0xFFFFFFFFull) return THAPI_E_UNSUPPORTED;
+      L.host_name[host_at[t] + h] = (uint32_t)L.strings.size();
+      L.strings.insert(L.strings.end(), nm, nm + len);
     }
-  });
+  }
+  L.srow.resize(4 * streams);
+  for (uint32_t t = 0; t < nt; ++t) {
+    const HostLayout &b = blay_[t];
+    for (uint32_t s = 0; s < b.n_streams; ++s) {
+      uint32_t *row = L.srow.data() + 4 * (stream_at[t] + s);
+      row[0] = b.srow[4ull * s] + (uint32_t)host_at[t];
+      for (int j = 1; j < 4; ++j) row[j] = b.srow[4ull * s + j];
+    }
+  }
   L.n_streams = (uint32_t)streams;
   L.n_hosts = (uint32_t)hosts;
   L.n_packets = packets;

@@ -126,3 +126,77 @@ def test_batch_errors_name_the_trace_or_the_packet(ctx):
     with pytest.raises(thapi.ThapiError) as ei:
         ctx.load_batch(bad)
     assert ei.value.code == o.code and ei.value.location == o.loc
+
+
+def _named_trace(host: str, funcs=("alpha", "beta", "gamma"), seed: int = 0):
+    """A small hand-built trace with one host of the given name and three call
+    functions; its tables equal those of any other trace built with the same
+    functions (a batch takes the head of such a trace without parsing its
+    tables again)."""
+    from tracegen.handbuilt import Ev, TraceBuilder
+    tb = TraceBuilder(packet_bytes=1024)
+    h = tb.add_host(host)
+    fs = [tb.add_call_func(f) for f in funcs]
+    for k in range(2):
+        s = tb.add_stream(h, 10 + seed, 100 + k)
+        evs, t = [], 1_000 + 7 * seed
+        for i in range(40):
+            _f, e, x = fs[(i + k + seed) % len(fs)]
+            evs += [Ev(e, t), Ev(x, t + 5 + i, result=i % 7 == 0)]
+            t += 20
+        tb.place(tb.stream_events(s, evs, ts_begin=1_000))
+    return np.frombuffer(tb.build(), dtype=np.uint8).copy()
+
+
+def test_batch_host_names_and_head_checks(ctx):
+    """Traces whose class and function tables equal the first trace's: each
+    keeps its own host name, rows and intervals equal the oracle's on the
+    union, and a bad host-name offset or stream-row host in a later trace is
+    reported at that trace, as a full parse reports it.  A trace whose
+    function names differ still makes the batch unsupported."""
+    import struct
+    from paper_2504_03683_b300 import thapi
+    names = ["node-a", "n-b", "a-much-longer-host-name", "z"]
+    traces = [_named_trace(n, seed=k) for k, n in enumerate(names)]
+    union = concat_batch(traces)
+    o = oracle.run(union)
+    assert o.code == oracle.OK
+    tid = ctx.load_batch(traces)
+    try:
+        rows, diag = ctx.tally(tid)
+        ivs = ctx.timeline(tid)
+        assert [thapi.thapi_trace_strings(ctx.handle, tid, 0, h) for h in range(len(names))] == names
+        assert [thapi.thapi_trace_strings(ctx.handle, tid, 1, f) for f in range(3)] == ["alpha", "beta", "gamma"]
+    finally:
+        ctx.free(tid)
+    assert rows_equal(rows, o.rows) and intervals_equal(ivs, o.intervals)
+    for k in oracle.DIAG_FIELDS:
+        assert diag[k] == o.diag[k], k
+
+    def head(t):
+        b = bytes(t[:128])
+        return {k: struct.unpack_from("<Q", b, off)[0] for k, off in (("st", 40), ("ho", 64), ("sb", 80))}
+
+    # trace 2's host name offset past its string block
+    bad = [t.copy() for t in traces]
+    h2 = head(bad[2])
+    struct.pack_into("<I", bad[2], h2["ho"], h2["sb"] + 3)
+    with pytest.raises(thapi.ThapiError) as ei:
+        ctx.load_batch(bad)
+    assert ei.value.code == thapi.E_FORMAT and ei.value.location == (0, 2, 0)
+    # trace 3's second stream names host 1 of a trace with one host
+    bad = [t.copy() for t in traces]
+    struct.pack_into("<I", bad[3], head(bad[3])["st"] + 16, 1)
+    with pytest.raises(thapi.ThapiError) as ei:
+        ctx.load_batch(bad)
+    assert ei.value.code == thapi.E_FORMAT and ei.value.location == (0, 3, 0)
+    # the same errors in a batch whose tables all differ from the first trace's are reported alike
+    other = [_named_trace(n, funcs=("alpha", "beta", "delta"), seed=k) for k, n in enumerate(names)]
+    with pytest.raises(thapi.ThapiError) as ei:
+        ctx.load_batch([traces[0]] + other[1:])
+    assert ei.value.code == thapi.E_UNSUPPORTED
+    bad = [traces[0]] + [t.copy() for t in other[1:]]
+    struct.pack_into("<I", bad[2], head(bad[2])["ho"], head(bad[2])["sb"] + 3)
+    with pytest.raises(thapi.ThapiError) as ei:
+        ctx.load_batch(bad)
+    assert ei.value.code == thapi.E_FORMAT and ei.value.location == (0, 2, 0)
