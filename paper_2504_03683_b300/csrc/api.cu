@@ -1783,6 +1783,16 @@ static int window_to_host(thapi_ctx *c, TraceRec *tr, uint64_t t0, uint64_t t1, 
   return rc;
 }
 
+int timeline_copy_id(thapi_ctx *c, thapi_trace_id id, void *out, uint64_t n, bool device_out, cudaStream_t s) {
+  TraceRec *tr = find(c, id);
+  if (!tr || n != tr->info.intervals) return THAPI_E_INVALID;
+  if (!n) return THAPI_OK;
+  return cudaMemcpyAsync(out, tr->tl, n * sizeof(thapi_interval),
+                         device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) == cudaSuccess
+             ? THAPI_OK
+             : THAPI_E_CUDA;
+}
+
 int window_to_host_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, void *out, uint64_t n,
                       thapi_interval *stage, WinWork *w, unsigned long long *total, cudaStream_t s) {
   TraceRec *tr = find(c, id);

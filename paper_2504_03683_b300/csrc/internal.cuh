@@ -306,6 +306,9 @@ int window_enqueue_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1,
 int free_trace_on(thapi_ctx *c, thapi_trace_id id, cudaStream_t s);
 int window_to_host_id(thapi_ctx *c, thapi_trace_id id, uint64_t t0, uint64_t t1, void *out, uint64_t n,
                       thapi_interval *stage, WinWork *w, unsigned long long *total, cudaStream_t s);
+// The whole ordered timeline (n intervals, the trace's count) to out, host or
+// device memory, enqueued on s (one copy).
+int timeline_copy_id(thapi_ctx *c, thapi_trace_id id, void *out, uint64_t n, bool device_out, cudaStream_t s);
 void *device_view(void *p);
 // A context that allocates only through the given hooks (creates nothing on the device).
 thapi_ctx *hooked_ctx_create(int device, thapi_alloc_fn alloc, thapi_free_fn free_fn, void *user);

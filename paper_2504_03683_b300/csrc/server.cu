@@ -335,11 +335,27 @@ int execute(thapi_server *S, Slot *sl, Req *q) {
   }
   // WINDOW: a device destination takes the matches in the counting pass; host
   // destinations (the caller's, or the server's pinned result memory) are
-  // written once the count is known
+  // written once the count is known.  The whole time range is the whole
+  // ordered timeline: one copy, no counting pass.
   cudaPointerAttributes pa{};
   const bool to_device = r.out && cudaPointerGetAttributes(&pa, r.out) == cudaSuccess &&
                          (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
   cudaGetLastError();
+  if (r.t0 == 0 && r.t1 == ~0ull) {
+    res.n = ivs;
+    void *dst = r.out;
+    if (dst && res.n > r.cap) return THAPI_E_RANGE;
+    if (!dst && res.n) {
+      q->buf_bytes = res.n * sizeof(thapi_interval);
+      q->buf = S->arena.get(q->buf_bytes, &q->buf_own);
+      if (!q->buf) return THAPI_E_NOMEM;
+      dst = q->buf;
+    }
+    rc = thapi::timeline_copy_id(S->ctx, q->trace, dst, res.n, to_device, sl->stream);
+    if (rc == THAPI_OK && cudaStreamSynchronize(sl->stream) != cudaSuccess) rc = THAPI_E_CUDA;
+    if (rc == THAPI_OK) res.data = dst;
+    return rc;
+  }
   if ((rc = window_once(S, sl, q->trace, r, to_device ? static_cast<thapi_interval *>(r.out) : nullptr,
                         to_device ? r.cap : 0, &res.n)) != THAPI_OK)
     return rc;

@@ -219,3 +219,41 @@ def test_serial_baseline_gives_the_same_answers():
             elif s.kind == "window":
                 assert o.n == len(oracle.run(traces[src_of[s.handle]], t0=s.t0, t1=s.t1).intervals)
     del keep
+
+
+def test_whole_timeline_windows():
+    """A window over the whole time range (t0 = 0, t1 = 2^64 - 1) returns the
+    whole ordered timeline into every kind of destination: server-owned
+    pinned memory, pageable and pinned host buffers, a device buffer; a
+    buffer one interval short is refused with the count needed."""
+    import torch
+    t = _pool()[1]
+    want = oracle.run(t).intervals
+    with thapi.Context(0, 0, use_torch_allocator=False) as ctx:
+        tid = thapi.thapi_trace_load(ctx.handle, t)
+        srv = serve.Server(ctx, 1, 2)
+        try:
+            def window(out=None, cap=0):
+                req = thapi.Request()
+                req.kind, req.trace, req.t0, req.t1 = thapi.REQ_WINDOW, tid, 0, 2**64 - 1
+                if out is not None:
+                    req.out, req.cap = out, cap
+                tk = srv.submit(req)
+                return tk, srv.wait(tk)
+            tk, r = window()
+            assert r.status == thapi.OK and intervals_equal(thapi.result_intervals(r), want)
+            srv.release(tk)
+            n = len(want)
+            bufs = {"pageable": np.zeros(n, dtype=thapi.INTERVAL_DTYPE),
+                    "pinned": torch.empty(n * 24, dtype=torch.uint8).pin_memory(),
+                    "device": torch.empty(n * 24, dtype=torch.uint8, device="cuda")}
+            for name, b in bufs.items():
+                _tk, r = window(b.ctypes.data if name == "pageable" else b.data_ptr(), n)
+                assert r.status == thapi.OK and r.n == n, name
+                got = b if name == "pageable" else b.cpu().numpy().view(thapi.INTERVAL_DTYPE)
+                assert intervals_equal(got, want), name
+            short = np.zeros(n - 1, dtype=thapi.INTERVAL_DTYPE)
+            _tk, r = window(short.ctypes.data, n - 1)
+            assert r.status == thapi.E_RANGE and r.n == n
+        finally:
+            srv.close()
