@@ -816,8 +816,11 @@ def main():
 
         if not args.self_time:  # the serving loop has no self-time request
             serial = e2e
-            e2e = e2e_pipelined(local, host, info, events, h2d, d2h, max(4, args.e2e_steps))
-            e2e["serial"] = serial
+            try:
+                e2e = e2e_pipelined(local, host, info, events, h2d, d2h, max(4, args.e2e_steps))
+                e2e["serial"] = serial
+            except Exception as exc:  # keep the one-at-a-time number, say why
+                e2e = dict(serial, pipelined_error="%s: %s" % (type(exc).__name__, exc))
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0:
