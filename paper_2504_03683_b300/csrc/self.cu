@@ -14,7 +14,8 @@
 //  3. the direct parent of an interval at level L > 0 is the entry open at
 //     depth L - 1 when its own entry is pushed: within the (stream, L - 1)
 //     run, the last interval whose entry comes first, provided its exit comes
-//     after.  When that open entry is no interval (mismatched or never
+//     after.  That run ends where the interval's own run starts (no key lies
+//     between them), and a table of run starts by key bounds the search.  When that open entry is no interval (mismatched or never
 //     closed), the run's last earlier interval closed before it was pushed,
 //     so the test fails and no call takes the child's duration;
 //  4. self = duration - the children's durations (u64), tallied per
@@ -140,10 +141,45 @@ __device__ __forceinline__ uint64_t lower_kp(const uint64_t *key, const P *pos, 
   return lo;
 }
 
+// run_start[key] = the first sorted index of key's run (the table holds ~0
+// for keys without a run).
+__global__ void k_self_runs(const uint64_t *key, uint64_t n, uint64_t sentinel, uint64_t *run_start) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint64_t kk = key[k];
+  if (kk < sentinel && (k == 0 || key[k - 1] != kk)) run_start[kk] = k;
+}
+
+// The parent of the interval at k, if it is one: the last entry of the
+// (stream, level - 1) run before it in entry order, a binary search of that
+// run's positions (neighbouring lanes share its first steps in cache).
+__global__ void k_self_child_runs(const uint64_t *key, const uint32_t *val, const uint64_t *spos, const SelfRec *rec,
+                                  const uint64_t *run_start, uint64_t n, int lb, uint64_t sentinel,
+                                  unsigned long long *child) {
+  const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint64_t kk = key[k];
+  if (kk >= sentinel || (kk & ((1ull << lb) - 1)) == 0) return;
+  uint64_t lo = run_start[kk - 1];
+  if (lo == ~0ull) return;  // no interval one level up on this stream
+  uint64_t hi = run_start[kk];
+  const uint64_t p0 = lo, pos = spos[k];
+  while (lo < hi) {  // the first of the run's positions not below pos
+    const uint64_t mid = (lo + hi) >> 1;
+    if (spos[mid] < pos)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo == p0) return;
+  const uint32_t pj = val[lo - 1];
+  if (rec[pj].exit_pos > pos) atomicAdd(&child[pj], (unsigned long long)rec[val[k]].dur);
+}
+
 // Sorted order: the parent of the interval at k, if it is one, is the last
 // entry of the (stream, level - 1) run before it in entry order (a binary
 // search over the positions before k; neighbouring lanes share its first
-// steps in cache).
+// steps in cache).  For key spaces too large for a table of run starts.
 __global__ void k_self_child(const uint64_t *key, const uint32_t *val, const uint64_t *spos, const SelfRec *rec,
                              uint64_t n, int lb, uint64_t sentinel, unsigned long long *child) {
   const uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -206,7 +242,19 @@ int self_time(const SelfIn &in, Cell *cells, uint64_t *word, Scratch &sc, cudaSt
   const uint64_t *key = alt ? k2 : k1;
   const uint32_t *val = alt ? v2 : v1;
   k_self_spos<<<blocks(n), kT, 0, s>>>(rec, val, n, spos);
-  k_self_child<<<blocks(n), kT, 0, s>>>(key, val, spos, rec, n, lb, sentinel, child);
+  // a table of run starts when the keys (stream, level) are few next to the intervals
+  uint64_t *run_start = sentinel <= std::max<uint64_t>(n, 1u << 20) ? static_cast<uint64_t *>(
+                                                                          sc.get(sentinel * sizeof(uint64_t)))
+                                                                    : nullptr;
+  if (run_start) {
+    if (cudaMemsetAsync(run_start, 0xFF, sentinel * sizeof(uint64_t), s) != cudaSuccess) return THAPI_E_CUDA;
+    k_self_runs<<<blocks(n), kT, 0, s>>>(key, n, sentinel, run_start);
+    k_self_child_runs<<<blocks(n), kT, 0, s>>>(key, val, spos, rec, run_start, n, lb, sentinel, child);
+    count_launches(1);
+  } else {
+    sc.failed = 0;  // the table was optional
+    k_self_child<<<blocks(n), kT, 0, s>>>(key, val, spos, rec, n, lb, sentinel, child);
+  }
   k_self_tally<<<blocks(n), kT, 0, s>>>(rec, child, n, cells);
   count_launches(5);
   return cudaGetLastError() == cudaSuccess ? THAPI_OK : THAPI_E_CUDA;
